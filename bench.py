@@ -1,0 +1,315 @@
+"""Benchmark: clover-dslash GB/s vs HBM peak and time to a 1e-10 true residual vs plain FP64 eo-CG.
+
+One step = one pass of the hot path on the 32^3 x 64 workload (eps = 0.4, q = +2/3, m0 = -0.2,
+c_sw = 1.9, c_sw^QED = 1.0, antiperiodic time): ingest the device-resident canonical gauge
+arrays, build the clover term and its odd-site inverse, and solve D psi = eta with the
+mixed-precision even-odd solver (16-bit inner dslash with per-site norms, FP32 reliable
+updates, FP64 outer defect correction) to a true relative residual of 1e-10.
+
+value = algorithmic bytes of every dslash launch in the timed steps / timed wall time (GB/s),
+summed over ranks / max time over ranks.  The roofline object reports the dominant hop kernel
+(its algorithmic bytes per launch / its average CUDA-event duration).  N > 1 runs independent
+replicas (one lattice per GPU; the path has no exchange step on one lattice per GPU).
+
+--impl reference times the CPU oracle (FP64 numpy) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "clover-dslash GB/s vs HBM peak; time to 1e-10 residual vs plain FP64 eo-CG"
+WORKLOAD = dict(L=(64, 32, 32, 32), eps=0.4, q=2 / 3, m0=-0.2, csw=1.9, csw_qed=1.0, gauge_seed=1001,
+                source_seed=2001)
+KSTAT = {0: "hop_f64", 1: "hop_f32", 2: "hop_f16n", 3: "hop_bf16n"}
+PREC_NAMES = {"f32": 1, "f16n": 2, "bf16n": 3}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p.get("hbm_gbs", 6800.0), "measured"
+    except OSError:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_inputs(rank):
+    from paper_2502_02490_gb300 import synth
+
+    w = WORKLOAD
+    U, A = synth.gauge_field(w["L"], w["gauge_seed"], w["eps"])
+    eta = synth.gaussian_spinor(w["L"], w["source_seed"] + 100 * rank)
+    return U, A, eta
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_2502_02490_gb300 import qxd
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    w = WORKLOAD
+    U, A, eta = make_inputs(rank)
+    V = U.shape[0]
+    su3_h = torch.from_numpy(U.view(np.float64)).pin_memory()
+    a_h = torch.from_numpy(A).pin_memory()
+    b_h = torch.from_numpy(eta.view(np.float64)).pin_memory()
+    x_h = torch.empty_like(b_h).pin_memory()
+    su3_d, a_d, b_d = su3_h.to(dev), a_h.to(dev), b_h.to(dev)
+    x_d = torch.empty_like(b_d)
+    lat = qxd.create_lattice(w["L"], qxd.BC_ANTIPERIODIC, 0, qxd.ORDER_LEXI, stream.cuda_stream)
+    prec = PREC_NAMES[args.inner]
+    params = qxd.default_params(solver=qxd.SOLVER_MP_CG_EO, inner_prec=prec, tol=1e-10, inner_tol=args.inner_tol,
+                                reliable_delta=args.delta, check_every=args.check_every)
+
+    def step(host=False):
+        if host:
+            qxd.load_gauge(lat, su3_h.numpy(), a_h.numpy(), w["q"])
+        else:
+            qxd.load_gauge(lat, su3_d, a_d, w["q"])
+        qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
+        if host:
+            st, info = qxd.solve(lat, x_h.numpy(), b_h.numpy(), params=params)
+        else:
+            st, info = qxd.solve(lat, x_d, b_d, params=params)
+        return info
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        info = step()
+    # ---- timed region (device-resident inputs) ----
+    qxd.set_profiling(lat, 1)
+    n0 = qxd.launch_count(lat)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    with Clocks(dev.index) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(step())
+        e1.record(stream)
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    launches = qxd.launch_count(lat) - n0
+    stats = {KSTAT[k]: qxd.kernel_stats(lat, k) for k in KSTAT}
+    qxd.set_profiling(lat, 0)
+    hop_bytes = sum(b for (_, _, b) in stats.values())
+    # ---- end-to-end through host buffers ----
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(host=True)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    # ---- plain FP64 eo-CG on the same field and source (the comparison baseline) ----
+    fp64 = None
+    if not args.skip_fp64:
+        p64 = qxd.default_params(solver=qxd.SOLVER_CG_EO, tol=1e-10, check_every=args.check_every)
+        qxd.load_gauge(lat, su3_d, a_d, w["q"])
+        qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
+        barrier()
+        t0 = time.perf_counter()
+        st, info64 = qxd.solve(lat, x_d, b_d, params=p64)
+        barrier()
+        fp64 = {"seconds": time.perf_counter() - t0, "iterations": info64["iters_inner"],
+                "true_rel_res": info64["true_rel_res"]}
+    qxd.destroy_lattice(lat)
+
+    # ---- aggregate over ranks ----
+    t_s = ms_total / 1e3
+    if world > 1:
+        tt = torch.tensor([t_s, e2e_s], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_s, e2e_s = float(tt[0]), float(tt[1])
+        hb = torch.tensor([hop_bytes], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(hb)
+        hop_total = float(hb[0])
+    else:
+        hop_total = hop_bytes
+    dom = max(stats, key=lambda k: stats[k][1])
+    n_l, ms_l, b_l = stats[dom]
+    peak, peak_kind = measured_peaks()
+    achieved = (b_l / n_l) / (ms_l / n_l / 1e3) / 1e9 if n_l else 0.0
+    tts = t_s / args.steps
+    iters = [i["iters_inner"] for i in infos]
+    out = {
+        "metric": METRIC,
+        "value": hop_total / t_s / 1e9,
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": tts * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"f16n": "f16+f32norm", "bf16n": "bf16+f32norm", "f32": "f32"}[args.inner] + "/f32/f64",
+        "data": "synthetic (seeded SplitMix64 gauge field U=exp(i eps H) exp(i q eps theta), Gaussian source)",
+        "config": {"workload": "32^3x64 mixed-precision clover solve to 1e-10 (eps=0.4, q=+2/3, m0=-0.2, "
+                               "c_sw=1.9, c_sw^QED=1.0, antiperiodic t)",
+                   "lattice": list(w["L"]), "sites": V, "inner_prec": args.inner, "inner_tol": args.inner_tol,
+                   "reliable_delta": args.delta, "l2": "inputs larger than L2 (links+clover > 1 GB)",
+                   "parallelism": f"replicas{world}", "step": "load_gauge + build_clover + MP solve"},
+        "time_to_solution_s": tts,
+        "solve": {"iters_inner_per_step": statistics.mean(iters), "iters_outer": infos[-1]["iters_outer"],
+                  "reliable_updates": infos[-1]["reliable_updates"],
+                  "true_rel_res": max(i["true_rel_res"] for i in infos)},
+        "fp64_eocg": fp64,
+        "speedup_vs_fp64_eocg": (fp64["seconds"] / tts) if fp64 else None,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
+                     "launches": n_l, "avg_launch_us": ms_l / n_l * 1e3 if n_l else None},
+        "kernels": {k: {"launches": v[0], "ms": v[1], "GB": v[2] / 1e9} for k, v in stats.items() if v[0]},
+        "e2e": {"value": hop_total / e2e_s / 1e9 * (1 if world == 1 else 1), "unit": "GB/s",
+                "seconds_per_step": e2e_s / args.steps,
+                "h2d_bytes_per_step": int(U.nbytes + A.nbytes + eta.nbytes),
+                "d2h_bytes_per_step": int(eta.nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    return out
+
+
+def cpu_sample(sample_slices=1):
+    """Time the oracle's D (clover + hop, FP64 numpy) on a bounded sample of the workload's sites:
+    every site of the first `sample_slices` time slices of the 32^3 x 64 lattice."""
+    from oracle import qxd_oracle as O
+
+    w = WORKLOAD
+    U, A, eta = make_inputs(0)
+    lat = O.Lattice(w["L"], antiperiodic=True)
+    n = sample_slices * (w["L"][1] * w["L"][2] * w["L"][3])
+    sites = np.arange(n)
+    t0 = time.perf_counter()
+    O.D_at_sites(lat, U, A, w["q"], w["m0"], w["csw"], w["csw_qed"], eta, sites)
+    dt = time.perf_counter() - t0
+    return {"value": n * 2112 / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle D (clover built at the sites + full-spinor hop) on {n} sites "
+                      f"({sample_slices} time slice(s) of 32^3x64), 2112 B/site FP64 convention, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    vals = []
+    for _ in range(args.warmup):
+        cpu_sample()
+    for _ in range(args.steps):
+        vals.append(cpu_sample())
+    v = statistics.mean(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "32^3x64 clover operator, sampled sites (CPU oracle)"},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inner", default="f16n", choices=["f32", "f16n", "bf16n"])
+    ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--delta", type=float, default=0.1)
+    ap.add_argument("--check-every", type=int, default=1)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_sample()
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * qxd.h -- C ABI of libqxd: the O(a)-improved QCD+QED Wilson-clover Dirac operator on one
+ * GB300 (sm_103a), its even-odd Schur complement, and solvers for D psi = eta.
+ *
+ * Operator (the method's operator, Sec. 1-2 and Sec. 4.3 of arXiv:2502.02490):
+ *   D = (4 + m0) - 1/2 sum_mu [ (1 - gamma_mu) W_mu(x) delta_{x+mu,y}
+ *                              + (1 + gamma_mu) W_mu(x-mu)^dag delta_{x-mu,y} ]
+ *       + c_sw (i/4) sigma_{mu nu} Fhat^SU(3)_{mu nu} + q c_sw^QED (i/4) sigma_{mu nu} Fhat^U(1)_{mu nu}
+ *   with U(3) hop links W_mu(x) = exp(i q A_mu(x)) U_mu(x)  (Sec. 4.3).
+ *
+ * Conventions (all fixed; they are the readings the CPU oracle also uses):
+ *   - chiral gamma basis, gamma5 = diag(1,1,-1,-1); clover block 0 (+) acts on spins 0,1;
+ *   - Fhat = (Q_{mu nu} - Q_{nu mu}) / 8 from the four plaquette leaves; SU(3) part traceless,
+ *     U(1) part from the unit-charge phases exp(iA), multiplied by q;
+ *   - 4 + m0 sits in the clover blocks A(x); antiperiodic time = -1 on hops across t=T-1 <-> 0;
+ *   - Schur complement Dhat = A_ee - 1/4 H_eo A_oo^-1 H_oe (= D_ee - D_eo D_oo^-1 D_oe).
+ *
+ * Site orders at the boundary (Sec. 4.1.1):
+ *   QXD_ORDER_LEXI : lexicographic Lambda(x, L) = L3 L2 L1 x0 + L3 L2 x1 + L3 x2 + x3 (Eq. lexi),
+ *                    i.e. C-contiguous over (t, x, y, z).
+ *   QXD_ORDER_IPT  : openQxD order with one cache block (Eq. ipt, B = L): even sites first, each
+ *                    parity in floor(Lambda/2) order.
+ *   "Even half" vectors (apply_Dhat_eo, solver internals) always list the V/2 even sites in
+ *   floor(Lambda/2) order, which is the first half of QXD_ORDER_IPT.
+ *
+ * Field layouts (all doubles, complex numbers interleaved re, im; site order as above):
+ *   spinor  [V][4 spin][3 colour][2]          (x, alpha, a) with a fastest (Sec. 2)
+ *   links   [V][4 mu][3 row][3 col][2]        forward links mu = 0..3 = t,x,y,z, row-major (Sec. 4.1.4)
+ *   angles  [V][4 mu]                         U(1) field A_mu(x)
+ *   clover  [V][2 chirality][36]              6 real diagonal entries, then (re, im) of the 15
+ *                                             strictly-upper entries in row-major order (Sec. 4.1.3);
+ *                                             within a block the index is 3*alpha' + a, alpha' in {0,1}
+ *
+ * C* boundaries (Sec. 4.2): a lattice created with cstar = 1 is doubled in x, so all spinors
+ * live on (T, 2 L1, L2, L3).  load_gauge takes the PHYSICAL field on (T, L1, L2, L3) and builds
+ * the charge-conjugated mirror (U -> U*, A -> -A) on the device; a hop across the y or z
+ * boundary lands on the mirror copy (x -> x + L1 mod 2 L1).
+ *
+ * Ownership: the caller owns every pointer it passes.  The library copies what it needs
+ * (gauge field at load_gauge) and owns its derived device fields until destroy.
+ * on_device = 1: pointers are CUDA device pointers, used on the lattice's stream, and the call
+ * returns without a host synchronisation.  on_device = 0: pointers are host memory; the call
+ * stages through device buffers and returns after the results are in host memory.
+ *
+ * Errors: every entry point returns a qxd_status and never exits or aborts.  The message of
+ * the last failure on a lattice is in qxd_last_error(lat).
+ */
+#ifndef QXD_H
+#define QXD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qxd_lattice qxd_lattice; /* opaque; owns all device fields of one lattice */
+
+typedef enum {
+  QXD_OK = 0,
+  QXD_EINVAL = 1,     /* bad argument: odd or non-positive extent, null pointer, nrhs <= 0, ... */
+  QXD_ENOMEM = 2,     /* device allocation failed */
+  QXD_ECUDA = 3,      /* a CUDA call failed (message in qxd_last_error) */
+  QXD_ESINGULAR = 4,  /* a 6x6 clover block is not invertible (pivot < 1e-14 * max |entry|) */
+  QXD_ENOCONV = 5,    /* tolerance not met within maxiter; x holds the best iterate */
+  QXD_ESTATE = 6,     /* call out of order, e.g. apply before build_clover */
+  QXD_ETIMEOUT = 7    /* a bounded device-side wait expired */
+} qxd_status;
+
+typedef enum { QXD_BC_PERIODIC = 0, QXD_BC_ANTIPERIODIC = 1 } qxd_tbc;
+typedef enum { QXD_ORDER_LEXI = 0, QXD_ORDER_IPT = 1 } qxd_order;
+
+/* Arithmetic/storage precision of an operator application.
+ *   F64  : FP64 fields, FP64 arithmetic.
+ *   F32  : FP32 fields, FP32 arithmetic.
+ *   F16N : FP16 spinors and clover with one FP32 scale per site (per clover block), FP16 links;
+ *          FP32 arithmetic.
+ *   BF16N: as F16N with BF16 storage. */
+typedef enum { QXD_F64 = 0, QXD_F32 = 1, QXD_F16N = 2, QXD_BF16N = 3 } qxd_prec;
+
+typedef enum {
+  QXD_SOLVER_CG_EO = 0,    /* plain FP64 even-odd CG (CG on Dhat^+ Dhat), true-residual judged */
+  QXD_SOLVER_MP_CG_EO = 1  /* FP64 outer defect correction around an inner even-odd CG in
+                              inner_prec with FP32 reliable updates */
+} qxd_solver;
+
+typedef struct {
+  int version;            /* must be QXD_PARAMS_VERSION */
+  int solver;             /* qxd_solver */
+  double tol;             /* target true relative residual ||eta - D psi|| / ||eta|| (e.g. 1e-10) */
+  int maxiter;            /* cap on inner iterations summed over all outer rounds */
+  int inner_prec;         /* qxd_prec of the inner iteration (MP_CG_EO) */
+  double inner_tol;       /* relative reduction asked of each inner solve (MP_CG_EO), e.g. 1e-5 */
+  double reliable_delta;  /* reliable update when ||s|| < delta * max||s|| since the last one */
+  int max_outer;          /* cap on outer (defect-correction) rounds */
+  int on_device;          /* x and b are device (1) or host (0) pointers */
+  int check_every;        /* read the residual norm back every this many iterations (>= 1) */
+} qxd_solve_params;
+
+#define QXD_PARAMS_VERSION 1
+
+typedef struct {
+  int iters_inner;        /* inner iterations summed over outer rounds */
+  int iters_outer;        /* outer rounds (defect corrections) */
+  int reliable_updates;   /* reliable updates performed */
+  double true_rel_res;    /* final ||eta - D psi|| / ||eta|| computed in FP64 on the GPU */
+  double seconds;         /* wall time of the solve */
+  int status;             /* qxd_status of the solve */
+} qxd_solve_info;
+
+/* Create a lattice of extents L = {T, L1, L2, L3} (txyz, Sec. 4.1.1), all even and >= 2.
+ * tbc: time boundary (qxd_tbc).  cstar: 0, or 1 for C* in x, y, z by x-doubling (Sec. 4.2).
+ * order: qxd_order of every site-indexed array passed to this lattice.
+ * cuda_stream: the cudaStream_t all work is enqueued on (NULL = legacy default stream).
+ * On success *out owns its device memory until qxd_destroy_lattice. */
+qxd_status qxd_create_lattice(const int L[4], int tbc, int cstar, int order, void *cuda_stream,
+                              qxd_lattice **out);
+
+/* Free every device buffer of the lattice; NULL is a no-op. */
+qxd_status qxd_destroy_lattice(qxd_lattice *lat);
+
+/* Load the gauge field (Sec. 4.1.4, Sec. 4.3).  su3: links [Vp][4][3][3][2], a_u1: angles
+ * [Vp][4] or NULL (= no U(1) field), q: the quark charge multiplying A in the hop links.
+ * Vp is the physical volume (V, or V/2 for a C* lattice, whose mirror half is built here).
+ * The library copies the data; the caller's arrays are not referenced after return.
+ * Invalidates a previously built clover field. */
+qxd_status qxd_load_gauge(qxd_lattice *lat, const double *su3, const double *a_u1, double q,
+                          int on_device);
+
+/* Build the clover blocks A(x) = (4+m0) + c_sw (i/4) sigma.Fhat^SU(3) + q c_sw^QED (i/4)
+ * sigma.Fhat^U(1) on every site (Sec. 2, Sec. 4.1.3, Sec. 4.3, Sec. 6: clover generated on the
+ * GPU) and their inverses on odd sites (6x6 Gauss-Jordan with partial pivoting, FP64), plus
+ * the FP32 / FP16 copies the low-precision operators use.
+ * Returns QXD_ESINGULAR if some odd-site block has a pivot below 1e-14 times its largest entry;
+ * QXD_ESTATE before load_gauge. */
+qxd_status qxd_build_clover(qxd_lattice *lat, double m0, double csw, double csw_qed);
+
+/* Copy the FP64 clover field out as [V][2][36] (packing of Sec. 4.1.3), site order of the
+ * lattice.  QXD_ESTATE before build_clover. */
+qxd_status qxd_get_clover(qxd_lattice *lat, double *out, int on_device);
+
+/* out = D in for nrhs right-hand sides: in, out are [nrhs][V][4][3][2] in the lattice's site
+ * order.  prec selects the operator's precision (inputs are rounded to it, outputs widened
+ * back to FP64).  QXD_ESTATE before build_clover; QXD_EINVAL for nrhs <= 0 or a null pointer. */
+qxd_status qxd_apply_D(qxd_lattice *lat, double *out, const double *in, int prec, int nrhs,
+                       int on_device);
+
+/* out_e = Dhat in_e (dagger = 0) or Dhat^dag in_e = gamma5 Dhat gamma5 in_e (dagger = 1), with
+ * Dhat = A_ee - 1/4 H_eo A_oo^-1 H_oe on even-half vectors [V/2][4][3][2]. */
+qxd_status qxd_apply_Dhat_eo(qxd_lattice *lat, double *out_e, const double *in_e, int prec,
+                             int dagger, int on_device);
+
+/* Solve D x = b to the true relative residual params->tol (x is overwritten; the solve starts
+ * from zero).  b, x: [V][4][3][2].  info (may be NULL) receives iteration counts, the final FP64
+ * true residual and the wall time.  QXD_ENOCONV when the tolerance is not met. */
+qxd_status qxd_solve(qxd_lattice *lat, double *x, const double *b, const qxd_solve_params *params,
+                     qxd_solve_info *info);
+
+/* Fill *p with the defaults: MP_CG_EO, tol 1e-10, maxiter 100000, inner F32, inner_tol 1e-5,
+ * reliable_delta 0.1, max_outer 20, on_device 1, check_every 1. */
+void qxd_default_params(qxd_solve_params *p);
+
+/* Fused BLAS-1 on device vectors of n complex numbers (interleaved re, im), on the lattice's
+ * stream, FP64.  Reductions are deterministic (fixed order) and return to host memory.
+ * n = 0 is allowed (pointers may then be NULL): dot and norm2 give 0, axpy does nothing.
+ *   dot:   *re + i *im = sum_k conj(a_k) b_k
+ *   norm2: *out = sum_k |a_k|^2
+ *   axpy:  y_k += (re + i im) x_k                                                         */
+qxd_status qxd_vec_dot(qxd_lattice *lat, const double *a, const double *b, int64_t n, double *re,
+                       double *im);
+qxd_status qxd_vec_norm2(qxd_lattice *lat, const double *a, int64_t n, double *out);
+qxd_status qxd_vec_axpy(qxd_lattice *lat, double re, double im, const double *x, double *y,
+                        int64_t n);
+
+/* Kernel timing.  With profiling on, the library brackets each launch of its hop kernels with
+ * CUDA events on the lattice stream; qxd_kernel_stats returns, for the kernel class `which`
+ * (0 = FP64 hop, 1 = FP32 hop, 2 = FP16N hop, 3 = BF16N hop), the number of timed launches, their
+ * summed device time in ms and the summed algorithmic bytes they moved.  Reading the stats
+ * synchronises the stream.  qxd_launch_count is the number of kernels the library launched. */
+qxd_status qxd_set_profiling(qxd_lattice *lat, int on);
+qxd_status qxd_kernel_stats(qxd_lattice *lat, int which, int64_t *launches, double *ms,
+                            double *bytes);
+int64_t qxd_launch_count(const qxd_lattice *lat);
+
+/* Message of the last failure on this lattice ("" if none); never NULL.  With lat == NULL,
+ * the message of the last failed qxd_create_lattice. */
+const char *qxd_last_error(const qxd_lattice *lat);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QXD_H */

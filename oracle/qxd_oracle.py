@@ -193,7 +193,7 @@ def hop(lat, W, psi):
     return out
 
 
-def _leaves(lat, M, mu, nu):
+def _leaves(lat, M, mu, nu, sites=None):
     """Q_{mu nu}(x): sum of the four plaquette leaves at x in the (mu, nu) plane.
 
     M has shape (V, 4, n, n) (n = 3 for SU(3), n = 1 for U(1) phases).  Each leaf is the
@@ -203,48 +203,76 @@ def _leaves(lat, M, mu, nu):
       U_nu(x) U_mu(x+nu-mu)^+ U_nu(x-mu)^+ U_mu(x-mu)
       U_mu(x-mu)^+ U_nu(x-mu-nu)^+ U_mu(x-mu-nu) U_nu(x-nu)
       U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^+
+    `sites` restricts x to the given site indices (default: all sites).
     """
+    x = np.arange(lat.V) if sites is None else np.asarray(sites)
     fm, fn, bm, bn = lat.fwd(mu), lat.fwd(nu), lat.bwd(mu), lat.bwd(nu)
     Um, Un = M[:, mu], M[:, nu]
-    q = Um @ Un[fm] @ dag(Um[fn]) @ dag(Un)
-    q = q + Un @ dag(Um[bm[fn]]) @ dag(Un[bm]) @ Um[bm]
-    bmn = bn[bm]
-    q = q + dag(Um[bm]) @ dag(Un[bmn]) @ Um[bmn] @ Un[bn]
-    q = q + dag(Un[bn]) @ Um[bn] @ Un[fm[bn]] @ dag(Um)
+    q = Um[x] @ Un[fm[x]] @ dag(Um[fn[x]]) @ dag(Un[x])
+    q = q + Un[x] @ dag(Um[bm[fn[x]]]) @ dag(Un[bm[x]]) @ Um[bm[x]]
+    bmn = bn[bm[x]]
+    q = q + dag(Um[bm[x]]) @ dag(Un[bmn]) @ Um[bmn] @ Un[bn[x]]
+    q = q + dag(Un[bn[x]]) @ Um[bn[x]] @ Un[fm[bn[x]]] @ dag(Um[x])
     return q
 
 
-def field_strength_su3(lat, U, mu, nu):
+def _leaf_sum(lat, M, mu, nu, sites):
+    return _leaves(lat, M, mu, nu) if sites is None else _leaves(lat, M, mu, nu, sites=sites)
+
+
+def field_strength_su3(lat, U, mu, nu, sites=None):
     """Fhat_{mu nu} = (Q_{mu nu} - Q_{nu mu}) / 8 minus its trace / 3 (traceless), per site."""
-    F = (_leaves(lat, U, mu, nu) - _leaves(lat, U, nu, mu)) / 8.0
+    F = (_leaf_sum(lat, U, mu, nu, sites) - _leaf_sum(lat, U, nu, mu, sites)) / 8.0
     tr = np.trace(F, axis1=-2, axis2=-1)
     return F - tr[:, None, None] / 3.0 * np.eye(3)
 
 
-def field_strength_u1(lat, A, mu, nu):
+def field_strength_u1(lat, A, mu, nu, sites=None):
     """Fhat^{U(1)}_{mu nu} = (Q_{mu nu} - Q_{nu mu}) / 8 from the unit-charge phases exp(i A)."""
     P = np.exp(1j * A)[..., None, None]
-    return ((_leaves(lat, P, mu, nu) - _leaves(lat, P, nu, mu)) / 8.0)[:, 0, 0]
+    return ((_leaf_sum(lat, P, mu, nu, sites) - _leaf_sum(lat, P, nu, mu, sites)) / 8.0)[:, 0, 0]
 
 
-def clover_matrix(lat, U, A, q, m0, csw, csw_qed):
+def clover_matrix(lat, U, A, q, m0, csw, csw_qed, sites=None):
     """Site-diagonal 12x12 matrix (4 + m0) + c_sw (i/4) sigma.F^SU(3) + q c_sw^QED (i/4) sigma.F^U(1).
 
-    Sums run over all ordered pairs mu != nu.  Index 3*alpha + a.  Shape (V, 12, 12).
+    Sums run over all ordered pairs mu != nu.  Index 3*alpha + a.  Shape (V, 12, 12), or
+    (len(sites), 12, 12) when `sites` is given.
     """
-    V = lat.V
-    C = np.zeros((V, 12, 12), dtype=np.complex128)
+    n = lat.V if sites is None else len(sites)
+    C = np.zeros((n, 12, 12), dtype=np.complex128)
     C += (4.0 + m0) * np.eye(12)
     for mu in range(4):
         for nu in range(4):
             if mu == nu:
                 continue
             s = sigma(mu, nu)
-            F = field_strength_su3(lat, U, mu, nu)
-            C += csw * 0.25j * np.einsum("st,xab->xsatb", s, F).reshape(V, 12, 12)
-            f1 = field_strength_u1(lat, A, mu, nu)
-            C += q * csw_qed * 0.25j * np.einsum("st,x,ab->xsatb", s, f1, np.eye(3)).reshape(V, 12, 12)
+            F = field_strength_su3(lat, U, mu, nu, sites)
+            C += csw * 0.25j * np.einsum("st,xab->xsatb", s, F).reshape(n, 12, 12)
+            f1 = field_strength_u1(lat, A, mu, nu, sites)
+            C += q * csw_qed * 0.25j * np.einsum("st,x,ab->xsatb", s, f1, np.eye(3)).reshape(n, 12, 12)
     return C
+
+
+def hop_at(lat, W, psi, sites):
+    """(H psi)(x) for x in `sites` only; the same sum as :func:`hop`."""
+    x = np.asarray(sites)
+    out = np.zeros((len(x), 4, 3), dtype=np.complex128)
+    for mu in range(4):
+        f, sf = lat.neighbour(mu, +1)
+        b, sb = lat.neighbour(mu, -1)
+        t = np.einsum("xab,xtb->xta", W[x, mu], psi[f[x]]) * sf[x, None, None]
+        out += np.einsum("st,xta->xsa", I4 - GAMMA[mu], t)
+        t = np.einsum("xab,xtb->xta", dag(W[b[x], mu]), psi[b[x]]) * sb[x, None, None]
+        out += np.einsum("st,xta->xsa", I4 + GAMMA[mu], t)
+    return out
+
+
+def D_at_sites(lat, U, A, q, m0, csw, csw_qed, psi, sites):
+    """(D psi)(x) for x in `sites`: the clover matrix and the hop evaluated at those sites only."""
+    C = clover_matrix(lat, U, A, q, m0, csw, csw_qed, sites=sites)
+    Cpsi = np.einsum("xij,xj->xi", C, psi[np.asarray(sites)].reshape(-1, 12)).reshape(-1, 4, 3)
+    return Cpsi - 0.5 * hop_at(lat, hop_links(U, A, q), psi, sites)
 
 
 class Operator:

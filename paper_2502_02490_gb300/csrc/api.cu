@@ -1,0 +1,436 @@
+// C ABI of libqxd (declared in include/qxd.h): argument checks, host/device staging, lattice
+// lifetime, work buffers and kernel timing.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "qxd_internal.cuh"
+
+namespace qxd {
+qxd_status apply_dhat_prec(qxd_lattice* lat, int prec, const double2* in64, double2* out64, int dag);
+qxd_status apply_D_prec(qxd_lattice* lat, int prec, const double2* in64, double2* out64);
+}  // namespace qxd
+
+using namespace qxd;
+
+static std::string g_create_error;
+
+enum { AS_IN = 24, AS_OUT = 25, AS_BND_IN = 26, AS_BND_OUT = 27 };
+
+namespace qxd {
+
+qxd_status fail(qxd_lattice* lat, qxd_status st, const std::string& msg) {
+  if (lat)
+    lat->err = msg;
+  else
+    g_create_error = msg;
+  return st;
+}
+
+qxd_status cuda_fail(qxd_lattice* lat, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(lat, e == cudaErrorMemoryAllocation ? QXD_ENOMEM : QXD_ECUDA, m);
+}
+
+qxd_status ensure_work(qxd_lattice* lat, int slot, size_t bytes, void** out) {
+  if (slot < 0 || slot >= 32) return fail(lat, QXD_EINVAL, "bad work slot");
+  if (lat->work_bytes[slot] < bytes) {
+    if (lat->work[slot]) {
+      QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+      cudaFree(lat->work[slot]);
+      lat->work[slot] = nullptr;
+      lat->work_bytes[slot] = 0;
+    }
+    QXD_CUDA(lat, cudaMalloc(&lat->work[slot], bytes));
+    QXD_CUDA(lat, cudaMemsetAsync(lat->work[slot], 0, bytes, lat->stream));
+    lat->work_bytes[slot] = bytes;
+  }
+  *out = lat->work[slot];
+  return QXD_OK;
+}
+
+void prof_begin(qxd_lattice* lat, int kind, double bytes) {
+  if (!lat->profiling) return;
+  size_t need = 2 * (size_t)(lat->ev_used + 1);
+  while (lat->ev_pool.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      lat->profiling = false;
+      return;
+    }
+    lat->ev_pool.push_back(e);
+  }
+  if ((int)lat->ev_kind.size() < lat->ev_used + 1) {
+    lat->ev_kind.resize(lat->ev_used + 1);
+    lat->ev_bytes.resize(lat->ev_used + 1);
+  }
+  lat->ev_kind[lat->ev_used] = kind;
+  lat->ev_bytes[lat->ev_used] = bytes;
+  cudaEventRecord(lat->ev_pool[2 * lat->ev_used], lat->stream);
+}
+
+void prof_end(qxd_lattice* lat) {
+  if (!lat->profiling) return;
+  cudaEventRecord(lat->ev_pool[2 * lat->ev_used + 1], lat->stream);
+  lat->ev_used++;
+}
+
+static qxd_status prof_flush(qxd_lattice* lat) {
+  if (lat->ev_used == 0) return QXD_OK;
+  QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  for (int i = 0; i < lat->ev_used; ++i) {
+    float ms = 0.f;
+    QXD_CUDA(lat, cudaEventElapsedTime(&ms, lat->ev_pool[2 * i], lat->ev_pool[2 * i + 1]));
+    int k = lat->ev_kind[i];
+    lat->kcount[k] += 1;
+    lat->kms[k] += ms;
+    lat->kbytes[k] += lat->ev_bytes[i];
+  }
+  lat->ev_used = 0;
+  return QXD_OK;
+}
+
+qxd_status ensure_stage(qxd_lattice* lat, size_t bytes) {
+  void* p;
+  qxd_status st = ensure_work(lat, AS_BND_IN, bytes, &p);
+  lat->stage = p;
+  lat->stage_bytes = bytes;
+  return st;
+}
+
+}  // namespace qxd
+
+#define CHECK_LAT(lat) \
+  if (!(lat)) return QXD_EINVAL
+
+#define TRY(x)                   \
+  do {                           \
+    qxd_status _s = (x);         \
+    if (_s != QXD_OK) return _s; \
+  } while (0)
+
+template <typename T>
+static qxd_status alloc(qxd_lattice* lat, T** p, size_t bytes) {
+  QXD_CUDA(lat, cudaMalloc((void**)p, bytes));
+  QXD_CUDA(lat, cudaMemsetAsync(*p, 0, bytes, lat->stream));
+  return QXD_OK;
+}
+
+extern "C" {
+
+void qxd_default_params(qxd_solve_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->version = QXD_PARAMS_VERSION;
+  p->solver = QXD_SOLVER_MP_CG_EO;
+  p->tol = 1e-10;
+  p->maxiter = 100000;
+  p->inner_prec = QXD_F32;
+  p->inner_tol = 1e-5;
+  p->reliable_delta = 0.1;
+  p->max_outer = 20;
+  p->on_device = 1;
+  p->check_every = 1;
+}
+
+qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
+  if (!lat) return QXD_OK;
+  if (lat->stream) cudaStreamSynchronize(lat->stream);
+  void* bufs[] = {lat->U,    lat->A,     lat->W64,   lat->W32,   lat->W16,   lat->WB16,  lat->C64,
+                  lat->Ci64, lat->C32,   lat->Ci32,  lat->C16,   lat->Ci16,  lat->C16n,  lat->Ci16n,
+                  lat->CB16, lat->CiB16, lat->CB16n, lat->CiB16n, lat->red,  lat->ticket, lat->scal};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (int i = 0; i < 32; ++i)
+    if (lat->work[i]) cudaFree(lat->work[i]);
+  if (lat->hscal) cudaFreeHost(lat->hscal);
+  for (cudaEvent_t e : lat->ev_pool) cudaEventDestroy(e);
+  delete lat;
+  return QXD_OK;
+}
+
+qxd_status qxd_create_lattice(const int L[4], int tbc, int cstar, int order, void* cuda_stream, qxd_lattice** out) {
+  if (!out || !L) return fail(nullptr, QXD_EINVAL, "null argument");
+  *out = nullptr;
+  for (int mu = 0; mu < 4; ++mu)
+    if (L[mu] < 2 || (L[mu] & 1)) return fail(nullptr, QXD_EINVAL, "every extent must be even and >= 2");
+  if (tbc != QXD_BC_PERIODIC && tbc != QXD_BC_ANTIPERIODIC) return fail(nullptr, QXD_EINVAL, "bad tbc");
+  if (cstar != 0 && cstar != 1) return fail(nullptr, QXD_EINVAL, "cstar must be 0 or 1");
+  if (order != QXD_ORDER_LEXI && order != QXD_ORDER_IPT) return fail(nullptr, QXD_EINVAL, "bad order");
+  qxd_lattice* lat = new qxd_lattice();
+  lat->stream = (cudaStream_t)cuda_stream;
+  lat->tbc = tbc;
+  lat->cstar = cstar;
+  lat->order = order;
+  for (int mu = 0; mu < 4; ++mu) {
+    lat->Lphys[mu] = L[mu];
+    lat->g.L[mu] = L[mu];
+  }
+  if (cstar) lat->g.L[1] = 2 * L[1];
+  lat->g.shift = cstar ? L[1] : 0;
+  lat->g.anti = tbc == QXD_BC_ANTIPERIODIC;
+  lat->V = (i64)lat->g.L[0] * lat->g.L[1] * lat->g.L[2] * lat->g.L[3];
+  lat->Vphys = (i64)L[0] * L[1] * L[2] * L[3];
+  lat->Vh = lat->V / 2;
+  lat->sv = (lat->Vh + 63) / 64 * 64;
+  lat->g.Vh = lat->Vh;
+  lat->g.sv = lat->sv;
+  cudaGetDevice(&lat->device);
+  const i64 sv = lat->sv;
+  qxd_status st = QXD_OK;
+#define ALLOC(p, bytes)                            \
+  if ((st = alloc(lat, &lat->p, (bytes))) != QXD_OK) { \
+    g_create_error = lat->err;                     \
+    qxd_destroy_lattice(lat);                      \
+    return st;                                     \
+  }
+  ALLOC(U, sizeof(double2) * 72 * sv);
+  ALLOC(A, sizeof(double) * 8 * sv);
+  ALLOC(W64, sizeof(double2) * 72 * sv);
+  ALLOC(W32, sizeof(float2) * 72 * sv);
+  ALLOC(W16, sizeof(uint32_t) * 72 * sv);
+  ALLOC(WB16, sizeof(uint32_t) * 72 * sv);
+  ALLOC(C64, sizeof(double2) * 72 * sv);
+  ALLOC(Ci64, sizeof(double2) * 72 * sv);
+  ALLOC(C32, sizeof(float4) * 36 * sv);
+  ALLOC(Ci32, sizeof(float4) * 36 * sv);
+  ALLOC(C16, sizeof(uint2) * 36 * sv);
+  ALLOC(Ci16, sizeof(uint2) * 36 * sv);
+  ALLOC(C16n, sizeof(float) * 4 * sv);
+  ALLOC(Ci16n, sizeof(float) * 4 * sv);
+  ALLOC(CB16, sizeof(uint2) * 36 * sv);
+  ALLOC(CiB16, sizeof(uint2) * 36 * sv);
+  ALLOC(CB16n, sizeof(float) * 4 * sv);
+  ALLOC(CiB16n, sizeof(float) * 4 * sv);
+  lat->red_blocks = 152 * 4;
+  ALLOC(red, sizeof(double) * 4 * lat->red_blocks);
+  ALLOC(ticket, sizeof(unsigned int) * 4);
+  ALLOC(scal, sizeof(double) * SC_N);
+#undef ALLOC
+  if (cudaMallocHost((void**)&lat->hscal, sizeof(double) * SC_N) != cudaSuccess) {
+    g_create_error = "cudaMallocHost failed";
+    qxd_destroy_lattice(lat);
+    return QXD_ENOMEM;
+  }
+  if (cudaStreamSynchronize(lat->stream) != cudaSuccess) {
+    g_create_error = "stream synchronisation failed after allocation";
+    qxd_destroy_lattice(lat);
+    return QXD_ECUDA;
+  }
+  *out = lat;
+  return QXD_OK;
+}
+
+qxd_status qxd_load_gauge(qxd_lattice* lat, const double* su3, const double* a_u1, double q, int on_device) {
+  CHECK_LAT(lat);
+  if (!su3) return fail(lat, QXD_EINVAL, "su3 is null");
+  const i64 Vp = lat->Vphys;
+  const size_t ub = sizeof(double2) * 36 * Vp, ab = sizeof(double) * 4 * Vp;
+  lat->q = q;
+  const double2* dsu3 = (const double2*)su3;
+  const double* da = a_u1;
+  if (!on_device) {
+    void* p;
+    TRY(ensure_work(lat, AS_BND_IN, ub, &p));
+    QXD_CUDA(lat, cudaMemcpyAsync(p, su3, ub, cudaMemcpyHostToDevice, lat->stream));
+    dsu3 = (const double2*)p;
+    if (a_u1) {
+      TRY(ensure_work(lat, AS_BND_OUT, ab, &p));
+      QXD_CUDA(lat, cudaMemcpyAsync(p, a_u1, ab, cudaMemcpyHostToDevice, lat->stream));
+      da = (const double*)p;
+    }
+  }
+  TRY(ingest_gauge(lat, dsu3, da));
+  TRY(convert_links_low(lat));
+  QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  lat->have_gauge = true;
+  lat->have_clover = false;
+  return QXD_OK;
+}
+
+qxd_status qxd_build_clover(qxd_lattice* lat, double m0, double csw, double csw_qed) {
+  CHECK_LAT(lat);
+  if (!lat->have_gauge) return fail(lat, QXD_ESTATE, "build_clover before load_gauge");
+  lat->m0 = m0;
+  lat->csw = csw;
+  lat->csw_qed = csw_qed;
+  lat->have_clover = false;
+  TRY(clover_build(lat));
+  lat->have_clover = true;
+  return QXD_OK;
+}
+
+qxd_status qxd_get_clover(qxd_lattice* lat, double* out, int on_device) {
+  CHECK_LAT(lat);
+  if (!out) return fail(lat, QXD_EINVAL, "out is null");
+  if (!lat->have_clover) return fail(lat, QXD_ESTATE, "get_clover before build_clover");
+  const size_t bytes = sizeof(double) * 72 * lat->V;
+  if (on_device) return clover_export(lat, out);
+  void* p;
+  TRY(ensure_work(lat, AS_BND_OUT, bytes, &p));
+  TRY(clover_export(lat, (double*)p));
+  QXD_CUDA(lat, cudaMemcpyAsync(out, p, bytes, cudaMemcpyDeviceToHost, lat->stream));
+  QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  return QXD_OK;
+}
+
+qxd_status qxd_apply_D(qxd_lattice* lat, double* out, const double* in, int prec, int nrhs, int on_device) {
+  CHECK_LAT(lat);
+  if (!out || !in) return fail(lat, QXD_EINVAL, "null field pointer");
+  if (nrhs <= 0) return fail(lat, QXD_EINVAL, "nrhs must be positive");
+  if (prec < QXD_F64 || prec > QXD_BF16N) return fail(lat, QXD_EINVAL, "bad precision");
+  if (!lat->have_clover) return fail(lat, QXD_ESTATE, "apply_D before build_clover");
+  const i64 sv = lat->sv;
+  const size_t fb = sizeof(double2) * 24 * sv, vb = sizeof(double) * 24 * lat->V;
+  double2 *fin, *fout;
+  void *bi, *bo;
+  TRY(ensure_work(lat, AS_IN, fb, (void**)&fin));
+  TRY(ensure_work(lat, AS_OUT, fb, (void**)&fout));
+  if (!on_device) {
+    TRY(ensure_work(lat, AS_BND_IN, vb, &bi));
+    TRY(ensure_work(lat, AS_BND_OUT, vb, &bo));
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    const double* src = in + (i64)r * 24 * lat->V;
+    double* dst = out + (i64)r * 24 * lat->V;
+    if (!on_device) {
+      QXD_CUDA(lat, cudaMemcpyAsync(bi, src, vb, cudaMemcpyHostToDevice, lat->stream));
+      src = (const double*)bi;
+    }
+    TRY(pack_spinor64(lat, (const double2*)src, fin, 0));
+    TRY(apply_D_prec(lat, prec, fin, fout));
+    TRY(unpack_spinor64(lat, fout, on_device ? (double2*)dst : (double2*)bo, 0));
+    if (!on_device) QXD_CUDA(lat, cudaMemcpyAsync(dst, bo, vb, cudaMemcpyDeviceToHost, lat->stream));
+  }
+  if (!on_device) QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  return QXD_OK;
+}
+
+qxd_status qxd_apply_Dhat_eo(qxd_lattice* lat, double* out_e, const double* in_e, int prec, int dagger,
+                             int on_device) {
+  CHECK_LAT(lat);
+  if (!out_e || !in_e) return fail(lat, QXD_EINVAL, "null field pointer");
+  if (prec < QXD_F64 || prec > QXD_BF16N) return fail(lat, QXD_EINVAL, "bad precision");
+  if (!lat->have_clover) return fail(lat, QXD_ESTATE, "apply_Dhat_eo before build_clover");
+  const i64 sv = lat->sv;
+  const size_t hb = sizeof(double2) * 12 * sv, vb = sizeof(double) * 24 * lat->Vh;
+  double2 *fin, *fout;
+  TRY(ensure_work(lat, AS_IN, sizeof(double2) * 24 * sv, (void**)&fin));
+  TRY(ensure_work(lat, AS_OUT, sizeof(double2) * 24 * sv, (void**)&fout));
+  (void)hb;
+  const double* src = in_e;
+  void *bi = nullptr, *bo = nullptr;
+  if (!on_device) {
+    TRY(ensure_work(lat, AS_BND_IN, vb, &bi));
+    TRY(ensure_work(lat, AS_BND_OUT, vb, &bo));
+    QXD_CUDA(lat, cudaMemcpyAsync(bi, in_e, vb, cudaMemcpyHostToDevice, lat->stream));
+    src = (const double*)bi;
+  }
+  TRY(pack_spinor64(lat, (const double2*)src, fin, 1));
+  TRY(apply_dhat_prec(lat, prec, fin, fout, dagger ? 1 : 0));
+  TRY(unpack_spinor64(lat, fout, on_device ? (double2*)out_e : (double2*)bo, 1));
+  if (!on_device) {
+    QXD_CUDA(lat, cudaMemcpyAsync(out_e, bo, vb, cudaMemcpyDeviceToHost, lat->stream));
+    QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  }
+  return QXD_OK;
+}
+
+qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_solve_params* p, qxd_solve_info* info) {
+  CHECK_LAT(lat);
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!x || !b || !p) return fail(lat, QXD_EINVAL, "null argument");
+  if (p->version != QXD_PARAMS_VERSION) return fail(lat, QXD_EINVAL, "qxd_solve_params version mismatch");
+  if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO) return fail(lat, QXD_EINVAL, "bad solver");
+  if (!(p->tol > 0) || p->maxiter <= 0) return fail(lat, QXD_EINVAL, "tol must be > 0 and maxiter > 0");
+  if (p->solver == QXD_SOLVER_MP_CG_EO && (p->inner_prec < QXD_F32 || p->inner_prec > QXD_BF16N))
+    return fail(lat, QXD_EINVAL, "inner_prec must be F32, F16N or BF16N");
+  if (!lat->have_clover) return fail(lat, QXD_ESTATE, "solve before build_clover");
+  const i64 sv = lat->sv;
+  const size_t fb = sizeof(double2) * 24 * sv, vb = sizeof(double) * 24 * lat->V;
+  double2 *fb_in, *fx;
+  TRY(ensure_work(lat, AS_IN, fb, (void**)&fb_in));
+  TRY(ensure_work(lat, AS_OUT, fb, (void**)&fx));
+  const double* src = b;
+  void *bi = nullptr, *bo = nullptr;
+  if (!p->on_device) {
+    TRY(ensure_work(lat, AS_BND_IN, vb, &bi));
+    TRY(ensure_work(lat, AS_BND_OUT, vb, &bo));
+    QXD_CUDA(lat, cudaMemcpyAsync(bi, b, vb, cudaMemcpyHostToDevice, lat->stream));
+    src = (const double*)bi;
+  }
+  TRY(pack_spinor64(lat, (const double2*)src, fb_in, 0));
+  qxd_status st = solve(lat, fx, fb_in, p, info);
+  if (st != QXD_OK && st != QXD_ENOCONV) return st;
+  qxd_status st2 = unpack_spinor64(lat, fx, p->on_device ? (double2*)x : (double2*)bo, 0);
+  if (st2 != QXD_OK) return st2;
+  if (!p->on_device) {
+    QXD_CUDA(lat, cudaMemcpyAsync(x, bo, vb, cudaMemcpyDeviceToHost, lat->stream));
+    QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  }
+  return st;
+}
+
+qxd_status qxd_vec_dot(qxd_lattice* lat, const double* a, const double* b, int64_t n, double* re, double* im) {
+  CHECK_LAT(lat);
+  if (!re || !im || n < 0 || (n > 0 && (!a || !b))) return fail(lat, QXD_EINVAL, "bad argument");
+  if (n == 0) {
+    *re = *im = 0.0;
+    return QXD_OK;
+  }
+  TRY(blas_dot_64(lat, (const double2*)a, (const double2*)b, n, SC_TMP2));
+  double v[2];
+  TRY(read_scalars(lat, SC_TMP2, 2, v));
+  *re = v[0];
+  *im = v[1];
+  return QXD_OK;
+}
+
+qxd_status qxd_vec_norm2(qxd_lattice* lat, const double* a, int64_t n, double* out) {
+  CHECK_LAT(lat);
+  if (!out || n < 0 || (n > 0 && !a)) return fail(lat, QXD_EINVAL, "bad argument");
+  if (n == 0) {
+    *out = 0.0;
+    return QXD_OK;
+  }
+  TRY(blas_norm2_64(lat, (const double2*)a, n, SC_TMP1));
+  return read_scalars(lat, SC_TMP1, 1, out);
+}
+
+qxd_status qxd_vec_axpy(qxd_lattice* lat, double re, double im, const double* x, double* y, int64_t n) {
+  CHECK_LAT(lat);
+  if (n < 0 || (n > 0 && (!x || !y))) return fail(lat, QXD_EINVAL, "bad argument");
+  if (n == 0) return QXD_OK;
+  return blas_axpy_64(lat, re, im, (const double2*)x, (double2*)y, n);
+}
+
+qxd_status qxd_set_profiling(qxd_lattice* lat, int on) {
+  CHECK_LAT(lat);
+  TRY(prof_flush(lat));
+  lat->profiling = on != 0;
+  for (int k = 0; k < KSTAT_N; ++k) {
+    lat->kcount[k] = 0;
+    lat->kms[k] = 0;
+    lat->kbytes[k] = 0;
+  }
+  return QXD_OK;
+}
+
+qxd_status qxd_kernel_stats(qxd_lattice* lat, int which, int64_t* launches, double* ms, double* bytes) {
+  CHECK_LAT(lat);
+  if (which < 0 || which >= KSTAT_N || !launches || !ms || !bytes) return fail(lat, QXD_EINVAL, "bad argument");
+  TRY(prof_flush(lat));
+  *launches = lat->kcount[which];
+  *ms = lat->kms[which];
+  *bytes = lat->kbytes[which];
+  return QXD_OK;
+}
+
+int64_t qxd_launch_count(const qxd_lattice* lat) { return lat ? lat->launches : 0; }
+
+const char* qxd_last_error(const qxd_lattice* lat) {
+  if (!lat) return g_create_error.c_str();
+  return lat->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,273 @@
+// The hopping term (dslash) of the Wilson-clover operator with fused clover epilogues.
+//
+// (H psi)(x) = sum_mu [(1 - gamma_mu) W_mu(x) psi(x+mu) + (1 + gamma_mu) W_mu(x-mu)^dag psi(x-mu)]
+// (the hop part of the method's operator; D = A - H/2, Sec. 1-2 and Sec. 4.3 for U(3) links W).
+//
+// Spin projection in the chiral basis (gamma_0 = [[0,-1],[-1,0]], gamma_k = [[0,-i s_k],[i s_k,0]]):
+//   (1 -+ gamma_0) psi = [h; +-h]        with h = up +- dn
+//   (1 -+ gamma_k) psi = [h; -+ i s_k h] with h = up +- i s_k dn
+// (up = spins 0,1; dn = spins 2,3), so each direction moves a 2-spin x 3-colour half spinor
+// through one 3x3 link multiply.  One thread per output site; the neighbour spinors come from
+// the opposite parity.  Time-boundary sign and C* neighbours follow nbr_cb().
+#include "qxd_internal.cuh"
+
+namespace qxd {
+
+template <typename R, int MU, bool FWD>
+__device__ __forceinline__ void project(const cplx<R> s[12], cplx<R> h[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cplx<R> up0 = s[c], up1 = s[3 + c], dn0 = s[6 + c], dn1 = s[9 + c];
+    if (MU == 0) {
+      h[c] = FWD ? up0 + dn0 : up0 - dn0;
+      h[3 + c] = FWD ? up1 + dn1 : up1 - dn1;
+    } else if (MU == 1) {  // i s_1 dn = (i dn1, i dn0)
+      h[c] = FWD ? up0 + timesI(dn1) : up0 - timesI(dn1);
+      h[3 + c] = FWD ? up1 + timesI(dn0) : up1 - timesI(dn0);
+    } else if (MU == 2) {  // i s_2 dn = (dn1, -dn0)
+      h[c] = FWD ? up0 + dn1 : up0 - dn1;
+      h[3 + c] = FWD ? up1 - dn0 : up1 + dn0;
+    } else {  // i s_3 dn = (i dn0, -i dn1)
+      h[c] = FWD ? up0 + timesI(dn0) : up0 - timesI(dn0);
+      h[3 + c] = FWD ? up1 - timesI(dn1) : up1 + timesI(dn1);
+    }
+  }
+}
+
+// acc += (1 -+ gamma_mu) reconstructed from the transported half spinor g
+template <typename R, int MU, bool FWD>
+__device__ __forceinline__ void accumulate(cplx<R> acc[12], const cplx<R> g[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cplx<R> g0 = g[c], g1 = g[3 + c];
+    acc[c] = acc[c] + g0;
+    acc[3 + c] = acc[3 + c] + g1;
+    if (MU == 0) {
+      acc[6 + c] = FWD ? acc[6 + c] + g0 : acc[6 + c] - g0;
+      acc[9 + c] = FWD ? acc[9 + c] + g1 : acc[9 + c] - g1;
+    } else if (MU == 1) {  // -i s_1 g = (-i g1, -i g0)
+      acc[6 + c] = FWD ? acc[6 + c] - timesI(g1) : acc[6 + c] + timesI(g1);
+      acc[9 + c] = FWD ? acc[9 + c] - timesI(g0) : acc[9 + c] + timesI(g0);
+    } else if (MU == 2) {  // -i s_2 g = (-g1, g0)
+      acc[6 + c] = FWD ? acc[6 + c] - g1 : acc[6 + c] + g1;
+      acc[9 + c] = FWD ? acc[9 + c] + g0 : acc[9 + c] - g0;
+    } else {  // -i s_3 g = (-i g0, i g1)
+      acc[6 + c] = FWD ? acc[6 + c] - timesI(g0) : acc[6 + c] + timesI(g0);
+      acc[9 + c] = FWD ? acc[9 + c] + timesI(g1) : acc[9 + c] - timesI(g1);
+    }
+  }
+}
+
+template <typename R, bool DAG>
+__device__ __forceinline__ void link_mul(const cplx<R> u[9], const cplx<R> h[6], cplx<R> g[6]) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cplx<R> r = DAG ? cjmul(u[a], h[3 * s]) : cmul(u[3 * a], h[3 * s]);
+#pragma unroll
+      for (int b = 1; b < 3; ++b) r = r + (DAG ? cjmul(u[3 * b + a], h[3 * s + b]) : cmul(u[3 * a + b], h[3 * s + b]));
+      g[3 * s + a] = r;
+    }
+}
+
+template <typename R, class SIN, class LNK, int MU, bool G5IN>
+__device__ __forceinline__ void hop_dir(const Geom& g, int par, i64 cb, const int x[4], const SIN& in,
+                                        const LNK& lk, cplx<R> acc[12]) {
+  cplx<R> s[12], h[6], u[9], t[6];
+  bool cr;
+  // forward: (1 - gamma_mu) W_mu(x) psi(x + mu)
+  i64 n = nbr_cb(g, x, MU, +1, cr);
+  in.load(n, s);
+  if (G5IN) {
+#pragma unroll
+    for (int k = 6; k < 12; ++k) s[k] = neg(s[k]);
+  }
+  project<R, MU, true>(s, h);
+  if (MU == 0 && cr && g.anti) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) h[k] = neg(h[k]);
+  }
+  lk.load(par, MU, cb, u);
+  link_mul<R, false>(u, h, t);
+  accumulate<R, MU, true>(acc, t);
+  // backward: (1 + gamma_mu) W_mu(x - mu)^dag psi(x - mu)
+  n = nbr_cb(g, x, MU, -1, cr);
+  in.load(n, s);
+  if (G5IN) {
+#pragma unroll
+    for (int k = 6; k < 12; ++k) s[k] = neg(s[k]);
+  }
+  project<R, MU, false>(s, h);
+  if (MU == 0 && cr && g.anti) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) h[k] = neg(h[k]);
+  }
+  lk.load(1 - par, MU, n, u);
+  link_mul<R, true>(u, h, t);
+  accumulate<R, MU, false>(acc, t);
+}
+
+template <typename R, class CLV>
+__device__ __forceinline__ void clover_mul(const CLV& cl, int par, i64 cb, const cplx<R> v[12], cplx<R> y[12]) {
+#pragma unroll
+  for (int blk = 0; blk < 2; ++blk) {
+    R r[36];
+    cl.load(par, blk, cb, r);
+    herm6_apply<R>(r, v + 6 * blk, y + 6 * blk);
+  }
+}
+
+struct NoSpinor {
+  typedef float real;
+  template <typename T>
+  __device__ __forceinline__ void load(i64, cplx<T>*) const {}
+  template <typename T>
+  __device__ __forceinline__ void store(i64, const cplx<T>*) const {}
+};
+
+template <typename R, class SIN, class SSAME, class SOUT, class LNK, class CLV, int EPI, bool G5>
+__global__ void __launch_bounds__(128) k_hop(Geom g, int par, SIN in, SSAME same, SOUT out, LNK lk, CLV cl,
+                                             R coef) {
+  i64 cb = blockIdx.x * (i64)blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  int x[4];
+  cb_coords(g, cb, par, x);
+  cplx<R> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = mk((R)0, (R)0);
+  constexpr bool G5IN = G5 && (EPI == EPI_INV);
+  hop_dir<R, SIN, LNK, 0, G5IN>(g, par, cb, x, in, lk, acc);
+  hop_dir<R, SIN, LNK, 1, G5IN>(g, par, cb, x, in, lk, acc);
+  hop_dir<R, SIN, LNK, 2, G5IN>(g, par, cb, x, in, lk, acc);
+  hop_dir<R, SIN, LNK, 3, G5IN>(g, par, cb, x, in, lk, acc);
+
+  cplx<R> o[12];
+  if (EPI == EPI_HOP) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = coef * acc[k];
+  } else if (EPI == EPI_DFULL || EPI == EPI_DHAT2) {
+    cplx<R> v[12], y[12];
+    same.load(cb, v);
+    clover_mul<R, CLV>(cl, par, cb, v, y);
+    R c = EPI == EPI_DFULL ? (R)-0.5 : coef;
+    if (EPI == EPI_DHAT2 && G5) {
+#pragma unroll
+      for (int k = 6; k < 12; ++k) acc[k] = neg(acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = y[k] + c * acc[k];
+  } else if (EPI == EPI_INV) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = coef * acc[k];
+    clover_mul<R, CLV>(cl, par, cb, acc, o);
+  } else if (EPI == EPI_INVXPAY) {
+    cplx<R> v[12];
+    same.load(cb, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = v[k] + coef * acc[k];
+    clover_mul<R, CLV>(cl, par, cb, v, o);
+  } else {  // EPI_XPAY
+    cplx<R> v[12];
+    same.load(cb, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = v[k] + coef * acc[k];
+  }
+  out.store(cb, o);
+}
+
+// Algorithmic bytes of one launch (per output site: neighbour spinors counted once, 8 links,
+// the clover block pair, the diagonal input where used, the output).
+static double hop_bytes(qxd_lattice* lat, int epi, double sp_in, double sp_out, double link, double clov) {
+  double b = sp_in + sp_out + 8 * link;
+  if (epi != EPI_HOP && epi != EPI_XPAY) b += clov;
+  if (epi == EPI_DFULL || epi == EPI_DHAT2 || epi == EPI_INVXPAY || epi == EPI_XPAY) b += sp_in;
+  return b * (double)lat->Vh;
+}
+
+template <typename R, class SIN, class SSAME, class SOUT, class LNK, class CLV>
+static qxd_status launch_hop(qxd_lattice* lat, int par, int epi, int g5, SIN in, SSAME same, SOUT out, LNK lk,
+                             CLV cl, R coef) {
+  const Geom& g = lat->g;
+  dim3 grid(grid_for(g.Vh, 128)), block(128);
+  cudaStream_t st = lat->stream;
+#define QXD_HOP_CASE(E, G)                                                                              \
+  if (epi == E && (g5 != 0) == G) {                                                                     \
+    k_hop<R, SIN, SSAME, SOUT, LNK, CLV, E, G><<<grid, block, 0, st>>>(g, par, in, same, out, lk, cl, coef); \
+  } else
+  QXD_HOP_CASE(EPI_HOP, false)
+  QXD_HOP_CASE(EPI_DFULL, false)
+  QXD_HOP_CASE(EPI_INV, false)
+  QXD_HOP_CASE(EPI_INV, true)
+  QXD_HOP_CASE(EPI_DHAT2, false)
+  QXD_HOP_CASE(EPI_DHAT2, true)
+  QXD_HOP_CASE(EPI_XPAY, false)
+  QXD_HOP_CASE(EPI_INVXPAY, false) { return fail(lat, QXD_EINVAL, "unsupported hop epilogue"); }
+#undef QXD_HOP_CASE
+  QXD_CHECK_LAUNCH(lat, "k_hop");
+  return QXD_OK;
+}
+
+qxd_status hop64(qxd_lattice* lat, int par, int epi, int g5, const double2* in, const double2* same, double2* out,
+                 double coef) {
+  const i64 sv = lat->sv;
+  SpinorF64 si{const_cast<double2*>(in), sv}, ss{const_cast<double2*>(same), sv}, so{out, sv};
+  LinkF64 lk{lat->W64, sv};
+  bool inv = epi == EPI_INV || epi == EPI_INVXPAY;
+  CloverF64 cl{inv ? lat->Ci64 : lat->C64, sv};
+  prof_begin(lat, KSTAT_F64, hop_bytes(lat, epi, 192, 192, 144, 576));
+  qxd_status st = launch_hop<double>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
+  prof_end(lat);
+  return st;
+}
+
+qxd_status hop32(qxd_lattice* lat, int par, int epi, int g5, const float4* in, const float4* same, float4* out,
+                 float coef) {
+  const i64 sv = lat->sv;
+  SpinorF32 si{const_cast<float4*>(in), sv}, ss{const_cast<float4*>(same), sv}, so{out, sv};
+  LinkF32 lk{lat->W32, sv};
+  bool inv = epi == EPI_INV || epi == EPI_INVXPAY;
+  CloverF32 cl{inv ? lat->Ci32 : lat->C32, sv};
+  prof_begin(lat, KSTAT_F32, hop_bytes(lat, epi, 96, 96, 72, 288));
+  qxd_status st = launch_hop<float>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
+  prof_end(lat);
+  return st;
+}
+
+template <class FMT>
+static qxd_status hop16_t(qxd_lattice* lat, int kind, int par, int epi, int g5, const uint2* in, const float* in_nrm,
+                          const uint2* same, const float* same_nrm, uint2* out, float* out_nrm, float4* out32,
+                          float coef, const uint32_t* W, const uint2* C, const float* Cn) {
+  const i64 sv = lat->sv;
+  SpinorN16<FMT> si{const_cast<uint2*>(in), const_cast<float*>(in_nrm), sv};
+  SpinorN16<FMT> ss{const_cast<uint2*>(same), const_cast<float*>(same_nrm), sv};
+  Link16<FMT> lk{W, sv};
+  Clover16<FMT> cl{C, Cn, sv};
+  double bytes;
+  qxd_status st;
+  if (out32) {
+    SpinorF32 so{out32, sv};
+    bytes = hop_bytes(lat, epi, 52, 96, 36, 152);
+    prof_begin(lat, kind, bytes);
+    st = launch_hop<float>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
+  } else {
+    SpinorN16<FMT> so{out, out_nrm, sv};
+    bytes = hop_bytes(lat, epi, 52, 52, 36, 152);
+    prof_begin(lat, kind, bytes);
+    st = launch_hop<float>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
+  }
+  prof_end(lat);
+  return st;
+}
+
+qxd_status hop16(qxd_lattice* lat, int bf16, int par, int epi, int g5, const uint2* in, const float* in_nrm,
+                 const uint2* same, const float* same_nrm, uint2* out, float* out_nrm, float4* out32, float coef) {
+  bool inv = epi == EPI_INV || epi == EPI_INVXPAY;
+  if (bf16)
+    return hop16_t<B16>(lat, KSTAT_BF16N, par, epi, g5, in, in_nrm, same, same_nrm, out, out_nrm, out32, coef,
+                        lat->WB16, inv ? lat->CiB16 : lat->CB16, inv ? lat->CiB16n : lat->CB16n);
+  return hop16_t<H16>(lat, KSTAT_F16N, par, epi, g5, in, in_nrm, same, same_nrm, out, out_nrm, out32, coef,
+                      lat->W16, inv ? lat->Ci16 : lat->C16, inv ? lat->Ci16n : lat->C16n);
+}
+
+}  // namespace qxd

@@ -1,0 +1,491 @@
+// Internal types of libqxd: lattice geometry, device field layouts, precision accessors.
+//
+// Device layout (structure of arrays, one "plane" per component, stride sv >= Vh, padded to a
+// multiple of 64 sites; padding entries stay zero):
+//   FP64 spinor, one parity : double2 [12][sv]        component k = 3*alpha + a
+//   FP32 spinor, one parity : float4  [6][sv]         components (2j, 2j+1)
+//   16-bit spinor, one parity: uint2  [6][sv] + float norm [sv]   value = h * norm
+//   links  : [parity][mu][9][sv]  (double2 / float2 / 32-bit half2-or-bf162), entry 3*row + col
+//   clover : [parity][block][..][sv], 36 reals per block in the 36-real packing of Sec. 4.1.3
+//            (double2 x18 / float4 x9 / uint2 x9 + float norm [parity][block][sv])
+// A site of parity p with lexicographic index Lambda has checkerboard index cb = floor(Lambda/2),
+// the openQxD in-parity index of Eq. ipt with one block.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qxd.h"
+
+namespace qxd {
+
+typedef int64_t i64;
+
+// ------------------------------------------------------------------------------------------
+// Geometry: pure index functions (no lookup tables), Sec. 4.1.1
+// ------------------------------------------------------------------------------------------
+struct Geom {
+  int L[4];    // extents on the device lattice (x doubled for C*)
+  int shift;   // C*: physical L1 (mirror offset); 0 without C*
+  int anti;    // 1: antiperiodic in time
+  i64 Vh;      // sites per parity
+  i64 sv;      // plane stride
+};
+
+__host__ __device__ __forceinline__ i64 lexi(const Geom& g, const int x[4]) {
+  return (((i64)x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3];
+}
+
+// Coordinates of the site with checkerboard index cb and parity par.  Lambda = 2 cb or
+// 2 cb + 1; the two candidates differ only in x3 (L3 is even), and the parity decides.
+__host__ __device__ __forceinline__ void cb_coords(const Geom& g, i64 cb, int par, int x[4]) {
+  i64 lam = 2 * cb;
+  x[3] = (int)(lam % g.L[3]);
+  i64 t = lam / g.L[3];
+  x[2] = (int)(t % g.L[2]);
+  t /= g.L[2];
+  x[1] = (int)(t % g.L[1]);
+  x[0] = (int)(t / g.L[1]);
+  if (((x[0] + x[1] + x[2] + x[3]) & 1) != par) x[3] += 1;
+}
+
+// Checkerboard index of x + dir * mu_hat; `crossed` reports a wrap in direction mu.  With C*,
+// a wrap in y or z lands on the mirror copy: x1 -> x1 + shift (mod 2 shift), Sec. 4.2.
+__host__ __device__ __forceinline__ i64 nbr_cb(const Geom& g, const int x[4], int mu, int dir,
+                                               bool& crossed) {
+  int y[4] = {x[0], x[1], x[2], x[3]};
+  y[mu] += dir;
+  crossed = false;
+  if (y[mu] >= g.L[mu]) {
+    y[mu] = 0;
+    crossed = true;
+  } else if (y[mu] < 0) {
+    y[mu] = g.L[mu] - 1;
+    crossed = true;
+  }
+  if (crossed && g.shift && mu >= 2) {
+    y[1] += g.shift;
+    if (y[1] >= g.L[1]) y[1] -= g.L[1];
+  }
+  return lexi(g, y) >> 1;
+}
+
+// ------------------------------------------------------------------------------------------
+// Complex arithmetic
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct cplx {
+  T re, im;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> mk(T r, T i) {
+  cplx<T> c;
+  c.re = r;
+  c.im = i;
+  return c;
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename T>
+__device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename T>
+__device__ __forceinline__ cplx<T> operator*(T s, cplx<T> a) { return mk(s * a.re, s * a.im); }
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// conj(a) * b
+template <typename T>
+__device__ __forceinline__ cplx<T> cjmul(cplx<T> a, cplx<T> b) {
+  return mk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> timesI(cplx<T> a) { return mk(-a.im, a.re); }
+template <typename T>
+__device__ __forceinline__ cplx<T> neg(cplx<T> a) { return mk(-a.re, -a.im); }
+
+// ------------------------------------------------------------------------------------------
+// 16-bit storage helpers
+// ------------------------------------------------------------------------------------------
+struct H16 {  // IEEE half
+  static __device__ __forceinline__ float lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+  static __device__ __forceinline__ float hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+  static __device__ __forceinline__ uint32_t pack(float a, float b) {
+    return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
+  }
+};
+struct B16 {  // bfloat16
+  static __device__ __forceinline__ float lo(uint32_t w) { return __uint_as_float(w << 16); }
+  static __device__ __forceinline__ float hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+  static __device__ __forceinline__ uint32_t pack(float a, float b) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// Spinor accessors (one parity)
+// ------------------------------------------------------------------------------------------
+struct SpinorF64 {
+  typedef double real;
+  double2* p;
+  i64 sv;
+  __device__ __forceinline__ void load(i64 cb, cplx<double> s[12]) const {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 v = __ldg(p + k * sv + cb);
+      s[k] = mk(v.x, v.y);
+    }
+  }
+  template <typename T>
+  __device__ __forceinline__ void store(i64 cb, const cplx<T> s[12]) const {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[k * sv + cb] = make_double2((double)s[k].re, (double)s[k].im);
+  }
+};
+
+struct SpinorF32 {
+  typedef float real;
+  float4* p;
+  i64 sv;
+  __device__ __forceinline__ void load(i64 cb, cplx<float> s[12]) const {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      float4 v = __ldg(p + j * sv + cb);
+      s[2 * j] = mk(v.x, v.y);
+      s[2 * j + 1] = mk(v.z, v.w);
+    }
+  }
+  template <typename T>
+  __device__ __forceinline__ void store(i64 cb, const cplx<T> s[12]) const {
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      p[j * sv + cb] = make_float4((float)s[2 * j].re, (float)s[2 * j].im, (float)s[2 * j + 1].re,
+                                   (float)s[2 * j + 1].im);
+  }
+};
+
+// 16-bit spinor with one FP32 scale per site: value = stored * norm, norm = max |component|.
+template <class FMT>
+struct SpinorN16 {
+  typedef float real;
+  uint2* p;
+  float* nrm;
+  i64 sv;
+  __device__ __forceinline__ void load(i64 cb, cplx<float> s[12]) const {
+    float n = __ldg(nrm + cb);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      uint2 v = __ldg(p + j * sv + cb);
+      s[2 * j] = mk(n * FMT::lo(v.x), n * FMT::hi(v.x));
+      s[2 * j + 1] = mk(n * FMT::lo(v.y), n * FMT::hi(v.y));
+    }
+  }
+  template <typename T>
+  __device__ __forceinline__ void store(i64 cb, const cplx<T> s[12]) const {
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf((float)s[k].re), fabsf((float)s[k].im)));
+    float inv = m > 0.f ? 1.0f / m : 0.f;
+    nrm[cb] = m;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      uint2 v;
+      v.x = FMT::pack((float)s[2 * j].re * inv, (float)s[2 * j].im * inv);
+      v.y = FMT::pack((float)s[2 * j + 1].re * inv, (float)s[2 * j + 1].im * inv);
+      p[j * sv + cb] = v;
+    }
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// Link accessors: [parity][mu][9][sv]
+// ------------------------------------------------------------------------------------------
+struct LinkF64 {
+  typedef double real;
+  const double2* p;
+  i64 sv;
+  __device__ __forceinline__ void load(int par, int mu, i64 cb, cplx<double> u[9]) const {
+    const double2* b = p + (i64)((par * 4 + mu) * 9) * sv + cb;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double2 v = __ldg(b + k * sv);
+      u[k] = mk(v.x, v.y);
+    }
+  }
+};
+struct LinkF32 {
+  typedef float real;
+  const float2* p;
+  i64 sv;
+  __device__ __forceinline__ void load(int par, int mu, i64 cb, cplx<float> u[9]) const {
+    const float2* b = p + (i64)((par * 4 + mu) * 9) * sv + cb;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      float2 v = __ldg(b + k * sv);
+      u[k] = mk(v.x, v.y);
+    }
+  }
+};
+template <class FMT>
+struct Link16 {
+  typedef float real;
+  const uint32_t* p;
+  i64 sv;
+  __device__ __forceinline__ void load(int par, int mu, i64 cb, cplx<float> u[9]) const {
+    const uint32_t* b = p + (i64)((par * 4 + mu) * 9) * sv + cb;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      uint32_t v = __ldg(b + k * sv);
+      u[k] = mk(FMT::lo(v), FMT::hi(v));
+    }
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// Clover accessors: 36 reals per (parity, block, site)
+// ------------------------------------------------------------------------------------------
+struct CloverF64 {
+  typedef double real;
+  const double2* p;
+  i64 sv;
+  __device__ __forceinline__ void load(int par, int blk, i64 cb, double r[36]) const {
+    const double2* b = p + (i64)((par * 2 + blk) * 18) * sv + cb;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+      double2 v = __ldg(b + k * sv);
+      r[2 * k] = v.x;
+      r[2 * k + 1] = v.y;
+    }
+  }
+};
+struct CloverF32 {
+  typedef float real;
+  const float4* p;
+  i64 sv;
+  __device__ __forceinline__ void load(int par, int blk, i64 cb, float r[36]) const {
+    const float4* b = p + (i64)((par * 2 + blk) * 9) * sv + cb;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      float4 v = __ldg(b + k * sv);
+      r[4 * k] = v.x;
+      r[4 * k + 1] = v.y;
+      r[4 * k + 2] = v.z;
+      r[4 * k + 3] = v.w;
+    }
+  }
+};
+template <class FMT>
+struct Clover16 {
+  typedef float real;
+  const uint2* p;
+  const float* nrm;  // [parity][block][sv]
+  i64 sv;
+  __device__ __forceinline__ void load(int par, int blk, i64 cb, float r[36]) const {
+    const uint2* b = p + (i64)((par * 2 + blk) * 9) * sv + cb;
+    float n = __ldg(nrm + (i64)(par * 2 + blk) * sv + cb);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      uint2 v = __ldg(b + k * sv);
+      r[4 * k] = n * FMT::lo(v.x);
+      r[4 * k + 1] = n * FMT::hi(v.x);
+      r[4 * k + 2] = n * FMT::lo(v.y);
+      r[4 * k + 3] = n * FMT::hi(v.y);
+    }
+  }
+};
+
+// y = M x for the Hermitian 6x6 block M packed in 36 reals (diagonal, then upper row-major).
+template <typename R>
+__device__ __forceinline__ void herm6_apply(const R r[36], const cplx<R> x[6], cplx<R> y[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) y[i] = r[i] * x[i];
+  int k = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < 6; ++j) {
+      cplx<R> c = mk(r[6 + 2 * k], r[7 + 2 * k]);
+      y[i] = y[i] + cmul(c, x[j]);
+      y[j] = y[j] + cjmul(c, x[i]);
+      ++k;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// The lattice object (host side)
+// ------------------------------------------------------------------------------------------
+enum { KSTAT_F64 = 0, KSTAT_F32 = 1, KSTAT_F16N = 2, KSTAT_BF16N = 3, KSTAT_N = 4 };
+
+// Device scalar slots used by the solvers and reductions.
+enum {
+  SC_GAMMA = 0, SC_GAMMA_NEW, SC_QQ, SC_SS, SC_TMP0, SC_TMP1, SC_TMP2, SC_TMP3, SC_N = 16
+};
+
+struct Field64 {  // FP64 full field: two parities of double2 [12][sv]
+  double2* p = nullptr;
+};
+
+}  // namespace qxd
+
+struct qxd_lattice {
+  qxd::Geom g;
+  int Lphys[4];
+  int tbc, cstar, order;
+  qxd::i64 V, Vh, sv, Vphys;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+
+  // gauge field (FP64): SU(3) links, U(1) angles, hop links W = exp(iqA) U
+  double2* U = nullptr;   // [2][4][9][sv]
+  double* A = nullptr;    // [2][4][sv]
+  double2* W64 = nullptr; // [2][4][9][sv]
+  float2* W32 = nullptr;
+  uint32_t* W16 = nullptr;   // FP16 pairs
+  uint32_t* WB16 = nullptr;  // BF16 pairs
+  double q = 0;
+  bool have_gauge = false;
+
+  // clover A (both parities) and inverse (index [parity]; filled on odd sites)
+  double2* C64 = nullptr;  // [2][2][18][sv]
+  double2* Ci64 = nullptr;
+  float4* C32 = nullptr;   // [2][2][9][sv]
+  float4* Ci32 = nullptr;
+  uint2* C16 = nullptr;    // [2][2][9][sv]
+  uint2* Ci16 = nullptr;
+  float* C16n = nullptr;   // [2][2][sv]
+  float* Ci16n = nullptr;
+  uint2* CB16 = nullptr;
+  uint2* CiB16 = nullptr;
+  float* CB16n = nullptr;
+  float* CiB16n = nullptr;
+  bool have_clover = false;
+  double m0 = 0, csw = 0, csw_qed = 0;
+
+  // reductions: per-block partials, a ticket counter, device scalars, pinned host mirror
+  double* red = nullptr;
+  unsigned int* ticket = nullptr;
+  double* scal = nullptr;
+  double* hscal = nullptr;
+  int red_blocks = 0;
+
+  // staging buffer for host/device boundary arrays
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  // work buffers (lazily allocated): slots 0..21 solver, 22 clover flag, 24..27 API staging fields
+  void* work[32] = {nullptr};
+  size_t work_bytes[32] = {0};
+
+  // profiling
+  bool profiling = false;
+  qxd::i64 kcount[qxd::KSTAT_N] = {0};
+  double kms[qxd::KSTAT_N] = {0};
+  double kbytes[qxd::KSTAT_N] = {0};
+  std::vector<cudaEvent_t> ev_pool;  // pairs (begin, end) per timed launch, reused after a flush
+  std::vector<int> ev_kind;
+  std::vector<double> ev_bytes;
+  int ev_used = 0;
+  qxd::i64 launches = 0;
+
+  std::string err;
+};
+
+namespace qxd {
+
+// Record an error message and return the status.
+qxd_status fail(qxd_lattice* lat, qxd_status st, const std::string& msg);
+qxd_status cuda_fail(qxd_lattice* lat, cudaError_t e, const char* where);
+
+#define QXD_CUDA(lat, call)                                   \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return qxd::cuda_fail(lat, _e, #call); \
+  } while (0)
+
+#define QXD_CHECK_LAUNCH(lat, name)                                \
+  do {                                                             \
+    cudaError_t _e = cudaGetLastError();                           \
+    if (_e != cudaSuccess) return qxd::cuda_fail(lat, _e, name);   \
+    (lat)->launches++;                                             \
+  } while (0)
+
+qxd_status ensure_work(qxd_lattice* lat, int slot, size_t bytes, void** out);
+qxd_status ensure_stage(qxd_lattice* lat, size_t bytes);
+
+inline int grid_for(i64 n, int bs) { return (int)((n + bs - 1) / bs); }
+
+// ---- layout.cu ----
+qxd_status pack_spinor64(qxd_lattice* lat, const double2* bnd, double2* field, int nsites_half_only);
+qxd_status unpack_spinor64(qxd_lattice* lat, const double2* field, double2* bnd, int nsites_half_only);
+qxd_status ingest_gauge(qxd_lattice* lat, const double2* su3, const double* a);
+qxd_status convert_links_low(qxd_lattice* lat);
+qxd_status f64_to_f32(qxd_lattice* lat, const double2* in, float4* out, i64 nplanes_sites);
+qxd_status f32_to_f64(qxd_lattice* lat, const float4* in, double2* out, i64 nplanes_sites);
+qxd_status f32_to_n16(qxd_lattice* lat, const float4* in, uint2* out, float* nrm, int bf16);
+qxd_status n16_to_f32(qxd_lattice* lat, const uint2* in, const float* nrm, float4* out, int bf16);
+
+// ---- clover.cu ----
+qxd_status clover_build(qxd_lattice* lat);
+qxd_status clover_export(qxd_lattice* lat, double* bnd);
+// out = C in on one parity (site-local); which = 0 clover, 1 inverse
+qxd_status clover_apply64(qxd_lattice* lat, int par, int which, const double2* in, double2* out);
+
+// ---- dslash.cu ----
+enum Epi { EPI_HOP = 0, EPI_DFULL = 1, EPI_INV = 2, EPI_DHAT2 = 3, EPI_XPAY = 4, EPI_INVXPAY = 5 };
+// One hop kernel launch for output parity `par`:
+//   in   : spinor field of parity 1-par (neighbours)
+//   same : spinor field of parity par (diagonal term), may be null for EPI_HOP/EPI_INV
+//   out  : spinor field of parity par
+// Epilogues:  HOP: out = coef H in;  DFULL: out = A same - 1/2 H in;
+//             INV: out = A^-1 (coef H g5? in);  DHAT2: out = A same + coef g5? H in;
+//             XPAY: out = same + coef H in;  INVXPAY: out = A^-1 (same + coef H in).
+// g5 = 1 applies gamma5 to the neighbours (INV) or to the hop sum (DHAT2).
+qxd_status hop64(qxd_lattice* lat, int par, int epi, int g5, const double2* in, const double2* same,
+                 double2* out, double coef);
+qxd_status hop32(qxd_lattice* lat, int par, int epi, int g5, const float4* in, const float4* same,
+                 float4* out, float coef);
+// 16-bit operator: spinors with per-site norms; output 16-bit (out_nrm != null) or FP32 (out32)
+qxd_status hop16(qxd_lattice* lat, int bf16, int par, int epi, int g5, const uint2* in, const float* in_nrm,
+                 const uint2* same, const float* same_nrm, uint2* out, float* out_nrm, float4* out32,
+                 float coef);
+
+// ---- blas.cu ----
+// n = number of complex entries; arrays are double2 (FP64) or float2-pairs (FP32 as float4 * n/2)
+qxd_status blas_norm2_64(qxd_lattice* lat, const double2* a, i64 n, int slot);
+qxd_status blas_dot_64(qxd_lattice* lat, const double2* a, const double2* b, i64 n, int slot_re);
+qxd_status blas_axpy_64(qxd_lattice* lat, double re, double im, const double2* x, double2* y, i64 n);
+qxd_status blas_xpay_64(qxd_lattice* lat, const double2* x, double a, double2* y, i64 n);  // y = x + a y
+qxd_status blas_copy(qxd_lattice* lat, void* dst, const void* src, size_t bytes);
+qxd_status blas_zero(qxd_lattice* lat, void* dst, size_t bytes);
+qxd_status blas_norm2_32(qxd_lattice* lat, const float4* a, i64 n4, int slot);
+// CG (CGLS) fused updates; alpha = scal[SC_GAMMA] / scal[SC_QQ]
+//   x += alpha p; s -= alpha q; scal[SC_SS] = ||s||^2
+qxd_status cg_update_xs_64(qxd_lattice* lat, double2* x, const double2* p, double2* s, const double2* q, i64 n);
+qxd_status cg_update_xs_32(qxd_lattice* lat, float4* x, const float4* p, float4* s, const float4* q, i64 n4);
+//   p = r + (scal[SC_GAMMA_NEW] / scal[SC_GAMMA]) p; then scal[SC_GAMMA] = scal[SC_GAMMA_NEW]
+qxd_status cg_update_p_64(qxd_lattice* lat, const double2* r, double2* p, i64 n);
+qxd_status cg_update_p_32(qxd_lattice* lat, const float4* r, float4* p, i64 n4);
+qxd_status read_scalars(qxd_lattice* lat, int first, int count, double* out);
+qxd_status set_scalar(qxd_lattice* lat, int slot, double v);
+// y += x (FP32 x widened into FP64 y), n = complex entries of y
+qxd_status blas_acc_f32_into_f64(qxd_lattice* lat, const float4* x, double2* y, i64 n4);
+qxd_status blas_axpy_32(qxd_lattice* lat, float a, const float4* x, float4* y, i64 n4);
+
+// ---- profiling helpers (api.cu) ----
+void prof_begin(qxd_lattice* lat, int kind, double bytes);
+void prof_end(qxd_lattice* lat);
+
+// ---- solver.cu ----
+qxd_status solve(qxd_lattice* lat, double2* x_field, const double2* b_field, const qxd_solve_params* p,
+                 qxd_solve_info* info);
+// full D on FP64 fields (both parities): out = D in
+qxd_status apply_D64(qxd_lattice* lat, const double2* in, double2* out);
+
+}  // namespace qxd

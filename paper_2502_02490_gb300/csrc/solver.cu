@@ -1,0 +1,358 @@
+// Solvers for D psi = eta on the even-odd preconditioned system.
+//
+//   Dhat = A_ee - 1/4 H_eo A_oo^-1 H_oe,  eta_hat_e = eta_e + 1/2 H_eo A_oo^-1 eta_o,
+//   psi_o = A_oo^-1 (eta_o + 1/2 H_oe psi_e).
+//
+// CG_EO     : CG on Dhat^+ Dhat psi_e = Dhat^+ eta_hat_e (tracking s = eta_hat - Dhat psi_e), all FP64,
+//             the plain FP64 even-odd CG baseline.  Judged by the full FP64 true residual.
+// MP_CG_EO  : FP64 outer defect correction r = eta - D psi (FP64 D, FP64 norms), around an inner
+//             CG whose iteration runs in FP32 vectors with the Dhat applications in inner_prec
+//             (FP32, or 16-bit spinors/links/clover with per-site norms), with FP32 reliable
+//             updates: when ||s|| has fallen by reliable_delta since the last update, the inner
+//             solution is folded into an FP32 accumulator and s is recomputed with the FP32 Dhat.
+// Every global inner product and norm is an FP64 reduction.
+#include <chrono>
+#include <cmath>
+
+#include "qxd_internal.cuh"
+
+namespace qxd {
+
+enum {
+  // FP64
+  WS_R64 = 0,   // full residual field [2][12][sv]
+  WS_T64,       // full temporary
+  WS_BH64,      // even-half vectors [12][sv]
+  WS_XE64,
+  WS_S64,
+  WS_RR64,
+  WS_P64,
+  WS_Q64,
+  WS_TO64,
+  // FP32 even/odd halves [6][sv] float4
+  WS_BH32,
+  WS_Y32,
+  WS_X32,
+  WS_S32,
+  WS_RR32,
+  WS_P32,
+  WS_Q32,
+  WS_TO32,
+  // 16-bit halves [6][sv] uint2 and their norms [sv]
+  WS_P16,
+  WS_S16,
+  WS_TO16,
+  WS_NRM16,     // 3 norm arrays
+  WS_NRM16B,    // 2 norm arrays for full-field 16-bit applies
+};
+
+#define TRY(x)                      \
+  do {                              \
+    qxd_status _s = (x);            \
+    if (_s != QXD_OK) return _s;    \
+  } while (0)
+
+template <typename T>
+static qxd_status get(qxd_lattice* lat, int slot, size_t bytes, T** out) {
+  void* p;
+  qxd_status st = ensure_work(lat, slot, bytes, &p);
+  *out = (T*)p;
+  return st;
+}
+
+qxd_status apply_D64(qxd_lattice* lat, const double2* in, double2* out) {
+  const i64 h = 12 * lat->sv;
+  TRY(hop64(lat, 0, EPI_DFULL, 0, in + h, in, out, 0.0));
+  TRY(hop64(lat, 1, EPI_DFULL, 0, in, in + h, out + h, 0.0));
+  return QXD_OK;
+}
+
+// out_e = Dhat in_e (dag: gamma5 Dhat gamma5), FP64, tmp_o odd-half scratch
+static qxd_status dhat64(qxd_lattice* lat, const double2* in, double2* out, double2* tmp, int dag) {
+  TRY(hop64(lat, 1, EPI_INV, dag, in, nullptr, tmp, 1.0));
+  TRY(hop64(lat, 0, EPI_DHAT2, dag, tmp, in, out, -0.25));
+  return QXD_OK;
+}
+
+static qxd_status dhat32(qxd_lattice* lat, const float4* in, float4* out, float4* tmp, int dag) {
+  TRY(hop32(lat, 1, EPI_INV, dag, in, nullptr, tmp, 1.0f));
+  TRY(hop32(lat, 0, EPI_DHAT2, dag, tmp, in, out, -0.25f));
+  return QXD_OK;
+}
+
+// 16-bit operator: in16 (with norm) -> out FP32
+static qxd_status dhat16(qxd_lattice* lat, int bf16, const uint2* in, const float* in_n, float4* out, uint2* tmp,
+                         float* tmp_n, int dag) {
+  TRY(hop16(lat, bf16, 1, EPI_INV, dag, in, in_n, nullptr, nullptr, tmp, tmp_n, nullptr, 1.0f));
+  TRY(hop16(lat, bf16, 0, EPI_DHAT2, dag, tmp, tmp_n, in, in_n, nullptr, nullptr, out, -0.25f));
+  return QXD_OK;
+}
+
+qxd_status apply_dhat_prec(qxd_lattice* lat, int prec, const double2* in64, double2* out64, int dag) {
+  const i64 sv = lat->sv;
+  if (prec == QXD_F64) {
+    double2* t;
+    TRY(get(lat, WS_TO64, sizeof(double2) * 12 * sv, &t));
+    return dhat64(lat, in64, out64, t, dag);
+  }
+  float4 *a, *b, *t;
+  TRY(get(lat, WS_P32, sizeof(float4) * 6 * sv, &a));
+  TRY(get(lat, WS_Q32, sizeof(float4) * 6 * sv, &b));
+  TRY(get(lat, WS_TO32, sizeof(float4) * 6 * sv, &t));
+  TRY(f64_to_f32(lat, in64, a, 6 * sv));
+  if (prec == QXD_F32) {
+    TRY(dhat32(lat, a, b, t, dag));
+  } else {
+    int bf = prec == QXD_BF16N;
+    uint2 *a16, *t16;
+    float* nrm;
+    TRY(get(lat, WS_P16, sizeof(uint2) * 6 * sv, &a16));
+    TRY(get(lat, WS_TO16, sizeof(uint2) * 6 * sv, &t16));
+    TRY(get(lat, WS_NRM16, sizeof(float) * 3 * sv, &nrm));
+    TRY(f32_to_n16(lat, a, a16, nrm, bf));
+    TRY(dhat16(lat, bf, a16, nrm, b, t16, nrm + sv, dag));
+  }
+  TRY(f32_to_f64(lat, b, out64, 6 * sv));
+  return QXD_OK;
+}
+
+// full D in a lower precision (both parities), FP64 in/out
+qxd_status apply_D_prec(qxd_lattice* lat, int prec, const double2* in64, double2* out64) {
+  const i64 sv = lat->sv;
+  if (prec == QXD_F64) return apply_D64(lat, in64, out64);
+  float4 *a, *b;
+  TRY(get(lat, WS_BH32, sizeof(float4) * 12 * sv, &a));  // full field (two halves)
+  TRY(get(lat, WS_Y32, sizeof(float4) * 12 * sv, &b));
+  TRY(f64_to_f32(lat, in64, a, 12 * sv));
+  if (prec == QXD_F32) {
+    TRY(hop32(lat, 0, EPI_DFULL, 0, a + 6 * sv, a, b, 0.f));
+    TRY(hop32(lat, 1, EPI_DFULL, 0, a, a + 6 * sv, b + 6 * sv, 0.f));
+  } else {
+    int bf = prec == QXD_BF16N;
+    uint2* a16;
+    float* nrm;
+    TRY(get(lat, WS_S16, sizeof(uint2) * 12 * sv, &a16));
+    TRY(get(lat, WS_NRM16B, sizeof(float) * 2 * sv, &nrm));
+    TRY(f32_to_n16(lat, a, a16, nrm, bf));
+    TRY(f32_to_n16(lat, a + 6 * sv, a16 + 6 * sv, nrm + sv, bf));
+    TRY(hop16(lat, bf, 0, EPI_DFULL, 0, a16 + 6 * sv, nrm + sv, a16, nrm, nullptr, nullptr, b, 0.f));
+    TRY(hop16(lat, bf, 1, EPI_DFULL, 0, a16, nrm, a16 + 6 * sv, nrm + sv, nullptr, nullptr, b + 6 * sv, 0.f));
+  }
+  TRY(f32_to_f64(lat, b, out64, 12 * sv));
+  return QXD_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 CGLS on Dhat: solve Dhat xe = bh to ||bh - Dhat xe|| <= target (absolute)
+// ------------------------------------------------------------------------------------------
+static qxd_status cgls64(qxd_lattice* lat, const double2* bh, double2* xe, double target, int maxiter,
+                         int check_every, int* iters) {
+  const i64 sv = lat->sv, n = 12 * sv;
+  const size_t hb = sizeof(double2) * n;
+  double2 *s, *rr, *p, *q, *t;
+  TRY(get(lat, WS_S64, hb, &s));
+  TRY(get(lat, WS_RR64, hb, &rr));
+  TRY(get(lat, WS_P64, hb, &p));
+  TRY(get(lat, WS_Q64, hb, &q));
+  TRY(get(lat, WS_TO64, hb, &t));
+  TRY(blas_zero(lat, xe, hb));
+  TRY(blas_copy(lat, s, bh, hb));
+  TRY(dhat64(lat, s, rr, t, 1));
+  TRY(blas_copy(lat, p, rr, hb));
+  TRY(blas_norm2_64(lat, rr, n, SC_GAMMA));
+  int it = 0;
+  double ss;
+  TRY(blas_norm2_64(lat, s, n, SC_SS));
+  TRY(read_scalars(lat, SC_SS, 1, &ss));
+  while (std::sqrt(ss) > target && it < maxiter) {
+    TRY(dhat64(lat, p, q, t, 0));
+    TRY(blas_norm2_64(lat, q, n, SC_QQ));
+    TRY(cg_update_xs_64(lat, xe, p, s, q, n));
+    TRY(dhat64(lat, s, rr, t, 1));
+    TRY(blas_norm2_64(lat, rr, n, SC_GAMMA_NEW));
+    TRY(cg_update_p_64(lat, rr, p, n));
+    ++it;
+    if (it % check_every == 0) {
+      TRY(read_scalars(lat, SC_SS, 1, &ss));
+      if (!std::isfinite(ss)) return fail(lat, QXD_ENOCONV, "non-finite residual in the FP64 CG");
+    }
+  }
+  *iters = it;
+  return QXD_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Inner mixed-precision CGLS: FP32 vectors, Dhat in `prec`, FP32 reliable updates.
+// Solves Dhat y = bh32 to ||bh32 - Dhat y|| <= target; y accumulates into y32.
+// ------------------------------------------------------------------------------------------
+static qxd_status inner_mp(qxd_lattice* lat, int prec, const float4* bh, float4* y, double target, double delta,
+                           int maxiter, int check_every, int* iters, int* nrel) {
+  const i64 sv = lat->sv, n4 = 6 * sv;
+  const size_t hb = sizeof(float4) * n4;
+  float4 *x, *s, *rr, *p, *q, *t;
+  TRY(get(lat, WS_X32, hb, &x));
+  TRY(get(lat, WS_S32, hb, &s));
+  TRY(get(lat, WS_RR32, hb, &rr));
+  TRY(get(lat, WS_P32, hb, &p));
+  TRY(get(lat, WS_Q32, hb, &q));
+  TRY(get(lat, WS_TO32, hb, &t));
+  const bool low = prec == QXD_F16N || prec == QXD_BF16N;
+  const int bf = prec == QXD_BF16N;
+  uint2 *p16 = nullptr, *s16 = nullptr, *t16 = nullptr;
+  float* nrm = nullptr;
+  if (low) {
+    TRY(get(lat, WS_P16, sizeof(uint2) * n4, &p16));
+    TRY(get(lat, WS_S16, sizeof(uint2) * n4, &s16));
+    TRY(get(lat, WS_TO16, sizeof(uint2) * n4, &t16));
+    TRY(get(lat, WS_NRM16, sizeof(float) * 3 * sv, &nrm));
+  }
+  float* p16n = nrm;
+  float* s16n = nrm ? nrm + sv : nullptr;
+  float* t16n = nrm ? nrm + 2 * sv : nullptr;
+
+  auto apply = [&](const float4* in32, const uint2* in16, const float* in16n, float4* out, int dag) -> qxd_status {
+    if (low) return dhat16(lat, bf, in16, in16n, out, t16, t16n, dag);
+    return dhat32(lat, in32, out, t, dag);
+  };
+
+  // s = bh - Dhat y (y is zero on entry, so s = bh); rr = Dhat^+ s; p = rr
+  TRY(blas_zero(lat, x, hb));
+  TRY(blas_copy(lat, s, bh, hb));
+  if (low) TRY(f32_to_n16(lat, s, s16, s16n, bf));
+  TRY(apply(s, s16, s16n, rr, 1));
+  TRY(blas_copy(lat, p, rr, hb));
+  if (low) TRY(f32_to_n16(lat, p, p16, p16n, bf));
+  TRY(blas_norm2_32(lat, rr, n4, SC_GAMMA));
+  TRY(blas_norm2_32(lat, s, n4, SC_SS));
+  double ss;
+  TRY(read_scalars(lat, SC_SS, 1, &ss));
+  double rmax = std::sqrt(ss);
+  int it = 0, rel = 0;
+  while (std::sqrt(ss) > target && it < maxiter) {
+    TRY(apply(p, p16, p16n, q, 0));
+    TRY(blas_norm2_32(lat, q, n4, SC_QQ));
+    TRY(cg_update_xs_32(lat, x, p, s, q, n4));
+    if (low) TRY(f32_to_n16(lat, s, s16, s16n, bf));
+    TRY(apply(s, s16, s16n, rr, 1));
+    TRY(blas_norm2_32(lat, rr, n4, SC_GAMMA_NEW));
+    TRY(cg_update_p_32(lat, rr, p, n4));
+    if (low) TRY(f32_to_n16(lat, p, p16, p16n, bf));
+    ++it;
+    if (it % check_every == 0) {
+      TRY(read_scalars(lat, SC_SS, 1, &ss));
+      if (!std::isfinite(ss)) return fail(lat, QXD_ENOCONV, "non-finite residual in the inner CG");
+      double sn = std::sqrt(ss);
+      if (sn > rmax) rmax = sn;
+      if (sn < delta * rmax || sn <= target) {
+        // reliable update: fold x into y, recompute s = bh - Dhat32 y in FP32
+        TRY(blas_axpy_32(lat, 1.0f, x, y, n4));
+        TRY(blas_zero(lat, x, hb));
+        TRY(dhat32(lat, y, q, t, 0));
+        TRY(blas_copy(lat, s, bh, hb));
+        TRY(blas_axpy_32(lat, -1.0f, q, s, n4));
+        TRY(blas_norm2_32(lat, s, n4, SC_SS));
+        TRY(read_scalars(lat, SC_SS, 1, &ss));
+        rmax = std::sqrt(ss);
+        ++rel;
+        if (std::sqrt(ss) > target) {
+          // keep p; refresh rr and gamma from the new residual
+          if (low) TRY(f32_to_n16(lat, s, s16, s16n, bf));
+          TRY(apply(s, s16, s16n, rr, 1));
+          TRY(blas_norm2_32(lat, rr, n4, SC_GAMMA));
+        }
+      }
+    }
+  }
+  // fold the rest
+  TRY(blas_axpy_32(lat, 1.0f, x, y, n4));
+  *iters = it;
+  *nrel = rel;
+  return QXD_OK;
+}
+
+qxd_status solve(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve_params* prm, qxd_solve_info* info) {
+  auto t0 = std::chrono::steady_clock::now();
+  const i64 sv = lat->sv, nh = 12 * sv, nf = 24 * sv;
+  const size_t fb = sizeof(double2) * nf, hb = sizeof(double2) * nh;
+  double2 *r, *tf, *bh, *xe, *to;
+  TRY(get(lat, WS_R64, fb, &r));
+  TRY(get(lat, WS_T64, fb, &tf));
+  TRY(get(lat, WS_BH64, hb, &bh));
+  TRY(get(lat, WS_XE64, hb, &xe));
+  TRY(get(lat, WS_TO64, hb, &to));
+  const bool mp = prm->solver == QXD_SOLVER_MP_CG_EO;
+  float4 *bh32 = nullptr, *y32 = nullptr;
+  if (mp) {
+    TRY(get(lat, WS_BH32, sizeof(float4) * 12 * sv, &bh32));  // sized for full fields (apply_D_prec shares it)
+    TRY(get(lat, WS_Y32, sizeof(float4) * 12 * sv, &y32));
+  }
+  double bn2;
+  TRY(blas_norm2_64(lat, b, nf, SC_TMP0));
+  TRY(read_scalars(lat, SC_TMP0, 1, &bn2));
+  const double bnorm = std::sqrt(bn2);
+  TRY(blas_zero(lat, x, fb));
+  int total = 0, outer = 0, nrel_total = 0;
+  double rel = 1.0;
+  qxd_status result = QXD_ENOCONV;
+  if (bnorm == 0.0) {
+    rel = 0.0;
+    result = QXD_OK;
+  }
+  const int max_outer = prm->max_outer > 0 ? prm->max_outer : 20;
+  for (; result != QXD_OK && outer <= max_outer; ++outer) {
+    // r = b - D x (FP64)
+    if (outer == 0) {
+      TRY(blas_copy(lat, r, b, fb));
+    } else {
+      TRY(apply_D64(lat, x, tf));
+      TRY(blas_copy(lat, r, b, fb));
+      TRY(blas_axpy_64(lat, -1.0, 0.0, tf, r, nf));
+    }
+    double rn2;
+    TRY(blas_norm2_64(lat, r, nf, SC_TMP0));
+    TRY(read_scalars(lat, SC_TMP0, 1, &rn2));
+    rel = std::sqrt(rn2) / bnorm;
+    if (!std::isfinite(rel)) return fail(lat, QXD_ENOCONV, "non-finite residual");
+    if (rel <= prm->tol) {
+      result = QXD_OK;
+      break;
+    }
+    if (outer == max_outer || total >= prm->maxiter) break;
+    // Schur source bh = r_e + 1/2 H_eo A_oo^-1 r_o
+    TRY(clover_apply64(lat, 1, 1, r + nh, to));
+    TRY(hop64(lat, 0, EPI_XPAY, 0, to, r, bh, 0.5));
+    int it = 0;
+    const double target = 0.5 * prm->tol * bnorm;
+    if (!mp) {
+      TRY(cgls64(lat, bh, xe, target, prm->maxiter - total, prm->check_every > 0 ? prm->check_every : 1, &it));
+    } else {
+      int nrel = 0;
+      TRY(f64_to_f32(lat, bh, bh32, 6 * sv));
+      TRY(blas_zero(lat, y32, sizeof(float4) * 6 * sv));
+      double inner_target = prm->inner_tol * std::sqrt(rn2);
+      if (inner_target < target) inner_target = target;
+      TRY(inner_mp(lat, prm->inner_prec, bh32, y32, inner_target, prm->reliable_delta, prm->maxiter - total,
+                   prm->check_every > 0 ? prm->check_every : 1, &it, &nrel));
+      TRY(f32_to_f64(lat, y32, xe, 6 * sv));
+      nrel_total += nrel;
+    }
+    total += it;
+    // reconstruct: x_e += xe;  x_o += A_oo^-1 (r_o + 1/2 H_oe xe)
+    TRY(hop64(lat, 1, EPI_INVXPAY, 0, xe, r + nh, to, 0.5));
+    TRY(blas_axpy_64(lat, 1.0, 0.0, xe, x, nh));
+    TRY(blas_axpy_64(lat, 1.0, 0.0, to, x + nh, nh));
+  }
+  QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  if (info) {
+    info->iters_inner = total;
+    info->iters_outer = outer;
+    info->reliable_updates = nrel_total;
+    info->true_rel_res = rel;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->status = result;
+  }
+  if (result != QXD_OK) return fail(lat, QXD_ENOCONV, "tolerance not reached within maxiter / max_outer");
+  return QXD_OK;
+}
+
+}  // namespace qxd

@@ -1,0 +1,197 @@
+"""Thin ctypes binding of libqxd (include/qxd.h): argument marshalling only.
+
+Every function keeps the C name without the ``qxd_`` prefix.  Field arguments may be numpy
+arrays (host memory, float64 or complex128, C-contiguous) or torch tensors (their data pointer
+is passed; CUDA tensors are device pointers on the lattice's stream).  Failures raise
+:class:`QxdError` carrying the status and the library's message.  There is no fallback: if
+libqxd.so is absent this module fails to import.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqxd.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libqxd.so not built at {LIB_PATH}; run __graft_entry__.build()")
+lib = C.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ENOCONV, ESTATE, ETIMEOUT = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESINGULAR", "ENOCONV", "ESTATE", "ETIMEOUT"]
+BC_PERIODIC, BC_ANTIPERIODIC = 0, 1
+ORDER_LEXI, ORDER_IPT = 0, 1
+F64, F32, F16N, BF16N = 0, 1, 2, 3
+SOLVER_CG_EO, SOLVER_MP_CG_EO = 0, 1
+PARAMS_VERSION = 1
+PREC = {"f64": F64, "f32": F32, "f16n": F16N, "bf16n": BF16N}
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("version", C.c_int), ("solver", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int),
+                ("inner_prec", C.c_int), ("inner_tol", C.c_double), ("reliable_delta", C.c_double),
+                ("max_outer", C.c_int), ("on_device", C.c_int), ("check_every", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters_inner", C.c_int), ("iters_outer", C.c_int), ("reliable_updates", C.c_int),
+                ("true_rel_res", C.c_double), ("seconds", C.c_double), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp, _i, _d, _i64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+_SIGS = {
+    "qxd_create_lattice": [C.POINTER(C.c_int), _i, _i, _i, _vp, C.POINTER(_vp)],
+    "qxd_destroy_lattice": [_vp],
+    "qxd_load_gauge": [_vp, _vp, _vp, _d, _i],
+    "qxd_build_clover": [_vp, _d, _d, _d],
+    "qxd_get_clover": [_vp, _vp, _i],
+    "qxd_apply_D": [_vp, _vp, _vp, _i, _i, _i],
+    "qxd_apply_Dhat_eo": [_vp, _vp, _vp, _i, _i, _i],
+    "qxd_solve": [_vp, _vp, _vp, C.POINTER(SolveParams), C.POINTER(SolveInfo)],
+    "qxd_vec_dot": [_vp, _vp, _vp, _i64, C.POINTER(_d), C.POINTER(_d)],
+    "qxd_vec_norm2": [_vp, _vp, _i64, C.POINTER(_d)],
+    "qxd_vec_axpy": [_vp, _d, _d, _vp, _vp, _i64],
+    "qxd_set_profiling": [_vp, _i],
+    "qxd_kernel_stats": [_vp, _i, C.POINTER(_i64), C.POINTER(_d), C.POINTER(_d)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+lib.qxd_default_params.argtypes = [C.POINTER(SolveParams)]
+lib.qxd_default_params.restype = None
+lib.qxd_last_error.argtypes = [_vp]
+lib.qxd_last_error.restype = C.c_char_p
+lib.qxd_launch_count.argtypes = [_vp]
+lib.qxd_launch_count.restype = C.c_int64
+
+
+class QxdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def last_error(lat=None) -> str:
+    return (lib.qxd_last_error(lat) or b"").decode()
+
+
+def _check(st, lat=None):
+    if st != OK:
+        raise QxdError(st, last_error(lat))
+
+
+def _ptr(a):
+    """(address, is_device) of a numpy array or torch tensor."""
+    if a is None:
+        return None, False
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, False
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), bool(a.is_cuda)
+    raise TypeError(f"unsupported field type {type(a)}")
+
+
+def create_lattice(L, tbc=BC_ANTIPERIODIC, cstar=0, order=ORDER_LEXI, stream=None):
+    """qxd_create_lattice; returns the opaque handle (an int).  stream: a cudaStream_t address or None."""
+    arr = (C.c_int * 4)(*[int(v) for v in L])
+    out = _vp()
+    _check(lib.qxd_create_lattice(arr, int(tbc), int(cstar), int(order), stream, C.byref(out)))
+    return out.value
+
+
+def destroy_lattice(lat):
+    _check(lib.qxd_destroy_lattice(lat))
+
+
+def load_gauge(lat, su3, a_u1, q):
+    p, dev = _ptr(su3)
+    pa, _ = _ptr(a_u1)
+    _check(lib.qxd_load_gauge(lat, p, pa, float(q), int(dev)), lat)
+
+
+def build_clover(lat, m0, csw, csw_qed):
+    _check(lib.qxd_build_clover(lat, float(m0), float(csw), float(csw_qed)), lat)
+
+
+def get_clover(lat, out):
+    p, dev = _ptr(out)
+    _check(lib.qxd_get_clover(lat, p, int(dev)), lat)
+
+
+def apply_D(lat, out, inp, prec=F64, nrhs=1):
+    po, dev = _ptr(out)
+    pi, dev2 = _ptr(inp)
+    if dev != dev2:
+        raise ValueError("in and out must both be host or both be device buffers")
+    _check(lib.qxd_apply_D(lat, po, pi, int(prec), int(nrhs), int(dev)), lat)
+
+
+def apply_Dhat_eo(lat, out_e, in_e, prec=F64, dagger=0):
+    po, dev = _ptr(out_e)
+    pi, dev2 = _ptr(in_e)
+    if dev != dev2:
+        raise ValueError("in and out must both be host or both be device buffers")
+    _check(lib.qxd_apply_Dhat_eo(lat, po, pi, int(prec), int(dagger), int(dev)), lat)
+
+
+def default_params(**kw):
+    p = SolveParams()
+    lib.qxd_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def solve(lat, x, b, params=None, check=True, **kw):
+    """qxd_solve; returns (status, info dict).  Raises unless check=False or status is OK."""
+    p = params if params is not None else default_params(**kw)
+    px, dev = _ptr(x)
+    pb, dev2 = _ptr(b)
+    if dev != dev2:
+        raise ValueError("x and b must both be host or both be device buffers")
+    p.on_device = int(dev)
+    info = SolveInfo()
+    st = lib.qxd_solve(lat, px, pb, C.byref(p), C.byref(info))
+    if check:
+        _check(st, lat)
+    return st, info.as_dict()
+
+
+def vec_dot(lat, a, b, n):
+    re, im = C.c_double(), C.c_double()
+    _check(lib.qxd_vec_dot(lat, _ptr(a)[0], _ptr(b)[0], int(n), C.byref(re), C.byref(im)), lat)
+    return complex(re.value, im.value)
+
+
+def vec_norm2(lat, a, n):
+    out = C.c_double()
+    _check(lib.qxd_vec_norm2(lat, _ptr(a)[0], int(n), C.byref(out)), lat)
+    return out.value
+
+
+def vec_axpy(lat, alpha, x, y, n):
+    _check(lib.qxd_vec_axpy(lat, float(np.real(alpha)), float(np.imag(alpha)), _ptr(x)[0], _ptr(y)[0], int(n)), lat)
+
+
+def set_profiling(lat, on):
+    _check(lib.qxd_set_profiling(lat, int(on)), lat)
+
+
+def kernel_stats(lat, which):
+    n, ms, b = C.c_int64(), C.c_double(), C.c_double()
+    _check(lib.qxd_kernel_stats(lat, int(which), C.byref(n), C.byref(ms), C.byref(b)), lat)
+    return n.value, ms.value, b.value
+
+
+def launch_count(lat):
+    return int(lib.qxd_launch_count(lat))

@@ -113,3 +113,15 @@ def test_uniform_su3_diagonal_flux_closed_form():
     want = np.diag(d - d.sum() / 3)
     assert np.abs(F - want).max() < 1e-15
     assert np.abs(O.field_strength_su3(lat, U, 0, 3)).max() < 1e-15
+
+
+@pytest.mark.parametrize("L,cstar", [((4, 4, 2, 6), False), ((2, 2, 4, 2), True)])
+def test_sampled_sites_equal_full_operator(L, cstar):
+    lat = O.Lattice(L, antiperiodic=True, cstar=cstar)
+    U, A = synth.gauge_field(lat.dims, 1004, 0.4)
+    op = O.Operator(lat, U, A, **PARAMS)
+    psi = rand_spinor(lat.dims, 5)
+    sites = np.random.default_rng(0).choice(lat.V, 17, replace=False)
+    full = op.D(psi)[sites]
+    got = O.D_at_sites(lat, U, A, PARAMS["q"], PARAMS["m0"], PARAMS["csw"], PARAMS["csw_qed"], psi, sites)
+    assert np.abs(got - full).max() < 1e-14 * np.abs(full).max()

@@ -85,7 +85,7 @@ def _leaves_drop_third(lat, M, mu, nu):
     return q
 
 
-def _su3_not_traceless(lat, U, mu, nu):
+def _su3_not_traceless(lat, U, mu, nu, sites=None):
     return (O._leaves(lat, U, mu, nu) - O._leaves(lat, U, nu, mu)) / 8.0
 
 
