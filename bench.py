@@ -233,6 +233,31 @@ def run_ours(args, rank, world):
     return out
 
 
+def profile_run(args):
+    """One untimed pass of the step (for ncu launch lists and kernel captures)."""
+    import torch
+
+    from paper_2502_02490_gb300 import qxd
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    w = WORKLOAD
+    U, A, eta = make_inputs(0)
+    su3_d = torch.from_numpy(U.view(np.float64)).to(dev)
+    a_d = torch.from_numpy(A).to(dev)
+    b_d = torch.from_numpy(eta.view(np.float64)).to(dev)
+    x_d = torch.empty_like(b_d)
+    lat = qxd.create_lattice(w["L"], qxd.BC_ANTIPERIODIC, 0, qxd.ORDER_LEXI, stream.cuda_stream)
+    params = qxd.default_params(solver=qxd.SOLVER_MP_CG_EO, inner_prec=PREC_NAMES[args.inner], tol=1e-10,
+                                inner_tol=args.inner_tol, reliable_delta=args.delta, check_every=args.check_every)
+    qxd.load_gauge(lat, su3_d, a_d, w["q"])
+    qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
+    st, info = qxd.solve(lat, x_d, b_d, params=params)
+    torch.cuda.synchronize()
+    print(f"profile run: lattice {w['L']}, {info}, launches {qxd.launch_count(lat)}", file=sys.stderr)
+    qxd.destroy_lattice(lat)
+
+
 def cpu_sample(sample_slices=1):
     """Time the oracle's D (clover + hop, FP64 numpy) on a bounded sample of the workload's sites:
     every site of the first `sample_slices` time slices of the 32^3 x 64 lattice."""
@@ -282,7 +307,20 @@ def main():
     ap.add_argument("--check-every", type=int, default=1)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="profiling aid for ncu: one untimed step, no JSON line (never a bench value)")
+    ap.add_argument("--lattice", default=None, help="T,L1,L2,L3 override, for --profile-run captures only")
     args = ap.parse_args()
+    if args.lattice:
+        if not args.profile_run:
+            ap.error("--lattice is only for --profile-run")
+        WORKLOAD["L"] = tuple(int(v) for v in args.lattice.split(","))
+    if args.profile_run:
+        import __graft_entry__
+
+        __graft_entry__.build()
+        profile_run(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))

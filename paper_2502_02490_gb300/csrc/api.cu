@@ -175,6 +175,13 @@ qxd_status qxd_create_lattice(const int L[4], int tbc, int cstar, int order, voi
   lat->sv = (lat->Vh + 63) / 64 * 64;
   lat->g.Vh = lat->Vh;
   lat->g.sv = lat->sv;
+  if (lat->V >= (i64)1 << 31) {
+    delete lat;
+    return fail(nullptr, QXD_EINVAL, "volume must be below 2^31 sites");
+  }
+  lat->g.dL1 = make_fastdiv((uint32_t)lat->g.L[1]);
+  lat->g.dL2 = make_fastdiv((uint32_t)lat->g.L[2]);
+  lat->g.dL3 = make_fastdiv((uint32_t)lat->g.L[3]);
   cudaGetDevice(&lat->device);
   const i64 sv = lat->sv;
   qxd_status st = QXD_OK;

@@ -71,41 +71,39 @@ __device__ __forceinline__ void link_mul(const cplx<R> u[9], const cplx<R> h[6],
     }
 }
 
-template <typename R, class SIN, class LNK, int MU, bool G5IN>
-__device__ __forceinline__ void hop_dir(const Geom& g, int par, i64 cb, const int x[4], const SIN& in,
-                                        const LNK& lk, cplx<R> acc[12]) {
-  cplx<R> s[12], h[6], u[9], t[6];
-  bool cr;
-  // forward: (1 - gamma_mu) W_mu(x) psi(x + mu)
-  i64 n = nbr_cb(g, x, MU, +1, cr);
-  in.load(n, s);
+// One of the eight hops ("legs": 2*mu + 0 forward, 2*mu + 1 backward) of the software-pipelined
+// kernel: decode the raw neighbour spinor and link fetched PF legs earlier, refill the slot with
+// the raw data of leg LEG + PF, then project, scale (per-site norm and time-boundary sign, applied
+// once to the 6-component half spinor), transport and accumulate.
+#ifndef QXD_HOP_PF16
+#define QXD_HOP_PF16 4  // prefetch depth of the 16-bit kernels (legs in flight); 4 measured best on GB300
+#endif
+
+template <int LEG, int PF, typename R, class SIN, class LNK, bool G5IN>
+__device__ __forceinline__ void leg_step(const Geom& g, int par, uint32_t cb, const uint32_t nb[8], bool cr_f,
+                                         bool cr_b, const SIN& in, const LNK& lk, typename SIN::Raw* sr,
+                                         typename LNK::Raw* lr, cplx<R> acc[12]) {
+  constexpr int MU = LEG >> 1;
+  constexpr bool FWD = (LEG & 1) == 0;
+  constexpr int slot = LEG % PF;
+  cplx<R> s[12], u[9], h[6], t[6];
+  R sc = in.decode(sr[slot], s);
+  lk.decode(lr[slot], u);
+  if constexpr (LEG + PF < 8) {
+    constexpr int nl = LEG + PF;
+    sr[slot] = in.fetch(nb[nl]);
+    lr[slot] = lk.fetch((nl & 1) ? 1 - par : par, nl >> 1, (nl & 1) ? nb[nl] : cb);
+  }
   if (G5IN) {
 #pragma unroll
     for (int k = 6; k < 12; ++k) s[k] = neg(s[k]);
   }
-  project<R, MU, true>(s, h);
-  if (MU == 0 && cr && g.anti) {
+  project<R, MU, FWD>(s, h);
+  if (MU == 0 && (FWD ? cr_f : cr_b) && g.anti) sc = -sc;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) h[k] = neg(h[k]);
-  }
-  lk.load(par, MU, cb, u);
-  link_mul<R, false>(u, h, t);
-  accumulate<R, MU, true>(acc, t);
-  // backward: (1 + gamma_mu) W_mu(x - mu)^dag psi(x - mu)
-  n = nbr_cb(g, x, MU, -1, cr);
-  in.load(n, s);
-  if (G5IN) {
-#pragma unroll
-    for (int k = 6; k < 12; ++k) s[k] = neg(s[k]);
-  }
-  project<R, MU, false>(s, h);
-  if (MU == 0 && cr && g.anti) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) h[k] = neg(h[k]);
-  }
-  lk.load(1 - par, MU, n, u);
-  link_mul<R, true>(u, h, t);
-  accumulate<R, MU, false>(acc, t);
+  for (int k = 0; k < 6; ++k) h[k] = sc * h[k];
+  link_mul<R, !FWD>(u, h, t);
+  accumulate<R, MU, FWD>(acc, t);
 }
 
 template <typename R, class CLV>
@@ -126,21 +124,41 @@ struct NoSpinor {
   __device__ __forceinline__ void store(i64, const cplx<T>*) const {}
 };
 
-template <typename R, class SIN, class SSAME, class SOUT, class LNK, class CLV, int EPI, bool G5>
+template <typename R, class SIN, class SSAME, class SOUT, class LNK, class CLV, int EPI, bool G5, int PF>
 __global__ void __launch_bounds__(128) k_hop(Geom g, int par, SIN in, SSAME same, SOUT out, LNK lk, CLV cl,
                                              R coef) {
-  i64 cb = blockIdx.x * (i64)blockDim.x + threadIdx.x;
-  if (cb >= g.Vh) return;
+  const uint32_t cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= (uint32_t)g.Vh) return;
   int x[4];
-  cb_coords(g, cb, par, x);
+  cb_coords32(g, cb, par, x);
+  uint32_t nb[8];
+  bool cr_f = false, cr_b = false, c;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    nb[2 * mu] = nbr_cb32(g, x, mu, +1, c);
+    if (mu == 0) cr_f = c;
+    nb[2 * mu + 1] = nbr_cb32(g, x, mu, -1, c);
+    if (mu == 0) cr_b = c;
+  }
+  typename SIN::Raw sr[PF];
+  typename LNK::Raw lr[PF];
+#pragma unroll
+  for (int l = 0; l < PF; ++l) {
+    sr[l] = in.fetch(nb[l]);
+    lr[l] = lk.fetch((l & 1) ? 1 - par : par, l >> 1, (l & 1) ? nb[l] : cb);
+  }
   cplx<R> acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = mk((R)0, (R)0);
   constexpr bool G5IN = G5 && (EPI == EPI_INV);
-  hop_dir<R, SIN, LNK, 0, G5IN>(g, par, cb, x, in, lk, acc);
-  hop_dir<R, SIN, LNK, 1, G5IN>(g, par, cb, x, in, lk, acc);
-  hop_dir<R, SIN, LNK, 2, G5IN>(g, par, cb, x, in, lk, acc);
-  hop_dir<R, SIN, LNK, 3, G5IN>(g, par, cb, x, in, lk, acc);
+  leg_step<0, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
+  leg_step<1, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
+  leg_step<2, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
+  leg_step<3, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
+  leg_step<4, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
+  leg_step<5, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
+  leg_step<6, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
+  leg_step<7, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
 
   cplx<R> o[12];
   if (EPI == EPI_HOP) {
@@ -185,7 +203,7 @@ static double hop_bytes(qxd_lattice* lat, int epi, double sp_in, double sp_out, 
   return b * (double)lat->Vh;
 }
 
-template <typename R, class SIN, class SSAME, class SOUT, class LNK, class CLV>
+template <typename R, int PF, class SIN, class SSAME, class SOUT, class LNK, class CLV>
 static qxd_status launch_hop(qxd_lattice* lat, int par, int epi, int g5, SIN in, SSAME same, SOUT out, LNK lk,
                              CLV cl, R coef) {
   const Geom& g = lat->g;
@@ -193,7 +211,7 @@ static qxd_status launch_hop(qxd_lattice* lat, int par, int epi, int g5, SIN in,
   cudaStream_t st = lat->stream;
 #define QXD_HOP_CASE(E, G)                                                                              \
   if (epi == E && (g5 != 0) == G) {                                                                     \
-    k_hop<R, SIN, SSAME, SOUT, LNK, CLV, E, G><<<grid, block, 0, st>>>(g, par, in, same, out, lk, cl, coef); \
+    k_hop<R, SIN, SSAME, SOUT, LNK, CLV, E, G, PF><<<grid, block, 0, st>>>(g, par, in, same, out, lk, cl, coef); \
   } else
   QXD_HOP_CASE(EPI_HOP, false)
   QXD_HOP_CASE(EPI_DFULL, false)
@@ -216,7 +234,7 @@ qxd_status hop64(qxd_lattice* lat, int par, int epi, int g5, const double2* in, 
   bool inv = epi == EPI_INV || epi == EPI_INVXPAY;
   CloverF64 cl{inv ? lat->Ci64 : lat->C64, sv};
   prof_begin(lat, KSTAT_F64, hop_bytes(lat, epi, 192, 192, 144, 576));
-  qxd_status st = launch_hop<double>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
+  qxd_status st = launch_hop<double, 2>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
   prof_end(lat);
   return st;
 }
@@ -229,7 +247,7 @@ qxd_status hop32(qxd_lattice* lat, int par, int epi, int g5, const float4* in, c
   bool inv = epi == EPI_INV || epi == EPI_INVXPAY;
   CloverF32 cl{inv ? lat->Ci32 : lat->C32, sv};
   prof_begin(lat, KSTAT_F32, hop_bytes(lat, epi, 96, 96, 72, 288));
-  qxd_status st = launch_hop<float>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
+  qxd_status st = launch_hop<float, 2>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
   prof_end(lat);
   return st;
 }
@@ -249,12 +267,12 @@ static qxd_status hop16_t(qxd_lattice* lat, int kind, int par, int epi, int g5, 
     SpinorF32 so{out32, sv};
     bytes = hop_bytes(lat, epi, 52, 96, 36, 152);
     prof_begin(lat, kind, bytes);
-    st = launch_hop<float>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
+    st = launch_hop<float, QXD_HOP_PF16>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
   } else {
     SpinorN16<FMT> so{out, out_nrm, sv};
     bytes = hop_bytes(lat, epi, 52, 52, 36, 152);
     prof_begin(lat, kind, bytes);
-    st = launch_hop<float>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
+    st = launch_hop<float, QXD_HOP_PF16>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
   }
   prof_end(lat);
   return st;

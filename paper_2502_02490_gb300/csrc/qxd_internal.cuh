@@ -29,12 +29,39 @@ typedef int64_t i64;
 // ------------------------------------------------------------------------------------------
 // Geometry: pure index functions (no lookup tables), Sec. 4.1.1
 // ------------------------------------------------------------------------------------------
+// Division by a constant d >= 2 for 0 <= n < 2^31: with s = ceil(log2 d) and
+// m = ceil(2^(31+s) / d) (< 2^32), n / d = umulhi(n, m) >> (s - 1).  The rounding error of m
+// adds less than 2^-s <= 1/d to n/d, which cannot carry past the next integer.
+struct FastDiv {
+  uint32_t d, m, s1;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t s = 0;
+  while ((1ull << s) < d) ++s;
+  unsigned long long m = ((1ull << (31 + s)) + d - 1) / d;
+  FastDiv f;
+  f.d = d;
+  f.m = (uint32_t)m;
+  f.s1 = s - 1;
+  return f;
+}
+
+__host__ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(n, f.m) >> f.s1;
+#else
+  return (uint32_t)(((unsigned long long)n * f.m) >> 32) >> f.s1;
+#endif
+}
+
 struct Geom {
   int L[4];    // extents on the device lattice (x doubled for C*)
   int shift;   // C*: physical L1 (mirror offset); 0 without C*
   int anti;    // 1: antiperiodic in time
   i64 Vh;      // sites per parity
   i64 sv;      // plane stride
+  FastDiv dL1, dL2, dL3;  // divisions by L1, L2, L3 (V < 2^31)
 };
 
 __host__ __device__ __forceinline__ i64 lexi(const Geom& g, const int x[4]) {
@@ -52,6 +79,38 @@ __host__ __device__ __forceinline__ void cb_coords(const Geom& g, i64 cb, int pa
   x[1] = (int)(t % g.L[1]);
   x[0] = (int)(t / g.L[1]);
   if (((x[0] + x[1] + x[2] + x[3]) & 1) != par) x[3] += 1;
+}
+
+// 32-bit version for V < 2^31 using the precomputed divisions.
+__device__ __forceinline__ void cb_coords32(const Geom& g, uint32_t cb, int par, int x[4]) {
+  uint32_t lam = 2u * cb;
+  uint32_t q1 = fdiv(lam, g.dL3);
+  x[3] = (int)(lam - q1 * g.dL3.d);
+  uint32_t q2 = fdiv(q1, g.dL2);
+  x[2] = (int)(q1 - q2 * g.dL2.d);
+  uint32_t q3 = fdiv(q2, g.dL1);
+  x[1] = (int)(q2 - q3 * g.dL1.d);
+  x[0] = (int)q3;
+  if (((x[0] + x[1] + x[2] + x[3]) & 1) != par) x[3] += 1;
+}
+
+// Checkerboard index of x + dir * mu_hat (32-bit); sets crossed on a wrap in direction mu.
+__device__ __forceinline__ uint32_t nbr_cb32(const Geom& g, const int x[4], int mu, int dir, bool& crossed) {
+  int y[4] = {x[0], x[1], x[2], x[3]};
+  y[mu] += dir;
+  crossed = false;
+  if (y[mu] >= g.L[mu]) {
+    y[mu] = 0;
+    crossed = true;
+  } else if (y[mu] < 0) {
+    y[mu] = g.L[mu] - 1;
+    crossed = true;
+  }
+  if (crossed && g.shift && mu >= 2) {
+    y[1] += g.shift;
+    if (y[1] >= g.L[1]) y[1] -= g.L[1];
+  }
+  return ((((uint32_t)y[0] * g.L[1] + y[1]) * g.L[2] + y[2]) * g.L[3] + y[3]) >> 1;
 }
 
 // Checkerboard index of x + dir * mu_hat; `crossed` reports a wrap in direction mu.  With C*,
@@ -134,8 +193,23 @@ struct B16 {  // bfloat16
 // ------------------------------------------------------------------------------------------
 struct SpinorF64 {
   typedef double real;
+  struct Raw {
+    double2 v[12];
+  };
   double2* p;
   i64 sv;
+  __device__ __forceinline__ Raw fetch(uint32_t cb) const {
+    Raw r;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) r.v[k] = __ldg(p + k * sv + cb);
+    return r;
+  }
+  // unscaled components; returns the scale (1 here)
+  __device__ __forceinline__ double decode(const Raw& r, cplx<double> s[12]) const {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s[k] = mk(r.v[k].x, r.v[k].y);
+    return 1.0;
+  }
   __device__ __forceinline__ void load(i64 cb, cplx<double> s[12]) const {
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -152,8 +226,25 @@ struct SpinorF64 {
 
 struct SpinorF32 {
   typedef float real;
+  struct Raw {
+    float4 v[6];
+  };
   float4* p;
   i64 sv;
+  __device__ __forceinline__ Raw fetch(uint32_t cb) const {
+    Raw r;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) r.v[j] = __ldg(p + j * sv + cb);
+    return r;
+  }
+  __device__ __forceinline__ float decode(const Raw& r, cplx<float> s[12]) const {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      s[2 * j] = mk(r.v[j].x, r.v[j].y);
+      s[2 * j + 1] = mk(r.v[j].z, r.v[j].w);
+    }
+    return 1.0f;
+  }
   __device__ __forceinline__ void load(i64 cb, cplx<float> s[12]) const {
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
@@ -175,9 +266,29 @@ struct SpinorF32 {
 template <class FMT>
 struct SpinorN16 {
   typedef float real;
+  struct Raw {
+    uint2 v[6];
+    float n;
+  };
   uint2* p;
   float* nrm;
   i64 sv;
+  __device__ __forceinline__ Raw fetch(uint32_t cb) const {
+    Raw r;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) r.v[j] = __ldg(p + j * sv + cb);
+    r.n = __ldg(nrm + cb);
+    return r;
+  }
+  // stored (unscaled) components; the caller applies the returned per-site scale
+  __device__ __forceinline__ float decode(const Raw& r, cplx<float> s[12]) const {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      s[2 * j] = mk(FMT::lo(r.v[j].x), FMT::hi(r.v[j].x));
+      s[2 * j + 1] = mk(FMT::lo(r.v[j].y), FMT::hi(r.v[j].y));
+    }
+    return r.n;
+  }
   __device__ __forceinline__ void load(i64 cb, cplx<float> s[12]) const {
     float n = __ldg(nrm + cb);
 #pragma unroll
@@ -209,8 +320,22 @@ struct SpinorN16 {
 // ------------------------------------------------------------------------------------------
 struct LinkF64 {
   typedef double real;
+  struct Raw {
+    double2 w[9];
+  };
   const double2* p;
   i64 sv;
+  __device__ __forceinline__ Raw fetch(int par, int mu, uint32_t cb) const {
+    const double2* b = p + (i64)((par * 4 + mu) * 9) * sv + cb;
+    Raw r;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) r.w[k] = __ldg(b + k * sv);
+    return r;
+  }
+  __device__ __forceinline__ void decode(const Raw& r, cplx<double> u[9]) const {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = mk(r.w[k].x, r.w[k].y);
+  }
   __device__ __forceinline__ void load(int par, int mu, i64 cb, cplx<double> u[9]) const {
     const double2* b = p + (i64)((par * 4 + mu) * 9) * sv + cb;
 #pragma unroll
@@ -222,8 +347,22 @@ struct LinkF64 {
 };
 struct LinkF32 {
   typedef float real;
+  struct Raw {
+    float2 w[9];
+  };
   const float2* p;
   i64 sv;
+  __device__ __forceinline__ Raw fetch(int par, int mu, uint32_t cb) const {
+    const float2* b = p + (i64)((par * 4 + mu) * 9) * sv + cb;
+    Raw r;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) r.w[k] = __ldg(b + k * sv);
+    return r;
+  }
+  __device__ __forceinline__ void decode(const Raw& r, cplx<float> u[9]) const {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = mk(r.w[k].x, r.w[k].y);
+  }
   __device__ __forceinline__ void load(int par, int mu, i64 cb, cplx<float> u[9]) const {
     const float2* b = p + (i64)((par * 4 + mu) * 9) * sv + cb;
 #pragma unroll
@@ -236,8 +375,22 @@ struct LinkF32 {
 template <class FMT>
 struct Link16 {
   typedef float real;
+  struct Raw {
+    uint32_t w[9];
+  };
   const uint32_t* p;
   i64 sv;
+  __device__ __forceinline__ Raw fetch(int par, int mu, uint32_t cb) const {
+    const uint32_t* b = p + (i64)((par * 4 + mu) * 9) * sv + cb;
+    Raw r;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) r.w[k] = __ldg(b + k * sv);
+    return r;
+  }
+  __device__ __forceinline__ void decode(const Raw& r, cplx<float> u[9]) const {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = mk(FMT::lo(r.w[k]), FMT::hi(r.w[k]));
+  }
   __device__ __forceinline__ void load(int par, int mu, i64 cb, cplx<float> u[9]) const {
     const uint32_t* b = p + (i64)((par * 4 + mu) * 9) * sv + cb;
 #pragma unroll
