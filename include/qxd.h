@@ -173,6 +173,28 @@ qxd_status qxd_vec_norm2(qxd_lattice *lat, const double *a, int64_t n, double *o
 qxd_status qxd_vec_axpy(qxd_lattice *lat, double re, double im, const double *x, double *y,
                         int64_t n);
 
+/* Dot product for callers that cannot allocate device memory.  The paper has no counterpart:
+ * this entry point exists for callers that must not call cudaMalloc -- code running while a
+ * stream is being captured into a CUDA graph, code inside a framework whose device memory
+ * belongs to its own caching allocator, and latency-critical loops that cannot afford the
+ * device synchronisation an allocation can cause.
+ *   out[0] + i out[1] = sum_k conj(a_k) b_k over n complex numbers (FP64, interleaved re, im).
+ * a, b: device vectors; out: DEVICE memory for 2 doubles; cuda_stream: stream to run on (NULL =
+ * legacy default stream).  No lattice is needed and the call returns without synchronising.
+ * Scratch: a static device array inside the library (64 KiB of per-block partial sums plus a
+ * counter), which every GPU that loads the library keeps until process exit.  Limit: n <=
+ * QXD_NOALLOC_MAX_N; larger n returns QXD_EINVAL.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture begins.  All calls share the one array: calls that overlap on the GPU (e.g. on two
+ * streams at once) race and give wrong results; serialise them.  The result is deterministic
+ * for a given n (fixed blocking) and agrees with qxd_vec_dot to rounding.  Allocates nothing
+ * and calls no allocating routine.  Errors: QXD_EINVAL for n < 0, n > QXD_NOALLOC_MAX_N or a
+ * null pointer (a and b may be NULL when n = 0); QXD_ECUDA if a CUDA call fails; the message
+ * is in qxd_last_error(NULL). */
+#define QXD_NOALLOC_MAX_N 16777216
+qxd_status qxd_vec_dot_noalloc(const double *a, const double *b, int64_t n, double *out,
+                               void *cuda_stream);
+
 /* Kernel timing.  With profiling on, the library brackets each launch of its hop kernels with
  * CUDA events on the lattice stream; qxd_kernel_stats returns, for the kernel class `which`
  * (0 = FP64 hop, 1 = FP32 hop, 2 = FP16N hop, 3 = BF16N hop), the number of timed launches, their
@@ -184,7 +206,8 @@ qxd_status qxd_kernel_stats(qxd_lattice *lat, int which, int64_t *launches, doub
 int64_t qxd_launch_count(const qxd_lattice *lat);
 
 /* Message of the last failure on this lattice ("" if none); never NULL.  With lat == NULL,
- * the message of the last failed qxd_create_lattice. */
+ * the message of the last failed call made without a lattice (qxd_create_lattice,
+ * qxd_vec_dot_noalloc). */
 const char *qxd_last_error(const qxd_lattice *lat);
 
 #ifdef __cplusplus

@@ -56,6 +56,7 @@ _SIGS = {
     "qxd_vec_dot": [_vp, _vp, _vp, _i64, C.POINTER(_d), C.POINTER(_d)],
     "qxd_vec_norm2": [_vp, _vp, _i64, C.POINTER(_d)],
     "qxd_vec_axpy": [_vp, _d, _d, _vp, _vp, _i64],
+    "qxd_vec_dot_noalloc": [_vp, _vp, _i64, _vp, _vp],
     "qxd_set_profiling": [_vp, _i],
     "qxd_kernel_stats": [_vp, _i, C.POINTER(_i64), C.POINTER(_d), C.POINTER(_d)],
 }
@@ -181,6 +182,15 @@ def vec_norm2(lat, a, n):
 
 def vec_axpy(lat, alpha, x, y, n):
     _check(lib.qxd_vec_axpy(lat, float(np.real(alpha)), float(np.imag(alpha)), _ptr(x)[0], _ptr(y)[0], int(n)), lat)
+
+
+NOALLOC_MAX_N = 16777216
+
+
+def vec_dot_noalloc(a, b, n, out, stream=None):
+    """qxd_vec_dot_noalloc: <a, b> of n complex entries into the 2 doubles of device memory `out`,
+    with scratch in a static device array (no allocation).  stream: a cudaStream_t address or None."""
+    _check(lib.qxd_vec_dot_noalloc(_ptr(a)[0], _ptr(b)[0], int(n), _ptr(out)[0], stream))
 
 
 def set_profiling(lat, on):
