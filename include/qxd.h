@@ -81,8 +81,10 @@ typedef enum { QXD_F64 = 0, QXD_F32 = 1, QXD_F16N = 2, QXD_BF16N = 3 } qxd_prec;
 
 typedef enum {
   QXD_SOLVER_CG_EO = 0,    /* plain FP64 even-odd CG (CG on Dhat^+ Dhat), true-residual judged */
-  QXD_SOLVER_MP_CG_EO = 1  /* FP64 outer defect correction around an inner even-odd CG in
+  QXD_SOLVER_MP_CG_EO = 1, /* FP64 outer defect correction around an inner even-odd CG in
                               inner_prec with FP32 reliable updates */
+  QXD_SOLVER_MP_BICGSTAB_EO = 2 /* as MP_CG_EO with BiCGStab on Dhat as the inner solver (each
+                                   reliable update restarts it from the recomputed residual) */
 } qxd_solver;
 
 typedef struct {

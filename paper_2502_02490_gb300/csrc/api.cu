@@ -209,8 +209,8 @@ qxd_status qxd_create_lattice(const int L[4], int tbc, int cstar, int order, voi
   ALLOC(CiB16, sizeof(uint2) * 36 * sv);
   ALLOC(CB16n, sizeof(float) * 4 * sv);
   ALLOC(CiB16n, sizeof(float) * 4 * sv);
-  lat->red_blocks = 152 * 4;
-  ALLOC(red, sizeof(double) * 4 * lat->red_blocks);
+  lat->red_blocks = 152 * 8;
+  ALLOC(red, sizeof(double) * 4 * lat->red_blocks);  // partial sums: up to 4 values per reduction block
   ALLOC(ticket, sizeof(unsigned int) * 4);
   ALLOC(scal, sizeof(double) * SC_N);
 #undef ALLOC
@@ -348,9 +348,10 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
   if (info) std::memset(info, 0, sizeof(*info));
   if (!x || !b || !p) return fail(lat, QXD_EINVAL, "null argument");
   if (p->version != QXD_PARAMS_VERSION) return fail(lat, QXD_EINVAL, "qxd_solve_params version mismatch");
-  if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO) return fail(lat, QXD_EINVAL, "bad solver");
+  if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO && p->solver != QXD_SOLVER_MP_BICGSTAB_EO)
+    return fail(lat, QXD_EINVAL, "bad solver");
   if (!(p->tol > 0) || p->maxiter <= 0) return fail(lat, QXD_EINVAL, "tol must be > 0 and maxiter > 0");
-  if (p->solver == QXD_SOLVER_MP_CG_EO && (p->inner_prec < QXD_F32 || p->inner_prec > QXD_BF16N))
+  if (p->solver != QXD_SOLVER_CG_EO && (p->inner_prec < QXD_F32 || p->inner_prec > QXD_BF16N))
     return fail(lat, QXD_EINVAL, "inner_prec must be F32, F16N or BF16N");
   if (!lat->have_clover) return fail(lat, QXD_ESTATE, "solve before build_clover");
   const i64 sv = lat->sv;

@@ -1,0 +1,247 @@
+// Fused vector kernels of BiCGStab on the even-odd system (FP32 vectors, FP64 reductions).
+//
+// BiCGStab for Dhat x = b (r_hat the fixed shadow residual):
+//   v = Dhat p;  alpha = rho / <r_hat, v>;  s = r - alpha v;  t = Dhat s;
+//   omega = <t, s> / <t, t>;  x += alpha p + omega s;  r = s - omega t;
+//   rho' = <r_hat, r>;  beta = (rho' / rho)(alpha / omega);  p = r + beta (p - omega v).
+// The complex scalars live in device slots (SC_RHO, SC_RV, SC_TS, SC_TT, SC_RR, SC_RN); each
+// kernel recomputes alpha, omega, beta from them, so an iteration needs no host round trip.
+// Kernels work site by site (one thread per site, six float4 per site) so they can also write
+// the 16-bit copies (with per-site scale) that the next 16-bit Dhat reads; per-site products
+// are summed in FP32 and everything beyond in FP64.
+#include "reduce.cuh"
+
+namespace qxd {
+
+static const int BB = 256;
+
+static int bgrid(qxd_lattice* lat) {
+  i64 b = (lat->sv + BB - 1) / BB;
+  if (b > lat->red_blocks) b = lat->red_blocks;
+  return (int)(b < 1 ? 1 : b);
+}
+
+struct cd2 {
+  double re, im;
+};
+__device__ __forceinline__ cd2 cdiv(cd2 a, cd2 b) {
+  double d = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+__device__ __forceinline__ cd2 cmul2(cd2 a, cd2 b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+__device__ __forceinline__ float4 caxpy4(float ar, float ai, float4 x, float4 y) {  // y + a x (two complex)
+  return make_float4(y.x + ar * x.x - ai * x.y, y.y + ar * x.y + ai * x.x, y.z + ar * x.z - ai * x.w,
+                     y.w + ar * x.w + ai * x.z);
+}
+
+template <class FMT>
+__device__ __forceinline__ void store16(const float4 v[6], uint2* __restrict__ o, float* __restrict__ on, i64 sv,
+                                        i64 cb) {
+  float m = 0.f;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) m = fmaxf(m, fmaxf(fmaxf(fabsf(v[j].x), fabsf(v[j].y)), fmaxf(fabsf(v[j].z), fabsf(v[j].w))));
+  const float inv = m > 0.f ? 1.f / m : 0.f;
+  on[cb] = m;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    uint2 h;
+    h.x = FMT::pack(v[j].x * inv, v[j].y * inv);
+    h.y = FMT::pack(v[j].z * inv, v[j].w * inv);
+    o[j * sv + cb] = h;
+  }
+}
+
+// conj(a) b summed over the two complex numbers of a float4 pair
+__device__ __forceinline__ void cdot4(float4 a, float4 b, float& re, float& im) {
+  re += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+  im += a.x * b.y - a.y * b.x + a.z * b.w - a.w * b.z;
+}
+
+// scal[slot..slot+1] = <a, b>
+__global__ void __launch_bounds__(BB) k_cdot_32(const float4* __restrict__ a, const float4* __restrict__ b, i64 sv,
+                                                double* red, unsigned int* ticket, double* scal, int slot) {
+  double v[2] = {0.0, 0.0};
+  for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) cdot4(a[j * sv + cb], b[j * sv + cb], re, im);
+    v[0] += re;
+    v[1] += im;
+  }
+  block_sum<2, BB>(v);
+  finish_reduce<2, BB>(v, red, ticket, scal, slot);
+}
+
+// s = r - alpha v, alpha = rho / <r_hat, v>; optional 16-bit s
+template <class FMT, bool WR16>
+__global__ void __launch_bounds__(BB) k_bicg_s(const float4* __restrict__ r, const float4* __restrict__ v,
+                                               float4* __restrict__ s, uint2* __restrict__ s16, float* __restrict__ s16n,
+                                               i64 sv, const double* __restrict__ scal) {
+  const cd2 alpha = cdiv({scal[SC_RHO], scal[SC_RHO + 1]}, {scal[SC_RV], scal[SC_RV + 1]});
+  const float ar = (float)-alpha.re, ai = (float)-alpha.im;
+  for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
+    float4 o[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      o[j] = caxpy4(ar, ai, v[j * sv + cb], r[j * sv + cb]);
+      s[j * sv + cb] = o[j];
+    }
+    if (WR16) store16<FMT>(o, s16, s16n, sv, cb);
+  }
+}
+
+// scal[SC_TS..] = <t, s>, scal[SC_TT] = <t, t>
+__global__ void __launch_bounds__(BB) k_bicg_ts(const float4* __restrict__ t, const float4* __restrict__ s, i64 sv,
+                                                double* red, unsigned int* ticket, double* scal) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
+    float re = 0.f, im = 0.f, tt = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      float4 a = t[j * sv + cb];
+      cdot4(a, s[j * sv + cb], re, im);
+      tt += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+    }
+    v[0] += re;
+    v[1] += im;
+    v[2] += tt;
+  }
+  block_sum<3, BB>(v);
+  finish_reduce<3, BB>(v, red, ticket, scal, SC_TS);  // SC_TS, SC_TS + 1, SC_TT = SC_TS + 2
+}
+
+// x += alpha p + omega s;  r = s - omega t;  scal[SC_RR..] = <r_hat, r>, scal[SC_RN] = ||r||^2
+__global__ void __launch_bounds__(BB) k_bicg_xr(float4* __restrict__ x, const float4* __restrict__ p,
+                                                const float4* __restrict__ s, const float4* __restrict__ t,
+                                                const float4* __restrict__ rh, float4* __restrict__ r, i64 sv,
+                                                double* red, unsigned int* ticket, double* scal) {
+  const cd2 alpha = cdiv({scal[SC_RHO], scal[SC_RHO + 1]}, {scal[SC_RV], scal[SC_RV + 1]});
+  const cd2 omega = {scal[SC_TS] / scal[SC_TT], scal[SC_TS + 1] / scal[SC_TT]};
+  const float a_r = (float)alpha.re, a_i = (float)alpha.im, w_r = (float)omega.re, w_i = (float)omega.im;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
+    float re = 0.f, im = 0.f, rn = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const i64 i = j * sv + cb;
+      float4 sj = s[i];
+      x[i] = caxpy4(w_r, w_i, sj, caxpy4(a_r, a_i, p[i], x[i]));
+      float4 rj = caxpy4(-w_r, -w_i, t[i], sj);
+      r[i] = rj;
+      cdot4(rh[i], rj, re, im);
+      rn += rj.x * rj.x + rj.y * rj.y + rj.z * rj.z + rj.w * rj.w;
+    }
+    v[0] += re;
+    v[1] += im;
+    v[2] += rn;
+  }
+  block_sum<3, BB>(v);
+  finish_reduce<3, BB>(v, red, ticket, scal, SC_RR);  // SC_RR, SC_RR + 1, SC_RN = SC_RR + 2
+}
+
+// p = r + beta (p - omega v), beta = (<r_hat,r> / rho)(alpha / omega); optional 16-bit p; the
+// last block then sets rho = <r_hat, r> (after every block has read the old rho).
+template <class FMT, bool WR16>
+__global__ void __launch_bounds__(BB) k_bicg_p(const float4* __restrict__ r, const float4* __restrict__ v,
+                                               float4* __restrict__ p, uint2* __restrict__ p16, float* __restrict__ p16n,
+                                               i64 sv, unsigned int* ticket, double* scal) {
+  const cd2 rho = {scal[SC_RHO], scal[SC_RHO + 1]};
+  const cd2 alpha = cdiv(rho, {scal[SC_RV], scal[SC_RV + 1]});
+  const cd2 omega = {scal[SC_TS] / scal[SC_TT], scal[SC_TS + 1] / scal[SC_TT]};
+  const cd2 beta = cmul2(cdiv({scal[SC_RR], scal[SC_RR + 1]}, rho), cdiv(alpha, omega));
+  const float b_r = (float)beta.re, b_i = (float)beta.im, w_r = (float)omega.re, w_i = (float)omega.im;
+  for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
+    float4 o[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const i64 i = j * sv + cb;
+      float4 q = caxpy4(-w_r, -w_i, v[i], p[i]);  // p - omega v
+      o[j] = caxpy4(b_r, b_i, q, r[i]);
+      p[i] = o[j];
+    }
+    if (WR16) store16<FMT>(o, p16, p16n, sv, cb);
+  }
+  __shared__ bool is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (is_last) {
+      scal[SC_RHO] = scal[SC_RR];
+      scal[SC_RHO + 1] = scal[SC_RR + 1];
+      *ticket = 0u;
+    }
+  }
+}
+
+// p = r (restart), optional 16-bit copy
+template <class FMT, bool WR16>
+__global__ void __launch_bounds__(BB) k_copy16(const float4* __restrict__ r, float4* __restrict__ p,
+                                               uint2* __restrict__ p16, float* __restrict__ p16n, i64 sv) {
+  for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
+    float4 o[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      o[j] = r[j * sv + cb];
+      p[j * sv + cb] = o[j];
+    }
+    if (WR16) store16<FMT>(o, p16, p16n, sv, cb);
+  }
+}
+
+#define RARGS lat->red, lat->ticket, lat->scal
+
+qxd_status bicg_cdot(qxd_lattice* lat, const float4* a, const float4* b, int slot) {
+  k_cdot_32<<<bgrid(lat), BB, 0, lat->stream>>>(a, b, lat->sv, RARGS, slot);
+  QXD_CHECK_LAUNCH(lat, "k_cdot_32");
+  return QXD_OK;
+}
+
+qxd_status bicg_s(qxd_lattice* lat, const float4* r, const float4* v, float4* s, uint2* s16, float* s16n, int bf16) {
+  if (!s16)
+    k_bicg_s<H16, false><<<bgrid(lat), BB, 0, lat->stream>>>(r, v, s, nullptr, nullptr, lat->sv, lat->scal);
+  else if (bf16)
+    k_bicg_s<B16, true><<<bgrid(lat), BB, 0, lat->stream>>>(r, v, s, s16, s16n, lat->sv, lat->scal);
+  else
+    k_bicg_s<H16, true><<<bgrid(lat), BB, 0, lat->stream>>>(r, v, s, s16, s16n, lat->sv, lat->scal);
+  QXD_CHECK_LAUNCH(lat, "k_bicg_s");
+  return QXD_OK;
+}
+
+qxd_status bicg_ts(qxd_lattice* lat, const float4* t, const float4* s) {
+  k_bicg_ts<<<bgrid(lat), BB, 0, lat->stream>>>(t, s, lat->sv, RARGS);
+  QXD_CHECK_LAUNCH(lat, "k_bicg_ts");
+  return QXD_OK;
+}
+
+qxd_status bicg_xr(qxd_lattice* lat, float4* x, const float4* p, const float4* s, const float4* t, const float4* rh,
+                   float4* r) {
+  k_bicg_xr<<<bgrid(lat), BB, 0, lat->stream>>>(x, p, s, t, rh, r, lat->sv, RARGS);
+  QXD_CHECK_LAUNCH(lat, "k_bicg_xr");
+  return QXD_OK;
+}
+
+qxd_status bicg_p(qxd_lattice* lat, const float4* r, const float4* v, float4* p, uint2* p16, float* p16n, int bf16) {
+  if (!p16)
+    k_bicg_p<H16, false><<<bgrid(lat), BB, 0, lat->stream>>>(r, v, p, nullptr, nullptr, lat->sv, lat->ticket, lat->scal);
+  else if (bf16)
+    k_bicg_p<B16, true><<<bgrid(lat), BB, 0, lat->stream>>>(r, v, p, p16, p16n, lat->sv, lat->ticket, lat->scal);
+  else
+    k_bicg_p<H16, true><<<bgrid(lat), BB, 0, lat->stream>>>(r, v, p, p16, p16n, lat->sv, lat->ticket, lat->scal);
+  QXD_CHECK_LAUNCH(lat, "k_bicg_p");
+  return QXD_OK;
+}
+
+qxd_status bicg_copy(qxd_lattice* lat, const float4* r, float4* p, uint2* p16, float* p16n, int bf16) {
+  if (!p16)
+    k_copy16<H16, false><<<bgrid(lat), BB, 0, lat->stream>>>(r, p, nullptr, nullptr, lat->sv);
+  else if (bf16)
+    k_copy16<B16, true><<<bgrid(lat), BB, 0, lat->stream>>>(r, p, p16, p16n, lat->sv);
+  else
+    k_copy16<H16, true><<<bgrid(lat), BB, 0, lat->stream>>>(r, p, p16, p16n, lat->sv);
+  QXD_CHECK_LAUNCH(lat, "k_copy16");
+  return QXD_OK;
+}
+
+}  // namespace qxd

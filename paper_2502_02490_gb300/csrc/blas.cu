@@ -1,114 +1,86 @@
 // Fused BLAS-1 and FP64 global reductions.
 //
-// Reductions are deterministic: each block reduces a fixed grid-stride slice with warp shuffles,
-// writes one partial per block into the lattice's partial buffer, and the last block to finish
-// (ticket counter) sums the partials in block order and writes the result to a device scalar
-// slot.  Accumulation is FP64 whatever the vector precision (the method keeps global inner
-// products and norms in FP64).  Solver scalars (alpha, beta) are read from device slots, so a
-// solver iteration needs no host round trip.
-#include "qxd_internal.cuh"
+// Reductions are deterministic (reduce.cuh): fixed grid, per-block partials, the last block
+// sums them in block order into a device scalar slot.  Accumulation is FP64 whatever the
+// vector precision (global inner products and norms stay FP64).  Solver scalars (alpha, beta)
+// are read from device slots, so a solver iteration needs no host round trip.  Each thread
+// keeps UNROLL independent loads in flight.  For FP32 vectors the squares of one site (or of
+// one unrolled group of 16 values) are summed in FP32 and all further accumulation is FP64:
+// FP64 arithmetic on GB300 runs at 1/64 of the FP32 rate, so an FP64 operation per element would
+// make these bandwidth-bound kernels ALU-bound.  The CG updates work site by site so that they can
+// also write the 16-bit copy (with its per-site scale) that the next 16-bit hop reads.
+#include "reduce.cuh"
 
 namespace qxd {
 
-static const int RB_THREADS = 256;
+static const int RB = 256;   // threads per block
+static const int UNROLL = 4;
 
 static int red_grid(qxd_lattice* lat, i64 n) {
-  i64 b = (n + RB_THREADS - 1) / RB_THREADS;
+  i64 b = (n + (i64)RB * UNROLL - 1) / ((i64)RB * UNROLL);
   if (b > lat->red_blocks) b = lat->red_blocks;
   return (int)(b < 1 ? 1 : b);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
+static int site_grid(qxd_lattice* lat, i64 nsites) {
+  i64 b = (nsites + RB - 1) / RB;
+  if (b > lat->red_blocks) b = lat->red_blocks;
+  return (int)(b < 1 ? 1 : b);
 }
 
-// Block-reduce NV values; thread 0 of the block returns them in v.
-template <int NV>
-__device__ __forceinline__ void block_sum(double v[NV]) {
-  __shared__ double sh[NV][RB_THREADS / 32];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__global__ void __launch_bounds__(RB) k_norm2_64(const double2* __restrict__ a, i64 n, double* red,
+                                                 unsigned int* ticket, double* scal, int slot) {
+  double v[1] = {0.0};
+  const i64 stride = (i64)gridDim.x * RB * UNROLL;
+  for (i64 i0 = (i64)blockIdx.x * RB * UNROLL + threadIdx.x; i0 < n; i0 += stride) {
+    double2 x[UNROLL];
 #pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    v[j] = warp_sum(v[j]);
-    if (lane == 0) sh[j][w] = v[j];
+    for (int u = 0; u < UNROLL; ++u) x[u] = (i0 + u * RB < n) ? a[i0 + u * RB] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) v[0] += x[u].x * x[u].x + x[u].y * x[u].y;
   }
-  __syncthreads();
-  if (w == 0) {
+  block_sum<1, RB>(v);
+  finish_reduce<1, RB>(v, red, ticket, scal, slot);
+}
+
+__global__ void __launch_bounds__(RB) k_norm2_32(const float4* __restrict__ a, i64 n4, double* red,
+                                                 unsigned int* ticket, double* scal, int slot) {
+  double v[1] = {0.0};
+  const i64 stride = (i64)gridDim.x * RB * UNROLL;
+  for (i64 i0 = (i64)blockIdx.x * RB * UNROLL + threadIdx.x; i0 < n4; i0 += stride) {
+    float4 x[UNROLL];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      double x = lane < (int)(blockDim.x >> 5) ? sh[j][lane] : 0.0;
-      v[j] = warp_sum(x);
+    for (int u = 0; u < UNROLL; ++u) x[u] = (i0 + u * RB < n4) ? a[i0 + u * RB] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // the 16 squares of one unrolled group are summed in FP32, everything beyond in FP64
+    float g = 0.f;
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) g += (x[u].x * x[u].x + x[u].y * x[u].y) + (x[u].z * x[u].z + x[u].w * x[u].w);
+    v[0] += (double)g;
+  }
+  block_sum<1, RB>(v);
+  finish_reduce<1, RB>(v, red, ticket, scal, slot);
+}
+
+__global__ void __launch_bounds__(RB) k_dot_64(const double2* __restrict__ a, const double2* __restrict__ b, i64 n,
+                                               double* red, unsigned int* ticket, double* scal, int slot) {
+  double v[2] = {0.0, 0.0};
+  const i64 stride = (i64)gridDim.x * RB * UNROLL;
+  for (i64 i0 = (i64)blockIdx.x * RB * UNROLL + threadIdx.x; i0 < n; i0 += stride) {
+    double2 x[UNROLL], y[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      bool ok = i0 + u * RB < n;
+      x[u] = ok ? a[i0 + u * RB] : make_double2(0.0, 0.0);
+      y[u] = ok ? b[i0 + u * RB] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      v[0] += x[u].x * y[u].x + x[u].y * y[u].y;  // conj(x) y
+      v[1] += x[u].x * y[u].y - x[u].y * y[u].x;
     }
   }
-  __syncthreads();
-}
-
-// Store the block partials and let the last block finish the sum into scal[slot + j].
-// Also runs `last_hook` in the last block after the sums are written.
-template <int NV>
-__device__ __forceinline__ bool finish_reduce(double v[NV], double* red, unsigned int* ticket, double* scal,
-                                              int slot) {
-  __shared__ bool is_last;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) red[(i64)j * gridDim.x + blockIdx.x] = v[j];
-    __threadfence();
-    unsigned int t = atomicAdd(ticket, 1u);
-    is_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!is_last) return false;
-  __threadfence();
-  double s[NV];
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    s[j] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s[j] += __ldcg(red + (i64)j * gridDim.x + b);
-  }
-  block_sum<NV>(s);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) scal[slot + j] = s[j];
-    *ticket = 0u;
-  }
-  return true;
-}
-
-__global__ void __launch_bounds__(RB_THREADS) k_norm2_64(const double2* __restrict__ a, i64 n, double* red,
-                                                         unsigned int* ticket, double* scal, int slot) {
-  double v[1] = {0.0};
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-    double2 x = a[i];
-    v[0] += x.x * x.x + x.y * x.y;
-  }
-  block_sum<1>(v);
-  finish_reduce<1>(v, red, ticket, scal, slot);
-}
-
-__global__ void __launch_bounds__(RB_THREADS) k_norm2_32(const float4* __restrict__ a, i64 n4, double* red,
-                                                         unsigned int* ticket, double* scal, int slot) {
-  double v[1] = {0.0};
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n4; i += (i64)gridDim.x * blockDim.x) {
-    float4 x = a[i];
-    v[0] += (double)x.x * x.x + (double)x.y * x.y + (double)x.z * x.z + (double)x.w * x.w;
-  }
-  block_sum<1>(v);
-  finish_reduce<1>(v, red, ticket, scal, slot);
-}
-
-__global__ void __launch_bounds__(RB_THREADS) k_dot_64(const double2* __restrict__ a, const double2* __restrict__ b,
-                                                       i64 n, double* red, unsigned int* ticket, double* scal,
-                                                       int slot) {
-  double v[2] = {0.0, 0.0};
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-    double2 x = a[i], y = b[i];
-    v[0] += x.x * y.x + x.y * y.y;  // conj(x) y
-    v[1] += x.x * y.y - x.y * y.x;
-  }
-  block_sum<2>(v);
-  finish_reduce<2>(v, red, ticket, scal, slot);
+  block_sum<2, RB>(v);
+  finish_reduce<2, RB>(v, red, ticket, scal, slot);
 }
 
 __global__ void k_axpy_64(double re, double im, const double2* __restrict__ x, double2* __restrict__ y, i64 n) {
@@ -117,13 +89,6 @@ __global__ void k_axpy_64(double re, double im, const double2* __restrict__ x, d
     b.x += re * a.x - im * a.y;
     b.y += re * a.y + im * a.x;
     y[i] = b;
-  }
-}
-
-__global__ void k_xpay_64(const double2* __restrict__ x, double a, double2* __restrict__ y, i64 n) {
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-    double2 u = x[i], v = y[i];
-    y[i] = make_double2(u.x + a * v.x, u.y + a * v.y);
   }
 }
 
@@ -145,11 +110,28 @@ __global__ void k_acc_f32_f64(i64 sv, i64 n4, const float4* __restrict__ x, doub
   }
 }
 
-// x += alpha p;  s -= alpha q;  scal[SC_SS] = ||s||^2, alpha = scal[SC_GAMMA] / scal[SC_QQ]
-__global__ void __launch_bounds__(RB_THREADS) k_cg_xs_64(double2* __restrict__ x, const double2* __restrict__ p,
-                                                         double2* __restrict__ s, const double2* __restrict__ q,
-                                                         i64 n, double* red, unsigned int* ticket, double* scal) {
-  double alpha = scal[SC_GAMMA] / scal[SC_QQ];
+// 16-bit copy of one site's six float4 components with its per-site scale.
+template <class FMT>
+__device__ __forceinline__ void store_n16(const float4 v[6], uint2* __restrict__ o, float* __restrict__ on, i64 sv,
+                                          i64 cb) {
+  float m = 0.f;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) m = fmaxf(m, fmaxf(fmaxf(fabsf(v[j].x), fabsf(v[j].y)), fmaxf(fabsf(v[j].z), fabsf(v[j].w))));
+  const float inv = m > 0.f ? 1.f / m : 0.f;
+  on[cb] = m;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    uint2 h;
+    h.x = FMT::pack(v[j].x * inv, v[j].y * inv);
+    h.y = FMT::pack(v[j].z * inv, v[j].w * inv);
+    o[j * sv + cb] = h;
+  }
+}
+
+__global__ void __launch_bounds__(RB) k_cg_xs_64(double2* __restrict__ x, const double2* __restrict__ p,
+                                                 double2* __restrict__ s, const double2* __restrict__ q, i64 n,
+                                                 double* red, unsigned int* ticket, double* scal) {
+  const double alpha = scal[SC_GAMMA] / scal[SC_QQ];
   double v[1] = {0.0};
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
     double2 xi = x[i], pi = p[i], si = s[i], qi = q[i];
@@ -161,31 +143,44 @@ __global__ void __launch_bounds__(RB_THREADS) k_cg_xs_64(double2* __restrict__ x
     s[i] = si;
     v[0] += si.x * si.x + si.y * si.y;
   }
-  block_sum<1>(v);
-  finish_reduce<1>(v, red, ticket, scal, SC_SS);
+  block_sum<1, RB>(v);
+  finish_reduce<1, RB>(v, red, ticket, scal, SC_SS);
 }
 
-__global__ void __launch_bounds__(RB_THREADS) k_cg_xs_32(float4* __restrict__ x, const float4* __restrict__ p,
-                                                         float4* __restrict__ s, const float4* __restrict__ q,
-                                                         i64 n4, double* red, unsigned int* ticket, double* scal) {
-  float alpha = (float)(scal[SC_GAMMA] / scal[SC_QQ]);
+// x += alpha p; s -= alpha q; scal[SC_SS] = ||s||^2; optionally s16 = 16-bit copy of s.
+// alpha = scal[SC_GAMMA] / scal[SC_QQ].  One thread per site (sv sites incl. zero padding).
+template <class FMT, bool WR16>
+__global__ void __launch_bounds__(RB) k_cg_xs_32(float4* __restrict__ x, const float4* __restrict__ p,
+                                                 float4* __restrict__ s, const float4* __restrict__ q, i64 sv,
+                                                 uint2* __restrict__ s16, float* __restrict__ s16n, double* red,
+                                                 unsigned int* ticket, double* scal) {
+  const float alpha = (float)(scal[SC_GAMMA] / scal[SC_QQ]);
   double v[1] = {0.0};
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n4; i += (i64)gridDim.x * blockDim.x) {
-    float4 xi = x[i], pi = p[i], si = s[i], qi = q[i];
-    xi.x += alpha * pi.x;
-    xi.y += alpha * pi.y;
-    xi.z += alpha * pi.z;
-    xi.w += alpha * pi.w;
-    si.x -= alpha * qi.x;
-    si.y -= alpha * qi.y;
-    si.z -= alpha * qi.z;
-    si.w -= alpha * qi.w;
-    x[i] = xi;
-    s[i] = si;
-    v[0] += (double)si.x * si.x + (double)si.y * si.y + (double)si.z * si.z + (double)si.w * si.w;
+  for (i64 cb = blockIdx.x * (i64)blockDim.x + threadIdx.x; cb < sv; cb += (i64)gridDim.x * blockDim.x) {
+    float4 sn[6];
+    float g = 0.f;  // the 24 squares of one site in FP32, the sum over sites in FP64
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const i64 i = j * sv + cb;
+      float4 xi = x[i], pi = p[i], si = s[i], qi = q[i];
+      xi.x += alpha * pi.x;
+      xi.y += alpha * pi.y;
+      xi.z += alpha * pi.z;
+      xi.w += alpha * pi.w;
+      si.x -= alpha * qi.x;
+      si.y -= alpha * qi.y;
+      si.z -= alpha * qi.z;
+      si.w -= alpha * qi.w;
+      x[i] = xi;
+      s[i] = si;
+      sn[j] = si;
+      g += (si.x * si.x + si.y * si.y) + (si.z * si.z + si.w * si.w);
+    }
+    v[0] += (double)g;
+    if (WR16) store_n16<FMT>(sn, s16, s16n, sv, cb);
   }
-  block_sum<1>(v);
-  finish_reduce<1>(v, red, ticket, scal, SC_SS);
+  block_sum<1, RB>(v);
+  finish_reduce<1, RB>(v, red, ticket, scal, SC_SS);
 }
 
 // p = r + beta p, beta = scal[SC_GAMMA_NEW] / scal[SC_GAMMA]; the last block then moves
@@ -204,9 +199,9 @@ __device__ __forceinline__ void move_gamma(unsigned int* ticket, double* scal) {
   }
 }
 
-__global__ void __launch_bounds__(RB_THREADS) k_cg_p_64(const double2* __restrict__ r, double2* __restrict__ p,
-                                                        i64 n, unsigned int* ticket, double* scal) {
-  double beta = scal[SC_GAMMA_NEW] / scal[SC_GAMMA];
+__global__ void __launch_bounds__(RB) k_cg_p_64(const double2* __restrict__ r, double2* __restrict__ p, i64 n,
+                                                unsigned int* ticket, double* scal) {
+  const double beta = scal[SC_GAMMA_NEW] / scal[SC_GAMMA];
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
     double2 ri = r[i], pi = p[i];
     p[i] = make_double2(ri.x + beta * pi.x, ri.y + beta * pi.y);
@@ -214,12 +209,22 @@ __global__ void __launch_bounds__(RB_THREADS) k_cg_p_64(const double2* __restric
   move_gamma(ticket, scal);
 }
 
-__global__ void __launch_bounds__(RB_THREADS) k_cg_p_32(const float4* __restrict__ r, float4* __restrict__ p,
-                                                        i64 n4, unsigned int* ticket, double* scal) {
-  float beta = (float)(scal[SC_GAMMA_NEW] / scal[SC_GAMMA]);
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n4; i += (i64)gridDim.x * blockDim.x) {
-    float4 ri = r[i], pi = p[i];
-    p[i] = make_float4(ri.x + beta * pi.x, ri.y + beta * pi.y, ri.z + beta * pi.z, ri.w + beta * pi.w);
+template <class FMT, bool WR16>
+__global__ void __launch_bounds__(RB) k_cg_p_32(const float4* __restrict__ r, float4* __restrict__ p, i64 sv,
+                                                uint2* __restrict__ p16, float* __restrict__ p16n,
+                                                unsigned int* ticket, double* scal) {
+  const float beta = (float)(scal[SC_GAMMA_NEW] / scal[SC_GAMMA]);
+  for (i64 cb = blockIdx.x * (i64)blockDim.x + threadIdx.x; cb < sv; cb += (i64)gridDim.x * blockDim.x) {
+    float4 pn[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const i64 i = j * sv + cb;
+      float4 ri = r[i], pi = p[i];
+      pi = make_float4(ri.x + beta * pi.x, ri.y + beta * pi.y, ri.z + beta * pi.z, ri.w + beta * pi.w);
+      p[i] = pi;
+      pn[j] = pi;
+    }
+    if (WR16) store_n16<FMT>(pn, p16, p16n, sv, cb);
   }
   move_gamma(ticket, scal);
 }
@@ -229,57 +234,67 @@ __global__ void k_set_scalar(double* scal, int slot, double v) { scal[slot] = v;
 #define RED_ARGS lat->red, lat->ticket, lat->scal
 
 qxd_status blas_norm2_64(qxd_lattice* lat, const double2* a, i64 n, int slot) {
-  k_norm2_64<<<red_grid(lat, n), RB_THREADS, 0, lat->stream>>>(a, n, RED_ARGS, slot);
+  k_norm2_64<<<red_grid(lat, n), RB, 0, lat->stream>>>(a, n, RED_ARGS, slot);
   QXD_CHECK_LAUNCH(lat, "k_norm2_64");
   return QXD_OK;
 }
 qxd_status blas_norm2_32(qxd_lattice* lat, const float4* a, i64 n4, int slot) {
-  k_norm2_32<<<red_grid(lat, n4), RB_THREADS, 0, lat->stream>>>(a, n4, RED_ARGS, slot);
+  k_norm2_32<<<red_grid(lat, n4), RB, 0, lat->stream>>>(a, n4, RED_ARGS, slot);
   QXD_CHECK_LAUNCH(lat, "k_norm2_32");
   return QXD_OK;
 }
 qxd_status blas_dot_64(qxd_lattice* lat, const double2* a, const double2* b, i64 n, int slot) {
-  k_dot_64<<<red_grid(lat, n), RB_THREADS, 0, lat->stream>>>(a, b, n, RED_ARGS, slot);
+  k_dot_64<<<red_grid(lat, n), RB, 0, lat->stream>>>(a, b, n, RED_ARGS, slot);
   QXD_CHECK_LAUNCH(lat, "k_dot_64");
   return QXD_OK;
 }
 qxd_status blas_axpy_64(qxd_lattice* lat, double re, double im, const double2* x, double2* y, i64 n) {
-  k_axpy_64<<<red_grid(lat, n), RB_THREADS, 0, lat->stream>>>(re, im, x, y, n);
+  k_axpy_64<<<site_grid(lat, n), RB, 0, lat->stream>>>(re, im, x, y, n);
   QXD_CHECK_LAUNCH(lat, "k_axpy_64");
   return QXD_OK;
 }
-qxd_status blas_xpay_64(qxd_lattice* lat, const double2* x, double a, double2* y, i64 n) {
-  k_xpay_64<<<red_grid(lat, n), RB_THREADS, 0, lat->stream>>>(x, a, y, n);
-  QXD_CHECK_LAUNCH(lat, "k_xpay_64");
-  return QXD_OK;
-}
 qxd_status blas_axpy_32(qxd_lattice* lat, float a, const float4* x, float4* y, i64 n4) {
-  k_axpy_32<<<red_grid(lat, n4), RB_THREADS, 0, lat->stream>>>(a, x, y, n4);
+  k_axpy_32<<<site_grid(lat, n4), RB, 0, lat->stream>>>(a, x, y, n4);
   QXD_CHECK_LAUNCH(lat, "k_axpy_32");
   return QXD_OK;
 }
 qxd_status blas_acc_f32_into_f64(qxd_lattice* lat, const float4* x, double2* y, i64 n4) {
-  k_acc_f32_f64<<<red_grid(lat, n4), RB_THREADS, 0, lat->stream>>>(lat->sv, n4, x, y);
+  k_acc_f32_f64<<<site_grid(lat, n4), RB, 0, lat->stream>>>(lat->sv, n4, x, y);
   QXD_CHECK_LAUNCH(lat, "k_acc_f32_f64");
   return QXD_OK;
 }
 qxd_status cg_update_xs_64(qxd_lattice* lat, double2* x, const double2* p, double2* s, const double2* q, i64 n) {
-  k_cg_xs_64<<<red_grid(lat, n), RB_THREADS, 0, lat->stream>>>(x, p, s, q, n, RED_ARGS);
+  k_cg_xs_64<<<site_grid(lat, n), RB, 0, lat->stream>>>(x, p, s, q, n, RED_ARGS);
   QXD_CHECK_LAUNCH(lat, "k_cg_xs_64");
   return QXD_OK;
 }
-qxd_status cg_update_xs_32(qxd_lattice* lat, float4* x, const float4* p, float4* s, const float4* q, i64 n4) {
-  k_cg_xs_32<<<red_grid(lat, n4), RB_THREADS, 0, lat->stream>>>(x, p, s, q, n4, RED_ARGS);
+qxd_status cg_update_xs_32(qxd_lattice* lat, float4* x, const float4* p, float4* s, const float4* q, uint2* s16,
+                           float* s16n, int bf16) {
+  const i64 sv = lat->sv;
+  const int g = site_grid(lat, sv);
+  if (!s16)
+    k_cg_xs_32<H16, false><<<g, RB, 0, lat->stream>>>(x, p, s, q, sv, nullptr, nullptr, RED_ARGS);
+  else if (bf16)
+    k_cg_xs_32<B16, true><<<g, RB, 0, lat->stream>>>(x, p, s, q, sv, s16, s16n, RED_ARGS);
+  else
+    k_cg_xs_32<H16, true><<<g, RB, 0, lat->stream>>>(x, p, s, q, sv, s16, s16n, RED_ARGS);
   QXD_CHECK_LAUNCH(lat, "k_cg_xs_32");
   return QXD_OK;
 }
 qxd_status cg_update_p_64(qxd_lattice* lat, const double2* r, double2* p, i64 n) {
-  k_cg_p_64<<<red_grid(lat, n), RB_THREADS, 0, lat->stream>>>(r, p, n, lat->ticket, lat->scal);
+  k_cg_p_64<<<site_grid(lat, n), RB, 0, lat->stream>>>(r, p, n, lat->ticket, lat->scal);
   QXD_CHECK_LAUNCH(lat, "k_cg_p_64");
   return QXD_OK;
 }
-qxd_status cg_update_p_32(qxd_lattice* lat, const float4* r, float4* p, i64 n4) {
-  k_cg_p_32<<<red_grid(lat, n4), RB_THREADS, 0, lat->stream>>>(r, p, n4, lat->ticket, lat->scal);
+qxd_status cg_update_p_32(qxd_lattice* lat, const float4* r, float4* p, uint2* p16, float* p16n, int bf16) {
+  const i64 sv = lat->sv;
+  const int g = site_grid(lat, sv);
+  if (!p16)
+    k_cg_p_32<H16, false><<<g, RB, 0, lat->stream>>>(r, p, sv, nullptr, nullptr, lat->ticket, lat->scal);
+  else if (bf16)
+    k_cg_p_32<B16, true><<<g, RB, 0, lat->stream>>>(r, p, sv, p16, p16n, lat->ticket, lat->scal);
+  else
+    k_cg_p_32<H16, true><<<g, RB, 0, lat->stream>>>(r, p, sv, p16, p16n, lat->ticket, lat->scal);
   QXD_CHECK_LAUNCH(lat, "k_cg_p_32");
   return QXD_OK;
 }

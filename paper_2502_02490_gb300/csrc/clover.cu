@@ -406,7 +406,7 @@ qxd_status clover_build(qxd_lattice* lat) {
                                                                    lat->q * lat->csw_qed, lat->C64);
   QXD_CHECK_LAUNCH(lat, "k_clover_build");
   void* w;
-  qxd_status st = ensure_work(lat, 22, sizeof(int), &w);
+  qxd_status st = ensure_work(lat, 30, sizeof(int), &w);  // slot 30: clover singular flag
   if (st) return st;
   int* bad = (int*)w;
   QXD_CUDA(lat, cudaMemsetAsync(bad, 0, sizeof(int), lat->stream));
@@ -490,6 +490,44 @@ qxd_status clover_apply64(qxd_lattice* lat, int par, int which, const double2* i
   k_clover_apply64<<<grid_cap(lat->Vh, 128), 128, 0, lat->stream>>>(lat->g, par, which ? lat->Ci64 : lat->C64,
                                                                     in, out);
   QXD_CHECK_LAUNCH(lat, "k_clover_apply64");
+  return QXD_OK;
+}
+
+// out = C in on parity par (site-local), FP32 single-parity fields [6][sv] float4.
+__global__ void k_clover_apply32(Geom g, int par, const float4* __restrict__ C, const float4* __restrict__ in,
+                                 float4* __restrict__ out) {
+  for (i64 cb = blockIdx.x * (i64)blockDim.x + threadIdx.x; cb < g.Vh; cb += (i64)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int blkid = 0; blkid < 2; ++blkid) {
+      float r[36];
+      const float4* b = C + (i64)((par * 2 + blkid) * 9) * g.sv + cb;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        float4 v = b[k * g.sv];
+        r[4 * k] = v.x;
+        r[4 * k + 1] = v.y;
+        r[4 * k + 2] = v.z;
+        r[4 * k + 3] = v.w;
+      }
+      cplx<float> x[6], y[6];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        float4 v = in[(3 * blkid + k) * g.sv + cb];
+        x[2 * k] = mk(v.x, v.y);
+        x[2 * k + 1] = mk(v.z, v.w);
+      }
+      herm6_apply(r, x, y);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        out[(3 * blkid + k) * g.sv + cb] = make_float4(y[2 * k].re, y[2 * k].im, y[2 * k + 1].re, y[2 * k + 1].im);
+    }
+  }
+}
+
+qxd_status clover_apply32(qxd_lattice* lat, int par, int which, const float4* in, float4* out) {
+  k_clover_apply32<<<grid_cap(lat->Vh, 128), 128, 0, lat->stream>>>(lat->g, par, which ? lat->Ci32 : lat->C32,
+                                                                    in, out);
+  QXD_CHECK_LAUNCH(lat, "k_clover_apply32");
   return QXD_OK;
 }
 

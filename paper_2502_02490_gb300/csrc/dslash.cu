@@ -75,6 +75,8 @@ __device__ __forceinline__ void link_mul(const cplx<R> u[9], const cplx<R> h[6],
 // kernel: decode the raw neighbour spinor and link fetched PF legs earlier, refill the slot with
 // the raw data of leg LEG + PF, then project, scale (per-site norm and time-boundary sign, applied
 // once to the 6-component half spinor), transport and accumulate.
+constexpr int HOP_BLOCK = 128;
+
 #ifndef QXD_HOP_PF16
 #define QXD_HOP_PF16 4  // prefetch depth of the 16-bit kernels (legs in flight); 4 measured best on GB300
 #endif
@@ -124,9 +126,11 @@ struct NoSpinor {
   __device__ __forceinline__ void store(i64, const cplx<T>*) const {}
 };
 
+// (Norms of the output are taken by a separate BLAS pass: a block reduction inside this
+// latency-bound kernel measured slower on GB300 than the extra bandwidth-bound pass.)
 template <typename R, class SIN, class SSAME, class SOUT, class LNK, class CLV, int EPI, bool G5, int PF>
-__global__ void __launch_bounds__(128) k_hop(Geom g, int par, SIN in, SSAME same, SOUT out, LNK lk, CLV cl,
-                                             R coef) {
+__global__ void __launch_bounds__(HOP_BLOCK) k_hop(Geom g, int par, SIN in, SSAME same, SOUT out, LNK lk, CLV cl,
+                                                   R coef) {
   const uint32_t cb = blockIdx.x * blockDim.x + threadIdx.x;
   if (cb >= (uint32_t)g.Vh) return;
   int x[4];
@@ -207,10 +211,10 @@ template <typename R, int PF, class SIN, class SSAME, class SOUT, class LNK, cla
 static qxd_status launch_hop(qxd_lattice* lat, int par, int epi, int g5, SIN in, SSAME same, SOUT out, LNK lk,
                              CLV cl, R coef) {
   const Geom& g = lat->g;
-  dim3 grid(grid_for(g.Vh, 128)), block(128);
+  dim3 grid(grid_for(g.Vh, HOP_BLOCK)), block(HOP_BLOCK);
   cudaStream_t st = lat->stream;
-#define QXD_HOP_CASE(E, G)                                                                              \
-  if (epi == E && (g5 != 0) == G) {                                                                     \
+#define QXD_HOP_CASE(E, G)                                                                                  \
+  if (epi == E && (g5 != 0) == G) {                                                                         \
     k_hop<R, SIN, SSAME, SOUT, LNK, CLV, E, G, PF><<<grid, block, 0, st>>>(g, par, in, same, out, lk, cl, coef); \
   } else
   QXD_HOP_CASE(EPI_HOP, false)

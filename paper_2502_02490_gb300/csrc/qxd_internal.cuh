@@ -479,7 +479,11 @@ enum { KSTAT_F64 = 0, KSTAT_F32 = 1, KSTAT_F16N = 2, KSTAT_BF16N = 3, KSTAT_N = 
 
 // Device scalar slots used by the solvers and reductions.
 enum {
-  SC_GAMMA = 0, SC_GAMMA_NEW, SC_QQ, SC_SS, SC_TMP0, SC_TMP1, SC_TMP2, SC_TMP3, SC_N = 16
+  SC_GAMMA = 0, SC_GAMMA_NEW, SC_QQ, SC_SS, SC_TMP0, SC_TMP1, SC_TMP2, SC_TMP3,
+  // BiCGStab: complex pairs (re, im) at SC_RHO, SC_RV, SC_TS, SC_RR; reals SC_TT = SC_TS + 2,
+  // SC_RN = SC_RR + 2 (written together by 3-value reductions)
+  SC_RHO = 8, SC_RV = 10, SC_TS = 12, SC_TT = 14, SC_RR = 15, SC_RN = 17,
+  SC_N = 24
 };
 
 struct Field64 {  // FP64 full field: two parities of double2 [12][sv]
@@ -532,7 +536,7 @@ struct qxd_lattice {
   // staging buffer for host/device boundary arrays
   void* stage = nullptr;
   size_t stage_bytes = 0;
-  // work buffers (lazily allocated): slots 0..21 solver, 22 clover flag, 24..27 API staging fields
+  // work buffers (lazily allocated): slots 0..23 solver, 24..27 API staging fields, 30 clover flag
   void* work[32] = {nullptr};
   size_t work_bytes[32] = {0};
 
@@ -589,6 +593,7 @@ qxd_status clover_build(qxd_lattice* lat);
 qxd_status clover_export(qxd_lattice* lat, double* bnd);
 // out = C in on one parity (site-local); which = 0 clover, 1 inverse
 qxd_status clover_apply64(qxd_lattice* lat, int par, int which, const double2* in, double2* out);
+qxd_status clover_apply32(qxd_lattice* lat, int par, int which, const float4* in, float4* out);
 
 // ---- dslash.cu ----
 enum Epi { EPI_HOP = 0, EPI_DFULL = 1, EPI_INV = 2, EPI_DHAT2 = 3, EPI_XPAY = 4, EPI_INVXPAY = 5 };
@@ -621,15 +626,26 @@ qxd_status blas_norm2_32(qxd_lattice* lat, const float4* a, i64 n4, int slot);
 // CG (CGLS) fused updates; alpha = scal[SC_GAMMA] / scal[SC_QQ]
 //   x += alpha p; s -= alpha q; scal[SC_SS] = ||s||^2
 qxd_status cg_update_xs_64(qxd_lattice* lat, double2* x, const double2* p, double2* s, const double2* q, i64 n);
-qxd_status cg_update_xs_32(qxd_lattice* lat, float4* x, const float4* p, float4* s, const float4* q, i64 n4);
+// (one thread per site; s16/p16 non-null also writes the 16-bit copy with its per-site scale)
+qxd_status cg_update_xs_32(qxd_lattice* lat, float4* x, const float4* p, float4* s, const float4* q, uint2* s16,
+                           float* s16n, int bf16);
 //   p = r + (scal[SC_GAMMA_NEW] / scal[SC_GAMMA]) p; then scal[SC_GAMMA] = scal[SC_GAMMA_NEW]
 qxd_status cg_update_p_64(qxd_lattice* lat, const double2* r, double2* p, i64 n);
-qxd_status cg_update_p_32(qxd_lattice* lat, const float4* r, float4* p, i64 n4);
+qxd_status cg_update_p_32(qxd_lattice* lat, const float4* r, float4* p, uint2* p16, float* p16n, int bf16);
 qxd_status read_scalars(qxd_lattice* lat, int first, int count, double* out);
 qxd_status set_scalar(qxd_lattice* lat, int slot, double v);
 // y += x (FP32 x widened into FP64 y), n = complex entries of y
 qxd_status blas_acc_f32_into_f64(qxd_lattice* lat, const float4* x, double2* y, i64 n4);
 qxd_status blas_axpy_32(qxd_lattice* lat, float a, const float4* x, float4* y, i64 n4);
+
+// ---- bicgstab.cu (FP32 vectors, one thread per site; 16-bit copies written when non-null) ----
+qxd_status bicg_cdot(qxd_lattice* lat, const float4* a, const float4* b, int slot);  // <a, b>
+qxd_status bicg_s(qxd_lattice* lat, const float4* r, const float4* v, float4* s, uint2* s16, float* s16n, int bf16);
+qxd_status bicg_ts(qxd_lattice* lat, const float4* t, const float4* s);
+qxd_status bicg_xr(qxd_lattice* lat, float4* x, const float4* p, const float4* s, const float4* t, const float4* rh,
+                   float4* r);
+qxd_status bicg_p(qxd_lattice* lat, const float4* r, const float4* v, float4* p, uint2* p16, float* p16n, int bf16);
+qxd_status bicg_copy(qxd_lattice* lat, const float4* r, float4* p, uint2* p16, float* p16n, int bf16);
 
 // ---- profiling helpers (api.cu) ----
 void prof_begin(qxd_lattice* lat, int kind, double bytes);

@@ -44,6 +44,11 @@ enum {
   WS_TO16,
   WS_NRM16,     // 3 norm arrays
   WS_NRM16B,    // 2 norm arrays for full-field 16-bit applies
+  WS_R32,       // FP32 copy of the full outer residual
+  WS_TO32B,     // FP32 odd-half temporary of the outer correction
+  // slots 24..27 belong to the API; BiCGStab's extra vectors reuse the CG ones (RR32 = r_hat,
+  // Q32 = v, TO32 = t, S32 = s, X32 = x, P32 = p) plus this one:
+  WS_R32B = 28, // BiCGStab residual r
 };
 
 #define TRY(x)                      \
@@ -210,33 +215,35 @@ static qxd_status inner_mp(qxd_lattice* lat, int prec, const float4* bh, float4*
   float* s16n = nrm ? nrm + sv : nullptr;
   float* t16n = nrm ? nrm + 2 * sv : nullptr;
 
-  auto apply = [&](const float4* in32, const uint2* in16, const float* in16n, float4* out, int dag) -> qxd_status {
-    if (low) return dhat16(lat, bf, in16, in16n, out, t16, t16n, dag);
-    return dhat32(lat, in32, out, t, dag);
+  // out = Dhat in (dag: Dhat^+), then ||out||^2 into the device scalar `slot`
+  auto apply = [&](const float4* in32, const uint2* in16, const float* in16n, float4* out, int dag,
+                   int slot) -> qxd_status {
+    if (low)
+      TRY(dhat16(lat, bf, in16, in16n, out, t16, t16n, dag));
+    else
+      TRY(dhat32(lat, in32, out, t, dag));
+    return blas_norm2_32(lat, out, n4, slot);
   };
 
   // s = bh - Dhat y (y is zero on entry, so s = bh); rr = Dhat^+ s; p = rr
   TRY(blas_zero(lat, x, hb));
   TRY(blas_copy(lat, s, bh, hb));
   if (low) TRY(f32_to_n16(lat, s, s16, s16n, bf));
-  TRY(apply(s, s16, s16n, rr, 1));
+  TRY(apply(s, s16, s16n, rr, 1, SC_GAMMA));
   TRY(blas_copy(lat, p, rr, hb));
   if (low) TRY(f32_to_n16(lat, p, p16, p16n, bf));
-  TRY(blas_norm2_32(lat, rr, n4, SC_GAMMA));
   TRY(blas_norm2_32(lat, s, n4, SC_SS));
   double ss;
   TRY(read_scalars(lat, SC_SS, 1, &ss));
   double rmax = std::sqrt(ss);
   int it = 0, rel = 0;
   while (std::sqrt(ss) > target && it < maxiter) {
-    TRY(apply(p, p16, p16n, q, 0));
-    TRY(blas_norm2_32(lat, q, n4, SC_QQ));
-    TRY(cg_update_xs_32(lat, x, p, s, q, n4));
-    if (low) TRY(f32_to_n16(lat, s, s16, s16n, bf));
-    TRY(apply(s, s16, s16n, rr, 1));
-    TRY(blas_norm2_32(lat, rr, n4, SC_GAMMA_NEW));
-    TRY(cg_update_p_32(lat, rr, p, n4));
-    if (low) TRY(f32_to_n16(lat, p, p16, p16n, bf));
+    // q = Dhat p, ||q||^2; x += alpha p, s -= alpha q (+ 16-bit s); rr = Dhat^+ s, ||rr||^2;
+    // p = rr + beta p (+ 16-bit p)
+    TRY(apply(p, p16, p16n, q, 0, SC_QQ));
+    TRY(cg_update_xs_32(lat, x, p, s, q, low ? s16 : nullptr, s16n, bf));
+    TRY(apply(s, s16, s16n, rr, 1, SC_GAMMA_NEW));
+    TRY(cg_update_p_32(lat, rr, p, low ? p16 : nullptr, p16n, bf));
     ++it;
     if (it % check_every == 0) {
       TRY(read_scalars(lat, SC_SS, 1, &ss));
@@ -257,13 +264,96 @@ static qxd_status inner_mp(qxd_lattice* lat, int prec, const float4* bh, float4*
         if (std::sqrt(ss) > target) {
           // keep p; refresh rr and gamma from the new residual
           if (low) TRY(f32_to_n16(lat, s, s16, s16n, bf));
-          TRY(apply(s, s16, s16n, rr, 1));
-          TRY(blas_norm2_32(lat, rr, n4, SC_GAMMA));
+          TRY(apply(s, s16, s16n, rr, 1, SC_GAMMA));
         }
       }
     }
   }
   // fold the rest
+  TRY(blas_axpy_32(lat, 1.0f, x, y, n4));
+  *iters = it;
+  *nrel = rel;
+  return QXD_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Inner mixed-precision BiCGStab on Dhat: FP32 vectors, Dhat in `prec`, FP32 reliable updates
+// (each one recomputes r = bh - Dhat32 y and restarts with r_hat = p = r).
+// ------------------------------------------------------------------------------------------
+static qxd_status inner_bicg(qxd_lattice* lat, int prec, const float4* bh, float4* y, double target, double delta,
+                             int maxiter, int check_every, int* iters, int* nrel) {
+  const i64 sv = lat->sv, n4 = 6 * sv;
+  const size_t hb = sizeof(float4) * n4;
+  float4 *x, *r, *rh, *p, *v, *s, *t, *tmp;
+  TRY(get(lat, WS_X32, hb, &x));
+  TRY(get(lat, WS_R32B, hb, &r));
+  TRY(get(lat, WS_RR32, hb, &rh));
+  TRY(get(lat, WS_P32, hb, &p));
+  TRY(get(lat, WS_Q32, hb, &v));
+  TRY(get(lat, WS_S32, hb, &s));
+  TRY(get(lat, WS_TO32, hb, &t));
+  TRY(get(lat, WS_BH32 + 0, sizeof(float4) * 12 * sv, &tmp));  // only its odd half is used below
+  float4* tmp_o = tmp + 6 * sv;
+  const bool low = prec == QXD_F16N || prec == QXD_BF16N;
+  const int bf = prec == QXD_BF16N;
+  uint2 *p16 = nullptr, *s16 = nullptr, *t16 = nullptr;
+  float* nrm = nullptr;
+  if (low) {
+    TRY(get(lat, WS_P16, sizeof(uint2) * n4, &p16));
+    TRY(get(lat, WS_S16, sizeof(uint2) * n4, &s16));
+    TRY(get(lat, WS_TO16, sizeof(uint2) * n4, &t16));
+    TRY(get(lat, WS_NRM16, sizeof(float) * 3 * sv, &nrm));
+  }
+  float* p16n = nrm;
+  float* s16n = nrm ? nrm + sv : nullptr;
+  float* t16n = nrm ? nrm + 2 * sv : nullptr;
+  auto apply = [&](const float4* in32, const uint2* in16, const float* in16n, float4* out) -> qxd_status {
+    if (low) return dhat16(lat, bf, in16, in16n, out, t16, t16n, 0);
+    return dhat32(lat, in32, out, tmp_o, 0);
+  };
+  // restart from the current residual r: r_hat = p = r, rho = <r, r>
+  auto restart = [&]() -> qxd_status {
+    TRY(blas_copy(lat, rh, r, hb));
+    TRY(bicg_copy(lat, r, p, low ? p16 : nullptr, p16n, bf));
+    TRY(bicg_cdot(lat, rh, r, SC_RHO));
+    return QXD_OK;
+  };
+  TRY(blas_zero(lat, x, hb));
+  TRY(blas_copy(lat, r, bh, hb));
+  TRY(restart());
+  TRY(blas_norm2_32(lat, r, n4, SC_RN));
+  double rn2;
+  TRY(read_scalars(lat, SC_RN, 1, &rn2));
+  double rmax = std::sqrt(rn2);
+  int it = 0, rel = 0;
+  while (std::sqrt(rn2) > target && it < maxiter) {
+    TRY(apply(p, p16, p16n, v));                                  // v = Dhat p
+    TRY(bicg_cdot(lat, rh, v, SC_RV));                            // <r_hat, v>
+    TRY(bicg_s(lat, r, v, s, low ? s16 : nullptr, s16n, bf));     // s = r - alpha v
+    TRY(apply(s, s16, s16n, t));                                  // t = Dhat s
+    TRY(bicg_ts(lat, t, s));                                      // <t, s>, <t, t>
+    TRY(bicg_xr(lat, x, p, s, t, rh, r));                         // x, r, <r_hat, r>, ||r||^2
+    TRY(bicg_p(lat, r, v, p, low ? p16 : nullptr, p16n, bf));     // p, rho
+    ++it;
+    if (it % check_every == 0) {
+      TRY(read_scalars(lat, SC_RN, 1, &rn2));
+      if (!std::isfinite(rn2)) return fail(lat, QXD_ENOCONV, "non-finite residual in the inner BiCGStab");
+      double rn = std::sqrt(rn2);
+      if (rn > rmax) rmax = rn;
+      if (rn < delta * rmax || rn <= target) {
+        TRY(blas_axpy_32(lat, 1.0f, x, y, n4));
+        TRY(blas_zero(lat, x, hb));
+        TRY(dhat32(lat, y, v, tmp_o, 0));
+        TRY(blas_copy(lat, r, bh, hb));
+        TRY(blas_axpy_32(lat, -1.0f, v, r, n4));
+        TRY(blas_norm2_32(lat, r, n4, SC_RN));
+        TRY(read_scalars(lat, SC_RN, 1, &rn2));
+        rmax = std::sqrt(rn2);
+        ++rel;
+        if (std::sqrt(rn2) > target) TRY(restart());
+      }
+    }
+  }
   TRY(blas_axpy_32(lat, 1.0f, x, y, n4));
   *iters = it;
   *nrel = rel;
@@ -280,11 +370,13 @@ qxd_status solve(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve
   TRY(get(lat, WS_BH64, hb, &bh));
   TRY(get(lat, WS_XE64, hb, &xe));
   TRY(get(lat, WS_TO64, hb, &to));
-  const bool mp = prm->solver == QXD_SOLVER_MP_CG_EO;
-  float4 *bh32 = nullptr, *y32 = nullptr;
+  const bool mp = prm->solver == QXD_SOLVER_MP_CG_EO || prm->solver == QXD_SOLVER_MP_BICGSTAB_EO;
+  float4 *bh32 = nullptr, *y32 = nullptr, *r32 = nullptr, *to32 = nullptr;
   if (mp) {
     TRY(get(lat, WS_BH32, sizeof(float4) * 12 * sv, &bh32));  // sized for full fields (apply_D_prec shares it)
     TRY(get(lat, WS_Y32, sizeof(float4) * 12 * sv, &y32));
+    TRY(get(lat, WS_R32, sizeof(float4) * 12 * sv, &r32));
+    TRY(get(lat, WS_TO32B, sizeof(float4) * 6 * sv, &to32));
   }
   double bn2;
   TRY(blas_norm2_64(lat, b, nf, SC_TMP0));
@@ -318,29 +410,38 @@ qxd_status solve(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve
       break;
     }
     if (outer == max_outer || total >= prm->maxiter) break;
-    // Schur source bh = r_e + 1/2 H_eo A_oo^-1 r_o
-    TRY(clover_apply64(lat, 1, 1, r + nh, to));
-    TRY(hop64(lat, 0, EPI_XPAY, 0, to, r, bh, 0.5));
     int it = 0;
     const double target = 0.5 * prm->tol * bnorm;
     if (!mp) {
+      // Schur source bh = r_e + 1/2 H_eo A_oo^-1 r_o, CG, reconstruct x_o += A_oo^-1 (r_o + 1/2 H_oe xe)
+      TRY(clover_apply64(lat, 1, 1, r + nh, to));
+      TRY(hop64(lat, 0, EPI_XPAY, 0, to, r, bh, 0.5));
       TRY(cgls64(lat, bh, xe, target, prm->maxiter - total, prm->check_every > 0 ? prm->check_every : 1, &it));
+      TRY(hop64(lat, 1, EPI_INVXPAY, 0, xe, r + nh, to, 0.5));
+      TRY(blas_axpy_64(lat, 1.0, 0.0, xe, x, nh));
+      TRY(blas_axpy_64(lat, 1.0, 0.0, to, x + nh, nh));
     } else {
+      // the correction equation D e = r only needs the inner accuracy, so its Schur source and
+      // reconstruction run in FP32; x accumulates in FP64
       int nrel = 0;
-      TRY(f64_to_f32(lat, bh, bh32, 6 * sv));
+      TRY(f64_to_f32(lat, r, r32, 12 * sv));
+      TRY(clover_apply32(lat, 1, 1, r32 + 6 * sv, to32));
+      TRY(hop32(lat, 0, EPI_XPAY, 0, to32, r32, bh32, 0.5f));
       TRY(blas_zero(lat, y32, sizeof(float4) * 6 * sv));
       double inner_target = prm->inner_tol * std::sqrt(rn2);
       if (inner_target < target) inner_target = target;
-      TRY(inner_mp(lat, prm->inner_prec, bh32, y32, inner_target, prm->reliable_delta, prm->maxiter - total,
-                   prm->check_every > 0 ? prm->check_every : 1, &it, &nrel));
-      TRY(f32_to_f64(lat, y32, xe, 6 * sv));
+      if (prm->solver == QXD_SOLVER_MP_BICGSTAB_EO)
+        TRY(inner_bicg(lat, prm->inner_prec, bh32, y32, inner_target, prm->reliable_delta, prm->maxiter - total,
+                       prm->check_every > 0 ? prm->check_every : 1, &it, &nrel));
+      else
+        TRY(inner_mp(lat, prm->inner_prec, bh32, y32, inner_target, prm->reliable_delta, prm->maxiter - total,
+                     prm->check_every > 0 ? prm->check_every : 1, &it, &nrel));
+      TRY(hop32(lat, 1, EPI_INVXPAY, 0, y32, r32 + 6 * sv, to32, 0.5f));
+      TRY(blas_acc_f32_into_f64(lat, y32, x, 6 * sv));
+      TRY(blas_acc_f32_into_f64(lat, to32, x + nh, 6 * sv));
       nrel_total += nrel;
     }
     total += it;
-    // reconstruct: x_e += xe;  x_o += A_oo^-1 (r_o + 1/2 H_oe xe)
-    TRY(hop64(lat, 1, EPI_INVXPAY, 0, xe, r + nh, to, 0.5));
-    TRY(blas_axpy_64(lat, 1.0, 0.0, xe, x, nh));
-    TRY(blas_axpy_64(lat, 1.0, 0.0, to, x + nh, nh));
   }
   QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
   if (info) {

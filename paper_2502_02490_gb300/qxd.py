@@ -24,7 +24,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESINGULAR", "ENOCONV", "ESTA
 BC_PERIODIC, BC_ANTIPERIODIC = 0, 1
 ORDER_LEXI, ORDER_IPT = 0, 1
 F64, F32, F16N, BF16N = 0, 1, 2, 3
-SOLVER_CG_EO, SOLVER_MP_CG_EO = 0, 1
+SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO = 0, 1, 2
 PARAMS_VERSION = 1
 PREC = {"f64": F64, "f32": F32, "f16n": F16N, "bf16n": BF16N}
 

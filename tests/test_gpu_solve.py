@@ -29,7 +29,7 @@ def run_solve(qxd, c, eta, **kw):
     return st, info, c.from_boundary(as_c128(x, eta.shape))
 
 
-@pytest.mark.parametrize("solver,prec", [(0, 1), (1, 1), (1, 2), (1, 3)])
+@pytest.mark.parametrize("solver,prec", [(0, 1), (1, 1), (1, 2), (1, 3), (2, 1), (2, 2), (2, 3)])
 @pytest.mark.parametrize("L,cstar,order", [((4, 4, 4, 4), False, 0), ((6, 4, 4, 6), False, 1),
                                            ((4, 2, 2, 4), True, 0)])
 def test_solve_reaches_tolerance(qxd, L, cstar, order, solver, prec):
