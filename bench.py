@@ -45,6 +45,28 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def recorded_traffic(kernel, lattice):
+    """DRAM bytes per launch from the committed ncu record, or None if the hop sources changed."""
+    import hashlib
+
+    rec = {}
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "roofline_traffic.txt")):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.strip().split("=", 1)
+                rec[k] = v
+    except OSError:
+        return None
+    h = hashlib.sha256()
+    for f in ("dslash.cu", "qxd_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2502_02490_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if (rec.get("kernel") != kernel or rec.get("source_sha256") != h.hexdigest()
+            or rec.get("lattice") != ",".join(str(v) for v in lattice)):
+        return None
+    return float(rec["bytes_per_launch"])
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -223,9 +245,12 @@ def run_ours(args, rank, world):
         "fp64_eocg": fp64,
         "speedup_vs_fp64_eocg": (fp64["seconds"] / statistics.mean(i["seconds"] for i in infos)) if fp64 else None,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "traffic": recorded_traffic(dom, w["L"]),
+                     "algorithmic_bytes_per_launch": b_l / n_l if n_l else None,
                      "launches": n_l, "avg_launch_us": ms_l / n_l * 1e3 if n_l else None},
         "kernels": {k: {"launches": v[0], "ms": v[1], "GB": v[2] / 1e9} for k, v in stats.items() if v[0]},
+        "dslash_kernel_GBps": hop_total / sum(v[1] for v in stats.values()) / 1e6 if world == 1 else None,
         "e2e": {"value": hop_total / e2e_s / 1e9 * (1 if world == 1 else 1), "unit": "GB/s",
                 "seconds_per_step": e2e_s / args.steps,
                 "h2d_bytes_per_step": int(U.nbytes + A.nbytes + eta.nbytes),

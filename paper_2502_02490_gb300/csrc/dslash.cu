@@ -76,6 +76,9 @@ __device__ __forceinline__ void link_mul(const cplx<R> u[9], const cplx<R> h[6],
 // the raw data of leg LEG + PF, then project, scale (per-site norm and time-boundary sign, applied
 // once to the 6-component half spinor), transport and accumulate.
 constexpr int HOP_BLOCK = 128;
+#ifndef QXD_HOP16_MINB
+#define QXD_HOP16_MINB 5  // min resident blocks per SM for the 16-bit kernels (swept 1,4..7 on GB300; 5 best)
+#endif
 
 #ifndef QXD_HOP_PF16
 #define QXD_HOP_PF16 4  // prefetch depth of the 16-bit kernels (legs in flight); 4 measured best on GB300
@@ -108,6 +111,28 @@ __device__ __forceinline__ void leg_step(const Geom& g, int par, uint32_t cb, co
   accumulate<R, MU, FWD>(acc, t);
 }
 
+// Epilogue prefetch: for the 16-bit kernels the clover block pair and the diagonal input spinor
+// are fetched two legs before the end, so their latency overlaps the last two hops.
+template <class T>
+struct is16 {
+  static constexpr bool value = false;
+};
+template <class F>
+struct is16<Clover16<F>> {
+  static constexpr bool value = true;
+};
+
+template <typename R, class CLV>
+__device__ __forceinline__ void clover_mul_raw(const CLV& cl, const typename CLV::Raw& raw, const cplx<R> v[12],
+                                               cplx<R> y[12]) {
+#pragma unroll
+  for (int blk = 0; blk < 2; ++blk) {
+    R r[36];
+    cl.decode(raw, blk, r);
+    herm6_apply<R>(r, v + 6 * blk, y + 6 * blk);
+  }
+}
+
 template <typename R, class CLV>
 __device__ __forceinline__ void clover_mul(const CLV& cl, int par, i64 cb, const cplx<R> v[12], cplx<R> y[12]) {
 #pragma unroll
@@ -129,7 +154,7 @@ struct NoSpinor {
 // (Norms of the output are taken by a separate BLAS pass: a block reduction inside this
 // latency-bound kernel measured slower on GB300 than the extra bandwidth-bound pass.)
 template <typename R, class SIN, class SSAME, class SOUT, class LNK, class CLV, int EPI, bool G5, int PF>
-__global__ void __launch_bounds__(HOP_BLOCK) k_hop(Geom g, int par, SIN in, SSAME same, SOUT out, LNK lk, CLV cl,
+__global__ void __launch_bounds__(HOP_BLOCK, is16<CLV>::value ? QXD_HOP16_MINB : 1) k_hop(Geom g, int par, SIN in, SSAME same, SOUT out, LNK lk, CLV cl,
                                                    R coef) {
   const uint32_t cb = blockIdx.x * blockDim.x + threadIdx.x;
   if (cb >= (uint32_t)g.Vh) return;
@@ -161,8 +186,34 @@ __global__ void __launch_bounds__(HOP_BLOCK) k_hop(Geom g, int par, SIN in, SSAM
   leg_step<3, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
   leg_step<4, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
   leg_step<5, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
+  constexpr bool EPF = is16<CLV>::value;  // epilogue prefetch (16-bit kernels)
+  constexpr bool USES_CLOVER = EPI != EPI_HOP && EPI != EPI_XPAY;
+  constexpr bool USES_SAME = EPI == EPI_DFULL || EPI == EPI_DHAT2 || EPI == EPI_INVXPAY || EPI == EPI_XPAY;
+  typename CLV::Raw craw;
+  typename SSAME::Raw sraw;
+  if constexpr (EPF) {
+    if constexpr (USES_CLOVER) craw = cl.fetch(par, cb);
+    if constexpr (USES_SAME) sraw = same.fetch(cb);
+  }
   leg_step<6, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
   leg_step<7, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
+
+  // the diagonal input spinor (prefetched raw data for the 16-bit kernels)
+  auto load_same = [&](cplx<R> v[12]) {
+    if constexpr (EPF) {
+      R n = same.decode(sraw, v);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = n * v[k];
+    } else {
+      same.load(cb, v);
+    }
+  };
+  auto cmul = [&](const cplx<R> v[12], cplx<R> y[12]) {
+    if constexpr (EPF)
+      clover_mul_raw<R, CLV>(cl, craw, v, y);
+    else
+      clover_mul<R, CLV>(cl, par, cb, v, y);
+  };
 
   cplx<R> o[12];
   if (EPI == EPI_HOP) {
@@ -170,8 +221,8 @@ __global__ void __launch_bounds__(HOP_BLOCK) k_hop(Geom g, int par, SIN in, SSAM
     for (int k = 0; k < 12; ++k) o[k] = coef * acc[k];
   } else if (EPI == EPI_DFULL || EPI == EPI_DHAT2) {
     cplx<R> v[12], y[12];
-    same.load(cb, v);
-    clover_mul<R, CLV>(cl, par, cb, v, y);
+    load_same(v);
+    cmul(v, y);
     R c = EPI == EPI_DFULL ? (R)-0.5 : coef;
     if (EPI == EPI_DHAT2 && G5) {
 #pragma unroll
@@ -182,16 +233,16 @@ __global__ void __launch_bounds__(HOP_BLOCK) k_hop(Geom g, int par, SIN in, SSAM
   } else if (EPI == EPI_INV) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = coef * acc[k];
-    clover_mul<R, CLV>(cl, par, cb, acc, o);
+    cmul(acc, o);
   } else if (EPI == EPI_INVXPAY) {
     cplx<R> v[12];
-    same.load(cb, v);
+    load_same(v);
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = v[k] + coef * acc[k];
-    clover_mul<R, CLV>(cl, par, cb, v, o);
+    cmul(v, o);
   } else {  // EPI_XPAY
     cplx<R> v[12];
-    same.load(cb, v);
+    load_same(v);
 #pragma unroll
     for (int k = 0; k < 12; ++k) o[k] = v[k] + coef * acc[k];
   }

@@ -406,6 +406,7 @@ struct Link16 {
 // ------------------------------------------------------------------------------------------
 struct CloverF64 {
   typedef double real;
+  struct Raw {};  // no epilogue prefetch for FP64
   const double2* p;
   i64 sv;
   __device__ __forceinline__ void load(int par, int blk, i64 cb, double r[36]) const {
@@ -420,6 +421,7 @@ struct CloverF64 {
 };
 struct CloverF32 {
   typedef float real;
+  struct Raw {};  // no epilogue prefetch for FP32
   const float4* p;
   i64 sv;
   __device__ __forceinline__ void load(int par, int blk, i64 cb, float r[36]) const {
@@ -437,9 +439,35 @@ struct CloverF32 {
 template <class FMT>
 struct Clover16 {
   typedef float real;
+  struct Raw {  // both chirality blocks of one site
+    uint2 v[2][9];
+    float n[2];
+  };
   const uint2* p;
   const float* nrm;  // [parity][block][sv]
   i64 sv;
+  __device__ __forceinline__ Raw fetch(int par, uint32_t cb) const {
+    Raw r;
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {
+      const uint2* b = p + (i64)((par * 2 + blk) * 9) * sv + cb;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) r.v[blk][k] = __ldg(b + k * sv);
+      r.n[blk] = __ldg(nrm + (i64)(par * 2 + blk) * sv + cb);
+    }
+    return r;
+  }
+  __device__ __forceinline__ void decode(const Raw& r, int blk, float o[36]) const {
+    const float n = r.n[blk];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      uint2 v = r.v[blk][k];
+      o[4 * k] = n * FMT::lo(v.x);
+      o[4 * k + 1] = n * FMT::hi(v.x);
+      o[4 * k + 2] = n * FMT::lo(v.y);
+      o[4 * k + 3] = n * FMT::hi(v.y);
+    }
+  }
   __device__ __forceinline__ void load(int par, int blk, i64 cb, float r[36]) const {
     const uint2* b = p + (i64)((par * 2 + blk) * 9) * sv + cb;
     float n = __ldg(nrm + (i64)(par * 2 + blk) * sv + cb);
