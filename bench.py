@@ -29,8 +29,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "clover-dslash GB/s vs HBM peak; time to 1e-10 residual vs plain FP64 eo-CG"
-WORKLOAD = dict(L=(64, 32, 32, 32), eps=0.4, q=2 / 3, m0=-0.2, csw=1.9, csw_qed=1.0, gauge_seed=1001,
-                source_seed=2001)
+WORKLOADS = {
+    # the workload the metric is quoted on (one GPU)
+    "c2": dict(L=(64, 32, 32, 32), cstar=0, eps=0.4, q=2 / 3, m0=-0.2, csw=1.9, csw_qed=1.0, gauge_seed=1001,
+               source_seed=2001,
+               name="32^3x64 mixed-precision clover solve to 1e-10 (eps=0.4, q=+2/3, m0=-0.2, c_sw=1.9, "
+                    "c_sw^QED=1.0, antiperiodic t)"),
+    # 48^3x96 with C* boundaries, doubled to 96x48x48x96 (extra measurement line, not the default)
+    "c5": dict(L=(96, 48, 48, 48), cstar=1, eps=0.35, q=-1 / 3, m0=-0.1, csw=1.9, csw_qed=1.0, gauge_seed=1004,
+               source_seed=2004,
+               name="48^3x96 C* (doubled 96x48x48x96) mixed-precision clover solve to 1e-10 (eps=0.35, q=-1/3, "
+                    "m0=-0.1, c_sw=1.9, c_sw^QED=1.0, antiperiodic t)"),
+}
+WORKLOAD = dict(WORKLOADS["c2"])
 KSTAT = {0: "hop_f64", 1: "hop_f32", 2: "hop_f16n", 3: "hop_bf16n"}
 PREC_NAMES = {"f32": 1, "f16n": 2, "bf16n": 3}
 SOLVERS = {"cg": 1, "bicgstab": 2}  # qxd_solver: MP_CG_EO, MP_BICGSTAB_EO
@@ -118,7 +129,8 @@ def make_inputs(rank):
 
     w = WORKLOAD
     U, A = synth.gauge_field(w["L"], w["gauge_seed"], w["eps"])
-    eta = synth.gaussian_spinor(w["L"], w["source_seed"] + 100 * rank)
+    dims = (w["L"][0], 2 * w["L"][1], w["L"][2], w["L"][3]) if w["cstar"] else w["L"]
+    eta = synth.gaussian_spinor(dims, w["source_seed"] + 100 * rank)
     return U, A, eta
 
 
@@ -132,14 +144,14 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     w = WORKLOAD
     U, A, eta = make_inputs(rank)
-    V = U.shape[0]
+    V = eta.shape[0]
     su3_h = torch.from_numpy(U.view(np.float64)).pin_memory()
     a_h = torch.from_numpy(A).pin_memory()
     b_h = torch.from_numpy(eta.view(np.float64)).pin_memory()
     x_h = torch.empty_like(b_h).pin_memory()
     su3_d, a_d, b_d = su3_h.to(dev), a_h.to(dev), b_h.to(dev)
     x_d = torch.empty_like(b_d)
-    lat = qxd.create_lattice(w["L"], qxd.BC_ANTIPERIODIC, 0, qxd.ORDER_LEXI, stream.cuda_stream)
+    lat = qxd.create_lattice(w["L"], qxd.BC_ANTIPERIODIC, w["cstar"], qxd.ORDER_LEXI, stream.cuda_stream)
     prec = PREC_NAMES[args.inner]
     params = qxd.default_params(solver=SOLVERS[args.solver], inner_prec=prec, tol=1e-10, inner_tol=args.inner_tol,
                                 reliable_delta=args.delta, check_every=args.check_every)
@@ -231,9 +243,8 @@ def run_ours(args, rank, world):
         "vs_baseline": None,
         "dtype": {"f16n": "f16+f32norm", "bf16n": "bf16+f32norm", "f32": "f32"}[args.inner] + "/f32/f64",
         "data": "synthetic (seeded SplitMix64 gauge field U=exp(i eps H) exp(i q eps theta), Gaussian source)",
-        "config": {"workload": "32^3x64 mixed-precision clover solve to 1e-10 (eps=0.4, q=+2/3, m0=-0.2, "
-                               "c_sw=1.9, c_sw^QED=1.0, antiperiodic t)",
-                   "lattice": list(w["L"]), "sites": V, "solver": f"mp-{args.solver}", "inner_prec": args.inner,
+        "config": {"workload": w["name"],
+                   "lattice": list(w["L"]), "cstar": w["cstar"], "sites": V, "solver": f"mp-{args.solver}", "inner_prec": args.inner,
                    "inner_tol": args.inner_tol,
                    "reliable_delta": args.delta, "l2": "inputs larger than L2 (links+clover > 1 GB)",
                    "parallelism": f"replicas{world}", "step": "load_gauge + build_clover + MP solve"},
@@ -275,7 +286,7 @@ def profile_run(args):
     a_d = torch.from_numpy(A).to(dev)
     b_d = torch.from_numpy(eta.view(np.float64)).to(dev)
     x_d = torch.empty_like(b_d)
-    lat = qxd.create_lattice(w["L"], qxd.BC_ANTIPERIODIC, 0, qxd.ORDER_LEXI, stream.cuda_stream)
+    lat = qxd.create_lattice(w["L"], qxd.BC_ANTIPERIODIC, w["cstar"], qxd.ORDER_LEXI, stream.cuda_stream)
     params = qxd.default_params(solver=SOLVERS[args.solver], inner_prec=PREC_NAMES[args.inner], tol=1e-10,
                                 inner_tol=args.inner_tol, reliable_delta=args.delta, check_every=args.check_every)
     qxd.load_gauge(lat, su3_d, a_d, w["q"])
@@ -339,7 +350,11 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="profiling aid for ncu: one untimed step, no JSON line (never a bench value)")
     ap.add_argument("--lattice", default=None, help="T,L1,L2,L3 override, for --profile-run captures only")
+    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS),
+                    help="c2: 32^3x64 (the metric's workload, default); c5: 48^3x96 C* doubled")
     args = ap.parse_args()
+    WORKLOAD.clear()
+    WORKLOAD.update(WORKLOADS[args.workload])
     if args.lattice:
         if not args.profile_run:
             ap.error("--lattice is only for --profile-run")
@@ -369,7 +384,7 @@ def main():
     __graft_entry__.build()
     out = run_ours(args, rank, world)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.workload == "c2":
             out["cpu_baseline"] = cpu_sample()
         print(json.dumps(out))
     if world > 1:

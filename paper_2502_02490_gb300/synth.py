@@ -90,25 +90,43 @@ def _expi_hermitian(H, eps):
     return np.einsum("nab,nb,ncb->nac", v, np.exp(1j * eps * w), v.conj())
 
 
-def gauge_field(L, seed, eps, chunk=1 << 18):
+def _gauge_chunk(s0, s1, seed, eps):
+    links = np.arange(4 * s0, 4 * s1, dtype=np.uint64)
+    pair = links[:, None] * np.uint64(_PER_LINK // 2) + np.arange(_PER_LINK // 2, dtype=np.uint64)[None, :]
+    a, b = normal_pairs(pair, seed)
+    z = np.stack([a, b], axis=-1).reshape(len(links), _PER_LINK)
+    H = np.einsum("nk,kab->nab", z[:, :8], _LAMBDA) * 0.5
+    return _expi_hermitian(H, eps).reshape(s1 - s0, 4, 3, 3), eps * z[:, 8].reshape(s1 - s0, 4)
+
+
+def gauge_field(L, seed, eps, chunk=1 << 18, workers=None):
     """SU(3) links and U(1) angles on the lattice L = (T, L1, L2, L3).
 
     Returns (U, A): U complex128 of shape (V, 4, 3, 3) with U[x, mu] = exp(i eps H_{x,mu}),
     A float64 of shape (V, 4) with A[x, mu] = eps * theta_{x,mu}.  Site x is the
-    lexicographic index.  Link (x, mu) uses normals (4x+mu)*10 + k, k = 0..9.
+    lexicographic index.  Link (x, mu) uses normals (4x+mu)*10 + k, k = 0..9, so the result does
+    not depend on the chunking; lattices of 2^21 sites or more are generated by a pool of
+    processes (spawn context) unless workers=1.
     """
+    import os
+
     V = volume(L)
     U = np.empty((V, 4, 3, 3), dtype=np.complex128)
     A = np.empty((V, 4), dtype=np.float64)
-    for s0 in range(0, V, chunk):
-        s1 = min(V, s0 + chunk)
-        links = np.arange(4 * s0, 4 * s1, dtype=np.uint64)
-        pair = links[:, None] * np.uint64(_PER_LINK // 2) + np.arange(_PER_LINK // 2, dtype=np.uint64)[None, :]
-        a, b = normal_pairs(pair, seed)
-        z = np.stack([a, b], axis=-1).reshape(len(links), _PER_LINK)
-        H = np.einsum("nk,kab->nab", z[:, :8], _LAMBDA) * 0.5
-        U[s0:s1] = _expi_hermitian(H, eps).reshape(s1 - s0, 4, 3, 3)
-        A[s0:s1] = eps * z[:, 8].reshape(s1 - s0, 4)
+    bounds = [(s0, min(V, s0 + chunk)) for s0 in range(0, V, chunk)]
+    if workers is None:
+        workers = min(16, os.cpu_count() or 1) if V >= (1 << 21) else 1
+    if workers > 1 and len(bounds) > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            futs = [ex.submit(_gauge_chunk, s0, s1, seed, eps) for s0, s1 in bounds]
+            for (s0, s1), f in zip(bounds, futs):
+                U[s0:s1], A[s0:s1] = f.result()
+    else:
+        for s0, s1 in bounds:
+            U[s0:s1], A[s0:s1] = _gauge_chunk(s0, s1, seed, eps)
     return U, A
 
 
