@@ -40,9 +40,14 @@ WORKLOADS = {
                source_seed=2004,
                name="48^3x96 C* (doubled 96x48x48x96) mixed-precision clover solve to 1e-10 (eps=0.35, q=-1/3, "
                     "m0=-0.1, c_sw=1.9, c_sw^QED=1.0, antiperiodic t)"),
+    # 12 spin-colour point sources on 24^3x48 through the multi-RHS solve (extra line)
+    "c3a": dict(L=(48, 24, 24, 24), cstar=0, eps=0.3, q=-1 / 3, m0=-0.1, csw=1.9, csw_qed=1.0, gauge_seed=1002,
+                source_seed=2002,
+                name="24^3x48 multi-RHS solve of the 12 spin-colour point sources to 1e-10 (FP32 inner, "
+                     "eps=0.3, q=-1/3, m0=-0.1, c_sw=1.9, c_sw^QED=1.0, antiperiodic t)"),
 }
 WORKLOAD = dict(WORKLOADS["c2"])
-KSTAT = {0: "hop_f64", 1: "hop_f32", 2: "hop_f16n", 3: "hop_bf16n"}
+KSTAT = {0: "hop_f64", 1: "hop_f32", 2: "hop_f16n", 3: "hop_bf16n", 4: "hop_f32_mrhs"}
 PREC_NAMES = {"f32": 1, "f16n": 2, "bf16n": 3}
 SOLVERS = {"cg": 1, "bicgstab": 2}  # qxd_solver: MP_CG_EO, MP_BICGSTAB_EO
 
@@ -272,6 +277,71 @@ def run_ours(args, rank, world):
     return out
 
 
+def run_mrhs(args):
+    """12 point sources solved together (multi-RHS kernel) vs one after another."""
+    import torch
+
+    from paper_2502_02490_gb300 import qxd, synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    w = WORKLOAD
+    U, A = synth.gauge_field(w["L"], w["gauge_seed"], w["eps"])
+    eta = np.stack([synth.point_source(w["L"], k // 3, k % 3) for k in range(12)])
+    b = torch.from_numpy(eta.view(np.float64)).to(dev)
+    x = torch.empty_like(b)
+    lat = qxd.create_lattice(w["L"], qxd.BC_ANTIPERIODIC, 0, qxd.ORDER_LEXI, stream.cuda_stream)
+    qxd.load_gauge(lat, torch.from_numpy(U.view(np.float64)).to(dev), torch.from_numpy(A).to(dev), w["q"])
+    qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
+    p = qxd.default_params(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=qxd.F32, tol=1e-10,
+                           reliable_delta=args.delta, check_every=args.check_every)
+    for _ in range(args.warmup):
+        qxd.solve_mrhs(lat, x, b, 12, params=p)
+    qxd.set_profiling(lat, 1)
+    n0 = qxd.launch_count(lat)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            st, infos = qxd.solve_mrhs(lat, x, b, 12, params=p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    launches = qxd.launch_count(lat) - n0
+    stats = {KSTAT[k]: qxd.kernel_stats(lat, k) for k in KSTAT}
+    qxd.set_profiling(lat, 0)
+    # the same 12 sources one after another (single-RHS MP BiCGStab, FP32 and 16-bit inner)
+    seq = {}
+    for name, prec in (("f32", qxd.F32), ("f16n", qxd.F16N)):
+        ps = qxd.default_params(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=prec, tol=1e-10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(12):
+            qxd.solve(lat, x[k], b[k], params=ps)
+        torch.cuda.synchronize()
+        seq[name] = time.perf_counter() - t0
+    qxd.destroy_lattice(lat)
+    n_l, ms_l, b_l = stats["hop_f32_mrhs"]
+    peak, kind = measured_peaks()
+    achieved = b_l / (ms_l / 1e3) / 1e9
+    hop_bytes = sum(v[2] for v in stats.values())
+    return {"metric": METRIC, "value": hop_bytes / (t * args.steps) / 1e9, "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": w["name"], "lattice": list(w["L"]), "nrhs": 12, "solver": "mp-bicgstab-mrhs"},
+            "time_to_solution_s": t, "solve": {"iters_inner": infos[0]["iters_inner"],
+                                               "iters_outer": infos[0]["iters_outer"],
+                                               "true_rel_res": max(i["true_rel_res"] for i in infos)},
+            "sequential_single_rhs_s": seq, "speedup_vs_sequential_f32": seq["f32"] / t,
+            "roofline": {"bound": "hbm", "kernel": "hop_f32_mrhs", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{kind} hbm_gbs", "traffic": None,
+                         "launches": n_l, "avg_launch_us": ms_l / n_l * 1e3 if n_l else None,
+                         "bytes_per_site_rhs": "96*(2 or 3) spinor + (8*72 links + 288 clover)/12"},
+            "kernels": {k: {"launches": v[0], "ms": v[1], "GB": v[2] / 1e9} for k, v in stats.items() if v[0]},
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+
+
 def profile_run(args):
     """One untimed pass of the step (for ncu launch lists and kernel captures)."""
     import torch
@@ -351,7 +421,8 @@ def main():
                     help="profiling aid for ncu: one untimed step, no JSON line (never a bench value)")
     ap.add_argument("--lattice", default=None, help="T,L1,L2,L3 override, for --profile-run captures only")
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS),
-                    help="c2: 32^3x64 (the metric's workload, default); c5: 48^3x96 C* doubled")
+                    help="c2: 32^3x64 (the metric's workload, default); c5: 48^3x96 C* doubled; "
+                         "c3a: 12 point sources on 24^3x48 (multi-RHS)")
     args = ap.parse_args()
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[args.workload])
@@ -382,6 +453,9 @@ def main():
     import __graft_entry__
 
     __graft_entry__.build()
+    if args.workload == "c3a":
+        print(json.dumps(run_mrhs(args)))
+        return
     out = run_ours(args, rank, world)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline and args.workload == "c2":

@@ -144,7 +144,8 @@ qxd_status qxd_get_clover(qxd_lattice *lat, double *out, int on_device);
 
 /* out = D in for nrhs right-hand sides: in, out are [nrhs][V][4][3][2] in the lattice's site
  * order.  prec selects the operator's precision (inputs are rounded to it, outputs widened
- * back to FP64).  QXD_ESTATE before build_clover; QXD_EINVAL for nrhs <= 0 or a null pointer. */
+ * back to FP64).  With prec F32 and nrhs > 1 the multi-RHS kernel applies D to up to 12
+ * right-hand sides per link and clover load.  QXD_ESTATE before build_clover; QXD_EINVAL for nrhs <= 0 or a null pointer. */
 qxd_status qxd_apply_D(qxd_lattice *lat, double *out, const double *in, int prec, int nrhs,
                        int on_device);
 
@@ -158,6 +159,15 @@ qxd_status qxd_apply_Dhat_eo(qxd_lattice *lat, double *out_e, const double *in_e
  * true residual and the wall time.  QXD_ENOCONV when the tolerance is not met. */
 qxd_status qxd_solve(qxd_lattice *lat, double *x, const double *b, const qxd_solve_params *params,
                      qxd_solve_info *info);
+
+/* Solve D x_r = b_r for nrhs right-hand sides in lock step (e.g. the 12 spin-colour point
+ * sources of a propagator): FP64 outer defect correction per right-hand side and one inner
+ * FP32 BiCGStab over all of them whose Dhat applications load each site's links and clover once
+ * for every right-hand side.  x, b: [nrhs][V][4][3][2]; info: nrhs entries (or NULL).
+ * params: solver MP_BICGSTAB_EO, inner_prec F32 (else QXD_EINVAL); the other fields as for
+ * qxd_solve.  QXD_ENOCONV if some right-hand side misses the tolerance. */
+qxd_status qxd_solve_mrhs(qxd_lattice *lat, double *x, const double *b, int nrhs,
+                          const qxd_solve_params *params, qxd_solve_info *info);
 
 /* Fill *p with the defaults: MP_CG_EO, tol 1e-10, maxiter 100000, inner F32, inner_tol 1e-5,
  * reliable_delta 0.1, max_outer 20, on_device 1, check_every 1. */
@@ -199,7 +209,8 @@ qxd_status qxd_vec_dot_noalloc(const double *a, const double *b, int64_t n, doub
 
 /* Kernel timing.  With profiling on, the library brackets each launch of its hop kernels with
  * CUDA events on the lattice stream; qxd_kernel_stats returns, for the kernel class `which`
- * (0 = FP64 hop, 1 = FP32 hop, 2 = FP16N hop, 3 = BF16N hop), the number of timed launches, their
+ * (0 = FP64 hop, 1 = FP32 hop, 2 = FP16N hop, 3 = BF16N hop, 4 = FP32 multi-RHS hop), the number of
+ * timed launches, their
  * summed device time in ms and the summed algorithmic bytes they moved.  Reading the stats
  * synchronises the stream.  qxd_launch_count is the number of kernels the library launched. */
 qxd_status qxd_set_profiling(qxd_lattice *lat, int on);

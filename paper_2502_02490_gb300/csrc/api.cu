@@ -33,7 +33,7 @@ qxd_status cuda_fail(qxd_lattice* lat, cudaError_t e, const char* where) {
 }
 
 qxd_status ensure_work(qxd_lattice* lat, int slot, size_t bytes, void** out) {
-  if (slot < 0 || slot >= 32) return fail(lat, QXD_EINVAL, "bad work slot");
+  if (slot < 0 || slot >= 40) return fail(lat, QXD_EINVAL, "bad work slot");
   if (lat->work_bytes[slot] < bytes) {
     if (lat->work[slot]) {
       QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
@@ -141,8 +141,12 @@ qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
                   lat->CB16, lat->CiB16, lat->CB16n, lat->CiB16n, lat->red,  lat->ticket, lat->scal};
   for (void* b : bufs)
     if (b) cudaFree(b);
-  for (int i = 0; i < 32; ++i)
+  for (int i = 0; i < 40; ++i)
     if (lat->work[i]) cudaFree(lat->work[i]);
+  void* mr[] = {lat->mr_red, lat->mr_ticket, lat->mr_scal};
+  for (void* b : mr)
+    if (b) cudaFree(b);
+  if (lat->mr_hscal) cudaFreeHost(lat->mr_hscal);
   if (lat->hscal) cudaFreeHost(lat->hscal);
   for (cudaEvent_t e : lat->ev_pool) cudaEventDestroy(e);
   delete lat;
@@ -297,6 +301,34 @@ qxd_status qxd_apply_D(qxd_lattice* lat, double* out, const double* in, int prec
     TRY(ensure_work(lat, AS_BND_IN, vb, &bi));
     TRY(ensure_work(lat, AS_BND_OUT, vb, &bo));
   }
+  if (prec == QXD_F32 && nrhs > 1) {
+    // multi-RHS FP32 path: one link/clover load per site serves every right-hand side
+    float4 *mi, *mo;
+    TRY(ensure_work(lat, 37, sizeof(float4) * 12 * sv * nrhs, (void**)&mi));
+    TRY(ensure_work(lat, 38, sizeof(float4) * 12 * sv * nrhs, (void**)&mo));
+    for (int r = 0; r < nrhs; ++r) {
+      const double* src = in + (i64)r * 24 * lat->V;
+      if (!on_device) {
+        QXD_CUDA(lat, cudaMemcpyAsync(bi, src, vb, cudaMemcpyHostToDevice, lat->stream));
+        src = (const double*)bi;
+      }
+      TRY(pack_spinor64(lat, (const double2*)src, fin, 0));
+      TRY(f64_to_f32(lat, fin, mi + (i64)r * 12 * sv, 12 * sv));
+    }
+    const i64 rs = 12 * sv;
+    TRY(hop32_mrhs(lat, 0, EPI_DFULL, 0, mi + 6 * sv, mi, mo, 0.f, nrhs, rs));
+    TRY(hop32_mrhs(lat, 1, EPI_DFULL, 0, mi, mi + 6 * sv, mo + 6 * sv, 0.f, nrhs, rs));
+    for (int r = 0; r < nrhs; ++r) {
+      double* dst = out + (i64)r * 24 * lat->V;
+      TRY(f32_to_f64(lat, mo + (i64)r * 12 * sv, fout, 12 * sv));
+      TRY(unpack_spinor64(lat, fout, on_device ? (double2*)dst : (double2*)bo, 0));
+      if (!on_device) {
+        QXD_CUDA(lat, cudaMemcpyAsync(dst, bo, vb, cudaMemcpyDeviceToHost, lat->stream));
+        QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+      }
+    }
+    return QXD_OK;
+  }
   for (int r = 0; r < nrhs; ++r) {
     const double* src = in + (i64)r * 24 * lat->V;
     double* dst = out + (i64)r * 24 * lat->V;
@@ -375,6 +407,48 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
   if (!p->on_device) {
     QXD_CUDA(lat, cudaMemcpyAsync(x, bo, vb, cudaMemcpyDeviceToHost, lat->stream));
     QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  }
+  return st;
+}
+
+qxd_status qxd_solve_mrhs(qxd_lattice* lat, double* x, const double* b, int nrhs, const qxd_solve_params* p,
+                          qxd_solve_info* info) {
+  CHECK_LAT(lat);
+  if (info && nrhs > 0) std::memset(info, 0, sizeof(*info) * nrhs);
+  if (!x || !b || !p) return fail(lat, QXD_EINVAL, "null argument");
+  if (nrhs <= 0) return fail(lat, QXD_EINVAL, "nrhs must be positive");
+  if (p->version != QXD_PARAMS_VERSION) return fail(lat, QXD_EINVAL, "qxd_solve_params version mismatch");
+  if (p->solver != QXD_SOLVER_MP_BICGSTAB_EO || p->inner_prec != QXD_F32)
+    return fail(lat, QXD_EINVAL, "multi-RHS solve: solver must be MP_BICGSTAB_EO with inner_prec F32");
+  if (!(p->tol > 0) || p->maxiter <= 0) return fail(lat, QXD_EINVAL, "tol must be > 0 and maxiter > 0");
+  if (!lat->have_clover) return fail(lat, QXD_ESTATE, "solve before build_clover");
+  const i64 sv = lat->sv;
+  const size_t vb = sizeof(double) * 24 * lat->V;
+  double2 *fb, *fx;
+  TRY(ensure_work(lat, 37, sizeof(double2) * 24 * sv * nrhs, (void**)&fb));
+  TRY(ensure_work(lat, 38, sizeof(double2) * 24 * sv * nrhs, (void**)&fx));
+  void *bi = nullptr, *bo = nullptr;
+  if (!p->on_device) {
+    TRY(ensure_work(lat, AS_BND_IN, vb, &bi));
+    TRY(ensure_work(lat, AS_BND_OUT, vb, &bo));
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    const double* src = b + (i64)r * 24 * lat->V;
+    if (!p->on_device) {
+      QXD_CUDA(lat, cudaMemcpyAsync(bi, src, vb, cudaMemcpyHostToDevice, lat->stream));
+      src = (const double*)bi;
+    }
+    TRY(pack_spinor64(lat, (const double2*)src, fb + (i64)r * 24 * sv, 0));
+  }
+  qxd_status st = solve_mrhs(lat, fx, fb, nrhs, p, info);
+  if (st != QXD_OK && st != QXD_ENOCONV) return st;
+  for (int r = 0; r < nrhs; ++r) {
+    double* dst = x + (i64)r * 24 * lat->V;
+    TRY(unpack_spinor64(lat, fx + (i64)r * 24 * sv, p->on_device ? (double2*)dst : (double2*)bo, 0));
+    if (!p->on_device) {
+      QXD_CUDA(lat, cudaMemcpyAsync(dst, bo, vb, cudaMemcpyDeviceToHost, lat->stream));
+      QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    }
   }
   return st;
 }

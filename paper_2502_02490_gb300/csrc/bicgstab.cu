@@ -9,16 +9,41 @@
 // Kernels work site by site (one thread per site, six float4 per site) so they can also write
 // the 16-bit copies (with per-site scale) that the next 16-bit Dhat reads; per-site products
 // are summed in FP32 and everything beyond in FP64.
+//
+// Multi-RHS: blockIdx.y selects the right-hand side.  Its vectors sit at base + rhs * rs
+// (float4s), its scalars at scal + rhs * SC_N, its ticket at ticket + rhs and its partial sums
+// at red + rhs * 3 * gridDim.x.  A right-hand side whose slot SC_ACTIVE is 0 is frozen (no
+// vector update).  One right-hand side is gridDim.y = 1.
 #include "reduce.cuh"
 
 namespace qxd {
 
 static const int BB = 256;
 
-static int bgrid(qxd_lattice* lat) {
+static dim3 bgrid(qxd_lattice* lat, int nrhs) {
   i64 b = (lat->sv + BB - 1) / BB;
   if (b > lat->red_blocks) b = lat->red_blocks;
-  return (int)(b < 1 ? 1 : b);
+  return dim3((unsigned)(b < 1 ? 1 : b), (unsigned)nrhs);
+}
+
+// Per-RHS views of the reduction state.
+struct RhsView {
+  double* red;
+  unsigned int* ticket;
+  double* scal;
+  i64 off;  // float4 offset of this RHS's vectors
+  bool active;
+};
+
+__device__ __forceinline__ RhsView rhs_view(double* red, unsigned int* ticket, double* scal, i64 rs) {
+  const int r = blockIdx.y;
+  RhsView v;
+  v.red = red + (i64)r * 3 * gridDim.x;
+  v.ticket = ticket + r;
+  v.scal = scal + (i64)r * SC_N;
+  v.off = (i64)r * rs;
+  v.active = v.scal[SC_ACTIVE] != 0.0;
+  return v;
 }
 
 struct cd2 {
@@ -60,7 +85,13 @@ __device__ __forceinline__ void cdot4(float4 a, float4 b, float& re, float& im) 
 
 // scal[slot..slot+1] = <a, b>
 __global__ void __launch_bounds__(BB) k_cdot_32(const float4* __restrict__ a, const float4* __restrict__ b, i64 sv,
-                                                double* red, unsigned int* ticket, double* scal, int slot) {
+                                                i64 rs, double* red0, unsigned int* ticket0, double* scal0, int slot) {
+  const RhsView rv = rhs_view(red0, ticket0, scal0, rs);
+  a += rv.off;
+  b += rv.off;
+  double* red = rv.red;
+  unsigned int* ticket = rv.ticket;
+  double* scal = rv.scal;
   double v[2] = {0.0, 0.0};
   for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
     float re = 0.f, im = 0.f;
@@ -77,7 +108,12 @@ __global__ void __launch_bounds__(BB) k_cdot_32(const float4* __restrict__ a, co
 template <class FMT, bool WR16>
 __global__ void __launch_bounds__(BB) k_bicg_s(const float4* __restrict__ r, const float4* __restrict__ v,
                                                float4* __restrict__ s, uint2* __restrict__ s16, float* __restrict__ s16n,
-                                               i64 sv, const double* __restrict__ scal) {
+                                               i64 sv, i64 rs, double* scal0) {
+  const double* scal = scal0 + (i64)blockIdx.y * SC_N;
+  if (scal[SC_ACTIVE] == 0.0) return;
+  r += (i64)blockIdx.y * rs;
+  v += (i64)blockIdx.y * rs;
+  s += (i64)blockIdx.y * rs;
   const cd2 alpha = cdiv({scal[SC_RHO], scal[SC_RHO + 1]}, {scal[SC_RV], scal[SC_RV + 1]});
   const float ar = (float)-alpha.re, ai = (float)-alpha.im;
   for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
@@ -93,7 +129,13 @@ __global__ void __launch_bounds__(BB) k_bicg_s(const float4* __restrict__ r, con
 
 // scal[SC_TS..] = <t, s>, scal[SC_TT] = <t, t>
 __global__ void __launch_bounds__(BB) k_bicg_ts(const float4* __restrict__ t, const float4* __restrict__ s, i64 sv,
-                                                double* red, unsigned int* ticket, double* scal) {
+                                                i64 rs, double* red0, unsigned int* ticket0, double* scal0) {
+  const RhsView rv = rhs_view(red0, ticket0, scal0, rs);
+  t += rv.off;
+  s += rv.off;
+  double* red = rv.red;
+  unsigned int* ticket = rv.ticket;
+  double* scal = rv.scal;
   double v[3] = {0.0, 0.0, 0.0};
   for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
     float re = 0.f, im = 0.f, tt = 0.f;
@@ -115,7 +157,18 @@ __global__ void __launch_bounds__(BB) k_bicg_ts(const float4* __restrict__ t, co
 __global__ void __launch_bounds__(BB) k_bicg_xr(float4* __restrict__ x, const float4* __restrict__ p,
                                                 const float4* __restrict__ s, const float4* __restrict__ t,
                                                 const float4* __restrict__ rh, float4* __restrict__ r, i64 sv,
-                                                double* red, unsigned int* ticket, double* scal) {
+                                                i64 rs, double* red0, unsigned int* ticket0, double* scal0) {
+  const RhsView rv = rhs_view(red0, ticket0, scal0, rs);
+  if (!rv.active) return;  // uniform over the RHS's blocks: none of them takes part
+  x += rv.off;
+  p += rv.off;
+  s += rv.off;
+  t += rv.off;
+  rh += rv.off;
+  r += rv.off;
+  double* red = rv.red;
+  unsigned int* ticket = rv.ticket;
+  double* scal = rv.scal;
   const cd2 alpha = cdiv({scal[SC_RHO], scal[SC_RHO + 1]}, {scal[SC_RV], scal[SC_RV + 1]});
   const cd2 omega = {scal[SC_TS] / scal[SC_TT], scal[SC_TS + 1] / scal[SC_TT]};
   const float a_r = (float)alpha.re, a_i = (float)alpha.im, w_r = (float)omega.re, w_i = (float)omega.im;
@@ -145,7 +198,13 @@ __global__ void __launch_bounds__(BB) k_bicg_xr(float4* __restrict__ x, const fl
 template <class FMT, bool WR16>
 __global__ void __launch_bounds__(BB) k_bicg_p(const float4* __restrict__ r, const float4* __restrict__ v,
                                                float4* __restrict__ p, uint2* __restrict__ p16, float* __restrict__ p16n,
-                                               i64 sv, unsigned int* ticket, double* scal) {
+                                               i64 sv, i64 rs, unsigned int* ticket0, double* scal0) {
+  double* scal = scal0 + (i64)blockIdx.y * SC_N;
+  unsigned int* ticket = ticket0 + blockIdx.y;
+  if (scal[SC_ACTIVE] == 0.0) return;
+  r += (i64)blockIdx.y * rs;
+  v += (i64)blockIdx.y * rs;
+  p += (i64)blockIdx.y * rs;
   const cd2 rho = {scal[SC_RHO], scal[SC_RHO + 1]};
   const cd2 alpha = cdiv(rho, {scal[SC_RV], scal[SC_RV + 1]});
   const cd2 omega = {scal[SC_TS] / scal[SC_TT], scal[SC_TS + 1] / scal[SC_TT]};
@@ -179,6 +238,8 @@ __global__ void __launch_bounds__(BB) k_bicg_p(const float4* __restrict__ r, con
 template <class FMT, bool WR16>
 __global__ void __launch_bounds__(BB) k_copy16(const float4* __restrict__ r, float4* __restrict__ p,
                                                uint2* __restrict__ p16, float* __restrict__ p16n, i64 sv) {
+  r += (i64)blockIdx.y * 6 * sv;
+  p += (i64)blockIdx.y * 6 * sv;
   for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
     float4 o[6];
 #pragma unroll
@@ -190,56 +251,107 @@ __global__ void __launch_bounds__(BB) k_copy16(const float4* __restrict__ r, flo
   }
 }
 
-#define RARGS lat->red, lat->ticket, lat->scal
+// Reduction state of a launch over R.nrhs right-hand sides starting at R.r0.
+struct RedState {
+  double* red;
+  unsigned int* ticket;
+  double* scal;
+};
+static RedState red_state(qxd_lattice* lat, const Rhs& R) {
+  if (!R.mr) return {lat->red, lat->ticket, lat->scal};
+  const i64 gx = bgrid(lat, 1).x;
+  return {lat->mr_red + (i64)R.r0 * 3 * gx, lat->mr_ticket + R.r0, lat->mr_scal + (i64)R.r0 * SC_N};
+}
 
-qxd_status bicg_cdot(qxd_lattice* lat, const float4* a, const float4* b, int slot) {
-  k_cdot_32<<<bgrid(lat), BB, 0, lat->stream>>>(a, b, lat->sv, RARGS, slot);
+qxd_status bicg_cdot(qxd_lattice* lat, const float4* a, const float4* b, int slot, Rhs R) {
+  RedState S = red_state(lat, R);
+  k_cdot_32<<<bgrid(lat, R.nrhs), BB, 0, lat->stream>>>(a, b, lat->sv, R.rs, S.red, S.ticket, S.scal, slot);
   QXD_CHECK_LAUNCH(lat, "k_cdot_32");
   return QXD_OK;
 }
 
-qxd_status bicg_s(qxd_lattice* lat, const float4* r, const float4* v, float4* s, uint2* s16, float* s16n, int bf16) {
+qxd_status bicg_s(qxd_lattice* lat, const float4* r, const float4* v, float4* s, uint2* s16, float* s16n, int bf16,
+                  Rhs R) {
+  RedState S = red_state(lat, R);
+  const dim3 g = bgrid(lat, R.nrhs);
   if (!s16)
-    k_bicg_s<H16, false><<<bgrid(lat), BB, 0, lat->stream>>>(r, v, s, nullptr, nullptr, lat->sv, lat->scal);
+    k_bicg_s<H16, false><<<g, BB, 0, lat->stream>>>(r, v, s, nullptr, nullptr, lat->sv, R.rs, S.scal);
   else if (bf16)
-    k_bicg_s<B16, true><<<bgrid(lat), BB, 0, lat->stream>>>(r, v, s, s16, s16n, lat->sv, lat->scal);
+    k_bicg_s<B16, true><<<g, BB, 0, lat->stream>>>(r, v, s, s16, s16n, lat->sv, R.rs, S.scal);
   else
-    k_bicg_s<H16, true><<<bgrid(lat), BB, 0, lat->stream>>>(r, v, s, s16, s16n, lat->sv, lat->scal);
+    k_bicg_s<H16, true><<<g, BB, 0, lat->stream>>>(r, v, s, s16, s16n, lat->sv, R.rs, S.scal);
   QXD_CHECK_LAUNCH(lat, "k_bicg_s");
   return QXD_OK;
 }
 
-qxd_status bicg_ts(qxd_lattice* lat, const float4* t, const float4* s) {
-  k_bicg_ts<<<bgrid(lat), BB, 0, lat->stream>>>(t, s, lat->sv, RARGS);
+qxd_status bicg_ts(qxd_lattice* lat, const float4* t, const float4* s, Rhs R) {
+  RedState S = red_state(lat, R);
+  k_bicg_ts<<<bgrid(lat, R.nrhs), BB, 0, lat->stream>>>(t, s, lat->sv, R.rs, S.red, S.ticket, S.scal);
   QXD_CHECK_LAUNCH(lat, "k_bicg_ts");
   return QXD_OK;
 }
 
 qxd_status bicg_xr(qxd_lattice* lat, float4* x, const float4* p, const float4* s, const float4* t, const float4* rh,
-                   float4* r) {
-  k_bicg_xr<<<bgrid(lat), BB, 0, lat->stream>>>(x, p, s, t, rh, r, lat->sv, RARGS);
+                   float4* r, Rhs R) {
+  RedState S = red_state(lat, R);
+  k_bicg_xr<<<bgrid(lat, R.nrhs), BB, 0, lat->stream>>>(x, p, s, t, rh, r, lat->sv, R.rs, S.red, S.ticket, S.scal);
   QXD_CHECK_LAUNCH(lat, "k_bicg_xr");
   return QXD_OK;
 }
 
-qxd_status bicg_p(qxd_lattice* lat, const float4* r, const float4* v, float4* p, uint2* p16, float* p16n, int bf16) {
+qxd_status bicg_p(qxd_lattice* lat, const float4* r, const float4* v, float4* p, uint2* p16, float* p16n, int bf16,
+                  Rhs R) {
+  RedState S = red_state(lat, R);
+  const dim3 g = bgrid(lat, R.nrhs);
   if (!p16)
-    k_bicg_p<H16, false><<<bgrid(lat), BB, 0, lat->stream>>>(r, v, p, nullptr, nullptr, lat->sv, lat->ticket, lat->scal);
+    k_bicg_p<H16, false><<<g, BB, 0, lat->stream>>>(r, v, p, nullptr, nullptr, lat->sv, R.rs, S.ticket, S.scal);
   else if (bf16)
-    k_bicg_p<B16, true><<<bgrid(lat), BB, 0, lat->stream>>>(r, v, p, p16, p16n, lat->sv, lat->ticket, lat->scal);
+    k_bicg_p<B16, true><<<g, BB, 0, lat->stream>>>(r, v, p, p16, p16n, lat->sv, R.rs, S.ticket, S.scal);
   else
-    k_bicg_p<H16, true><<<bgrid(lat), BB, 0, lat->stream>>>(r, v, p, p16, p16n, lat->sv, lat->ticket, lat->scal);
+    k_bicg_p<H16, true><<<g, BB, 0, lat->stream>>>(r, v, p, p16, p16n, lat->sv, R.rs, S.ticket, S.scal);
   QXD_CHECK_LAUNCH(lat, "k_bicg_p");
   return QXD_OK;
 }
 
+__global__ void k_set_at(double* p, double v) { *p = v; }
+
+qxd_status set_scalar_at(qxd_lattice* lat, double* p, double v) {
+  k_set_at<<<1, 1, 0, lat->stream>>>(p, v);
+  QXD_CHECK_LAUNCH(lat, "k_set_at");
+  return QXD_OK;
+}
+
+qxd_status ensure_mrhs(qxd_lattice* lat, int n) {
+  if (lat->mr_cap >= n) return QXD_OK;
+  QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  if (lat->mr_red) cudaFree(lat->mr_red);
+  if (lat->mr_ticket) cudaFree(lat->mr_ticket);
+  if (lat->mr_scal) cudaFree(lat->mr_scal);
+  if (lat->mr_hscal) cudaFreeHost(lat->mr_hscal);
+  lat->mr_red = nullptr;
+  lat->mr_ticket = nullptr;
+  lat->mr_scal = nullptr;
+  lat->mr_hscal = nullptr;
+  lat->mr_cap = 0;
+  const i64 gx = bgrid(lat, 1).x;
+  QXD_CUDA(lat, cudaMalloc((void**)&lat->mr_red, sizeof(double) * 3 * gx * n));
+  QXD_CUDA(lat, cudaMalloc((void**)&lat->mr_ticket, sizeof(unsigned int) * n));
+  QXD_CUDA(lat, cudaMalloc((void**)&lat->mr_scal, sizeof(double) * SC_N * n));
+  QXD_CUDA(lat, cudaMallocHost((void**)&lat->mr_hscal, sizeof(double) * SC_N * n));
+  QXD_CUDA(lat, cudaMemsetAsync(lat->mr_ticket, 0, sizeof(unsigned int) * n, lat->stream));
+  QXD_CUDA(lat, cudaMemsetAsync(lat->mr_scal, 0, sizeof(double) * SC_N * n, lat->stream));
+  lat->mr_cap = n;
+  return QXD_OK;
+}
+
 qxd_status bicg_copy(qxd_lattice* lat, const float4* r, float4* p, uint2* p16, float* p16n, int bf16) {
+  const dim3 g = bgrid(lat, 1);
   if (!p16)
-    k_copy16<H16, false><<<bgrid(lat), BB, 0, lat->stream>>>(r, p, nullptr, nullptr, lat->sv);
+    k_copy16<H16, false><<<g, BB, 0, lat->stream>>>(r, p, nullptr, nullptr, lat->sv);
   else if (bf16)
-    k_copy16<B16, true><<<bgrid(lat), BB, 0, lat->stream>>>(r, p, p16, p16n, lat->sv);
+    k_copy16<B16, true><<<g, BB, 0, lat->stream>>>(r, p, p16, p16n, lat->sv);
   else
-    k_copy16<H16, true><<<bgrid(lat), BB, 0, lat->stream>>>(r, p, p16, p16n, lat->sv);
+    k_copy16<H16, true><<<g, BB, 0, lat->stream>>>(r, p, p16, p16n, lat->sv);
   QXD_CHECK_LAUNCH(lat, "k_copy16");
   return QXD_OK;
 }

@@ -503,7 +503,7 @@ __device__ __forceinline__ void herm6_apply(const R r[36], const cplx<R> x[6], c
 // ------------------------------------------------------------------------------------------
 // The lattice object (host side)
 // ------------------------------------------------------------------------------------------
-enum { KSTAT_F64 = 0, KSTAT_F32 = 1, KSTAT_F16N = 2, KSTAT_BF16N = 3, KSTAT_N = 4 };
+enum { KSTAT_F64 = 0, KSTAT_F32 = 1, KSTAT_F16N = 2, KSTAT_BF16N = 3, KSTAT_F32_MRHS = 4, KSTAT_N = 5 };
 
 // Device scalar slots used by the solvers and reductions.
 enum {
@@ -511,6 +511,7 @@ enum {
   // BiCGStab: complex pairs (re, im) at SC_RHO, SC_RV, SC_TS, SC_RR; reals SC_TT = SC_TS + 2,
   // SC_RN = SC_RR + 2 (written together by 3-value reductions)
   SC_RHO = 8, SC_RV = 10, SC_TS = 12, SC_TT = 14, SC_RR = 15, SC_RN = 17,
+  SC_ACTIVE = 20,  // 1.0 while a right-hand side iterates, 0.0 once it is frozen
   SC_N = 24
 };
 
@@ -560,13 +561,20 @@ struct qxd_lattice {
   double* scal = nullptr;
   double* hscal = nullptr;
   int red_blocks = 0;
+  // multi-RHS reduction state (allocated on first use): per-RHS partials, tickets, scalars
+  double* mr_red = nullptr;
+  unsigned int* mr_ticket = nullptr;
+  double* mr_scal = nullptr;
+  double* mr_hscal = nullptr;
+  int mr_cap = 0;
 
   // staging buffer for host/device boundary arrays
   void* stage = nullptr;
   size_t stage_bytes = 0;
-  // work buffers (lazily allocated): slots 0..23 solver, 24..27 API staging fields, 30 clover flag
-  void* work[32] = {nullptr};
-  size_t work_bytes[32] = {0};
+  // work buffers (lazily allocated): slots 0..23 and 28 solver, 24..27 API staging fields, 30 clover flag,
+  // 32..39 multi-RHS fields
+  void* work[40] = {nullptr};
+  size_t work_bytes[40] = {0};
 
   // profiling
   bool profiling = false;
@@ -642,6 +650,10 @@ qxd_status hop16(qxd_lattice* lat, int bf16, int par, int epi, int g5, const uin
                  const uint2* same, const float* same_nrm, uint2* out, float* out_nrm, float4* out32,
                  float coef);
 
+// ---- mrhs.cu: FP32 hop on nrhs right-hand sides (fields at base + r * rs float4s) ----
+qxd_status hop32_mrhs(qxd_lattice* lat, int par, int epi, int g5, const float4* in, const float4* same, float4* out,
+                      float coef, int nrhs, i64 rs);
+
 // ---- blas.cu ----
 // n = number of complex entries; arrays are double2 (FP64) or float2-pairs (FP32 as float4 * n/2)
 qxd_status blas_norm2_64(qxd_lattice* lat, const double2* a, i64 n, int slot);
@@ -667,12 +679,27 @@ qxd_status blas_acc_f32_into_f64(qxd_lattice* lat, const float4* x, double2* y, 
 qxd_status blas_axpy_32(qxd_lattice* lat, float a, const float4* x, float4* y, i64 n4);
 
 // ---- bicgstab.cu (FP32 vectors, one thread per site; 16-bit copies written when non-null) ----
-qxd_status bicg_cdot(qxd_lattice* lat, const float4* a, const float4* b, int slot);  // <a, b>
-qxd_status bicg_s(qxd_lattice* lat, const float4* r, const float4* v, float4* s, uint2* s16, float* s16n, int bf16);
-qxd_status bicg_ts(qxd_lattice* lat, const float4* t, const float4* s);
+// Reduction state the BiCGStab kernels use: the lattice's own (single RHS), or the multi-RHS
+// buffers starting at right-hand side r0 (mr = true).  nrhs consecutive right-hand sides run
+// in one launch; RHS r's vectors sit at base + r * rs float4s.
+struct Rhs {
+  int nrhs = 1;
+  i64 rs = 0;
+  bool mr = false;
+  int r0 = 0;
+};
+qxd_status bicg_cdot(qxd_lattice* lat, const float4* a, const float4* b, int slot, Rhs R = Rhs());
+qxd_status bicg_s(qxd_lattice* lat, const float4* r, const float4* v, float4* s, uint2* s16, float* s16n, int bf16,
+                  Rhs R = Rhs());
+qxd_status bicg_ts(qxd_lattice* lat, const float4* t, const float4* s, Rhs R = Rhs());
 qxd_status bicg_xr(qxd_lattice* lat, float4* x, const float4* p, const float4* s, const float4* t, const float4* rh,
-                   float4* r);
-qxd_status bicg_p(qxd_lattice* lat, const float4* r, const float4* v, float4* p, uint2* p16, float* p16n, int bf16);
+                   float4* r, Rhs R = Rhs());
+qxd_status bicg_p(qxd_lattice* lat, const float4* r, const float4* v, float4* p, uint2* p16, float* p16n, int bf16,
+                  Rhs R = Rhs());
+// device scalar write anywhere in the scalar arrays
+qxd_status set_scalar_at(qxd_lattice* lat, double* p, double v);
+// multi-RHS reduction state for up to n right-hand sides
+qxd_status ensure_mrhs(qxd_lattice* lat, int n);
 qxd_status bicg_copy(qxd_lattice* lat, const float4* r, float4* p, uint2* p16, float* p16n, int bf16);
 
 // ---- profiling helpers (api.cu) ----
@@ -684,5 +711,8 @@ qxd_status solve(qxd_lattice* lat, double2* x_field, const double2* b_field, con
                  qxd_solve_info* info);
 // full D on FP64 fields (both parities): out = D in
 qxd_status apply_D64(qxd_lattice* lat, const double2* in, double2* out);
+// ---- solver_mrhs.cu ----
+qxd_status solve_mrhs(qxd_lattice* lat, double2* x, const double2* b, int n, const qxd_solve_params* p,
+                      qxd_solve_info* info);
 
 }  // namespace qxd

@@ -318,6 +318,7 @@ static qxd_status inner_bicg(qxd_lattice* lat, int prec, const float4* bh, float
     TRY(bicg_cdot(lat, rh, r, SC_RHO));
     return QXD_OK;
   };
+  TRY(set_scalar(lat, SC_ACTIVE, 1.0));
   TRY(blas_zero(lat, x, hb));
   TRY(blas_copy(lat, r, bh, hb));
   TRY(restart());

@@ -53,6 +53,7 @@ _SIGS = {
     "qxd_apply_D": [_vp, _vp, _vp, _i, _i, _i],
     "qxd_apply_Dhat_eo": [_vp, _vp, _vp, _i, _i, _i],
     "qxd_solve": [_vp, _vp, _vp, C.POINTER(SolveParams), C.POINTER(SolveInfo)],
+    "qxd_solve_mrhs": [_vp, _vp, _vp, _i, C.POINTER(SolveParams), _vp],
     "qxd_vec_dot": [_vp, _vp, _vp, _i64, C.POINTER(_d), C.POINTER(_d)],
     "qxd_vec_norm2": [_vp, _vp, _i64, C.POINTER(_d)],
     "qxd_vec_axpy": [_vp, _d, _d, _vp, _vp, _i64],
@@ -166,6 +167,21 @@ def solve(lat, x, b, params=None, check=True, **kw):
     if check:
         _check(st, lat)
     return st, info.as_dict()
+
+
+def solve_mrhs(lat, x, b, nrhs, params=None, check=True, **kw):
+    """qxd_solve_mrhs; returns (status, list of nrhs info dicts)."""
+    p = params if params is not None else default_params(**kw)
+    px, dev = _ptr(x)
+    pb, dev2 = _ptr(b)
+    if dev != dev2:
+        raise ValueError("x and b must both be host or both be device buffers")
+    p.on_device = int(dev)
+    infos = (SolveInfo * int(nrhs))()
+    st = lib.qxd_solve_mrhs(lat, px, pb, int(nrhs), C.byref(p), C.cast(infos, C.c_void_p))
+    if check:
+        _check(st, lat)
+    return st, [i.as_dict() for i in infos]
 
 
 def vec_dot(lat, a, b, n):
