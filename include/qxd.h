@@ -56,6 +56,7 @@ extern "C" {
 #endif
 
 typedef struct qxd_lattice qxd_lattice; /* opaque; owns all device fields of one lattice */
+typedef struct qxd_net qxd_net;         /* opaque; a learned preconditioner bound to one lattice */
 
 typedef enum {
   QXD_OK = 0,
@@ -83,8 +84,11 @@ typedef enum {
   QXD_SOLVER_CG_EO = 0,    /* plain FP64 even-odd CG (CG on Dhat^+ Dhat), true-residual judged */
   QXD_SOLVER_MP_CG_EO = 1, /* FP64 outer defect correction around an inner even-odd CG in
                               inner_prec with FP32 reliable updates */
-  QXD_SOLVER_MP_BICGSTAB_EO = 2 /* as MP_CG_EO with BiCGStab on Dhat as the inner solver (each
+  QXD_SOLVER_MP_BICGSTAB_EO = 2, /* as MP_CG_EO with BiCGStab on Dhat as the inner solver (each
                                    reliable update restarts it from the recomputed residual) */
+  QXD_SOLVER_MP_FGCR_NET = 3     /* FP64 outer defect correction around flexible GCR(gcr_restart) on
+                                   the full D in FP32 with the learned network `net` as right
+                                   preconditioner (net NULL: no preconditioner) */
 } qxd_solver;
 
 typedef struct {
@@ -98,9 +102,11 @@ typedef struct {
   int max_outer;          /* cap on outer (defect-correction) rounds */
   int on_device;          /* x and b are device (1) or host (0) pointers */
   int check_every;        /* read the residual norm back every this many iterations (>= 1) */
+  int gcr_restart;        /* FGCR restart length (MP_FGCR_NET), 1..64 */
+  const qxd_net *net;     /* preconditioner of MP_FGCR_NET, or NULL */
 } qxd_solve_params;
 
-#define QXD_PARAMS_VERSION 1
+#define QXD_PARAMS_VERSION 2
 
 typedef struct {
   int iters_inner;        /* inner iterations summed over outer rounds */
@@ -170,7 +176,7 @@ qxd_status qxd_solve_mrhs(qxd_lattice *lat, double *x, const double *b, int nrhs
                           const qxd_solve_params *params, qxd_solve_info *info);
 
 /* Fill *p with the defaults: MP_CG_EO, tol 1e-10, maxiter 100000, inner F32, inner_tol 1e-5,
- * reliable_delta 0.1, max_outer 20, on_device 1, check_every 1. */
+ * reliable_delta 0.1, max_outer 20, on_device 1, check_every 1, gcr_restart 16, net NULL. */
 void qxd_default_params(qxd_solve_params *p);
 
 /* Fused BLAS-1 on device vectors of n complex numbers (interleaved re, im), on the lattice's
@@ -184,6 +190,47 @@ qxd_status qxd_vec_dot(qxd_lattice *lat, const double *a, const double *b, int64
 qxd_status qxd_vec_norm2(qxd_lattice *lat, const double *a, int64_t n, double *out);
 qxd_status qxd_vec_axpy(qxd_lattice *lat, double re, double im, const double *x, double *y,
                         int64_t n);
+
+/* ---- Learned preconditioner (gauge-equivariant parallel-transport convolution network) ----
+ * Layer: out_c(x) = sum_{c'} sum_{p=0..8} Omega[c][c'][p] (T_p h_{c'})(x) with T_0 = 1,
+ * T_{1+mu} h(x) = W_mu(x) h(x+mu), T_{5+mu} h(x) = W_mu(x-mu)^dag h(x-mu) (hop links and
+ * boundary conditions of the lattice; gauge-equivariant by construction) and Omega a complex
+ * 4x4 spin matrix per (output channel, input channel, path).  The network is the chain of
+ * nlayers linear layers with channel counts channels[0..nlayers] (first and last 1, others
+ * 1..16).  FP32 weights and activations.  Weights are laid out [layer][Cout][Cin][9][4][4] complex
+ * (interleaved re, im doubles at the boundary).  The paper has no learned part; this follows the
+ * method's learned-preconditioner extension.
+ * create: weights initialised from `seed` (identity path near 1/4, small noise elsewhere). */
+qxd_status qxd_net_create(qxd_lattice *lat, int nlayers, const int *channels, uint64_t seed,
+                          qxd_net **out);
+qxd_status qxd_net_destroy(qxd_net *net);
+int64_t qxd_net_num_weights(const qxd_net *net); /* complex weights */
+qxd_status qxd_net_set_weights(qxd_net *net, const double *w); /* host [n][2] */
+qxd_status qxd_net_get_weights(const qxd_net *net, double *w);
+/* out = M in on full fields [V][4][3][2] (FP32 arithmetic). */
+qxd_status qxd_net_apply(qxd_net *net, double *out, const double *in, int on_device);
+/* loss = sum_i ||M(b_i) - v_i||^2 over nsamp samples ([nsamp][V][4][3][2] each) and, if grad is
+ * non-NULL, grad = dloss/d(conj w) (host [n][2]; the real-parameter gradient is twice its real
+ * and imaginary parts). */
+qxd_status qxd_net_loss_grad(qxd_net *net, const double *v, const double *b, int nsamp, int on_device,
+                             double *loss, double *grad);
+
+typedef struct {
+  int version;   /* QXD_TRAIN_VERSION */
+  int epochs;    /* passes over the training set */
+  int batch;     /* samples per Adam step */
+  double lr, beta1, beta2, eps; /* Adam */
+} qxd_train_params;
+#define QXD_TRAIN_VERSION 1
+
+/* Train on (b_i = D v_i, v_i), i < nsamp, generated by the lattice's own FP32 operator from the
+ * given v ([nsamp][V][4][3][2], e.g. Gaussian): Adam on sum_i ||M(b_i) - v_i||^2 with the
+ * network's own forward and backward kernels.  loss_hist (may be NULL): mean loss per epoch. */
+qxd_status qxd_net_train(qxd_net *net, const double *v, int nsamp, const qxd_train_params *p,
+                         double *loss_hist, int on_device);
+/* Checkpoint: "QXDNET1\n", int32 nlayers, int32 channels[nlayers+1], float32 weights (re, im). */
+qxd_status qxd_net_save(const qxd_net *net, const char *path);
+qxd_status qxd_net_load(qxd_lattice *lat, const char *path, qxd_net **out);
 
 /* Dot product for callers that cannot allocate device memory.  The paper has no counterpart:
  * this entry point exists for callers that must not call cudaMalloc -- code running while a

@@ -453,3 +453,89 @@ def clover_blocks(C):
 def packed_clover(op):
     """Clover field as [V][2][36] reals in lexicographic site order (openQxD 36-real packing)."""
     return pack36(clover_blocks(op.C))
+
+
+# ---------------------------------------------------------------------------------------
+# Gauge-equivariant parallel-transport convolution (PTC) network (learned preconditioner)
+# ---------------------------------------------------------------------------------------
+# Paths p = 0 (stay), 1 + mu (from x + mu_hat), 5 + mu (from x - mu_hat).  The transport uses the
+# hop links and the operator's boundary signs, so the network commutes with gauge
+# transformations and obeys the same boundary conditions as D.
+NPATH = 9
+
+
+def path_swap(p):
+    """The path whose transport is the adjoint of path p's: +mu <-> -mu, 0 -> 0."""
+    return 0 if p == 0 else (p + 4 if p < 5 else p - 4)
+
+
+def transport(lat, W, psi, p):
+    """(T_p psi)(x): psi itself (p = 0), W_mu(x) psi(x + mu) (p = 1 + mu), W_mu(x - mu)^+ psi(x - mu)
+    (p = 5 + mu), with the boundary sign of the hop."""
+    if p == 0:
+        return psi.copy()
+    if p < 5:
+        mu = p - 1
+        f, sf = lat.neighbour(mu, +1)
+        return np.einsum("xab,xsb->xsa", W[:, mu], psi[f]) * sf[:, None, None]
+    mu = p - 5
+    b, sb = lat.neighbour(mu, -1)
+    return np.einsum("xab,xsb->xsa", dag(W[b, mu]), psi[b]) * sb[:, None, None]
+
+
+def ptc_layer(lat, W, omega, h):
+    """out_c(x) = sum_{c', p} omega[c, c', p] (T_p h_{c'})(x); omega (Cout, Cin, 9, 4, 4) spin
+    matrices, h (Cin, V, 4, 3).  Linear, no nonlinearity."""
+    cout, cin = omega.shape[:2]
+    out = np.zeros((cout,) + h.shape[1:], dtype=np.complex128)
+    for ci in range(cin):
+        for p in range(NPATH):
+            T = transport(lat, W, h[ci], p)
+            out += np.einsum("ost,xta->oxsa", omega[:, ci, p], T)
+    return out
+
+
+def ptc_net(lat, W, weights, b):
+    """M(b): the layers applied in order to the one-channel input b (V, 4, 3); returns (V, 4, 3)."""
+    h = b[None]
+    for om in weights:
+        h = ptc_layer(lat, W, om, h)
+    return h[0]
+
+
+def ptc_loss(lat, W, weights, bs, vs):
+    """Sum over samples of ||M(b_i) - v_i||^2 (the training loss, b_i = D v_i)."""
+    return float(sum(np.vdot(ptc_net(lat, W, weights, b) - v, ptc_net(lat, W, weights, b) - v).real
+                     for b, v in zip(bs, vs)))
+
+
+def ptc_layer_adjoint(lat, W, omega, g):
+    """Adjoint of ptc_layer applied to g (Cout, V, 4, 3): sum_{c, p} T_{swap p}(omega[c, c', p]^+ g_c)."""
+    cout, cin = omega.shape[:2]
+    out = np.zeros((cin,) + g.shape[1:], dtype=np.complex128)
+    for c in range(cout):
+        for p in range(NPATH):
+            for ci in range(cin):
+                mg = np.einsum("ts,xta->xsa", omega[c, ci, p].conj(), g[c])
+                out[ci] += transport(lat, W, mg, path_swap(p))
+    return out
+
+
+def ptc_loss_grad(lat, W, weights, bs, vs):
+    """Gradient of ptc_loss with respect to the conjugate weights, dL/d(omega^*), per layer
+    (the real-parameter gradient is 2 Re / 2 Im of it), by the chain rule through the layers."""
+    grads = [np.zeros_like(om) for om in weights]
+    for b, v in zip(bs, vs):
+        hs = [b[None]]
+        for om in weights:
+            hs.append(ptc_layer(lat, W, om, hs[-1]))
+        g = (hs[-1][0] - v)[None]
+        for li in range(len(weights) - 1, -1, -1):
+            om, h = weights[li], hs[li]
+            cout, cin = om.shape[:2]
+            for ci in range(cin):
+                for p in range(NPATH):
+                    T = transport(lat, W, h[ci], p)
+                    grads[li][:, ci, p] += np.einsum("oxsa,xta->ost", g, T.conj())
+            g = ptc_layer_adjoint(lat, W, om, g)
+    return grads

@@ -131,6 +131,8 @@ void qxd_default_params(qxd_solve_params* p) {
   p->max_outer = 20;
   p->on_device = 1;
   p->check_every = 1;
+  p->gcr_restart = 16;
+  p->net = nullptr;
 }
 
 qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
@@ -380,8 +382,11 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
   if (info) std::memset(info, 0, sizeof(*info));
   if (!x || !b || !p) return fail(lat, QXD_EINVAL, "null argument");
   if (p->version != QXD_PARAMS_VERSION) return fail(lat, QXD_EINVAL, "qxd_solve_params version mismatch");
-  if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO && p->solver != QXD_SOLVER_MP_BICGSTAB_EO)
+  if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO && p->solver != QXD_SOLVER_MP_BICGSTAB_EO &&
+      p->solver != QXD_SOLVER_MP_FGCR_NET)
     return fail(lat, QXD_EINVAL, "bad solver");
+  if (p->solver == QXD_SOLVER_MP_FGCR_NET && (p->gcr_restart < 1 || p->gcr_restart > 64))
+    return fail(lat, QXD_EINVAL, "gcr_restart must be 1..64");
   if (!(p->tol > 0) || p->maxiter <= 0) return fail(lat, QXD_EINVAL, "tol must be > 0 and maxiter > 0");
   if (p->solver != QXD_SOLVER_CG_EO && (p->inner_prec < QXD_F32 || p->inner_prec > QXD_BF16N))
     return fail(lat, QXD_EINVAL, "inner_prec must be F32, F16N or BF16N");

@@ -711,6 +711,8 @@ qxd_status solve(qxd_lattice* lat, double2* x_field, const double2* b_field, con
                  qxd_solve_info* info);
 // full D on FP64 fields (both parities): out = D in
 qxd_status apply_D64(qxd_lattice* lat, const double2* in, double2* out);
+// ---- ptc.cu ----
+qxd_status net_apply32(qxd_net* net, const float4* in, float4* out);  // full FP32 fields
 // ---- solver_mrhs.cu ----
 qxd_status solve_mrhs(qxd_lattice* lat, double2* x, const double2* b, int n, const qxd_solve_params* p,
                       qxd_solve_info* info);

@@ -24,15 +24,22 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESINGULAR", "ENOCONV", "ESTA
 BC_PERIODIC, BC_ANTIPERIODIC = 0, 1
 ORDER_LEXI, ORDER_IPT = 0, 1
 F64, F32, F16N, BF16N = 0, 1, 2, 3
-SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO = 0, 1, 2
-PARAMS_VERSION = 1
+SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO, SOLVER_MP_FGCR_NET = 0, 1, 2, 3
+PARAMS_VERSION = 2
+TRAIN_VERSION = 1
 PREC = {"f64": F64, "f32": F32, "f16n": F16N, "bf16n": BF16N}
 
 
 class SolveParams(C.Structure):
     _fields_ = [("version", C.c_int), ("solver", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int),
                 ("inner_prec", C.c_int), ("inner_tol", C.c_double), ("reliable_delta", C.c_double),
-                ("max_outer", C.c_int), ("on_device", C.c_int), ("check_every", C.c_int)]
+                ("max_outer", C.c_int), ("on_device", C.c_int), ("check_every", C.c_int),
+                ("gcr_restart", C.c_int), ("net", C.c_void_p)]
+
+
+class TrainParams(C.Structure):
+    _fields_ = [("version", C.c_int), ("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double),
+                ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -59,6 +66,15 @@ _SIGS = {
     "qxd_vec_axpy": [_vp, _d, _d, _vp, _vp, _i64],
     "qxd_vec_dot_noalloc": [_vp, _vp, _i64, _vp, _vp],
     "qxd_set_profiling": [_vp, _i],
+    "qxd_net_create": [_vp, _i, C.POINTER(C.c_int), C.c_uint64, C.POINTER(_vp)],
+    "qxd_net_destroy": [_vp],
+    "qxd_net_set_weights": [_vp, _vp],
+    "qxd_net_get_weights": [_vp, _vp],
+    "qxd_net_apply": [_vp, _vp, _vp, _i],
+    "qxd_net_loss_grad": [_vp, _vp, _vp, _i, _i, C.POINTER(_d), _vp],
+    "qxd_net_train": [_vp, _vp, _i, C.POINTER(TrainParams), _vp, _i],
+    "qxd_net_save": [_vp, C.c_char_p],
+    "qxd_net_load": [_vp, C.c_char_p, C.POINTER(_vp)],
     "qxd_kernel_stats": [_vp, _i, C.POINTER(_i64), C.POINTER(_d), C.POINTER(_d)],
 }
 for _name, _args in _SIGS.items():
@@ -69,6 +85,8 @@ lib.qxd_default_params.argtypes = [C.POINTER(SolveParams)]
 lib.qxd_default_params.restype = None
 lib.qxd_last_error.argtypes = [_vp]
 lib.qxd_last_error.restype = C.c_char_p
+lib.qxd_net_num_weights.argtypes = [_vp]
+lib.qxd_net_num_weights.restype = C.c_int64
 lib.qxd_launch_count.argtypes = [_vp]
 lib.qxd_launch_count.restype = C.c_int64
 
@@ -221,3 +239,72 @@ def kernel_stats(lat, which):
 
 def launch_count(lat):
     return int(lib.qxd_launch_count(lat))
+
+
+# ---- learned preconditioner ----
+def net_create(lat, channels, seed=0):
+    """qxd_net_create with channels = [1, C, ..., 1]; returns the net handle."""
+    ch = (C.c_int * len(channels))(*[int(c) for c in channels])
+    out = _vp()
+    _check(lib.qxd_net_create(lat, len(channels) - 1, ch, int(seed), C.byref(out)), lat)
+    return out.value
+
+
+def net_destroy(net):
+    _check(lib.qxd_net_destroy(net))
+
+
+def net_num_weights(net):
+    return int(lib.qxd_net_num_weights(net))
+
+
+def net_set_weights(net, w):
+    w = np.ascontiguousarray(w, dtype=np.complex128)
+    _check(lib.qxd_net_set_weights(net, w.ctypes.data))
+
+
+def net_get_weights(net):
+    w = np.empty(net_num_weights(net), dtype=np.complex128)
+    _check(lib.qxd_net_get_weights(net, w.ctypes.data))
+    return w
+
+
+def net_apply(net, out, inp):
+    po, dev = _ptr(out)
+    pi, _ = _ptr(inp)
+    _check(lib.qxd_net_apply(net, po, pi, int(dev)))
+
+
+def net_loss_grad(net, v, b, nsamp, want_grad=True):
+    pv, dev = _ptr(v)
+    pb, _ = _ptr(b)
+    loss = C.c_double()
+    g = np.empty(net_num_weights(net), dtype=np.complex128) if want_grad else None
+    _check(lib.qxd_net_loss_grad(net, pv, pb, int(nsamp), int(dev), C.byref(loss),
+                                 g.ctypes.data if g is not None else None))
+    return loss.value, g
+
+
+def train_params(**kw):
+    p = TrainParams(version=TRAIN_VERSION, epochs=10, batch=4, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def net_train(net, v, nsamp, params=None, **kw):
+    p = params if params is not None else train_params(**kw)
+    pv, dev = _ptr(v)
+    hist = np.zeros(p.epochs)
+    _check(lib.qxd_net_train(net, pv, int(nsamp), C.byref(p), hist.ctypes.data, int(dev)))
+    return hist
+
+
+def net_save(net, path):
+    _check(lib.qxd_net_save(net, str(path).encode()))
+
+
+def net_load(lat, path):
+    out = _vp()
+    _check(lib.qxd_net_load(lat, str(path).encode(), C.byref(out)), lat)
+    return out.value

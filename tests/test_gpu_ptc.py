@@ -1,0 +1,117 @@
+"""The learned preconditioner on the GPU: network forward and gradient against the oracle,
+checkpointing, training, and flexible GCR with and without the network."""
+import numpy as np
+import pytest
+
+from oracle import qxd_oracle as O
+from paper_2502_02490_gb300 import synth
+from tests.gpu_util import Case, as_c128
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def qxd():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_02490_gb300 import qxd as q
+
+    return q
+
+
+def layer_weights(flat, chans):
+    out, off = [], 0
+    for ci, co in zip(chans[:-1], chans[1:]):
+        n = co * ci * 9 * 16
+        out.append(flat[off:off + n].reshape(co, ci, 9, 4, 4))
+        off += n
+    return out
+
+
+def random_flat(n, seed, scale=0.2):
+    r = np.random.default_rng(seed)
+    return scale * (r.standard_normal(n) + 1j * r.standard_normal(n))
+
+
+@pytest.mark.parametrize("L,cstar,chans", [((4, 2, 2, 4), False, [1, 3, 2, 1]), ((2, 2, 4, 2), True, [1, 4, 1]),
+                                           ((6, 4, 4, 6), False, [1, 16, 16, 1])])
+def test_net_forward_matches_oracle(qxd, L, cstar, chans):
+    c = Case(qxd, torch, L, cstar=cstar)
+    net = qxd.net_create(c.lat, chans, seed=1)
+    try:
+        w = random_flat(qxd.net_num_weights(net), 3)
+        qxd.net_set_weights(net, w)
+        w32 = w.real.astype(np.float32) + 1j * w.imag.astype(np.float32)  # the GPU holds FP32 weights
+        psi = synth.gaussian_spinor(c.dims, 11)
+        x = c.dev_tensor(psi)
+        y = torch.empty_like(x)
+        qxd.net_apply(net, y, x)
+        ref = O.ptc_net(c.lat_o, O.hop_links(c.U, c.A, c.q), layer_weights(w32, chans), psi)
+        got = as_c128(y, psi.shape)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-6
+    finally:
+        qxd.net_destroy(net)
+        c.close()
+
+
+def test_net_gradient_matches_oracle(qxd):
+    L, chans = (2, 2, 2, 4), [1, 2, 2, 1]
+    c = Case(qxd, torch, L)
+    net = qxd.net_create(c.lat, chans, seed=2)
+    try:
+        w = random_flat(qxd.net_num_weights(net), 5)
+        qxd.net_set_weights(net, w)
+        w32 = w.real.astype(np.float32) + 1j * w.imag.astype(np.float32)
+        vs = np.stack([synth.gaussian_spinor(c.dims, 40 + k) for k in range(2)])
+        bs = np.stack([synth.gaussian_spinor(c.dims, 50 + k) for k in range(2)])
+        loss, g = qxd.net_loss_grad(net, vs, bs, 2)
+        W = O.hop_links(c.U, c.A, c.q)
+        ws = layer_weights(w32, chans)
+        ref_loss = O.ptc_loss(c.lat_o, W, ws, list(bs), list(vs))
+        ref_g = np.concatenate([gl.ravel() for gl in O.ptc_loss_grad(c.lat_o, W, ws, list(bs), list(vs))])
+        assert abs(loss - ref_loss) < 1e-5 * ref_loss
+        assert np.linalg.norm(g - ref_g) / np.linalg.norm(ref_g) < 1e-5
+    finally:
+        qxd.net_destroy(net)
+        c.close()
+
+
+def test_net_checkpoint_roundtrip(qxd, tmp_path):
+    c = Case(qxd, torch, (2, 2, 2, 2))
+    net = qxd.net_create(c.lat, [1, 3, 1], seed=9)
+    try:
+        path = tmp_path / "net.qxdnet"
+        qxd.net_save(net, path)
+        net2 = qxd.net_load(c.lat, path)
+        assert np.array_equal(qxd.net_get_weights(net), qxd.net_get_weights(net2))
+        qxd.net_destroy(net2)
+    finally:
+        qxd.net_destroy(net)
+        c.close()
+
+
+def test_training_lowers_the_loss_and_fgcr_solves(qxd):
+    c = Case(qxd, torch, (4, 4, 4, 4), m0=-0.3)
+    net = qxd.net_create(c.lat, [1, 4, 4, 1], seed=3)
+    try:
+        vs = np.stack([synth.gaussian_spinor(c.dims, 100 + k) for k in range(8)])
+        hist = qxd.net_train(net, vs, 8, epochs=30, batch=4, lr=3e-3)
+        assert hist[-1] < 0.7 * hist[0], hist
+        eta = synth.gaussian_spinor(c.dims, 2000)
+        b = c.dev_tensor(eta)
+        res = {}
+        for name, n in (("net", net), ("none", None)):
+            x = torch.empty_like(b)
+            st, info = qxd.solve(c.lat, x, b, solver=qxd.SOLVER_MP_FGCR_NET, inner_prec=qxd.F32, tol=1e-10,
+                                 gcr_restart=16, net=n)
+            assert st == qxd.OK
+            assert O.true_rel_residual(c.op, as_c128(x, eta.shape), eta) <= 1e-10
+            res[name] = info["iters_inner"]
+        print("loss", hist[0], "->", hist[-1], "FGCR iterations with / without net:", res)
+    finally:
+        qxd.net_destroy(net)
+        c.close()
