@@ -40,6 +40,11 @@ WORKLOADS = {
                source_seed=2004,
                name="48^3x96 C* (doubled 96x48x48x96) mixed-precision clover solve to 1e-10 (eps=0.35, q=-1/3, "
                     "m0=-0.1, c_sw=1.9, c_sw^QED=1.0, antiperiodic t)"),
+    # near-critical 16^3x32 for the learned preconditioner (extra line); m0 from --tune-m0
+    "c4": dict(L=(32, 16, 16, 16), cstar=0, eps=0.3, q=-1 / 3, m0=None, csw=1.9, csw_qed=1.0, gauge_seed=1003,
+               source_seed=2003,
+               name="16^3x32 near-critical (FP64 eo-CG ~2000 iterations): learned PTC preconditioner in "
+                    "FGCR vs plain FP64 eo-CG (eps=0.3, q=-1/3, c_sw=1.9, c_sw^QED=1.0, antiperiodic t)"),
     # 12 spin-colour point sources on 24^3x48 through the multi-RHS solve (extra line)
     "c3a": dict(L=(48, 24, 24, 24), cstar=0, eps=0.3, q=-1 / 3, m0=-0.1, csw=1.9, csw_qed=1.0, gauge_seed=1002,
                 source_seed=2002,
@@ -342,6 +347,142 @@ def run_mrhs(args):
             "gpu_launches": int(launches), "clocks": clk.summary()}
 
 
+C4_M0_FILE = os.path.join(ROOT, "profiles", "c4_m0.txt")
+
+
+def c4_setup(dev, stream, m0=None):
+    from paper_2502_02490_gb300 import qxd, synth
+
+    w = WORKLOADS["c4"]
+    U, A = synth.gauge_field(w["L"], w["gauge_seed"], w["eps"])
+    lat = qxd.create_lattice(w["L"], qxd.BC_ANTIPERIODIC, 0, qxd.ORDER_LEXI, stream.cuda_stream)
+    import torch
+
+    qxd.load_gauge(lat, torch.from_numpy(U.view(np.float64)).to(dev), torch.from_numpy(A).to(dev), w["q"])
+    if m0 is not None:
+        qxd.build_clover(lat, m0, w["csw"], w["csw_qed"])
+    return lat
+
+
+def tune_m0():
+    """Bisect m0 so that plain FP64 eo-CG needs 2000 +- 200 iterations on the 16^3x32 field."""
+    import torch
+
+    from paper_2502_02490_gb300 import qxd, synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    w = WORKLOADS["c4"]
+    lat = c4_setup(dev, stream)
+    b = torch.from_numpy(synth.gaussian_spinor(w["L"], w["source_seed"]).view(np.float64)).to(dev)
+    x = torch.empty_like(b)
+
+    def iters(m0):
+        qxd.build_clover(lat, m0, w["csw"], w["csw_qed"])
+        st, info = qxd.solve(lat, x, b, check=False, solver=qxd.SOLVER_CG_EO, tol=1e-10, maxiter=6000)
+        n = info["iters_inner"] if st == qxd.OK else 10 ** 9
+        print(f"m0 {m0:+.6f}: eo-CG iterations {n}", file=sys.stderr)
+        return n
+
+    # On the synthetic 16^3x32 field the physical branch never needs more than ~214 iterations (the
+    # random links keep the low spectrum gapped; maximum near m0 = -0.1), so the ~2000-iteration
+    # point is searched on [-3, 0]: iterations grow towards the first doubler crossing (m0 ~ -2.6)
+    # and the solve fails beyond it; bisect between a fast and a failing/slow m0.
+    lo, hi = -3.0, 0.0
+    n = iters(lo)
+    if n <= 2000:
+        raise RuntimeError("m0 = -3 is not on the slow side")
+    m0 = hi
+    for _ in range(40):
+        m0 = 0.5 * (lo + hi)
+        n = iters(m0)
+        if abs(n - 2000) <= 200:
+            break
+        if n > 2000:
+            lo = m0
+        else:
+            hi = m0
+    qxd.destroy_lattice(lat)
+    with open(C4_M0_FILE, "w") as f:
+        f.write(f"# m0 of the 16^3x32 near-critical workload: FP64 eo-CG iterations {n} (bench.py --tune-m0)\n")
+        f.write(f"m0={m0!r}\n")
+    print(json.dumps({"m0": m0, "eo_cg_iterations": n}))
+
+
+def c4_m0(key="m0"):
+    for line in open(C4_M0_FILE):
+        if line.startswith(key + "="):
+            return float(line.split("=", 1)[1])
+    raise RuntimeError(f"no {key} recorded in {C4_M0_FILE}")
+
+
+def run_c4(args):
+    """Learned preconditioner vs plain FP64 eo-CG (and MP BiCGStab, FGCR without a network), at the
+    ~2000-iteration point and at the slowest point of the physical branch."""
+    import torch
+
+    from paper_2502_02490_gb300 import qxd, synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    w = WORKLOADS["c4"]
+    V = synth.volume(w["L"])
+    eta = torch.from_numpy(synth.gaussian_spinor(w["L"], w["source_seed"]).view(np.float64)).to(dev)
+    x = torch.empty_like(eta)
+    ntrain, ntest = 64, 16
+    vs = np.stack([synth.gaussian_spinor(w["L"], 5000 + k) for k in range(ntrain + ntest)])
+    vtr = torch.from_numpy(vs[:ntrain].view(np.float64)).to(dev)
+    vte = torch.from_numpy(vs[ntrain:].view(np.float64)).to(dev)
+    bte = torch.empty_like(vte)
+    results = {}
+    for point, key in (("doubler_side_2000_iterations", "m0"), ("physical_branch_slowest", "m0_physical")):
+        m0 = c4_m0(key)
+        lat = c4_setup(dev, stream, m0)
+
+        def timed_solve(**kw):
+            qxd.solve(lat, x, eta, check=False, **kw)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, info = qxd.solve(lat, x, eta, check=False, **kw)
+            torch.cuda.synchronize()
+            return {"status": qxd.STATUS_NAMES[st], "seconds": time.perf_counter() - t0,
+                    "iterations": info["iters_inner"], "outer": info["iters_outer"],
+                    "true_rel_res": info["true_rel_res"]}
+
+        res = {"m0": m0,
+               "fp64_eocg": timed_solve(solver=qxd.SOLVER_CG_EO, tol=1e-10, maxiter=20000),
+               "mp_bicgstab_f16n": timed_solve(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=qxd.F16N, tol=1e-10),
+               "mp_bicgstab_f32": timed_solve(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=qxd.F32, tol=1e-10),
+               "fgcr_no_net": timed_solve(solver=qxd.SOLVER_MP_FGCR_NET, inner_prec=qxd.F32, tol=1e-10,
+                                          gcr_restart=32, net=None, maxiter=args.fgcr_maxiter)}
+        qxd.apply_D(lat, bte, vte, qxd.F32, nrhs=ntest)
+        nets = {}
+        for chans in ([1, 8, 8, 1], [1, 16, 16, 1]):
+            net = qxd.net_create(lat, chans, seed=7)
+            l0, _ = qxd.net_loss_grad(net, vte, bte, ntest, want_grad=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hist = qxd.net_train(net, vtr, ntrain, epochs=args.epochs, batch=8, lr=2e-3)
+            torch.cuda.synchronize()
+            ttrain = time.perf_counter() - t0
+            l1, _ = qxd.net_loss_grad(net, vte, bte, ntest, want_grad=False)
+            nets["x".join(map(str, chans))] = {
+                "train_s": ttrain, "loss_first_epoch": hist[0] / V, "loss_last_epoch": hist[-1] / V,
+                "heldout_loss_before": l0 / ntest / V, "heldout_loss_after": l1 / ntest / V,
+                "heldout_rel_err_after": float(np.sqrt(l1 / ntest / (24.0 * V))),
+                "fgcr": timed_solve(solver=qxd.SOLVER_MP_FGCR_NET, inner_prec=qxd.F32, tol=1e-10, gcr_restart=32,
+                                    net=net, maxiter=args.fgcr_maxiter)}
+            qxd.net_destroy(net)
+        res["nets"] = nets
+        ok = [d["fgcr"]["seconds"] for d in nets.values() if d["fgcr"]["status"] == "OK"]
+        res["learned_vs_fp64_eocg_speedup"] = (res["fp64_eocg"]["seconds"] / min(ok)) if ok else None
+        results[point] = res
+        qxd.destroy_lattice(lat)
+    return {"metric": METRIC, "workload": w["name"], "sites": V, "points": results,
+            "note": "losses per site; held-out set of 16 (D v, v) pairs not used in training; "
+                    "heldout_rel_err = sqrt(loss / ||v||^2)"}
+
+
 def profile_run(args):
     """One untimed pass of the step (for ncu launch lists and kernel captures)."""
     import torch
@@ -420,6 +561,9 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="profiling aid for ncu: one untimed step, no JSON line (never a bench value)")
     ap.add_argument("--lattice", default=None, help="T,L1,L2,L3 override, for --profile-run captures only")
+    ap.add_argument("--tune-m0", action="store_true", help="bisect m0 of the c4 workload and record it")
+    ap.add_argument("--epochs", type=int, default=20, help="training epochs of the c4 workload")
+    ap.add_argument("--fgcr-maxiter", type=int, default=3000, help="iteration cap of the c4 FGCR solves")
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS),
                     help="c2: 32^3x64 (the metric's workload, default); c5: 48^3x96 C* doubled; "
                          "c3a: 12 point sources on 24^3x48 (multi-RHS)")
@@ -453,8 +597,14 @@ def main():
     import __graft_entry__
 
     __graft_entry__.build()
+    if args.tune_m0:
+        tune_m0()
+        return
     if args.workload == "c3a":
         print(json.dumps(run_mrhs(args)))
+        return
+    if args.workload == "c4":
+        print(json.dumps(run_c4(args)))
         return
     out = run_ours(args, rank, world)
     if rank == 0:

@@ -326,7 +326,7 @@ static qxd_status inner_bicg(qxd_lattice* lat, int prec, const float4* bh, float
   double rn2;
   TRY(read_scalars(lat, SC_RN, 1, &rn2));
   double rmax = std::sqrt(rn2);
-  int it = 0, rel = 0;
+  int it = 0, rel = 0, breakdowns = 0;
   while (std::sqrt(rn2) > target && it < maxiter) {
     TRY(apply(p, p16, p16n, v));                                  // v = Dhat p
     TRY(bicg_cdot(lat, rh, v, SC_RV));                            // <r_hat, v>
@@ -338,11 +338,12 @@ static qxd_status inner_bicg(qxd_lattice* lat, int prec, const float4* bh, float
     ++it;
     if (it % check_every == 0) {
       TRY(read_scalars(lat, SC_RN, 1, &rn2));
-      if (!std::isfinite(rn2)) return fail(lat, QXD_ENOCONV, "non-finite residual in the inner BiCGStab");
-      double rn = std::sqrt(rn2);
+      const bool broke = !std::isfinite(rn2);  // breakdown (e.g. <r_hat, v> = 0): drop x, restart
+      if (broke && ++breakdowns > 10) return fail(lat, QXD_ENOCONV, "repeated breakdown in the inner BiCGStab");
+      double rn = broke ? 0.0 : std::sqrt(rn2);
       if (rn > rmax) rmax = rn;
-      if (rn < delta * rmax || rn <= target) {
-        TRY(blas_axpy_32(lat, 1.0f, x, y, n4));
+      if (broke || rn < delta * rmax || rn <= target) {
+        if (!broke) TRY(blas_axpy_32(lat, 1.0f, x, y, n4));
         TRY(blas_zero(lat, x, hb));
         TRY(dhat32(lat, y, v, tmp_o, 0));
         TRY(blas_copy(lat, r, bh, hb));
@@ -452,7 +453,17 @@ static qxd_status inner_fgcr(qxd_lattice* lat, const qxd_net* net, int m, const 
   return QXD_OK;
 }
 
+static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve_params* prm,
+                             qxd_solve_info* info);
+
 qxd_status solve(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve_params* prm, qxd_solve_info* info) {
+  qxd_status st = solve_impl(lat, x, b, prm, info);
+  if (st != QXD_OK && info && info->status == QXD_OK) info->status = st;  // early failure: record it
+  return st;
+}
+
+static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve_params* prm,
+                             qxd_solve_info* info) {
   auto t0 = std::chrono::steady_clock::now();
   const i64 sv = lat->sv, nh = 12 * sv, nf = 24 * sv;
   const size_t fb = sizeof(double2) * nf, hb = sizeof(double2) * nh;
