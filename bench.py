@@ -50,9 +50,16 @@ WORKLOADS = {
                 source_seed=2002,
                 name="24^3x48 multi-RHS solve of the 12 spin-colour point sources to 1e-10 (FP32 inner, "
                      "eps=0.3, q=-1/3, m0=-0.1, c_sw=1.9, c_sw^QED=1.0, antiperiodic t)"),
+    # 8 independent lattices of uneven volume in one persistent batched solve (extra line)
+    "c3b": dict(L=None, cstar=0, eps=None, q=-1 / 3, m0=-0.1, csw=1.9, csw_qed=1.0, gauge_seed=1010, source_seed=2010,
+                lattices=[(16, 8, 8, 8), (20, 10, 10, 10), (16, 12, 12, 12), (24, 12, 12, 12), (28, 14, 14, 14),
+                          (16, 16, 16, 16), (24, 16, 16, 16), (32, 16, 16, 16)],
+                name="8 lattices 8^3x16 ... 16^3x32 (sum V = 469,056, eps = 0.2 + 0.3 i/7) solved to 1e-10 in one "
+                     "persistent cooperative launch per outer round (FP32 inner BiCGStab, FP64 outer, q=-1/3, "
+                     "m0=-0.1, c_sw=1.9, c_sw^QED=1.0, antiperiodic t)"),
 }
 WORKLOAD = dict(WORKLOADS["c2"])
-KSTAT = {0: "hop_f64", 1: "hop_f32", 2: "hop_f16n", 3: "hop_bf16n", 4: "hop_f32_mrhs"}
+KSTAT = {0: "hop_f64", 1: "hop_f32", 2: "hop_f16n", 3: "hop_bf16n", 4: "hop_f32_mrhs", 5: "batch_f32"}
 PREC_NAMES = {"f32": 1, "f16n": 2, "bf16n": 3}
 SOLVERS = {"cg": 1, "bicgstab": 2}  # qxd_solver: MP_CG_EO, MP_BICGSTAB_EO
 
@@ -347,6 +354,78 @@ def run_mrhs(args):
             "gpu_launches": int(launches), "clocks": clk.summary()}
 
 
+def run_batch(args):
+    """8 lattices of uneven volume solved together (one persistent kernel) vs one after another."""
+    import torch
+
+    from paper_2502_02490_gb300 import qxd, synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    w = WORKLOAD
+    lats, xs, bs = [], [], []
+    for i, L in enumerate(w["lattices"]):
+        eps = 0.2 + 0.3 * i / 7
+        U, A = synth.gauge_field(L, w["gauge_seed"] + i, eps)
+        lat = qxd.create_lattice(L, qxd.BC_ANTIPERIODIC, 0, qxd.ORDER_LEXI, stream.cuda_stream)
+        qxd.load_gauge(lat, torch.from_numpy(U.view(np.float64)).to(dev), torch.from_numpy(A).to(dev), w["q"])
+        qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
+        lats.append(lat)
+        bs.append(torch.from_numpy(synth.gaussian_spinor(L, w["source_seed"] + i).view(np.float64)).to(dev))
+        xs.append(torch.empty_like(bs[-1]))
+    p = qxd.default_params(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=qxd.F32, tol=1e-10)
+    for _ in range(args.warmup):  # the first call autotunes the tile shape
+        qxd.solve_batch(lats, xs, bs, params=p)
+    cfg = qxd.batch_last_config()
+    qxd.set_profiling(lats[0], 1)
+    n0 = qxd.launch_count(lats[0])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            st, infos = qxd.solve_batch(lats, xs, bs, params=p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    launches = qxd.launch_count(lats[0]) - n0
+    n_b, ms_b, b_b = qxd.kernel_stats(lats[0], 5)
+    qxd.set_profiling(lats[0], 0)
+    # the same 8 solves one after another (single-lattice MP BiCGStab, FP32 and 16-bit inner)
+    seq = {}
+    for name, prec in (("f32", qxd.F32), ("f16n", qxd.F16N)):
+        ps = qxd.default_params(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=prec, tol=1e-10)
+        for k in range(len(lats)):
+            qxd.solve(lats[k], xs[k], bs[k], params=ps)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for k in range(len(lats)):
+                qxd.solve(lats[k], xs[k], bs[k], params=ps)
+        torch.cuda.synchronize()
+        seq[name] = (time.perf_counter() - t0) / args.steps
+    for lat in lats:
+        qxd.destroy_lattice(lat)
+    peak, kind = measured_peaks()
+    achieved = b_b / (ms_b / 1e3) / 1e9 if ms_b else None
+    return {"metric": METRIC, "value": b_b / (t * args.steps) / 1e9, "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": w["name"], "lattices": [list(L) for L in w["lattices"]],
+                       "solver": "mp-bicgstab-batch", "tile": cfg,
+                       "l2": "inputs larger than L2: unique working set of the inner kernel ~0.47 GB (> 129 MB L2); no flush"},
+            "time_to_solution_s": t,
+            "solve": {"iters_inner": [i["iters_inner"] for i in infos], "iters_outer": infos[0]["iters_outer"],
+                      "true_rel_res": max(i["true_rel_res"] for i in infos)},
+            "sequential_single_lattice_s": seq, "speedup_vs_sequential_f32": seq["f32"] / t,
+            "speedup_vs_sequential_f16n": seq["f16n"] / t,
+            "roofline": {"bound": "hbm", "kernel": "batch_f32", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None, "peak_kind": f"{kind} hbm_gbs",
+                         "traffic": None, "launches": n_b, "avg_launch_ms": ms_b / n_b if n_b else None,
+                         "bytes_per_site_iteration": 6144},
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+
+
 C4_M0_FILE = os.path.join(ROOT, "profiles", "c4_m0.txt")
 
 
@@ -566,7 +645,8 @@ def main():
     ap.add_argument("--fgcr-maxiter", type=int, default=3000, help="iteration cap of the c4 FGCR solves")
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS),
                     help="c2: 32^3x64 (the metric's workload, default); c5: 48^3x96 C* doubled; "
-                         "c3a: 12 point sources on 24^3x48 (multi-RHS)")
+                         "c3a: 12 point sources on 24^3x48 (multi-RHS); c3b: 8 uneven lattices in one batched solve; "
+                         "c4: learned preconditioner on 16^3x32")
     args = ap.parse_args()
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[args.workload])
@@ -605,6 +685,9 @@ def main():
         return
     if args.workload == "c4":
         print(json.dumps(run_c4(args)))
+        return
+    if args.workload == "c3b":
+        print(json.dumps(run_batch(args)))
         return
     out = run_ours(args, rank, world)
     if rank == 0:

@@ -175,6 +175,27 @@ qxd_status qxd_solve(qxd_lattice *lat, double *x, const double *b, const qxd_sol
 qxd_status qxd_solve_mrhs(qxd_lattice *lat, double *x, const double *b, int nrhs,
                           const qxd_solve_params *params, qxd_solve_info *info);
 
+/* Solve D_k x_k = b_k for n <= 16 independent lattices (uneven volumes allowed) in one go: per
+ * lattice the FP64 outer defect correction of MP_BICGSTAB_EO, and ONE cooperative persistent
+ * kernel running the FP32 inner BiCGStab of all lattices together over a work list of site
+ * tiles, with bounded-wait grid barriers (QXD_ETIMEOUT if one expires; nothing hangs).  The
+ * inner launch is captured in a CUDA graph and replayed every outer round; the tile shape is
+ * autotuned on the first call for a set of volumes and remembered.  lats must share one stream
+ * and have their clover built; x[k], b[k] are DEVICE fields [V_k][4][3][2] (params->on_device
+ * must be 1); info: n entries (iters_inner per lattice, iters_outer the batch's rounds).  params:
+ * tol, maxiter (caps the largest lattice's inner iterations), inner_tol, max_outer as for
+ * qxd_solve (solver and inner_prec are implied).  The paper solves one lattice at a time; the
+ * batch is a throughput layer over the same even-odd mixed-precision solve (Sec. 3, Sec. 5.1). */
+qxd_status qxd_solve_batch(qxd_lattice *const *lats, int n, double *const *x, const double *const *b,
+                           const qxd_solve_params *params, qxd_solve_info *info);
+/* Iteration limit of the persistent kernel's barrier spin-waits (default 2e7, about 1.3 s);
+ * a tiny limit makes the waits run out (QXD_ETIMEOUT), for tests of that path. */
+qxd_status qxd_batch_set_spin_limit(long long limit);
+/* Tile shape and graph use of the last qxd_solve_batch: threads per block, sites per thread,
+ * resident blocks per SM of the persistent kernel (1 or 2), graph = 1 if the inner launch ran
+ * from a captured CUDA graph. */
+qxd_status qxd_batch_last_config(int *threads, int *sites_per_thread, int *blocks_per_sm, int *graph);
+
 /* Fill *p with the defaults: MP_CG_EO, tol 1e-10, maxiter 100000, inner F32, inner_tol 1e-5,
  * reliable_delta 0.1, max_outer 20, on_device 1, check_every 1, gcr_restart 16, net NULL. */
 void qxd_default_params(qxd_solve_params *p);
@@ -256,7 +277,8 @@ qxd_status qxd_vec_dot_noalloc(const double *a, const double *b, int64_t n, doub
 
 /* Kernel timing.  With profiling on, the library brackets each launch of its hop kernels with
  * CUDA events on the lattice stream; qxd_kernel_stats returns, for the kernel class `which`
- * (0 = FP64 hop, 1 = FP32 hop, 2 = FP16N hop, 3 = BF16N hop, 4 = FP32 multi-RHS hop), the number of
+ * (0 = FP64 hop, 1 = FP32 hop, 2 = FP16N hop, 3 = BF16N hop, 4 = FP32 multi-RHS hop, 5 = the
+ * persistent batch kernel of qxd_solve_batch, counted on the batch's first lattice), the number of
  * timed launches, their
  * summed device time in ms and the summed algorithmic bytes they moved.  Reading the stats
  * synchronises the stream.  qxd_launch_count is the number of kernels the library launched. */

@@ -75,6 +75,10 @@ void prof_end(qxd_lattice* lat) {
   lat->ev_used++;
 }
 
+void prof_set_last_bytes(qxd_lattice* lat, double bytes) {
+  if (lat->profiling && lat->ev_used > 0) lat->ev_bytes[lat->ev_used - 1] = bytes;
+}
+
 static qxd_status prof_flush(qxd_lattice* lat) {
   if (lat->ev_used == 0) return QXD_OK;
   QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
@@ -138,6 +142,7 @@ void qxd_default_params(qxd_solve_params* p) {
 qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
   if (!lat) return QXD_OK;
   if (lat->stream) cudaStreamSynchronize(lat->stream);
+  if (lat->batch && lat->batch_release) lat->batch_release(lat->batch);
   void* bufs[] = {lat->U,    lat->A,     lat->W64,   lat->W32,   lat->W16,   lat->WB16,  lat->C64,
                   lat->Ci64, lat->C32,   lat->Ci32,  lat->C16,   lat->Ci16,  lat->C16n,  lat->Ci16n,
                   lat->CB16, lat->CiB16, lat->CB16n, lat->CiB16n, lat->red,  lat->ticket, lat->scal};

@@ -503,7 +503,7 @@ __device__ __forceinline__ void herm6_apply(const R r[36], const cplx<R> x[6], c
 // ------------------------------------------------------------------------------------------
 // The lattice object (host side)
 // ------------------------------------------------------------------------------------------
-enum { KSTAT_F64 = 0, KSTAT_F32 = 1, KSTAT_F16N = 2, KSTAT_BF16N = 3, KSTAT_F32_MRHS = 4, KSTAT_N = 5 };
+enum { KSTAT_F64 = 0, KSTAT_F32 = 1, KSTAT_F16N = 2, KSTAT_BF16N = 3, KSTAT_F32_MRHS = 4, KSTAT_BATCH = 5, KSTAT_N = 6 };
 
 // Device scalar slots used by the solvers and reductions.
 enum {
@@ -523,6 +523,9 @@ struct Field64 {  // FP64 full field: two parities of double2 [12][sv]
 
 struct qxd_lattice {
   qxd::Geom g;
+  // device state of qxd_solve_batch when this lattice leads a batch (freed with the lattice)
+  void* batch = nullptr;
+  void (*batch_release)(void*) = nullptr;
   int Lphys[4];
   int tbc, cstar, order;
   qxd::i64 V, Vh, sv, Vphys;
@@ -705,6 +708,7 @@ qxd_status bicg_copy(qxd_lattice* lat, const float4* r, float4* p, uint2* p16, f
 // ---- profiling helpers (api.cu) ----
 void prof_begin(qxd_lattice* lat, int kind, double bytes);
 void prof_end(qxd_lattice* lat);
+void prof_set_last_bytes(qxd_lattice* lat, double bytes);  // bytes of the last timed launch, known after it ran
 
 // ---- solver.cu ----
 qxd_status solve(qxd_lattice* lat, double2* x_field, const double2* b_field, const qxd_solve_params* p,

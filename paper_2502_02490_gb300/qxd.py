@@ -66,6 +66,9 @@ _SIGS = {
     "qxd_vec_axpy": [_vp, _d, _d, _vp, _vp, _i64],
     "qxd_vec_dot_noalloc": [_vp, _vp, _i64, _vp, _vp],
     "qxd_set_profiling": [_vp, _i],
+    "qxd_solve_batch": [_vp, _i, _vp, _vp, C.POINTER(SolveParams), _vp],
+    "qxd_batch_last_config": [C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
+    "qxd_batch_set_spin_limit": [C.c_longlong],
     "qxd_net_create": [_vp, _i, C.POINTER(C.c_int), C.c_uint64, C.POINTER(_vp)],
     "qxd_net_destroy": [_vp],
     "qxd_net_set_weights": [_vp, _vp],
@@ -308,3 +311,30 @@ def net_load(lat, path):
     out = _vp()
     _check(lib.qxd_net_load(lat, str(path).encode(), C.byref(out)), lat)
     return out.value
+
+
+# ---- batched persistent solve ----
+def solve_batch(lats, xs, bs, params=None, check=True, **kw):
+    """qxd_solve_batch over device fields xs[k], bs[k]; returns (status, list of info dicts)."""
+    n = len(lats)
+    p = params if params is not None else default_params(**kw)
+    p.on_device = 1
+    L = (C.c_void_p * n)(*lats)
+    X = (C.c_void_p * n)(*[_ptr(x)[0] for x in xs])
+    B = (C.c_void_p * n)(*[_ptr(b)[0] for b in bs])
+    infos = (SolveInfo * n)()
+    st = lib.qxd_solve_batch(C.cast(L, C.c_void_p), n, C.cast(X, C.c_void_p), C.cast(B, C.c_void_p), C.byref(p),
+                             C.cast(infos, C.c_void_p))
+    if check:
+        _check(st, lats[0])
+    return st, [i.as_dict() for i in infos]
+
+
+def batch_last_config():
+    t, s, m, g = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(lib.qxd_batch_last_config(C.byref(t), C.byref(s), C.byref(m), C.byref(g)))
+    return {"threads": t.value, "sites_per_thread": s.value, "blocks_per_sm": m.value, "graph": bool(g.value)}
+
+
+def batch_set_spin_limit(limit):
+    _check(lib.qxd_batch_set_spin_limit(int(limit)))
