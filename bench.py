@@ -73,10 +73,22 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def recorded_traffic(kernel, lattice):
-    """DRAM bytes per launch from the committed ncu record, or None if the hop sources changed."""
+HOP_SOURCES = ("dslash.cu", "hop_site.cuh", "hop_common.cuh", "qxd_internal.cuh")
+
+
+def hop_source_hash():
+    """sha256 over the sources that define the hop kernels (the key of the traffic record)."""
     import hashlib
 
+    h = hashlib.sha256()
+    for f in HOP_SOURCES:
+        with open(os.path.join(ROOT, "paper_2502_02490_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel, lattice):
+    """DRAM bytes per launch from the committed ncu record, or None if the hop sources changed."""
     rec = {}
     try:
         for line in open(os.path.join(ROOT, "profiles", "roofline_traffic.txt")):
@@ -85,11 +97,7 @@ def recorded_traffic(kernel, lattice):
                 rec[k] = v
     except OSError:
         return None
-    h = hashlib.sha256()
-    for f in ("dslash.cu", "qxd_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2502_02490_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    if (rec.get("kernel") != kernel or rec.get("source_sha256") != h.hexdigest()
+    if (rec.get("kernel") != kernel or rec.get("source_sha256") != hop_source_hash()
             or rec.get("lattice") != ",".join(str(v) for v in lattice)):
         return None
     return float(rec["bytes_per_launch"])
