@@ -59,7 +59,8 @@ WORKLOADS = {
                      "m0=-0.1, c_sw=1.9, c_sw^QED=1.0, antiperiodic t)"),
 }
 WORKLOAD = dict(WORKLOADS["c2"])
-KSTAT = {0: "hop_f64", 1: "hop_f32", 2: "hop_f16n", 3: "hop_bf16n", 4: "hop_f32_mrhs", 5: "batch_f32"}
+KSTAT = {0: "hop_f64", 1: "hop_f32", 2: "hop_f16n", 3: "hop_bf16n", 4: "hop_f32_mrhs", 5: "batch_f32",
+         6: "ptc_layer_bf16_tc", 7: "ptc_layer_f32"}
 PREC_NAMES = {"f32": 1, "f16n": 2, "bf16n": 3}
 SOLVERS = {"cg": 1, "bicgstab": 2}  # qxd_solver: MP_CG_EO, MP_BICGSTAB_EO
 

@@ -102,7 +102,7 @@ typedef struct {
   int max_outer;          /* cap on outer (defect-correction) rounds */
   int on_device;          /* x and b are device (1) or host (0) pointers */
   int check_every;        /* read the residual norm back every this many iterations (>= 1) */
-  int gcr_restart;        /* FGCR restart length (MP_FGCR_NET), 1..64 */
+  int gcr_restart;        /* FGCR restart length (MP_FGCR_NET), 1..32 */
   const qxd_net *net;     /* preconditioner of MP_FGCR_NET, or NULL */
 } qxd_solve_params;
 
@@ -218,7 +218,7 @@ qxd_status qxd_vec_axpy(qxd_lattice *lat, double re, double im, const double *x,
  * boundary conditions of the lattice; gauge-equivariant by construction) and Omega a complex
  * 4x4 spin matrix per (output channel, input channel, path).  The network is the chain of
  * nlayers linear layers with channel counts channels[0..nlayers] (first and last 1, others
- * 1..16).  FP32 weights and activations.  Weights are laid out [layer][Cout][Cin][9][4][4] complex
+ * 1..16).  FP32 weights.  Weights are laid out [layer][Cout][Cin][9][4][4] complex
  * (interleaved re, im doubles at the boundary).  The paper has no learned part; this follows the
  * method's learned-preconditioner extension.
  * create: weights initialised from `seed` (identity path near 1/4, small noise elsewhere). */
@@ -228,7 +228,15 @@ qxd_status qxd_net_destroy(qxd_net *net);
 int64_t qxd_net_num_weights(const qxd_net *net); /* complex weights */
 qxd_status qxd_net_set_weights(qxd_net *net, const double *w); /* host [n][2] */
 qxd_status qxd_net_get_weights(const qxd_net *net, double *w);
-/* out = M in on full fields [V][4][3][2] (FP32 arithmetic). */
+/* Inference precision of qxd_net_apply and of the network inside QXD_SOLVER_MP_FGCR_NET:
+ * QXD_NET_BF16_TC (default): each layer's channel mix on the tensor cores (tcgen05), BF16
+ *   transported activations and weights, FP32 accumulation and FP32 activations between layers;
+ * QXD_NET_F32: FP32 on the CUDA cores.  Training (qxd_net_loss_grad, qxd_net_train) always runs
+ * in FP32.  QXD_ETIMEOUT from qxd_net_apply if a bounded wait of the tensor-core kernel expired. */
+#define QXD_NET_F32 0
+#define QXD_NET_BF16_TC 1
+qxd_status qxd_net_set_precision(qxd_net *net, int prec);
+/* out = M in on full fields [V][4][3][2]. */
 qxd_status qxd_net_apply(qxd_net *net, double *out, const double *in, int on_device);
 /* loss = sum_i ||M(b_i) - v_i||^2 over nsamp samples ([nsamp][V][4][3][2] each) and, if grad is
  * non-NULL, grad = dloss/d(conj w) (host [n][2]; the real-parameter gradient is twice its real
@@ -278,8 +286,9 @@ qxd_status qxd_vec_dot_noalloc(const double *a, const double *b, int64_t n, doub
 /* Kernel timing.  With profiling on, the library brackets each launch of its hop kernels with
  * CUDA events on the lattice stream; qxd_kernel_stats returns, for the kernel class `which`
  * (0 = FP64 hop, 1 = FP32 hop, 2 = FP16N hop, 3 = BF16N hop, 4 = FP32 multi-RHS hop, 5 = the
- * persistent batch kernel of qxd_solve_batch, counted on the batch's first lattice), the number of
- * timed launches, their
+ * persistent batch kernel of qxd_solve_batch, counted on the batch's first lattice, 6 = tensor-core
+ * PTC layer, 7 = FP32 PTC layer; bytes of a PTC layer: input channels, links and output channels
+ * once per site), the number of timed launches, their
  * summed device time in ms and the summed algorithmic bytes they moved.  Reading the stats
  * synchronises the stream.  qxd_launch_count is the number of kernels the library launched. */
 qxd_status qxd_set_profiling(qxd_lattice *lat, int on);

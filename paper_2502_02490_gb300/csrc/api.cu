@@ -33,7 +33,7 @@ qxd_status cuda_fail(qxd_lattice* lat, cudaError_t e, const char* where) {
 }
 
 qxd_status ensure_work(qxd_lattice* lat, int slot, size_t bytes, void** out) {
-  if (slot < 0 || slot >= 40) return fail(lat, QXD_EINVAL, "bad work slot");
+  if (slot < 0 || slot >= QXD_WORK_SLOTS) return fail(lat, QXD_EINVAL, "bad work slot");
   if (lat->work_bytes[slot] < bytes) {
     if (lat->work[slot]) {
       QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
@@ -148,7 +148,7 @@ qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
                   lat->CB16, lat->CiB16, lat->CB16n, lat->CiB16n, lat->red,  lat->ticket, lat->scal};
   for (void* b : bufs)
     if (b) cudaFree(b);
-  for (int i = 0; i < 40; ++i)
+  for (int i = 0; i < QXD_WORK_SLOTS; ++i)
     if (lat->work[i]) cudaFree(lat->work[i]);
   void* mr[] = {lat->mr_red, lat->mr_ticket, lat->mr_scal};
   for (void* b : mr)
@@ -390,8 +390,8 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
   if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO && p->solver != QXD_SOLVER_MP_BICGSTAB_EO &&
       p->solver != QXD_SOLVER_MP_FGCR_NET)
     return fail(lat, QXD_EINVAL, "bad solver");
-  if (p->solver == QXD_SOLVER_MP_FGCR_NET && (p->gcr_restart < 1 || p->gcr_restart > 64))
-    return fail(lat, QXD_EINVAL, "gcr_restart must be 1..64");
+  if (p->solver == QXD_SOLVER_MP_FGCR_NET && (p->gcr_restart < 1 || p->gcr_restart > 32))
+    return fail(lat, QXD_EINVAL, "gcr_restart must be 1..32");
   if (!(p->tol > 0) || p->maxiter <= 0) return fail(lat, QXD_EINVAL, "tol must be > 0 and maxiter > 0");
   if (p->solver != QXD_SOLVER_CG_EO && (p->inner_prec < QXD_F32 || p->inner_prec > QXD_BF16N))
     return fail(lat, QXD_EINVAL, "inner_prec must be F32, F16N or BF16N");

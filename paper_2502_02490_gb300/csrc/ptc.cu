@@ -298,6 +298,13 @@ struct qxd_net {
   float4* act[9] = {nullptr};   // activations of one sample (layer inputs/outputs)
   float4* gbuf[2] = {nullptr};  // gradient ping-pong buffers (max channels)
   int maxc = 1;
+  // inference precision: QXD_NET_BF16_TC (tensor-core channel mix) or QXD_NET_F32
+  int prec = QXD_NET_BF16_TC;
+  unsigned char* bp = nullptr;  // packed BF16 weights of every layer (tensor-core layout)
+  i64 bpoff[9] = {0};           // byte offset of each layer's packed weights
+  bool bp_valid = false;        // packed weights match w
+  int* tc_err = nullptr;        // error word of the tensor-core kernel
+  float4* tc_scratch = nullptr; // virtual channels of pull-form layers
 };
 
 namespace qxd {
@@ -318,20 +325,44 @@ static qxd_status layer_fwd(qxd_net* net, int l, const float4* in, float4* out, 
     Om = net->wadj;
   }
   dim3 grid((unsigned)((lat->Vh + PT_SITES - 1) / PT_SITES), 2), block(PT_SITES, co);
+  prof_begin(lat, KSTAT_PTC_F32, (96.0 * (ci + co) + 576.0) * (double)lat->V);
   k_ptc_layer<<<grid, block, 0, lat->stream>>>(lat->g, ci, co, in, Om, lat->W32, out);
+  prof_end(lat);
   QXD_CHECK_LAUNCH(lat, "k_ptc_layer");
   return QXD_OK;
 }
 
-// M(in) for one-channel full FP32 fields; uses net->act as scratch
+// M(in) for one-channel full FP32 fields; uses net->act as scratch.  With QXD_NET_BF16_TC the
+// layers run on the tensor cores (weights packed once per weight update).
 qxd_status net_apply32(qxd_net* net, const float4* in, float4* out) {
+  qxd_status st;
+  if (net->prec == QXD_NET_BF16_TC && !net->bp_valid) {
+    for (int l = 0; l < net->nlayers; ++l)
+      if ((st = ptc_pack_weights(net->lat, net->ch[l], net->ch[l + 1], net->w + net->woff[l], net->bp + net->bpoff[l])))
+        return st;
+    net->bp_valid = true;
+  }
   const float4* h = in;
   for (int l = 0; l < net->nlayers; ++l) {
     float4* o = (l == net->nlayers - 1) ? out : net->act[l + 1];
-    qxd_status st = layer_fwd(net, l, h, o, false);
+    if (net->prec == QXD_NET_BF16_TC)
+      st = ptc_layer_tc(net->lat, net->ch[l], net->ch[l + 1], h, net->bp + net->bpoff[l], o, net->tc_scratch,
+                        net->tc_err);
+    else
+      st = layer_fwd(net, l, h, o, false);
     if (st) return st;
     h = o;
   }
+  return QXD_OK;
+}
+
+// error word of the tensor-core kernel (synchronises the lattice stream)
+qxd_status net_check(qxd_net* net) {
+  if (!net || net->prec != QXD_NET_BF16_TC) return QXD_OK;
+  int e = 0;
+  QXD_CUDA(net->lat, cudaMemcpyAsync(&e, net->tc_err, sizeof(int), cudaMemcpyDeviceToHost, net->lat->stream));
+  QXD_CUDA(net->lat, cudaStreamSynchronize(net->lat->stream));
+  if (e) return fail(net->lat, QXD_ETIMEOUT, "a bounded wait of the tensor-core PTC layer expired");
   return QXD_OK;
 }
 
@@ -408,7 +439,18 @@ qxd_status qxd_net_create(qxd_lattice* lat, int nlayers, const int* channels, ui
             cudaMalloc(&net->grad, sizeof(double2) * off) == cudaSuccess &&
             cudaMalloc(&net->am, sizeof(float2) * off) == cudaSuccess &&
             cudaMalloc(&net->av, sizeof(float2) * off) == cudaSuccess &&
-            cudaMalloc(&net->part, sizeof(float2) * PT_MAXC * PT_MAXC * 9 * 16 * WG_BLOCKS) == cudaSuccess;
+            cudaMalloc(&net->part, sizeof(float2) * PT_MAXC * PT_MAXC * 9 * 16 * WG_BLOCKS) == cudaSuccess &&
+            cudaMalloc(&net->tc_err, sizeof(int)) == cudaSuccess;
+  i64 bpb = 0;
+  for (int l = 0; l < nlayers; ++l) {
+    net->bpoff[l] = bpb;
+    bpb += (i64)ptc_tc_packed_bytes(channels[l], channels[l + 1]);
+  }
+  ok = ok && cudaMalloc(&net->bp, (size_t)bpb) == cudaSuccess;
+  size_t scr = 0;
+  for (int l = 0; l < nlayers; ++l) scr = std::max(scr, ptc_tc_pull_scratch(channels[l], channels[l + 1], lat->sv));
+  if (scr) ok = ok && cudaMalloc(&net->tc_scratch, sizeof(float4) * scr) == cudaSuccess;
+  if (ok) cudaMemsetAsync(net->tc_err, 0, sizeof(int), lat->stream);
   for (int l = 1; l <= nlayers && ok; ++l) ok = cudaMalloc(&net->act[l], sizeof(float4) * cs * channels[l]) == cudaSuccess;
   for (int k = 0; k < 2 && ok; ++k) ok = cudaMalloc(&net->gbuf[k], sizeof(float4) * cs * net->maxc) == cudaSuccess;
   if (!ok) {
@@ -446,7 +488,8 @@ qxd_status qxd_net_create(qxd_lattice* lat, int nlayers, const int* channels, ui
 qxd_status qxd_net_destroy(qxd_net* net) {
   if (!net) return QXD_OK;
   if (net->lat) cudaStreamSynchronize(net->lat->stream);
-  void* b[] = {net->w, net->wadj, net->grad, net->am, net->av, net->part, net->gbuf[0], net->gbuf[1]};
+  void* b[] = {net->w, net->wadj, net->grad, net->am, net->av, net->part, net->gbuf[0], net->gbuf[1], net->bp,
+               net->tc_err, net->tc_scratch};
   for (void* p : b)
     if (p) cudaFree(p);
   for (int l = 1; l <= net->nlayers; ++l)
@@ -498,6 +541,7 @@ qxd_status qxd_net_apply(qxd_net* net, double* out, const double* in, int on_dev
   b = a + 12 * lat->sv;
   if ((st = to_internal32(lat, in, on_device, a))) return st;
   if ((st = net_apply32(net, a, b))) return st;
+  if ((st = net_check(net))) return st;
   return from_internal32(lat, b, on_device, out);
 }
 
@@ -561,6 +605,7 @@ qxd_status qxd_net_train(qxd_net* net, const double* v, int nsamp, const qxd_tra
       k_adam<<<ew_grid(net->nw), 256, 0, lat->stream>>>((int)net->nw, net->w, net->grad, net->am, net->av,
                                                         (float)p->lr, b1, b2, eps, c1, c2, 1.f / (float)(s1 - s0));
       QXD_CHECK_LAUNCH(lat, "k_adam");
+      net->bp_valid = false;
     }
     if (loss_hist) loss_hist[e] = epoch_loss / nsamp;
   }
@@ -628,6 +673,14 @@ qxd_status qxd_net_set_weights(qxd_net* net, const double* w) {
   for (i64 i = 0; i < net->nw; ++i) h[i] = make_float2((float)w[2 * i], (float)w[2 * i + 1]);
   QXD_CUDA(net->lat, cudaMemcpyAsync(net->w, h.data(), sizeof(float2) * net->nw, cudaMemcpyHostToDevice, net->lat->stream));
   QXD_CUDA(net->lat, cudaStreamSynchronize(net->lat->stream));
+  net->bp_valid = false;
+  return QXD_OK;
+}
+
+qxd_status qxd_net_set_precision(qxd_net* net, int prec) {
+  if (!net) return QXD_EINVAL;
+  if (prec != QXD_NET_F32 && prec != QXD_NET_BF16_TC) return fail(net->lat, QXD_EINVAL, "unknown net precision");
+  net->prec = prec;
   return QXD_OK;
 }
 

@@ -503,7 +503,17 @@ __device__ __forceinline__ void herm6_apply(const R r[36], const cplx<R> x[6], c
 // ------------------------------------------------------------------------------------------
 // The lattice object (host side)
 // ------------------------------------------------------------------------------------------
-enum { KSTAT_F64 = 0, KSTAT_F32 = 1, KSTAT_F16N = 2, KSTAT_BF16N = 3, KSTAT_F32_MRHS = 4, KSTAT_BATCH = 5, KSTAT_N = 6 };
+enum {
+  KSTAT_F64 = 0,
+  KSTAT_F32 = 1,
+  KSTAT_F16N = 2,
+  KSTAT_BF16N = 3,
+  KSTAT_F32_MRHS = 4,
+  KSTAT_BATCH = 5,
+  KSTAT_PTC_TC = 6,   // tensor-core PTC layer
+  KSTAT_PTC_F32 = 7,  // FP32 CUDA-core PTC layer
+  KSTAT_N = 8
+};
 
 // Device scalar slots used by the solvers and reductions.
 enum {
@@ -521,6 +531,10 @@ struct Field64 {  // FP64 full field: two parities of double2 [12][sv]
 
 }  // namespace qxd
 
+// device work buffers owned by a lattice (allocated on first use, grown on demand): slots 0..28 the
+// single-RHS solvers, 24..27 API staging, 29 and 31 FGCR vectors (31 also the training set), 30 the
+// clover singular flag, 32..38 multi-RHS, 39 network application, 40 FGCR coefficients
+#define QXD_WORK_SLOTS 48
 struct qxd_lattice {
   qxd::Geom g;
   // device state of qxd_solve_batch when this lattice leads a batch (freed with the lattice)
@@ -576,8 +590,8 @@ struct qxd_lattice {
   size_t stage_bytes = 0;
   // work buffers (lazily allocated): slots 0..23 and 28 solver, 24..27 API staging fields, 30 clover flag,
   // 32..39 multi-RHS fields
-  void* work[40] = {nullptr};
-  size_t work_bytes[40] = {0};
+  void* work[QXD_WORK_SLOTS] = {nullptr};
+  size_t work_bytes[QXD_WORK_SLOTS] = {0};
 
   // profiling
   bool profiling = false;
@@ -717,6 +731,12 @@ qxd_status solve(qxd_lattice* lat, double2* x_field, const double2* b_field, con
 qxd_status apply_D64(qxd_lattice* lat, const double2* in, double2* out);
 // ---- ptc.cu ----
 qxd_status net_apply32(qxd_net* net, const float4* in, float4* out);  // full FP32 fields
+qxd_status net_check(qxd_net* net);  // error word of the tensor-core layers (synchronises)
+size_t ptc_tc_packed_bytes(int cin, int cout);
+qxd_status ptc_pack_weights(qxd_lattice* lat, int cin, int cout, const float2* Om, void* Bp);
+size_t ptc_tc_pull_scratch(int cin, int cout, i64 sv);  // float4s of the pull form's virtual channels
+qxd_status ptc_layer_tc(qxd_lattice* lat, int cin, int cout, const float4* in, const void* Bp, float4* out,
+                        float4* scratch, int* err);
 // ---- solver_mrhs.cu ----
 qxd_status solve_mrhs(qxd_lattice* lat, double2* x, const double2* b, int n, const qxd_solve_params* p,
                       qxd_solve_info* info);

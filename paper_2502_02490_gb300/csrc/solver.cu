@@ -362,96 +362,9 @@ static qxd_status inner_bicg(qxd_lattice* lat, int prec, const float4* bh, float
   return QXD_OK;
 }
 
-// ------------------------------------------------------------------------------------------
-// Flexible GCR on the full D in FP32 with the learned network as right preconditioner:
-//   z_k = M r;  w_k = D z_k;  w_k, z_k orthogonalised against w_j (j < k) and normalised;
-//   alpha = <w_k, r>;  x += alpha z_k;  r -= alpha w_k;  restart after m steps (x, r kept).
-// Solves D e = rhs to ||rhs - D e|| <= target; e accumulates into y (full FP32 field).
-// ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_cdot_flat(const float4* __restrict__ a, const float4* __restrict__ b, i64 n4,
-                                                   double* red, unsigned int* ticket, double* scal, int slot) {
-  double v[2] = {0.0, 0.0};
-  for (i64 i = blockIdx.x * (i64)256 + threadIdx.x; i < n4; i += (i64)gridDim.x * 256) {
-    float4 x = a[i], y = b[i];
-    v[0] += (double)(x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w);
-    v[1] += (double)(x.x * y.y - x.y * y.x + x.z * y.w - x.w * y.z);
-  }
-  block_sum<2, 256>(v);
-  finish_reduce<2, 256>(v, red, ticket, scal, slot);
-}
-
-// y += (ar + i ai) x over n4 float4 (pairs of complex numbers)
-__global__ void k_caxpy_flat(float ar, float ai, const float4* __restrict__ x, float4* __restrict__ y, i64 n4) {
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n4; i += (i64)gridDim.x * blockDim.x) {
-    float4 u = x[i], v = y[i];
-    y[i] = make_float4(v.x + ar * u.x - ai * u.y, v.y + ar * u.y + ai * u.x, v.z + ar * u.z - ai * u.w,
-                       v.w + ar * u.w + ai * u.z);
-  }
-}
-
-static int flat_grid(qxd_lattice* lat, i64 n4) {
-  i64 b = (n4 + 255) / 256;
-  if (b > lat->red_blocks) b = lat->red_blocks;
-  return (int)(b < 1 ? 1 : b);
-}
-
-static qxd_status cdot_flat(qxd_lattice* lat, const float4* a, const float4* b, i64 n4, double out[2]) {
-  k_cdot_flat<<<flat_grid(lat, n4), 256, 0, lat->stream>>>(a, b, n4, lat->red, lat->ticket, lat->scal, SC_TMP2);
-  QXD_CHECK_LAUNCH(lat, "k_cdot_flat");
-  return read_scalars(lat, SC_TMP2, 2, out);
-}
-
-static qxd_status caxpy_flat(qxd_lattice* lat, double ar, double ai, const float4* x, float4* y, i64 n4) {
-  k_caxpy_flat<<<flat_grid(lat, n4), 256, 0, lat->stream>>>((float)ar, (float)ai, x, y, n4);
-  QXD_CHECK_LAUNCH(lat, "k_caxpy_flat");
-  return QXD_OK;
-}
-
-static qxd_status inner_fgcr(qxd_lattice* lat, const qxd_net* net, int m, const float4* rhs, float4* y, double target,
-                             int maxiter, int* iters) {
-  const i64 sv = lat->sv, n4 = 12 * sv;
-  const size_t fb = sizeof(float4) * n4;
-  float4 *r, *Z;
-  TRY(get(lat, 29, fb, &r));
-  TRY(get(lat, 31, fb * 2 * m, &Z));
-  auto z = [&](int k) { return Z + (i64)k * n4; };
-  auto w = [&](int k) { return Z + (i64)(m + k) * n4; };
-  TRY(blas_copy(lat, r, rhs, fb));
-  double d[2];
-  TRY(cdot_flat(lat, r, r, n4, d));
-  double rn = std::sqrt(d[0]);
-  int it = 0, k = 0;
-  while (rn > target && it < maxiter) {
-    if (net)
-      TRY(net_apply32(const_cast<qxd_net*>(net), r, z(k)));
-    else
-      TRY(blas_copy(lat, z(k), r, fb));
-    TRY(hop32(lat, 0, EPI_DFULL, 0, z(k) + 6 * sv, z(k), w(k), 0.f));
-    TRY(hop32(lat, 1, EPI_DFULL, 0, z(k), z(k) + 6 * sv, w(k) + 6 * sv, 0.f));
-    for (int j = 0; j < k; ++j) {
-      TRY(cdot_flat(lat, w(j), w(k), n4, d));
-      TRY(caxpy_flat(lat, -d[0], -d[1], w(j), w(k), n4));
-      TRY(caxpy_flat(lat, -d[0], -d[1], z(j), z(k), n4));
-    }
-    TRY(cdot_flat(lat, w(k), w(k), n4, d));
-    const double nw = std::sqrt(d[0]);
-    if (!(nw > 0) || !std::isfinite(nw)) return fail(lat, QXD_ENOCONV, "FGCR breakdown");
-    // alpha = <w, r> / ||w||^2 with w = w(k) / nw implied
-    TRY(cdot_flat(lat, w(k), r, n4, d));
-    TRY(caxpy_flat(lat, 1.0 / nw - 1.0, 0.0, w(k), w(k), n4));  // normalise w(k)
-    TRY(caxpy_flat(lat, 1.0 / nw - 1.0, 0.0, z(k), z(k), n4));  // and z(k) with it
-    const double ar = d[0] / nw, ai = d[1] / nw;
-    TRY(caxpy_flat(lat, ar, ai, z(k), y, n4));
-    TRY(caxpy_flat(lat, -ar, -ai, w(k), r, n4));
-    TRY(cdot_flat(lat, r, r, n4, d));
-    rn = std::sqrt(d[0]);
-    if (!std::isfinite(rn)) return fail(lat, QXD_ENOCONV, "non-finite residual in FGCR");
-    ++it;
-    k = (k + 1) % m;
-  }
-  *iters = it;
-  return QXD_OK;
-}
+// The inner flexible GCR of QXD_SOLVER_MP_FGCR_NET lives in fgcr.cu (device-resident coefficients).
+qxd_status fgcr32(qxd_lattice* lat, qxd_net* net, int m, int reorth, const float4* rhs, float4* y, double target,
+                  int maxiter, int check_every, int* iters);
 
 static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve_params* prm,
                              qxd_solve_info* info);
@@ -525,7 +438,8 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
       TRY(blas_zero(lat, e32, sizeof(float4) * 12 * sv));
       double inner_target = prm->inner_tol * std::sqrt(rn2);
       if (inner_target < target) inner_target = target;
-      TRY(inner_fgcr(lat, prm->net, prm->gcr_restart, r32f, e32, inner_target, prm->maxiter - total, &it));
+      TRY(fgcr32(lat, const_cast<qxd_net*>(prm->net), prm->gcr_restart, 1, r32f, e32, inner_target,
+                 prm->maxiter - total, prm->check_every, &it));
       TRY(blas_acc_f32_into_f64(lat, e32, x, 12 * sv));
     } else if (!mp) {
       // Schur source bh = r_e + 1/2 H_eo A_oo^-1 r_o, CG, reconstruct x_o += A_oo^-1 (r_o + 1/2 H_oe xe)

@@ -74,6 +74,7 @@ _SIGS = {
     "qxd_net_set_weights": [_vp, _vp],
     "qxd_net_get_weights": [_vp, _vp],
     "qxd_net_apply": [_vp, _vp, _vp, _i],
+    "qxd_net_set_precision": [_vp, _i],
     "qxd_net_loss_grad": [_vp, _vp, _vp, _i, _i, C.POINTER(_d), _vp],
     "qxd_net_train": [_vp, _vp, _i, C.POINTER(TrainParams), _vp, _i],
     "qxd_net_save": [_vp, C.c_char_p],
@@ -270,6 +271,13 @@ def net_get_weights(net):
     w = np.empty(net_num_weights(net), dtype=np.complex128)
     _check(lib.qxd_net_get_weights(net, w.ctypes.data))
     return w
+
+
+NET_F32, NET_BF16_TC = 0, 1
+
+
+def net_set_precision(net, prec):
+    _check(lib.qxd_net_set_precision(net, int(prec)))
 
 
 def net_apply(net, out, inp):

@@ -37,12 +37,21 @@ def random_flat(n, seed, scale=0.2):
     return scale * (r.standard_normal(n) + 1j * r.standard_normal(n))
 
 
+# BF16 tensor-core layers: operands rounded to 8 significant bits (unit roundoff u = 2^-8), FP32
+# accumulation; each layer's products carry at most 2u relative error, so the network output is
+# within 4 u per layer in norm with a factor 2 to spare for cancellation.
+TC_TOL_PER_LAYER = 4 * 2.0 ** -8
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16_tc"])
 @pytest.mark.parametrize("L,cstar,chans", [((4, 2, 2, 4), False, [1, 3, 2, 1]), ((2, 2, 4, 2), True, [1, 4, 1]),
-                                           ((6, 4, 4, 6), False, [1, 16, 16, 1])])
-def test_net_forward_matches_oracle(qxd, L, cstar, chans):
+                                           ((6, 4, 4, 6), False, [1, 16, 16, 1]),
+                                           ((8, 6, 6, 4), False, [1, 8, 5, 1])])
+def test_net_forward_matches_oracle(qxd, L, cstar, chans, prec):
     c = Case(qxd, torch, L, cstar=cstar)
     net = qxd.net_create(c.lat, chans, seed=1)
     try:
+        qxd.net_set_precision(net, qxd.NET_F32 if prec == "f32" else qxd.NET_BF16_TC)
         w = random_flat(qxd.net_num_weights(net), 3)
         qxd.net_set_weights(net, w)
         w32 = w.real.astype(np.float32) + 1j * w.imag.astype(np.float32)  # the GPU holds FP32 weights
@@ -52,7 +61,10 @@ def test_net_forward_matches_oracle(qxd, L, cstar, chans):
         qxd.net_apply(net, y, x)
         ref = O.ptc_net(c.lat_o, O.hop_links(c.U, c.A, c.q), layer_weights(w32, chans), psi)
         got = as_c128(y, psi.shape)
-        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-6
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        tol = 2e-6 if prec == "f32" else TC_TOL_PER_LAYER * (len(chans) - 1)
+        print(f"net {chans} {prec}: rel err {err:.3e} (tol {tol:.1e})")
+        assert err < tol
     finally:
         qxd.net_destroy(net)
         c.close()
@@ -112,6 +124,7 @@ def test_training_lowers_the_loss_and_fgcr_solves(qxd):
             assert O.true_rel_residual(c.op, as_c128(x, eta.shape), eta) <= 1e-10
             res[name] = info["iters_inner"]
         print("loss", hist[0], "->", hist[-1], "FGCR iterations with / without net:", res)
+        assert res["net"] < res["none"], res  # what the trained network gains
     finally:
         qxd.net_destroy(net)
         c.close()
