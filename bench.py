@@ -528,7 +528,8 @@ def run_c4(args):
         lat = c4_setup(dev, stream, m0)
 
         def timed_solve(**kw):
-            qxd.solve(lat, x, eta, check=False, **kw)  # warm-up
+            warm = dict(kw, maxiter=min(kw.get("maxiter", 100000), 50))
+            qxd.solve(lat, x, eta, check=False, **warm)  # warm-up (short)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st, info = qxd.solve(lat, x, eta, check=False, **kw)
@@ -560,6 +561,11 @@ def run_c4(args):
                 "heldout_rel_err_after": float(np.sqrt(l1 / ntest / (24.0 * V))),
                 "fgcr": timed_solve(solver=qxd.SOLVER_MP_FGCR_NET, inner_prec=qxd.F32, tol=1e-10, gcr_restart=32,
                                     net=net, maxiter=args.fgcr_maxiter)}
+            # the same network with its channel mix in FP32 on the CUDA cores
+            qxd.net_set_precision(net, qxd.NET_F32)
+            nets["x".join(map(str, chans))]["fgcr_net_f32"] = timed_solve(
+                solver=qxd.SOLVER_MP_FGCR_NET, inner_prec=qxd.F32, tol=1e-10, gcr_restart=32, net=net,
+                maxiter=args.fgcr_maxiter)
             qxd.net_destroy(net)
         res["nets"] = nets
         ok = [d["fgcr"]["seconds"] for d in nets.values() if d["fgcr"]["status"] == "OK"]
@@ -568,18 +574,50 @@ def run_c4(args):
         qxd.destroy_lattice(lat)
     return {"metric": METRIC, "workload": w["name"], "sites": V, "points": results,
             "note": "losses per site; held-out set of 16 (D v, v) pairs not used in training; "
-                    "heldout_rel_err = sqrt(loss / ||v||^2)"}
+                    "heldout_rel_err = sqrt(loss / ||v||^2); fgcr: network channel mix in BF16 on the tensor "
+                    "cores (default), fgcr_net_f32: the same network in FP32 on the CUDA cores"}
 
 
 def profile_run(args):
-    """One untimed pass of the step (for ncu launch lists and kernel captures)."""
+    """One untimed pass of the step (for ncu launch lists and kernel captures).  c4: 40 steps of
+    the learned FGCR with an untrained [1,8,8,1] network at m0 = -0.1; c3b: one batched solve."""
     import torch
 
-    from paper_2502_02490_gb300 import qxd
+    from paper_2502_02490_gb300 import qxd, synth
 
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     w = WORKLOAD
+    if args.workload == "c4":
+        lat = c4_setup(dev, stream, c4_m0("m0_physical"))
+        eta = torch.from_numpy(synth.gaussian_spinor(w["L"], w["source_seed"]).view(np.float64)).to(dev)
+        x = torch.empty_like(eta)
+        net = qxd.net_create(lat, [1, 8, 8, 1], seed=7)
+        st, info = qxd.solve(lat, x, eta, check=False, solver=qxd.SOLVER_MP_FGCR_NET, inner_prec=qxd.F32, tol=1e-10,
+                             gcr_restart=32, net=net, maxiter=40, max_outer=1)
+        torch.cuda.synchronize()
+        print(f"profile run: learned FGCR, 40 steps, {info}", file=sys.stderr)
+        qxd.net_destroy(net)
+        qxd.destroy_lattice(lat)
+        return
+    if args.workload == "c3b":
+        lats, xs, bs = [], [], []
+        for i, L in enumerate(w["lattices"]):
+            U, A = synth.gauge_field(L, w["gauge_seed"] + i, 0.2 + 0.3 * i / 7)
+            lat = qxd.create_lattice(L, qxd.BC_ANTIPERIODIC, 0, qxd.ORDER_LEXI, stream.cuda_stream)
+            qxd.load_gauge(lat, torch.from_numpy(U.view(np.float64)).to(dev), torch.from_numpy(A).to(dev), w["q"])
+            qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
+            lats.append(lat)
+            bs.append(torch.from_numpy(synth.gaussian_spinor(L, w["source_seed"] + i).view(np.float64)).to(dev))
+            xs.append(torch.empty_like(bs[-1]))
+        p = qxd.default_params(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=qxd.F32, tol=1e-10)
+        st, infos = qxd.solve_batch(lats, xs, bs, params=p)
+        torch.cuda.synchronize()
+        print(f"profile run: batched solve, {[i['iters_inner'] for i in infos]}, {qxd.batch_last_config()}",
+              file=sys.stderr)
+        for lat in lats:
+            qxd.destroy_lattice(lat)
+        return
     U, A, eta = make_inputs(0)
     su3_d = torch.from_numpy(U.view(np.float64)).to(dev)
     a_d = torch.from_numpy(A).to(dev)

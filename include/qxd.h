@@ -104,9 +104,10 @@ typedef struct {
   int check_every;        /* read the residual norm back every this many iterations (>= 1) */
   int gcr_restart;        /* FGCR restart length (MP_FGCR_NET), 1..32 */
   const qxd_net *net;     /* preconditioner of MP_FGCR_NET, or NULL */
+  int gcr_reorth;         /* MP_FGCR_NET: classical Gram-Schmidt passes per step, 1 or 2 */
 } qxd_solve_params;
 
-#define QXD_PARAMS_VERSION 2
+#define QXD_PARAMS_VERSION 3
 
 typedef struct {
   int iters_inner;        /* inner iterations summed over outer rounds */
@@ -197,7 +198,8 @@ qxd_status qxd_batch_set_spin_limit(long long limit);
 qxd_status qxd_batch_last_config(int *threads, int *sites_per_thread, int *blocks_per_sm, int *graph);
 
 /* Fill *p with the defaults: MP_CG_EO, tol 1e-10, maxiter 100000, inner F32, inner_tol 1e-5,
- * reliable_delta 0.1, max_outer 20, on_device 1, check_every 1, gcr_restart 16, net NULL. */
+ * reliable_delta 0.1, max_outer 20, on_device 1, check_every 1, gcr_restart 16, net NULL,
+ * gcr_reorth 1. */
 void qxd_default_params(qxd_solve_params *p);
 
 /* Fused BLAS-1 on device vectors of n complex numbers (interleaved re, im), on the lattice's

@@ -136,6 +136,7 @@ void qxd_default_params(qxd_solve_params* p) {
   p->on_device = 1;
   p->check_every = 1;
   p->gcr_restart = 16;
+  p->gcr_reorth = 1;
   p->net = nullptr;
 }
 
@@ -390,6 +391,8 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
   if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO && p->solver != QXD_SOLVER_MP_BICGSTAB_EO &&
       p->solver != QXD_SOLVER_MP_FGCR_NET)
     return fail(lat, QXD_EINVAL, "bad solver");
+  if (p->solver == QXD_SOLVER_MP_FGCR_NET && (p->gcr_reorth < 1 || p->gcr_reorth > 2))
+    return fail(lat, QXD_EINVAL, "gcr_reorth must be 1 or 2");
   if (p->solver == QXD_SOLVER_MP_FGCR_NET && (p->gcr_restart < 1 || p->gcr_restart > 32))
     return fail(lat, QXD_EINVAL, "gcr_restart must be 1..32");
   if (!(p->tol > 0) || p->maxiter <= 0) return fail(lat, QXD_EINVAL, "tol must be > 0 and maxiter > 0");

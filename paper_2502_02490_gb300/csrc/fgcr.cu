@@ -251,7 +251,7 @@ qxd_status fgcr32(qxd_lattice* lat, qxd_net* net, int m, int reorth, const float
       QXD_CUDA(lat, cudaMemcpyAsync(z(k), r, fb, cudaMemcpyDeviceToDevice, S));
     TRY_Q(hop32(lat, 0, EPI_DFULL, 0, z(k) + 6 * sv, z(k), w(k), 0.f));
     TRY_Q(hop32(lat, 1, EPI_DFULL, 0, z(k), z(k) + 6 * sv, w(k) + 6 * sv, 0.f));
-    for (int pass = 0; pass < (k > 0 ? reorth : 0); ++pass) {
+    for (int pass = 0; pass < (k > 0 ? reorth : 0); ++pass) {  // classical Gram-Schmidt, once or twice
       const int mb = (int)std::min<i64>((n4 + FG_BLOCK - 1) / FG_BLOCK, FG_MDOT_BLOCKS);
       k_fg_mdot<<<dim3(mb, (k + FG_ROWS - 1) / FG_ROWS), FG_BLOCK, 0, S>>>(w(0), n4, k, w(k), n4, part);
       QXD_CHECK_LAUNCH(lat, "k_fg_mdot");

@@ -103,11 +103,9 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-// The transported spinor of one input channel at one site (link u already carries the time sign):
-// forward path t = u h, backward path t = u^+ h, path 0 t = h.  Written as BF16 into the three
-// colour tiles of the stage, k = 8 slot + 2 beta + re/im (one 16-byte core-matrix row each).
-__device__ __forceinline__ void put_transported(unsigned char* a0, int s, int slot, int p, bool fwd,
-                                                const cplx<float> u[9], const float4 raw[6], bool zero) {
+template <int MODE>  // 0: zero, 1: identity (path 0), 2: forward u h, 3: backward u^+ h
+__device__ __forceinline__ void put_transported_m(unsigned char* a0, int s, int slot, const cplx<float> u[9],
+                                                  const float4 raw[6]) {
   // spinor component (beta, b) = complex index 3 beta + b; float4 j holds complex 2 j, 2 j + 1
   auto comp = [&](int idx) -> cplx<float> {
     const float4 q = raw[idx >> 1];
@@ -119,14 +117,15 @@ __device__ __forceinline__ void put_transported(unsigned char* a0, int s, int sl
     cplx<float> t[4];
 #pragma unroll
     for (int be = 0; be < 4; ++be) {
-      if (zero) {
+      if constexpr (MODE == 0) {
         t[be] = mk(0.f, 0.f);
-      } else if (p == 0) {
+      } else if constexpr (MODE == 1) {
         t[be] = comp(3 * be + a);
       } else {
         cplx<float> r = mk(0.f, 0.f);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) r = r + (fwd ? cmul(u[3 * a + b], comp(3 * be + b)) : cjmul(u[3 * b + a], comp(3 * be + b)));
+        for (int b = 0; b < 3; ++b)
+          r = r + (MODE == 2 ? cmul(u[3 * a + b], comp(3 * be + b)) : cjmul(u[3 * b + a], comp(3 * be + b)));
         t[be] = r;
       }
     }
@@ -137,6 +136,22 @@ __device__ __forceinline__ void put_transported(unsigned char* a0, int s, int sl
     v.w = pack_bf16x2(t[3].re, t[3].im);
     *(uint4*)(a0 + a * (TC_ABYTES / 3) + tc::kmajor_off(s, 8 * slot, TC_KC)) = v;
   }
+}
+
+// The transported spinor of one input channel at one site (link u already carries the time sign):
+// forward path t = u h, backward path t = u^+ h, path 0 t = h, written as BF16 into the three
+// colour tiles of the stage, k = 8 slot + 2 beta + re/im (one 16-byte core-matrix row each).
+// Separate instantiations per case, so that each executes only its own arithmetic.
+__device__ __forceinline__ void put_transported(unsigned char* a0, int s, int slot, int p, bool fwd,
+                                                const cplx<float> u[9], const float4 raw[6], bool zero) {
+  if (zero)
+    put_transported_m<0>(a0, s, slot, u, raw);
+  else if (p == 0)
+    put_transported_m<1>(a0, s, slot, u, raw);
+  else if (fwd)
+    put_transported_m<2>(a0, s, slot, u, raw);
+  else
+    put_transported_m<3>(a0, s, slot, u, raw);
 }
 
 // neighbour of site cb along path p (its checkerboard index and parity), and the path's link with

@@ -438,7 +438,7 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
       TRY(blas_zero(lat, e32, sizeof(float4) * 12 * sv));
       double inner_target = prm->inner_tol * std::sqrt(rn2);
       if (inner_target < target) inner_target = target;
-      TRY(fgcr32(lat, const_cast<qxd_net*>(prm->net), prm->gcr_restart, 1, r32f, e32, inner_target,
+      TRY(fgcr32(lat, const_cast<qxd_net*>(prm->net), prm->gcr_restart, prm->gcr_reorth, r32f, e32, inner_target,
                  prm->maxiter - total, prm->check_every, &it));
       TRY(blas_acc_f32_into_f64(lat, e32, x, 12 * sv));
     } else if (!mp) {

@@ -25,7 +25,7 @@ BC_PERIODIC, BC_ANTIPERIODIC = 0, 1
 ORDER_LEXI, ORDER_IPT = 0, 1
 F64, F32, F16N, BF16N = 0, 1, 2, 3
 SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO, SOLVER_MP_FGCR_NET = 0, 1, 2, 3
-PARAMS_VERSION = 2
+PARAMS_VERSION = 3
 TRAIN_VERSION = 1
 PREC = {"f64": F64, "f32": F32, "f16n": F16N, "bf16n": BF16N}
 
@@ -34,7 +34,7 @@ class SolveParams(C.Structure):
     _fields_ = [("version", C.c_int), ("solver", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int),
                 ("inner_prec", C.c_int), ("inner_tol", C.c_double), ("reliable_delta", C.c_double),
                 ("max_outer", C.c_int), ("on_device", C.c_int), ("check_every", C.c_int),
-                ("gcr_restart", C.c_int), ("net", C.c_void_p)]
+                ("gcr_restart", C.c_int), ("net", C.c_void_p), ("gcr_reorth", C.c_int)]
 
 
 class TrainParams(C.Structure):
