@@ -78,89 +78,121 @@ __device__ __forceinline__ M3 mul(const M3& a, const M3& b) {
   return c;
 }
 
-// Traceless anti-Hermitian Fhat_{mu nu}(x) = (Q - Q^dag)/8 - tr/3 and the U(1) fhat (imaginary part).
-__device__ void field_strength(const Geom& g, const double2* __restrict__ U, const double* __restrict__ A,
-                               const int x[4], int mu, int nu, M3& F, double& f1) {
-  int xp[4], t[4];
+// Traceless anti-Hermitian Fhat_{mu nu}(x) = (Q - Q^dag)/8 - tr/3 and the U(1) fhat (its imaginary
+// part, f1 = 1/4 sum_leaves sin(phi_leaf)), for the plane (MU, NU) fixed at compile time: every
+// site index stays in registers.
+template <int MU, int NU>
+__device__ __forceinline__ void field_strength_t(const Geom& g, const double2* __restrict__ U, const double* __restrict__ A,
+                                                 const int x[4], M3& F, double& f1) {
   M3 Q;
-  double s1 = 0.0;
-  // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
-  {
-    M3 a = load_u(g, U, x, mu);
-    for (int i = 0; i < 4; ++i) xp[i] = x[i];
-    step(g, xp, mu, +1);
-    M3 b = load_u(g, U, xp, nu);
-    for (int i = 0; i < 4; ++i) t[i] = x[i];
-    step(g, t, nu, +1);
-    M3 c = load_u(g, U, t, mu);
-    M3 d = load_u(g, U, x, nu);
+  double s1;
+  {  // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+    int xp[4] = {x[0], x[1], x[2], x[3]}, t[4] = {x[0], x[1], x[2], x[3]};
+    step(g, xp, MU, +1);
+    step(g, t, NU, +1);
+    const M3 a = load_u(g, U, x, MU), b = load_u(g, U, xp, NU), c = load_u(g, U, t, MU), d = load_u(g, U, x, NU);
     Q = mul<false, true>(mul<false, true>(mul<false, false>(a, b), c), d);
-    s1 += sin(load_a(g, A, x, mu) + load_a(g, A, xp, nu) - load_a(g, A, t, mu) - load_a(g, A, x, nu));
+    s1 = sin(load_a(g, A, x, MU) + load_a(g, A, xp, NU) - load_a(g, A, t, MU) - load_a(g, A, x, NU));
   }
-  // leaf 2: U_nu(x) U_mu(x+nu-mu)^+ U_nu(x-mu)^+ U_mu(x-mu)
-  {
-    int xm[4], xnm[4];
-    for (int i = 0; i < 4; ++i) xm[i] = x[i];
-    step(g, xm, mu, -1);
-    for (int i = 0; i < 4; ++i) xnm[i] = xm[i];
-    step(g, xnm, nu, +1);
-    M3 a = load_u(g, U, x, nu);
-    M3 b = load_u(g, U, xnm, mu);
-    M3 c = load_u(g, U, xm, nu);
-    M3 d = load_u(g, U, xm, mu);
-    M3 r = mul<false, false>(mul<false, true>(mul<false, true>(a, b), c), d);
+  {  // leaf 2: U_nu(x) U_mu(x+nu-mu)^+ U_nu(x-mu)^+ U_mu(x-mu)
+    int xm[4] = {x[0], x[1], x[2], x[3]};
+    step(g, xm, MU, -1);
+    int xnm[4] = {xm[0], xm[1], xm[2], xm[3]};
+    step(g, xnm, NU, +1);
+    const M3 a = load_u(g, U, x, NU), b = load_u(g, U, xnm, MU), c = load_u(g, U, xm, NU), d = load_u(g, U, xm, MU);
+    const M3 r = mul<false, false>(mul<false, true>(mul<false, true>(a, b), c), d);
 #pragma unroll
     for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
-    s1 += sin(load_a(g, A, x, nu) - load_a(g, A, xnm, mu) - load_a(g, A, xm, nu) + load_a(g, A, xm, mu));
+    s1 += sin(load_a(g, A, x, NU) - load_a(g, A, xnm, MU) - load_a(g, A, xm, NU) + load_a(g, A, xm, MU));
   }
-  // leaf 3: U_mu(x-mu)^+ U_nu(x-mu-nu)^+ U_mu(x-mu-nu) U_nu(x-nu)
-  {
-    int xm[4], xmn[4], xn[4];
-    for (int i = 0; i < 4; ++i) xm[i] = x[i];
-    step(g, xm, mu, -1);
-    for (int i = 0; i < 4; ++i) xmn[i] = xm[i];
-    step(g, xmn, nu, -1);
-    for (int i = 0; i < 4; ++i) xn[i] = x[i];
-    step(g, xn, nu, -1);
-    M3 a = load_u(g, U, xm, mu);
-    M3 b = load_u(g, U, xmn, nu);
-    M3 c = load_u(g, U, xmn, mu);
-    M3 d = load_u(g, U, xn, nu);
-    M3 ab = mul<true, true>(a, b);
-    M3 r = mul<false, false>(mul<false, false>(ab, c), d);
+  {  // leaf 3: U_mu(x-mu)^+ U_nu(x-mu-nu)^+ U_mu(x-mu-nu) U_nu(x-nu)
+    int xm[4] = {x[0], x[1], x[2], x[3]}, xn[4] = {x[0], x[1], x[2], x[3]};
+    step(g, xm, MU, -1);
+    int xmn[4] = {xm[0], xm[1], xm[2], xm[3]};
+    step(g, xmn, NU, -1);
+    step(g, xn, NU, -1);
+    const M3 a = load_u(g, U, xm, MU), b = load_u(g, U, xmn, NU), c = load_u(g, U, xmn, MU), d = load_u(g, U, xn, NU);
+    const M3 r = mul<false, false>(mul<false, false>(mul<true, true>(a, b), c), d);
 #pragma unroll
     for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
-    s1 += sin(-load_a(g, A, xm, mu) - load_a(g, A, xmn, nu) + load_a(g, A, xmn, mu) + load_a(g, A, xn, nu));
+    s1 += sin(-load_a(g, A, xm, MU) - load_a(g, A, xmn, NU) + load_a(g, A, xmn, MU) + load_a(g, A, xn, NU));
   }
-  // leaf 4: U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^+
-  {
-    int xn[4], xnp[4];
-    for (int i = 0; i < 4; ++i) xn[i] = x[i];
-    step(g, xn, nu, -1);
-    for (int i = 0; i < 4; ++i) xnp[i] = xn[i];
-    step(g, xnp, mu, +1);
-    M3 a = load_u(g, U, xn, nu);
-    M3 b = load_u(g, U, xn, mu);
-    M3 c = load_u(g, U, xnp, nu);
-    M3 d = load_u(g, U, x, mu);
-    M3 r = mul<false, true>(mul<false, false>(mul<true, false>(a, b), c), d);
+  {  // leaf 4: U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^+
+    int xn[4] = {x[0], x[1], x[2], x[3]};
+    step(g, xn, NU, -1);
+    int xnp[4] = {xn[0], xn[1], xn[2], xn[3]};
+    step(g, xnp, MU, +1);
+    const M3 a = load_u(g, U, xn, NU), b = load_u(g, U, xn, MU), c = load_u(g, U, xnp, NU), d = load_u(g, U, x, MU);
+    const M3 r = mul<false, true>(mul<false, false>(mul<true, false>(a, b), c), d);
 #pragma unroll
     for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
-    s1 += sin(-load_a(g, A, xn, nu) + load_a(g, A, xn, mu) + load_a(g, A, xnp, nu) - load_a(g, A, x, mu));
+    s1 += sin(-load_a(g, A, xn, NU) + load_a(g, A, xn, MU) + load_a(g, A, xnp, NU) - load_a(g, A, x, MU));
   }
-  // F = (Q - Q^+)/8, then remove the trace
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      cd a = Q.m[3 * i + j], b = Q.m[3 * j + i];
+      const cd a = Q.m[3 * i + j], b = Q.m[3 * j + i];
       F.m[3 * i + j] = mk((a.re - b.re) * 0.125, (a.im + b.im) * 0.125);
     }
-  double tr_im = (F.m[0].im + F.m[4].im + F.m[8].im) / 3.0;  // trace of an anti-Hermitian matrix is imaginary
+  const double tr_im = (F.m[0].im + F.m[4].im + F.m[8].im) / 3.0;
   F.m[0].im -= tr_im;
   F.m[4].im -= tr_im;
   F.m[8].im -= tr_im;
-  f1 = 0.25 * s1;  // fhat = i f1
+  f1 = 0.25 * s1;
+}
+
+// Field strength of plane p = blockIdx.y for every site (both parities):
+// planes 0..2 = (0,1) (0,2) (0,3), 3 = (2,3), 4 = (1,3), 5 = (1,2).  Stored compactly per site as
+// 10 doubles [plane][k][2 sv]: Im F_00, Im F_11, Im F_22, (Re, Im) F_01, F_02, F_12 (the lower
+// triangle is -conj), and fhat.
+__global__ void __launch_bounds__(128) k_clover_fs(Geom g, const double2* __restrict__ U, const double* __restrict__ A,
+                                                   double* __restrict__ Fb) {
+  const int p = blockIdx.y;
+  const i64 n = 2 * g.Vh;
+  for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x) {
+    const int par = e >= g.Vh ? 1 : 0;
+    const i64 cb = e - (i64)par * g.Vh;
+    int x[4];
+    cb_coords(g, cb, par, x);
+    M3 F;
+    double f1;
+    switch (p) {
+      case 0: field_strength_t<0, 1>(g, U, A, x, F, f1); break;
+      case 1: field_strength_t<0, 2>(g, U, A, x, F, f1); break;
+      case 2: field_strength_t<0, 3>(g, U, A, x, F, f1); break;
+      case 3: field_strength_t<2, 3>(g, U, A, x, F, f1); break;
+      case 4: field_strength_t<1, 3>(g, U, A, x, F, f1); break;
+      default: field_strength_t<1, 2>(g, U, A, x, F, f1); break;
+    }
+    const i64 st = 2 * g.sv, s = (i64)par * g.sv + cb;
+    double* o = Fb + (i64)p * 10 * st + s;
+    o[0 * st] = F.m[0].im;
+    o[1 * st] = F.m[4].im;
+    o[2 * st] = F.m[8].im;
+    o[3 * st] = F.m[1].re;
+    o[4 * st] = F.m[1].im;
+    o[5 * st] = F.m[2].re;
+    o[6 * st] = F.m[2].im;
+    o[7 * st] = F.m[5].re;
+    o[8 * st] = F.m[5].im;
+    o[9 * st] = f1;
+  }
+}
+
+__device__ __forceinline__ void load_fs(const double* __restrict__ Fb, i64 st, i64 s, int p, cd F[9], double& f1) {
+  const double* o = Fb + (i64)p * 10 * st + s;
+  const cd a01 = mk(o[3 * st], o[4 * st]), a02 = mk(o[5 * st], o[6 * st]), a12 = mk(o[7 * st], o[8 * st]);
+  F[0] = mk(0.0, o[0]);
+  F[4] = mk(0.0, o[st]);
+  F[8] = mk(0.0, o[2 * st]);
+  F[1] = a01;
+  F[2] = a02;
+  F[5] = a12;
+  F[3] = mk(-a01.re, a01.im);  // -conj
+  F[6] = mk(-a02.re, a02.im);
+  F[7] = mk(-a12.re, a12.im);
+  f1 = o[9 * st];
 }
 
 // blk (6x6, full storage) += s * sigma_l (x) Y,  s complex
@@ -199,70 +231,37 @@ __device__ __forceinline__ void pack_block(const cd blk[36], double r[36]) {
     }
 }
 
-__global__ void __launch_bounds__(128) k_clover_build(Geom g, const double2* __restrict__ U,
-                                                      const double* __restrict__ A, double diag, double csw,
-                                                      double cq, double2* __restrict__ C) {
-  i64 n = 2 * g.Vh;
-  for (i64 s = blockIdx.x * (i64)blockDim.x + threadIdx.x; s < n; s += (i64)gridDim.x * blockDim.x) {
-    int par = s >= g.Vh ? 1 : 0;
-    i64 cb = s - (i64)par * g.Vh;
-    int x[4];
-    cb_coords(g, cb, par, x);
-    cd Gp[3][9], Gm[3][9];
-    double gp[3], gm[3];
+// A_+- of every site from the stored field strengths: G^{+-}_l = F_{0l} -+ sgn_l F_mag(l) with the
+// magnetic planes (2,3), (1,3), (1,2) of sign +1, -1, +1; one chiral block at a time.
+__global__ void __launch_bounds__(128) k_clover_assemble(Geom g, const double* __restrict__ Fb, double diag, double csw,
+                                                         double cq, double2* __restrict__ C) {
+  const i64 n = 2 * g.Vh, st = 2 * g.sv;
+  for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x) {
+    const int par = e >= g.Vh ? 1 : 0;
+    const i64 cb = e - (i64)par * g.Vh;
+    const i64 s = (i64)par * g.sv + cb;
 #pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      gp[l] = gm[l] = 0.0;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) Gp[l][k] = Gm[l][k] = mk(0.0, 0.0);
-    }
-    // planes: (0,1) (0,2) (0,3) electric; (2,3) -> l=1 (+), (1,3) -> l=2 (-), (1,2) -> l=3 (+)
-    for (int p = 0; p < 6; ++p) {
-      int mu, nu, l;
-      double sgn;
-      bool electric;
-      if (p < 3) {
-        mu = 0; nu = p + 1; l = p; sgn = 1.0; electric = true;
-      } else if (p == 3) {
-        mu = 2; nu = 3; l = 0; sgn = 1.0; electric = false;
-      } else if (p == 4) {
-        mu = 1; nu = 3; l = 1; sgn = -1.0; electric = false;
-      } else {
-        mu = 1; nu = 2; l = 2; sgn = 1.0; electric = false;
-      }
-      M3 F;
-      double f1;
-      field_strength(g, U, A, x, mu, nu, F, f1);
-      // G^+ = F_0l - Ftilde_l, G^- = F_0l + Ftilde_l
-      double sp = electric ? 1.0 : -sgn, sm = electric ? 1.0 : sgn;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        Gp[l][k] = Gp[l][k] + sp * F.m[k];
-        Gm[l][k] = Gm[l][k] + sm * F.m[k];
-      }
-      gp[l] += sp * f1;
-      gm[l] += sm * f1;
-    }
     for (int blkid = 0; blkid < 2; ++blkid) {
       cd blk[36];
 #pragma unroll
       for (int k = 0; k < 36; ++k) blk[k] = mk(0.0, 0.0);
 #pragma unroll
       for (int i = 0; i < 6; ++i) blk[7 * i] = mk(diag, 0.0);
-      double side = blkid == 0 ? 0.5 : -0.5;  // +(i/2) on A_+, -(i/2) on A_-
+      const double side = blkid == 0 ? 0.5 : -0.5;  // +(i/2) on A_+, -(i/2) on A_-
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
-        cd Y[9];
+        const double sgn = l == 1 ? -1.0 : 1.0;
+        const double smag = blkid == 0 ? -sgn : sgn;
+        cd Fe[9], Fm[9], Y[9];
+        double fe, fm;
+        load_fs(Fb, st, s, l, Fe, fe);
+        load_fs(Fb, st, s, 3 + l, Fm, fm);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          // Y = c_sw G_l + q c_sw^QED g_l 1, where g_l = i * (gp or gm) (fhat is imaginary)
-          cd Gv = blkid == 0 ? Gp[l][k] : Gm[l][k];
-          Y[k] = csw * Gv;
-        }
-        double gv = blkid == 0 ? gp[l] : gm[l];
-        Y[0].im += cq * gv;
-        Y[4].im += cq * gv;
-        Y[8].im += cq * gv;
+        for (int k = 0; k < 9; ++k) Y[k] = csw * (Fe[k] + smag * Fm[k]);
+        const double gv = cq * (fe + smag * fm);
+        Y[0].im += gv;
+        Y[4].im += gv;
+        Y[8].im += gv;
         add_sigma(blk, l + 1, mk(0.0, side), Y);
       }
       double r[36];
@@ -274,94 +273,130 @@ __global__ void __launch_bounds__(128) k_clover_build(Geom g, const double2* __r
   }
 }
 
-// Inverse of each Hermitian 6x6 block by Gauss-Jordan elimination with partial pivoting (FP64).
-// A block whose pivot falls below 1e-14 times its largest entry sets *bad (odd sites only).
-__global__ void __launch_bounds__(128) k_clover_invert(Geom g, const double2* __restrict__ C,
-                                                       double2* __restrict__ Ci, int* __restrict__ bad) {
-  i64 n = 2 * g.Vh * 2;
-  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
-    int blkid = (int)(t & 1);
-    i64 s = t >> 1;
-    int par = s >= g.Vh ? 1 : 0;
-    i64 cb = s - (i64)par * g.Vh;
-    const double2* in = C + (i64)((par * 2 + blkid) * 18) * g.sv + cb;
-    double r[36];
+// One step (column C) of in-place Gauss-Jordan inversion with partial pivoting; C is a template
+// argument so that every index is static and the block stays in registers.
+template <int C>
+__device__ __forceinline__ void gj_step(cd a[6][6], double amax, int piv[6], bool& singular) {
+  int pc = C;
+  double best = a[C][C].re * a[C][C].re + a[C][C].im * a[C][C].im;
 #pragma unroll
-    for (int k = 0; k < 18; ++k) {
-      double2 v = in[k * g.sv];
-      r[2 * k] = v.x;
-      r[2 * k + 1] = v.y;
+  for (int i = C + 1; i < 6; ++i) {
+    const double m = a[i][C].re * a[i][C].re + a[i][C].im * a[i][C].im;
+    if (m > best) {
+      best = m;
+      pc = i;
     }
-    cd a[6][6], inv[6][6];
-    double amax = 0.0;
-    for (int i = 0; i < 6; ++i)
-      for (int j = 0; j < 6; ++j) inv[i][j] = mk(i == j ? 1.0 : 0.0, 0.0);
-    for (int i = 0; i < 6; ++i) {
-      a[i][i] = mk(r[i], 0.0);
-      amax = fmax(amax, fabs(r[i]));
+  }
+  piv[C] = pc;
+  if (!(sqrt(best) > 1e-14 * amax)) singular = true;  // strict: an all-zero block is singular
+#pragma unroll
+  for (int i = C + 1; i < 6; ++i) {
+    const bool sw = pc == i;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const cd u = a[C][j], v = a[i][j];
+      a[C][j] = sw ? v : u;
+      a[i][j] = sw ? u : v;
     }
-    int k = 0;
-    for (int i = 0; i < 6; ++i)
-      for (int j = i + 1; j < 6; ++j) {
-        a[i][j] = mk(r[6 + 2 * k], r[7 + 2 * k]);
-        a[j][i] = mk(r[6 + 2 * k], -r[7 + 2 * k]);
-        amax = fmax(amax, fabs(r[6 + 2 * k]) + fabs(r[7 + 2 * k]));
-        ++k;
-      }
-    bool singular = false;
-    for (int c = 0; c < 6; ++c) {
-      int piv = c;
-      double best = -1.0;
-      for (int i = c; i < 6; ++i) {
-        double m = a[i][c].re * a[i][c].re + a[i][c].im * a[i][c].im;
-        if (m > best) {
-          best = m;
-          piv = i;
-        }
-      }
-      if (!(sqrt(best) > 1e-14 * amax)) singular = true;  // strict: an all-zero block is singular
-      if (piv != c) {
-        for (int j = 0; j < 6; ++j) {
-          cd tmp = a[c][j];
-          a[c][j] = a[piv][j];
-          a[piv][j] = tmp;
-          tmp = inv[c][j];
-          inv[c][j] = inv[piv][j];
-          inv[piv][j] = tmp;
-        }
-      }
-      cd p = a[c][c];
-      double pm = p.re * p.re + p.im * p.im;
-      cd pinv = pm > 0.0 ? mk(p.re / pm, -p.im / pm) : mk(0.0, 0.0);
-      for (int j = 0; j < 6; ++j) {
-        a[c][j] = cmul(a[c][j], pinv);
-        inv[c][j] = cmul(inv[c][j], pinv);
-      }
-      for (int i = 0; i < 6; ++i) {
-        if (i == c) continue;
-        cd f = a[i][c];
-        for (int j = 0; j < 6; ++j) {
-          a[i][j] = a[i][j] - cmul(f, a[c][j]);
-          inv[i][j] = inv[i][j] - cmul(f, inv[c][j]);
-        }
-      }
-    }
-    if (singular && par == 1) atomicOr(bad, 1);
-    double o[36];
-    for (int i = 0; i < 6; ++i) o[i] = inv[i][i].re;
-    k = 0;
-    for (int i = 0; i < 6; ++i)
-      for (int j = i + 1; j < 6; ++j) {
-        o[6 + 2 * k] = 0.5 * (inv[i][j].re + inv[j][i].re);
-        o[7 + 2 * k] = 0.5 * (inv[i][j].im - inv[j][i].im);
-        ++k;
-      }
-    double2* out = Ci + (i64)((par * 2 + blkid) * 18) * g.sv + cb;
-    for (int k2 = 0; k2 < 18; ++k2) out[k2 * g.sv] = make_double2(o[2 * k2], o[2 * k2 + 1]);
+  }
+  const cd p = a[C][C];
+  const double pm = p.re * p.re + p.im * p.im;
+  const cd pinv = pm > 0.0 ? mk(p.re / pm, -p.im / pm) : mk(0.0, 0.0);
+  a[C][C] = mk(1.0, 0.0);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) a[C][j] = cmul(a[C][j], pinv);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    if (i == C) continue;
+    const cd f = a[i][C];
+    a[i][C] = mk(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) a[i][j] = a[i][j] - cmul(f, a[C][j]);
   }
 }
 
-// FP64 clover [2][2][18][sv] -> FP32 [2][2][9][sv] float4 and 16-bit with one scale per block.
+template <int C>
+__device__ __forceinline__ void gj_unswap(cd a[6][6], const int piv[6]) {
+#pragma unroll
+  for (int j = C + 1; j < 6; ++j) {
+    const bool sw = piv[C] == j;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const cd u = a[i][C], v = a[i][j];
+      a[i][C] = sw ? v : u;
+      a[i][j] = sw ? u : v;
+    }
+  }
+}
+
+// Inverse of each Hermitian 6x6 block of the odd sites by in-place Gauss-Jordan elimination with
+// partial pivoting (FP64), fully unrolled so that the block stays in registers (row swaps are
+// predicated; the row permutation is undone as column swaps at the end).  A block whose pivot
+// falls below 1e-14 times its largest entry sets *bad.  Only the odd-site inverse is used
+// (A_oo^-1 of the Schur complement and of the reconstruction).
+__global__ void __launch_bounds__(128) k_clover_invert(Geom g, const double2* __restrict__ C,
+                                                       double2* __restrict__ Ci, int* __restrict__ bad) {
+  const i64 n = 2 * g.Vh;  // (odd site, block)
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
+    const int blkid = (int)(t / g.Vh);
+    const i64 cb = t - (i64)blkid * g.Vh;
+    const double2* in = C + (i64)((2 + blkid) * 18) * g.sv + cb;
+    // packed: pairs 0..2 the six real diagonal entries, pairs 3..17 the strict upper triangle
+    cd a[6][6];
+    double amax = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double2 v = in[k * g.sv];
+      a[2 * k][2 * k] = mk(v.x, 0.0);
+      a[2 * k + 1][2 * k + 1] = mk(v.y, 0.0);
+      amax = fmax(amax, fmax(fabs(v.x), fabs(v.y)));
+    }
+    {
+      int k = 3;
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 6; ++j) {
+          const double2 v = in[k * g.sv];
+          a[i][j] = mk(v.x, v.y);
+          a[j][i] = mk(v.x, -v.y);
+          amax = fmax(amax, fabs(v.x) + fabs(v.y));
+          ++k;
+        }
+    }
+    bool singular = false;
+    int piv[6];
+    gj_step<0>(a, amax, piv, singular);
+    gj_step<1>(a, amax, piv, singular);
+    gj_step<2>(a, amax, piv, singular);
+    gj_step<3>(a, amax, piv, singular);
+    gj_step<4>(a, amax, piv, singular);
+    gj_step<5>(a, amax, piv, singular);
+    // undo the row interchanges as column interchanges, last first
+    gj_unswap<5>(a, piv);
+    gj_unswap<4>(a, piv);
+    gj_unswap<3>(a, piv);
+    gj_unswap<2>(a, piv);
+    gj_unswap<1>(a, piv);
+    gj_unswap<0>(a, piv);
+    if (singular) atomicOr(bad, 1);
+    double2* out = Ci + (i64)((2 + blkid) * 18) * g.sv + cb;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[k * g.sv] = make_double2(a[2 * k][2 * k].re, a[2 * k + 1][2 * k + 1].re);
+    {
+      int k = 3;
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 6; ++j) {
+          // symmetrise the rounding of the two triangles
+          out[k * g.sv] = make_double2(0.5 * (a[i][j].re + a[j][i].re), 0.5 * (a[i][j].im - a[j][i].im));
+          ++k;
+        }
+    }
+  }
+}
+
 __global__ void k_clover_low(Geom g, const double2* __restrict__ C, float4* __restrict__ C32,
                              uint2* __restrict__ C16, float* __restrict__ C16n, uint2* __restrict__ CB,
                              float* __restrict__ CBn) {
@@ -402,15 +437,31 @@ static int grid_cap(i64 n, int bs) {
 
 qxd_status clover_build(qxd_lattice* lat) {
   const Geom& g = lat->g;
-  k_clover_build<<<grid_cap(2 * g.Vh, 128), 128, 0, lat->stream>>>(g, lat->U, lat->A, 4.0 + lat->m0, lat->csw,
-                                                                   lat->q * lat->csw_qed, lat->C64);
-  QXD_CHECK_LAUNCH(lat, "k_clover_build");
+  // field strengths of the six planes (one thread per site and plane), then the blocks; the
+  // field-strength buffer (10 doubles per site and plane) is released afterwards
+  double* Fb;
+  QXD_CUDA(lat, cudaMalloc(&Fb, sizeof(double) * 6 * 10 * 2 * g.sv));
+  {
+    dim3 grid((unsigned)grid_cap(2 * g.Vh, 128), 6);
+    k_clover_fs<<<grid, 128, 0, lat->stream>>>(g, lat->U, lat->A, Fb);
+  }
+  cudaError_t le = cudaGetLastError();
+  if (le == cudaSuccess) {
+    lat->launches++;
+    k_clover_assemble<<<grid_cap(2 * g.Vh, 128), 128, 0, lat->stream>>>(g, Fb, 4.0 + lat->m0, lat->csw,
+                                                                        lat->q * lat->csw_qed, lat->C64);
+    le = cudaGetLastError();
+    if (le == cudaSuccess) lat->launches++;
+  }
+  cudaStreamSynchronize(lat->stream);
+  cudaFree(Fb);
+  if (le != cudaSuccess) return cuda_fail(lat, le, "k_clover_fs / k_clover_assemble");
   void* w;
   qxd_status st = ensure_work(lat, 30, sizeof(int), &w);  // slot 30: clover singular flag
   if (st) return st;
   int* bad = (int*)w;
   QXD_CUDA(lat, cudaMemsetAsync(bad, 0, sizeof(int), lat->stream));
-  k_clover_invert<<<grid_cap(4 * g.Vh, 128), 128, 0, lat->stream>>>(g, lat->C64, lat->Ci64, bad);
+  k_clover_invert<<<grid_cap(2 * g.Vh, 128), 128, 0, lat->stream>>>(g, lat->C64, lat->Ci64, bad);
   QXD_CHECK_LAUNCH(lat, "k_clover_invert");
   k_clover_low<<<grid_cap(4 * g.sv, 128), 128, 0, lat->stream>>>(g, lat->C64, lat->C32, lat->C16, lat->C16n,
                                                                  lat->CB16, lat->CB16n);
