@@ -18,10 +18,12 @@
  * Site orders at the boundary (Sec. 4.1.1):
  *   QXD_ORDER_LEXI : lexicographic Lambda(x, L) = L3 L2 L1 x0 + L3 L2 x1 + L3 x2 + x3 (Eq. lexi),
  *                    i.e. C-contiguous over (t, x, y, z).
- *   QXD_ORDER_IPT  : openQxD order with one cache block (Eq. ipt, B = L): even sites first, each
- *                    parity in floor(Lambda/2) order.
+ *   QXD_ORDER_IPT  : openQxD order (Eq. ipt): even sites first; within a parity the cache blocks
+ *                    of extents B (qxd_set_ipt_blocks; default B = L, one block) in
+ *                    lexicographic block order, the sites of a block lexicographic within it.
+ *                    With B = L each parity is in floor(Lambda/2) order.
  *   "Even half" vectors (apply_Dhat_eo, solver internals) always list the V/2 even sites in
- *   floor(Lambda/2) order, which is the first half of QXD_ORDER_IPT.
+ *   floor(Lambda/2) order, which is the first half of QXD_ORDER_IPT with one cache block.
  *
  * Field layouts (all doubles, complex numbers interleaved re, im; site order as above):
  *   spinor  [V][4 spin][3 colour][2]          (x, alpha, a) with a fastest (Sec. 2)
@@ -105,6 +107,9 @@ typedef struct {
   int gcr_restart;        /* FGCR restart length (MP_FGCR_NET), 1..32 */
   const qxd_net *net;     /* preconditioner of MP_FGCR_NET, or NULL */
   int gcr_reorth;         /* MP_FGCR_NET: classical Gram-Schmidt passes per step, 1 or 2 */
+  int fallback;           /* MP_FGCR_NET: solver run when the learned solve misses the tolerance
+                             (QXD_SOLVER_CG_EO, MP_CG_EO or MP_BICGSTAB_EO, with the library
+                             defaults except tol, on_device, check_every), or -1 for none */
 } qxd_solve_params;
 
 #define QXD_PARAMS_VERSION 3
@@ -116,6 +121,7 @@ typedef struct {
   double true_rel_res;    /* final ||eta - D psi|| / ||eta|| computed in FP64 on the GPU */
   double seconds;         /* wall time of the solve */
   int status;             /* qxd_status of the solve */
+  int fallback_used;      /* 1 if the fallback solver produced x (counts above are its own) */
 } qxd_solve_info;
 
 /* Create a lattice of extents L = {T, L1, L2, L3} (txyz, Sec. 4.1.1), all even and >= 2.
@@ -136,6 +142,22 @@ qxd_status qxd_destroy_lattice(qxd_lattice *lat);
  * Invalidates a previously built clover field. */
 qxd_status qxd_load_gauge(qxd_lattice *lat, const double *su3, const double *a_u1, double q,
                           int on_device);
+
+/* Cache blocks of QXD_ORDER_IPT (Eq. ipt, Sec. 4.1.1): B[mu] must divide the lattice extent L[mu]
+ * (for C* both the physical and the doubled x extent); default B = L.  Applies to every field
+ * exchanged afterwards (spinors, gauge field, clover export).  QXD_EINVAL for a LEXI lattice or
+ * a B that does not tile the lattice. */
+qxd_status qxd_set_ipt_blocks(qxd_lattice *lat, const int B[4]);
+
+/* Load the gauge field in openQxD's storage (Sec. 4.1.4): for each odd site x, in the order of
+ * its index x^ in Eq. ipt (odd sites are x^ = V/2 .. V-1), eight links: u8[8 (x^ - V/2) + 2 mu] =
+ * U_mu(x) and u8[8 (x^ - V/2) + 2 mu + 1] = U_mu(x - mu), each 3x3 row-major complex; every link
+ * of the lattice appears exactly once (each has one odd end).  u8: [V/2][8][3][3][2]; a8 (or
+ * NULL): the U(1) angles in the same arrangement, [V/2][8].  The field is the lattice's own: for
+ * C* the doubled lattice with its mirror half (no mirroring is done).  Needs QXD_ORDER_IPT.
+ * Otherwise as qxd_load_gauge. */
+qxd_status qxd_load_gauge_openqxd(qxd_lattice *lat, const double *u8, const double *a8, double q,
+                                  int on_device);
 
 /* Build the clover blocks A(x) = (4+m0) + c_sw (i/4) sigma.Fhat^SU(3) + q c_sw^QED (i/4)
  * sigma.Fhat^U(1) on every site (Sec. 2, Sec. 4.1.3, Sec. 4.3, Sec. 6: clover generated on the
@@ -199,7 +221,7 @@ qxd_status qxd_batch_last_config(int *threads, int *sites_per_thread, int *block
 
 /* Fill *p with the defaults: MP_CG_EO, tol 1e-10, maxiter 100000, inner F32, inner_tol 1e-5,
  * reliable_delta 0.1, max_outer 20, on_device 1, check_every 1, gcr_restart 16, net NULL,
- * gcr_reorth 1. */
+ * gcr_reorth 1, fallback -1. */
 void qxd_default_params(qxd_solve_params *p);
 
 /* Fused BLAS-1 on device vectors of n complex numbers (interleaved re, im), on the lattice's

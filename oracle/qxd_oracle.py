@@ -106,6 +106,36 @@ def from_ipt_order(arr, L, B=None):
     return arr[ipt(coords_of(L), L, B)]
 
 
+def openqxd_gauge(U, A, L, B=None, cstar=False):
+    """openQxD's gauge storage (Sec. 4.1.4): eight links at every odd site, none stored at even ones.
+
+    For the odd site x with index x^ (Eq. ipt, blocks B), row x^ - V/2 holds, for mu = 0..3,
+    U_mu(x) at 2 mu and U_mu(x - mu) at 2 mu + 1 (the reading of the forward/backward order; the
+    paper states only that forward and backward links are stored at odd points).  x - mu is the
+    lattice neighbour: periodic wrap, and with ``cstar`` (L the doubled lattice) a step across
+    the y or z boundary also moves x1 by L1 / 2 (Sec. 4.2).  U: [V][4][3][3] and A: [V][4] in
+    lexicographic order on L; returns (u8 [V/2][8][3][3], a8 [V/2][8]).
+    """
+    L = tuple(L)
+    V = int(np.prod(L))
+    c = coords_of(L)
+    odd = parity(c) == 1
+    row = ipt(c[odd], L, B) - V // 2
+    u8 = np.empty((V // 2, 8, 3, 3), dtype=U.dtype)
+    a8 = np.empty((V // 2, 8))
+    for mu in range(4):
+        back = c[odd].copy()
+        crossed = back[:, mu] == 0
+        back[:, mu] = (back[:, mu] - 1) % L[mu]
+        if cstar and mu >= 2:
+            back[crossed, 1] = (back[crossed, 1] + L[1] // 2) % L[1]
+        u8[row, 2 * mu] = U[lexi(c[odd], L), mu]
+        u8[row, 2 * mu + 1] = U[lexi(back, L), mu]
+        a8[row, 2 * mu] = A[lexi(c[odd], L), mu]
+        a8[row, 2 * mu + 1] = A[lexi(back, L), mu]
+    return u8, a8
+
+
 # ---------------------------------------------------------------------------------------
 # Lattice geometry with boundary conditions
 # ---------------------------------------------------------------------------------------

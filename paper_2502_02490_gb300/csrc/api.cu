@@ -137,6 +137,7 @@ void qxd_default_params(qxd_solve_params* p) {
   p->check_every = 1;
   p->gcr_restart = 16;
   p->gcr_reorth = 1;
+  p->fallback = -1;
   p->net = nullptr;
 }
 
@@ -191,6 +192,7 @@ qxd_status qxd_create_lattice(const int L[4], int tbc, int cstar, int order, voi
     delete lat;
     return fail(nullptr, QXD_EINVAL, "volume must be below 2^31 sites");
   }
+  for (int mu = 0; mu < 4; ++mu) lat->g.B[mu] = lat->g.L[mu];  // IPT order: one cache block
   lat->g.dL1 = make_fastdiv((uint32_t)lat->g.L[1]);
   lat->g.dL2 = make_fastdiv((uint32_t)lat->g.L[2]);
   lat->g.dL3 = make_fastdiv((uint32_t)lat->g.L[3]);
@@ -260,6 +262,47 @@ qxd_status qxd_load_gauge(qxd_lattice* lat, const double* su3, const double* a_u
     }
   }
   TRY(ingest_gauge(lat, dsu3, da));
+  TRY(convert_links_low(lat));
+  QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  lat->have_gauge = true;
+  lat->have_clover = false;
+  return QXD_OK;
+}
+
+qxd_status qxd_set_ipt_blocks(qxd_lattice* lat, const int B[4]) {
+  CHECK_LAT(lat);
+  if (!B) return fail(lat, QXD_EINVAL, "B is null");
+  if (lat->order != QXD_ORDER_IPT) return fail(lat, QXD_EINVAL, "cache blocks need QXD_ORDER_IPT");
+  for (int mu = 0; mu < 4; ++mu) {
+    // the blocks must tile the physical lattice (gauge input) and the device lattice (doubled in x for C*)
+    if (B[mu] < 1 || lat->Lphys[mu] % B[mu] != 0 || lat->g.L[mu] % B[mu] != 0)
+      return fail(lat, QXD_EINVAL, "each block extent must divide the lattice extent");
+  }
+  for (int mu = 0; mu < 4; ++mu) lat->g.B[mu] = B[mu];
+  return QXD_OK;
+}
+
+qxd_status qxd_load_gauge_openqxd(qxd_lattice* lat, const double* u8, const double* a8, double q, int on_device) {
+  CHECK_LAT(lat);
+  if (!u8) return fail(lat, QXD_EINVAL, "u8 is null");
+  if (lat->order != QXD_ORDER_IPT) return fail(lat, QXD_EINVAL, "the openQxD gauge format needs QXD_ORDER_IPT");
+  const i64 V = lat->V;
+  const size_t ub = sizeof(double2) * 36 * V, ab = sizeof(double) * 4 * V;  // V/2 odd sites x 8 links
+  lat->q = q;
+  const double2* du = (const double2*)u8;
+  const double* da = a8;
+  if (!on_device) {
+    void* p;
+    TRY(ensure_work(lat, AS_BND_IN, ub, &p));
+    QXD_CUDA(lat, cudaMemcpyAsync(p, u8, ub, cudaMemcpyHostToDevice, lat->stream));
+    du = (const double2*)p;
+    if (a8) {
+      TRY(ensure_work(lat, AS_BND_OUT, ab, &p));
+      QXD_CUDA(lat, cudaMemcpyAsync(p, a8, ab, cudaMemcpyHostToDevice, lat->stream));
+      da = (const double*)p;
+    }
+  }
+  TRY(ingest_gauge_openqxd(lat, du, da));
   TRY(convert_links_low(lat));
   QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
   lat->have_gauge = true;
@@ -391,6 +434,9 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
   if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO && p->solver != QXD_SOLVER_MP_BICGSTAB_EO &&
       p->solver != QXD_SOLVER_MP_FGCR_NET)
     return fail(lat, QXD_EINVAL, "bad solver");
+  if (p->solver == QXD_SOLVER_MP_FGCR_NET && p->fallback != -1 && p->fallback != QXD_SOLVER_CG_EO &&
+      p->fallback != QXD_SOLVER_MP_CG_EO && p->fallback != QXD_SOLVER_MP_BICGSTAB_EO)
+    return fail(lat, QXD_EINVAL, "fallback must be -1, CG_EO, MP_CG_EO or MP_BICGSTAB_EO");
   if (p->solver == QXD_SOLVER_MP_FGCR_NET && (p->gcr_reorth < 1 || p->gcr_reorth > 2))
     return fail(lat, QXD_EINVAL, "gcr_reorth must be 1 or 2");
   if (p->solver == QXD_SOLVER_MP_FGCR_NET && (p->gcr_restart < 1 || p->gcr_restart > 32))

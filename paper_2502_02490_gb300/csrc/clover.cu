@@ -486,8 +486,10 @@ __global__ void k_clover_export(Geom g, int order, const double2* __restrict__ C
     int par;
     i64 cb;
     if (order == QXD_ORDER_IPT) {
-      par = site >= g.Vh ? 1 : 0;
-      cb = site - (i64)par * g.Vh;
+      int x[4];
+      ipt_coords(g.L, g.B, site, x);
+      par = (x[0] + x[1] + x[2] + x[3]) & 1;
+      cb = lexi(g, x) >> 1;
     } else {
       i64 u = site;
       int x3 = (int)(u % g.L[3]);

@@ -2,7 +2,8 @@
 // Sec. 4.2: C* mirror, Sec. 4.3: U(3) hop links).
 //
 // Boundary site orders (pure index functions, no lookup arrays, as Sec. 4.1.1 recommends):
-//   LEXI: boundary index = Lambda(x, L).  IPT: boundary index = cb + P(x) V/2 (Eq. ipt, B = L).
+//   LEXI: boundary index = Lambda(x, L).  IPT: Eq. ipt with the lattice's cache blocks B
+//   (ipt_index / ipt_coords; B = L gives cb + P(x) V/2).
 // Both map onto the device's (parity, cb = floor(Lambda/2)) addressing.
 #include "qxd_internal.cuh"
 
@@ -11,8 +12,10 @@ namespace qxd {
 // (parity, cb) of the site with boundary index i.
 __device__ __forceinline__ void bnd_to_pc(const Geom& g, int order, i64 i, int& par, i64& cb) {
   if (order == QXD_ORDER_IPT) {
-    par = i >= g.Vh ? 1 : 0;
-    cb = i - (i64)par * g.Vh;
+    int x[4];
+    ipt_coords(g.L, g.B, i, x);
+    par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    cb = lexi(g, x) >> 1;
   } else {
     i64 t = i;
     int x3 = (int)(t % g.L[3]);
@@ -105,11 +108,15 @@ __global__ void k_ingest_gauge(Geom g, int order, int Lp1, int Lp2, int Lp3, i64
     i64 lam = (((i64)x[0] * Lp1 + x[1]) * Lp2 + x[2]) * Lp3 + x[3];
     i64 src;
     if (order == QXD_ORDER_IPT) {
-      int pp = (x[0] + x[1] + x[2] + x[3]) & 1;
-      src = (lam >> 1) + (i64)pp * (Vph / 2);
+      const int Lp[4] = {g.L[0], Lp1, Lp2, Lp3};  // the physical lattice
+      int Bp[4];  // one block of the device lattice (the default) is one block of the physical one
+#pragma unroll
+      for (int m = 0; m < 4; ++m) Bp[m] = g.B[m] == g.L[m] ? Lp[m] : g.B[m];
+      src = ipt_index(Lp, Bp, x);
     } else {
       src = lam;
     }
+    (void)Vph;
     double ang = a ? a[src * 4 + mu] : 0.0;
     if (mirror) ang = -ang;
     double sn, cs;
@@ -124,6 +131,51 @@ __global__ void k_ingest_gauge(Geom g, int order, int Lp1, int Lp2, int Lp3, i64
     }
     A[(i64)(par * 4 + mu) * g.sv + cb] = ang;
   }
+}
+
+// Gauge ingest from the openQxD storage: for the odd site x with boundary index x^ (Eq. ipt of
+// this lattice), entry 8 (x^ - V/2) + 2 mu holds U_mu(x) and entry 8 (x^ - V/2) + 2 mu + 1 holds
+// U_mu(x - mu), x - mu the lattice neighbour with the C* shift (every link has exactly one odd
+// end).  The field is the lattice's own (for C* the
+// doubled lattice, mirror half included): no mirroring here.  One thread per (device site, mu).
+__global__ void k_ingest_openqxd(Geom g, const double2* __restrict__ u8, const double* __restrict__ a8, double q,
+                                 double2* __restrict__ U, double* __restrict__ A, double2* __restrict__ W) {
+  const i64 n = 2 * g.Vh * 4;
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
+    const int mu = (int)(t & 3);
+    const i64 s = t >> 2;
+    const int par = s >= g.Vh ? 1 : 0;
+    const i64 cb = s - (i64)par * g.Vh;
+    int x[4];
+    cb_coords(g, cb, par, x);
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    int slot = 2 * mu;
+    if (par == 0) {  // even site: its forward link is the backward link of its neighbour x + mu
+      const bool crossed = y[mu] + 1 == g.L[mu];
+      y[mu] = crossed ? 0 : y[mu] + 1;
+      if (crossed && g.shift && mu >= 2) y[1] = (y[1] + g.shift) % g.L[1];  // C*: lands on the mirror copy
+      slot += 1;
+    }
+    const i64 e = (ipt_index(g.L, g.B, y) - g.Vh) * 8 + slot;
+    const double ang = a8 ? a8[e] : 0.0;
+    double sn, cs;
+    sincos(q * ang, &sn, &cs);
+    const i64 base = ((i64)(par * 4 + mu) * 9) * g.sv + cb;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double2 u = u8[e * 9 + k];
+      U[base + k * g.sv] = u;
+      W[base + k * g.sv] = make_double2(cs * u.x - sn * u.y, cs * u.y + sn * u.x);
+    }
+    A[(i64)(par * 4 + mu) * g.sv + cb] = ang;
+  }
+}
+
+qxd_status ingest_gauge_openqxd(qxd_lattice* lat, const double2* u8, const double* a8) {
+  i64 n = 2 * lat->Vh * 4;
+  k_ingest_openqxd<<<grid_cap(n, 128), 128, 0, lat->stream>>>(lat->g, u8, a8, lat->q, lat->U, lat->A, lat->W64);
+  QXD_CHECK_LAUNCH(lat, "k_ingest_openqxd");
+  return QXD_OK;
 }
 
 qxd_status ingest_gauge(qxd_lattice* lat, const double2* su3, const double* a) {

@@ -62,7 +62,49 @@ struct Geom {
   i64 Vh;      // sites per parity
   i64 sv;      // plane stride
   FastDiv dL1, dL2, dL3;  // divisions by L1, L2, L3 (V < 2^31)
+  int B[4];    // cache-block extents of the IPT boundary order (B = L: one block)
 };
+
+// Eq. ipt with cache blocks: the boundary index of site x on a lattice of extents L with blocks
+// B (each B_mu divides L_mu): floor((V_B Lambda(n, N_B) + Lambda(b, B)) / 2) + P(x) V / 2, with
+// n = floor(x / B) the block and b = x mod B the site within it.  A pure function, no table.
+__host__ __device__ __forceinline__ i64 ipt_index(const int L[4], const int B[4], const int x[4]) {
+  i64 lam_n = 0, lam_b = 0, VB = 1, V = 1;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    lam_n = lam_n * (L[mu] / B[mu]) + x[mu] / B[mu];
+    lam_b = lam_b * B[mu] + x[mu] % B[mu];
+    VB *= B[mu];
+    V *= L[mu];
+  }
+  const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+  return (VB * lam_n + lam_b) / 2 + (i64)par * (V / 2);
+}
+
+// Inverse of ipt_index: the site of boundary index i.  Of the two blocked lexicographic indices
+// 2k and 2k + 1 (k = i - P V/2) exactly one has parity P.
+__host__ __device__ __forceinline__ void ipt_coords(const int L[4], const int B[4], i64 i, int x[4]) {
+  i64 VB = 1, V = 1;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    VB *= B[mu];
+    V *= L[mu];
+  }
+  const int par = i >= V / 2 ? 1 : 0;
+  const i64 k = i - (i64)par * (V / 2);
+  for (int c = 0; c < 2; ++c) {
+    const i64 lam = 2 * k + c;
+    i64 ln = lam / VB, lb = lam % VB;
+#pragma unroll
+    for (int mu = 3; mu >= 0; --mu) {
+      const int nb = L[mu] / B[mu];
+      x[mu] = (int)(ln % nb) * B[mu] + (int)(lb % B[mu]);
+      ln /= nb;
+      lb /= B[mu];
+    }
+    if (((x[0] + x[1] + x[2] + x[3]) & 1) == par) return;
+  }
+}
 
 __host__ __device__ __forceinline__ i64 lexi(const Geom& g, const int x[4]) {
   return (((i64)x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3];
@@ -635,6 +677,7 @@ inline int grid_for(i64 n, int bs) { return (int)((n + bs - 1) / bs); }
 qxd_status pack_spinor64(qxd_lattice* lat, const double2* bnd, double2* field, int nsites_half_only);
 qxd_status unpack_spinor64(qxd_lattice* lat, const double2* field, double2* bnd, int nsites_half_only);
 qxd_status ingest_gauge(qxd_lattice* lat, const double2* su3, const double* a);
+qxd_status ingest_gauge_openqxd(qxd_lattice* lat, const double2* u8, const double* a8);
 qxd_status convert_links_low(qxd_lattice* lat);
 qxd_status f64_to_f32(qxd_lattice* lat, const double2* in, float4* out, i64 nplanes_sites);
 qxd_status f32_to_f64(qxd_lattice* lat, const float4* in, double2* out, i64 nplanes_sites);

@@ -13,6 +13,7 @@
 // Every global inner product and norm is an FP64 reduction.
 #include <chrono>
 #include <cmath>
+#include <cstring>
 
 #include "reduce.cuh"
 
@@ -370,8 +371,28 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
                              qxd_solve_info* info);
 
 qxd_status solve(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve_params* prm, qxd_solve_info* info) {
+  auto t0 = std::chrono::steady_clock::now();
   qxd_status st = solve_impl(lat, x, b, prm, info);
   if (st != QXD_OK && info && info->status == QXD_OK) info->status = st;  // early failure: record it
+  // the learned solve missed the tolerance (or broke down): the plain solver takes over from scratch
+  if (st != QXD_OK && st != QXD_EINVAL && st != QXD_ESTATE && st != QXD_ECUDA && st != QXD_ENOMEM &&
+      prm->solver == QXD_SOLVER_MP_FGCR_NET && prm->fallback >= 0) {
+    qxd_solve_params fp;
+    qxd_default_params(&fp);
+    fp.solver = prm->fallback;
+    fp.tol = prm->tol;
+    fp.on_device = prm->on_device;
+    fp.check_every = prm->check_every;
+    qxd_solve_info fi;
+    std::memset(&fi, 0, sizeof(fi));
+    st = solve_impl(lat, x, b, &fp, &fi);
+    if (st != QXD_OK && fi.status == QXD_OK) fi.status = st;
+    if (info) {
+      *info = fi;
+      info->fallback_used = 1;
+      info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+  }
   return st;
 }
 

@@ -34,7 +34,7 @@ class SolveParams(C.Structure):
     _fields_ = [("version", C.c_int), ("solver", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int),
                 ("inner_prec", C.c_int), ("inner_tol", C.c_double), ("reliable_delta", C.c_double),
                 ("max_outer", C.c_int), ("on_device", C.c_int), ("check_every", C.c_int),
-                ("gcr_restart", C.c_int), ("net", C.c_void_p), ("gcr_reorth", C.c_int)]
+                ("gcr_restart", C.c_int), ("net", C.c_void_p), ("gcr_reorth", C.c_int), ("fallback", C.c_int)]
 
 
 class TrainParams(C.Structure):
@@ -44,7 +44,8 @@ class TrainParams(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters_inner", C.c_int), ("iters_outer", C.c_int), ("reliable_updates", C.c_int),
-                ("true_rel_res", C.c_double), ("seconds", C.c_double), ("status", C.c_int)]
+                ("true_rel_res", C.c_double), ("seconds", C.c_double), ("status", C.c_int),
+                ("fallback_used", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -74,6 +75,8 @@ _SIGS = {
     "qxd_net_set_weights": [_vp, _vp],
     "qxd_net_get_weights": [_vp, _vp],
     "qxd_net_apply": [_vp, _vp, _vp, _i],
+    "qxd_set_ipt_blocks": [_vp, C.POINTER(C.c_int)],
+    "qxd_load_gauge_openqxd": [_vp, _vp, _vp, _d, _i],
     "qxd_net_set_precision": [_vp, _i],
     "qxd_net_loss_grad": [_vp, _vp, _vp, _i, _i, C.POINTER(_d), _vp],
     "qxd_net_train": [_vp, _vp, _i, C.POINTER(TrainParams), _vp, _i],
@@ -141,6 +144,18 @@ def load_gauge(lat, su3, a_u1, q):
     p, dev = _ptr(su3)
     pa, _ = _ptr(a_u1)
     _check(lib.qxd_load_gauge(lat, p, pa, float(q), int(dev)), lat)
+
+
+def set_ipt_blocks(lat, B):
+    arr = (C.c_int * 4)(*[int(v) for v in B])
+    _check(lib.qxd_set_ipt_blocks(lat, arr), lat)
+
+
+def load_gauge_openqxd(lat, u8, a8, q):
+    """qxd_load_gauge_openqxd: u8 [V/2][8][3][3] complex, a8 [V/2][8] (or None), host or device."""
+    pu, dev = _ptr(u8)
+    pa = _ptr(a8)[0] if a8 is not None else None
+    _check(lib.qxd_load_gauge_openqxd(lat, pu, pa, float(q), int(dev)), lat)
 
 
 def build_clover(lat, m0, csw, csw_qed):

@@ -20,9 +20,10 @@ class Case:
     """One lattice set up both on the GPU (through the C ABI) and in the oracle."""
 
     def __init__(self, qxd, torch, L, anti=True, cstar=False, order=0, eps=0.3, seed=1000, q=-1 / 3, m0=-0.1,
-                 csw=1.9, csw_qed=1.0, on_device=True, build=True):
+                 csw=1.9, csw_qed=1.0, on_device=True, build=True, blocks=None, openqxd_gauge=False):
         self.qxd, self.torch = qxd, torch
         self.L, self.anti, self.cstar, self.order = tuple(L), anti, cstar, order
+        self.blocks = tuple(blocks) if blocks is not None else None
         self.q, self.m0, self.csw, self.csw_qed = q, m0, csw, csw_qed
         self.lat_o = O.Lattice(L, antiperiodic=anti, cstar=cstar)
         self.dims = self.lat_o.dims
@@ -37,10 +38,16 @@ class Case:
         self.stream = torch.cuda.current_stream(self.dev)
         self.lat = qxd.create_lattice(L, qxd.BC_ANTIPERIODIC if anti else qxd.BC_PERIODIC, int(cstar), order,
                                       self.stream.cuda_stream)
+        if self.blocks is not None:
+            qxd.set_ipt_blocks(self.lat, self.blocks)
         Ub, Ab = U, A
         if order == qxd.ORDER_IPT:
-            Ub, Ab = O.to_ipt_order(U, L), O.to_ipt_order(A, L)
-        if on_device:
+            Ub, Ab = O.to_ipt_order(U, L, self.blocks), O.to_ipt_order(A, L, self.blocks)
+        if openqxd_gauge:  # the lattice's own field (doubled for C*) as eight links per odd site
+            u8, a8 = O.openqxd_gauge(self.U, self.A, self.dims, self.blocks, cstar=cstar)
+            qxd.load_gauge_openqxd(self.lat, torch.from_numpy(np.ascontiguousarray(u8).view(np.float64)).to(self.dev),
+                                   torch.from_numpy(np.ascontiguousarray(a8)).to(self.dev), q)
+        elif on_device:
             qxd.load_gauge(self.lat, torch.from_numpy(np.ascontiguousarray(Ub).view(np.float64)).to(self.dev),
                            torch.from_numpy(np.ascontiguousarray(Ab)).to(self.dev), q)
         else:
@@ -56,10 +63,10 @@ class Case:
         return self._op
 
     def to_boundary(self, arr):
-        return O.to_ipt_order(arr, self.dims) if self.order == self.qxd.ORDER_IPT else arr
+        return O.to_ipt_order(arr, self.dims, self.blocks) if self.order == self.qxd.ORDER_IPT else arr
 
     def from_boundary(self, arr):
-        return O.from_ipt_order(arr, self.dims) if self.order == self.qxd.ORDER_IPT else arr
+        return O.from_ipt_order(arr, self.dims, self.blocks) if self.order == self.qxd.ORDER_IPT else arr
 
     def dev_tensor(self, arr):
         return self.torch.from_numpy(np.ascontiguousarray(arr).view(np.float64)).to(self.dev)

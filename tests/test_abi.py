@@ -50,6 +50,6 @@ def test_invalid_extents_rejected_without_gpu(qxd):
 def test_default_params(qxd):
     p = qxd.default_params()
     assert p.version == qxd.PARAMS_VERSION and p.tol == 1e-10 and p.solver == qxd.SOLVER_MP_CG_EO
-    assert p.gcr_restart == 16 and p.gcr_reorth == 1 and p.check_every == 1
+    assert p.gcr_restart == 16 and p.gcr_reorth == 1 and p.check_every == 1 and p.fallback == -1
     assert qxd.lib.qxd_destroy_lattice(None) == qxd.OK
     assert qxd.launch_count(None) == 0

@@ -128,3 +128,23 @@ def test_training_lowers_the_loss_and_fgcr_solves(qxd):
     finally:
         qxd.net_destroy(net)
         c.close()
+
+
+def test_learned_solve_falls_back_to_plain_solver(qxd):
+    c = Case(qxd, torch, (4, 4, 4, 4), m0=-0.3)
+    net = qxd.net_create(c.lat, [1, 4, 1], seed=5)  # untrained
+    try:
+        eta = synth.gaussian_spinor(c.dims, 2100)
+        b = c.dev_tensor(eta)
+        x = torch.empty_like(b)
+        kw = dict(solver=qxd.SOLVER_MP_FGCR_NET, inner_prec=qxd.F32, tol=1e-10, gcr_restart=8, net=net, maxiter=3,
+                  max_outer=1)
+        st, info = qxd.solve(c.lat, x, b, check=False, **kw)
+        assert st == qxd.ENOCONV and info["fallback_used"] == 0
+        for fb in (qxd.SOLVER_CG_EO, qxd.SOLVER_MP_BICGSTAB_EO):
+            st, info = qxd.solve(c.lat, x, b, check=False, fallback=fb, **kw)
+            assert st == qxd.OK and info["fallback_used"] == 1 and info["status"] == qxd.OK, info
+            assert O.true_rel_residual(c.op, as_c128(x, eta.shape), eta) <= 1e-10
+    finally:
+        qxd.net_destroy(net)
+        c.close()
