@@ -71,7 +71,7 @@ __device__ __forceinline__ M3 mul(const M3& a, const M3& b) {
       for (int k = 0; k < 3; ++k) {
         cd x = DA ? mk(a.m[3 * k + i].re, -a.m[3 * k + i].im) : a.m[3 * i + k];
         cd y = DB ? mk(b.m[3 * j + k].re, -b.m[3 * j + k].im) : b.m[3 * k + j];
-        s = s + cmul(x, y);
+        s = cmac(s, x, y);  // fused: four FP64 FMAs per complex term
       }
       c.m[3 * i + j] = s;
     }

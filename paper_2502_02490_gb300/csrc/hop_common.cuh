@@ -65,7 +65,7 @@ __device__ __forceinline__ void link_mul(const cplx<R> u[9], const cplx<R> h[6],
     for (int a = 0; a < 3; ++a) {
       cplx<R> r = DAG ? cjmul(u[a], h[3 * s]) : cmul(u[3 * a], h[3 * s]);
 #pragma unroll
-      for (int b = 1; b < 3; ++b) r = r + (DAG ? cjmul(u[3 * b + a], h[3 * s + b]) : cmul(u[3 * a + b], h[3 * s + b]));
+      for (int b = 1; b < 3; ++b) r = DAG ? cjmac(r, u[3 * b + a], h[3 * s + b]) : cmac(r, u[3 * a + b], h[3 * s + b]);
       g[3 * s + a] = r;
     }
 }

@@ -206,6 +206,22 @@ template <typename T>
 __device__ __forceinline__ cplx<T> cjmul(cplx<T> a, cplx<T> b) {
   return mk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
 }
+// s + a b and s + conj(a) b as four fused multiply-adds (accumulating into s directly: one
+// rounding per product term, no separate products and additions)
+template <typename T>
+__device__ __forceinline__ cplx<T> cmac(cplx<T> s, cplx<T> a, cplx<T> b) {
+  T re = fma(a.re, b.re, s.re), im = fma(a.re, b.im, s.im);
+  re = fma(-a.im, b.im, re);
+  im = fma(a.im, b.re, im);
+  return mk(re, im);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cjmac(cplx<T> s, cplx<T> a, cplx<T> b) {
+  T re = fma(a.re, b.re, s.re), im = fma(a.re, b.im, s.im);
+  re = fma(a.im, b.im, re);
+  im = fma(-a.im, b.re, im);
+  return mk(re, im);
+}
 template <typename T>
 __device__ __forceinline__ cplx<T> timesI(cplx<T> a) { return mk(-a.im, a.re); }
 template <typename T>
@@ -535,8 +551,8 @@ __device__ __forceinline__ void herm6_apply(const R r[36], const cplx<R> x[6], c
 #pragma unroll
     for (int j = i + 1; j < 6; ++j) {
       cplx<R> c = mk(r[6 + 2 * k], r[7 + 2 * k]);
-      y[i] = y[i] + cmul(c, x[j]);
-      y[j] = y[j] + cjmul(c, x[i]);
+      y[i] = cmac(y[i], c, x[j]);
+      y[j] = cjmac(y[j], c, x[i]);
       ++k;
     }
   }
