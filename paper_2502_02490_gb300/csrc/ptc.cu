@@ -73,15 +73,27 @@ __device__ __forceinline__ void ptc_transport(const Geom& g, const float2* __res
     float2 w = __ldg(W + ((i64)(lp * 4 + mu) * 9 + k) * g.sv + ls);
     u[k] = mk(w.x, w.y);
   }
+  if (fwd) {  // separate loops: each path executes only its own products
 #pragma unroll
-  for (int sp = 0; sp < 4; ++sp)
+    for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      cplx<float> r = mk(0.f, 0.f);
+      for (int a = 0; a < 3; ++a) {
+        cplx<float> r = mk(0.f, 0.f);
 #pragma unroll
-      for (int b = 0; b < 3; ++b) r = r + (fwd ? cmul(u[3 * a + b], s[3 * sp + b]) : cjmul(u[3 * b + a], s[3 * sp + b]));
-      out[3 * sp + a] = r;
-    }
+        for (int b = 0; b < 3; ++b) r = cmac(r, u[3 * a + b], s[3 * sp + b]);
+        out[3 * sp + a] = r;
+      }
+  } else {
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        cplx<float> r = mk(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) r = cjmac(r, u[3 * b + a], s[3 * sp + b]);
+        out[3 * sp + a] = r;
+      }
+  }
 }
 
 // out[co] (par, cb) = sum_{ci, p} Om[co][ci][p] (T_p in_ci)(x)
@@ -130,7 +142,7 @@ __global__ void __launch_bounds__(PT_SITES* PT_MAXC) k_ptc_layer(Geom g, int cin
         for (int sp = 0; sp < 4; ++sp) {
           cplx<float> r = acc[3 * sp + a];
 #pragma unroll
-          for (int t = 0; t < 4; ++t) r = r + cmul(m[4 * sp + t], tv[t]);
+          for (int t = 0; t < 4; ++t) r = cmac(r, m[4 * sp + t], tv[t]);
           acc[3 * sp + a] = r;
         }
       }
@@ -220,7 +232,7 @@ __global__ void __launch_bounds__(WG_THREADS) k_ptc_wgrad(Geom g, int cin, int c
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             float2 gv = G[co][3 * sp + a][s], tv = T[ci][3 * t + a][s];
-            r = r + cjmul(mk(tv.x, tv.y), mk(gv.x, gv.y));  // g * conj(T)
+            r = cjmac(r, mk(tv.x, tv.y), mk(gv.x, gv.y));  // g * conj(T)
           }
         acc[k] = r;
       }

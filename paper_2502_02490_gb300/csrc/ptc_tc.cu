@@ -125,7 +125,7 @@ __device__ __forceinline__ void put_transported_m(unsigned char* a0, int s, int 
         cplx<float> r = mk(0.f, 0.f);
 #pragma unroll
         for (int b = 0; b < 3; ++b)
-          r = r + (MODE == 2 ? cmul(u[3 * a + b], comp(3 * be + b)) : cjmul(u[3 * b + a], comp(3 * be + b)));
+          r = MODE == 2 ? cmac(r, u[3 * a + b], comp(3 * be + b)) : cjmac(r, u[3 * b + a], comp(3 * be + b));
         t[be] = r;
       }
     }
@@ -409,15 +409,21 @@ __global__ void __launch_bounds__(256) k_ptc_pull(Geom g, int cout, const float4
         sp[2 * jj] = mk(q.x, q.y);
         sp[2 * jj + 1] = mk(q.z, q.w);
       }
+      if (fwd) {  // separate loops: each path executes only its own products
 #pragma unroll
-      for (int be = 0; be < 4; ++be)
+        for (int be = 0; be < 4; ++be)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          cplx<float> r = acc[3 * be + a];
+          for (int a = 0; a < 3; ++a)
 #pragma unroll
-          for (int b = 0; b < 3; ++b) r = r + (fwd ? cmul(u[3 * a + b], sp[3 * be + b]) : cjmul(u[3 * b + a], sp[3 * be + b]));
-          acc[3 * be + a] = r;
-        }
+            for (int b = 0; b < 3; ++b) acc[3 * be + a] = cmac(acc[3 * be + a], u[3 * a + b], sp[3 * be + b]);
+      } else {
+#pragma unroll
+        for (int be = 0; be < 4; ++be)
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) acc[3 * be + a] = cjmac(acc[3 * be + a], u[3 * b + a], sp[3 * be + b]);
+      }
     }
     float4* o = out + (i64)c * cs + (i64)par * 6 * g.sv + cb;
 #pragma unroll
