@@ -160,6 +160,20 @@ def make_inputs(rank):
     return U, A, eta
 
 
+def aggregate_ranks(t_s, e2e_s, nbytes, world, dev):
+    """Whole-job figures of a replicas run: the slowest rank's times (max over ranks) and the bytes
+    of all ranks (sum); identity on one rank.  dev: the tensors' device (the process group's)."""
+    if world <= 1:
+        return t_s, e2e_s, nbytes
+    import torch
+
+    tt = torch.tensor([t_s, e2e_s], device=dev, dtype=torch.float64)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    hb = torch.tensor([nbytes], device=dev, dtype=torch.float64)
+    torch.distributed.all_reduce(hb)
+    return float(tt[0]), float(tt[1]), float(hb[0])
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -240,16 +254,7 @@ def run_ours(args, rank, world):
     qxd.destroy_lattice(lat)
 
     # ---- aggregate over ranks ----
-    t_s = ms_total / 1e3
-    if world > 1:
-        tt = torch.tensor([t_s, e2e_s], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_s, e2e_s = float(tt[0]), float(tt[1])
-        hb = torch.tensor([hop_bytes], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(hb)
-        hop_total = float(hb[0])
-    else:
-        hop_total = hop_bytes
+    t_s, e2e_s, hop_total = aggregate_ranks(ms_total / 1e3, e2e_s, hop_bytes, world, dev)
     dom = max(stats, key=lambda k: stats[k][1])
     n_l, ms_l, b_l = stats[dom]
     peak, peak_kind = measured_peaks()
