@@ -78,95 +78,101 @@ __device__ __forceinline__ M3 mul(const M3& a, const M3& b) {
   return c;
 }
 
-// Traceless anti-Hermitian Fhat_{mu nu}(x) = (Q - Q^dag)/8 - tr/3 and the U(1) fhat (its imaginary
-// part, f1 = 1/4 sum_leaves sin(phi_leaf)), for the plane (MU, NU) fixed at compile time: every
-// site index stays in registers.
+// Plaquette half-products of the plane (MU, NU) at every site y: A(y) = U_mu(y) U_nu(y+mu),
+// B(y) = U_nu(y) U_mu(y+nu) (so the plaquette at y is A B^+), and the sine of the U(1)
+// plaquette angle A_mu(y) + A_nu(y+mu) - A_mu(y+nu) - A_nu(y).  Stored [k][2 sv]: k < 9 A,
+// 9 <= k < 18 B (double2), then the sines [2 sv] (doubles).
 template <int MU, int NU>
-__device__ __forceinline__ void field_strength_t(const Geom& g, const double2* __restrict__ U, const double* __restrict__ A,
-                                                 const int x[4], M3& F, double& f1) {
-  M3 Q;
-  double s1;
-  {  // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
-    int xp[4] = {x[0], x[1], x[2], x[3]}, t[4] = {x[0], x[1], x[2], x[3]};
-    step(g, xp, MU, +1);
-    step(g, t, NU, +1);
-    const M3 a = load_u(g, U, x, MU), b = load_u(g, U, xp, NU), c = load_u(g, U, t, MU), d = load_u(g, U, x, NU);
-    Q = mul<false, true>(mul<false, true>(mul<false, false>(a, b), c), d);
-    s1 = sin(load_a(g, A, x, MU) + load_a(g, A, xp, NU) - load_a(g, A, t, MU) - load_a(g, A, x, NU));
-  }
-  {  // leaf 2: U_nu(x) U_mu(x+nu-mu)^+ U_nu(x-mu)^+ U_mu(x-mu)
-    int xm[4] = {x[0], x[1], x[2], x[3]};
-    step(g, xm, MU, -1);
-    int xnm[4] = {xm[0], xm[1], xm[2], xm[3]};
-    step(g, xnm, NU, +1);
-    const M3 a = load_u(g, U, x, NU), b = load_u(g, U, xnm, MU), c = load_u(g, U, xm, NU), d = load_u(g, U, xm, MU);
-    const M3 r = mul<false, false>(mul<false, true>(mul<false, true>(a, b), c), d);
+__global__ void __launch_bounds__(128) k_clover_half(Geom g, const double2* __restrict__ U, const double* __restrict__ A,
+                                                     double2* __restrict__ Hb) {
+  const i64 n = 2 * g.Vh, st = 2 * g.sv;
+  for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x) {
+    const int par = e >= g.Vh ? 1 : 0;
+    const i64 cb = e - (i64)par * g.Vh;
+    int y[4];
+    cb_coords(g, cb, par, y);
+    int ym[4] = {y[0], y[1], y[2], y[3]}, yn[4] = {y[0], y[1], y[2], y[3]};
+    step(g, ym, MU, +1);
+    step(g, yn, NU, +1);
+    const M3 a = mul<false, false>(load_u(g, U, y, MU), load_u(g, U, ym, NU));
+    const M3 b = mul<false, false>(load_u(g, U, y, NU), load_u(g, U, yn, MU));
+    const i64 s0 = (i64)par * g.sv + cb;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
-    s1 += sin(load_a(g, A, x, NU) - load_a(g, A, xnm, MU) - load_a(g, A, xm, NU) + load_a(g, A, xm, MU));
-  }
-  {  // leaf 3: U_mu(x-mu)^+ U_nu(x-mu-nu)^+ U_mu(x-mu-nu) U_nu(x-nu)
-    int xm[4] = {x[0], x[1], x[2], x[3]}, xn[4] = {x[0], x[1], x[2], x[3]};
-    step(g, xm, MU, -1);
-    int xmn[4] = {xm[0], xm[1], xm[2], xm[3]};
-    step(g, xmn, NU, -1);
-    step(g, xn, NU, -1);
-    const M3 a = load_u(g, U, xm, MU), b = load_u(g, U, xmn, NU), c = load_u(g, U, xmn, MU), d = load_u(g, U, xn, NU);
-    const M3 r = mul<false, false>(mul<false, false>(mul<true, true>(a, b), c), d);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
-    s1 += sin(-load_a(g, A, xm, MU) - load_a(g, A, xmn, NU) + load_a(g, A, xmn, MU) + load_a(g, A, xn, NU));
-  }
-  {  // leaf 4: U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^+
-    int xn[4] = {x[0], x[1], x[2], x[3]};
-    step(g, xn, NU, -1);
-    int xnp[4] = {xn[0], xn[1], xn[2], xn[3]};
-    step(g, xnp, MU, +1);
-    const M3 a = load_u(g, U, xn, NU), b = load_u(g, U, xn, MU), c = load_u(g, U, xnp, NU), d = load_u(g, U, x, MU);
-    const M3 r = mul<false, true>(mul<false, false>(mul<true, false>(a, b), c), d);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
-    s1 += sin(-load_a(g, A, xn, NU) + load_a(g, A, xn, MU) + load_a(g, A, xnp, NU) - load_a(g, A, x, MU));
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const cd a = Q.m[3 * i + j], b = Q.m[3 * j + i];
-      F.m[3 * i + j] = mk((a.re - b.re) * 0.125, (a.im + b.im) * 0.125);
+    for (int k = 0; k < 9; ++k) {
+      Hb[k * st + s0] = make_double2(a.m[k].re, a.m[k].im);
+      Hb[(9 + k) * st + s0] = make_double2(b.m[k].re, b.m[k].im);
     }
-  const double tr_im = (F.m[0].im + F.m[4].im + F.m[8].im) / 3.0;
-  F.m[0].im -= tr_im;
-  F.m[4].im -= tr_im;
-  F.m[8].im -= tr_im;
-  f1 = 0.25 * s1;
+    ((double*)(Hb + 18 * st))[s0] =
+        sin(load_a(g, A, y, MU) + load_a(g, A, ym, NU) - load_a(g, A, yn, MU) - load_a(g, A, y, NU));
+  }
 }
 
-// Field strength of plane p = blockIdx.y for every site (both parities):
-// planes 0..2 = (0,1) (0,2) (0,3), 3 = (2,3), 4 = (1,3), 5 = (1,2).  Stored compactly per site as
-// 10 doubles [plane][k][2 sv]: Im F_00, Im F_11, Im F_22, (Re, Im) F_01, F_02, F_12 (the lower
-// triangle is -conj), and fhat.
-__global__ void __launch_bounds__(128) k_clover_fs(Geom g, const double2* __restrict__ U, const double* __restrict__ A,
-                                                   double* __restrict__ Fb) {
-  const int p = blockIdx.y;
-  const i64 n = 2 * g.Vh;
+__device__ __forceinline__ M3 load_h(const double2* __restrict__ Hb, i64 st, i64 s, int which) {
+  M3 r;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const double2 v = Hb[(which * 9 + k) * st + s];
+    r.m[k] = mk(v.x, v.y);
+  }
+  return r;
+}
+
+__device__ __forceinline__ i64 site_of(const Geom& g, const int y[4]) {
+  const int par = (y[0] + y[1] + y[2] + y[3]) & 1;
+  return (i64)par * g.sv + (lexi(g, y) >> 1);
+}
+
+// The four leaves of the plane (MU, NU) at x from the half-products of the plaquettes around it:
+//   leaf 1 = A(x) B(x)^+,  leaf 2 = U_nu(x) B(x-mu)^+ U_mu(x-mu),  leaf 3 = B(x-mu-nu)^+ A(x-mu-nu),
+//   leaf 4 = U_nu(x-nu)^+ A(x-nu) U_mu(x)^+
+// (each leaf is its plaquette rotated to start at x, so its U(1) angle is the plaquette's);
+// then Fhat = (Q - Q^+)/8 traceless and fhat = 1/4 sum of the sines, stored in the compact layout below.
+template <int MU, int NU>
+__global__ void __launch_bounds__(128) k_clover_leaves(Geom g, const double2* __restrict__ U, const double2* __restrict__ Hb,
+                                                       int p, double* __restrict__ Fb) {
+  const i64 n = 2 * g.Vh, st = 2 * g.sv;
+  const double* sn = (const double*)(Hb + 18 * st);
   for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x) {
     const int par = e >= g.Vh ? 1 : 0;
     const i64 cb = e - (i64)par * g.Vh;
     int x[4];
     cb_coords(g, cb, par, x);
-    M3 F;
-    double f1;
-    switch (p) {
-      case 0: field_strength_t<0, 1>(g, U, A, x, F, f1); break;
-      case 1: field_strength_t<0, 2>(g, U, A, x, F, f1); break;
-      case 2: field_strength_t<0, 3>(g, U, A, x, F, f1); break;
-      case 3: field_strength_t<2, 3>(g, U, A, x, F, f1); break;
-      case 4: field_strength_t<1, 3>(g, U, A, x, F, f1); break;
-      default: field_strength_t<1, 2>(g, U, A, x, F, f1); break;
+    int xm[4] = {x[0], x[1], x[2], x[3]}, xn[4] = {x[0], x[1], x[2], x[3]};
+    step(g, xm, MU, -1);
+    step(g, xn, NU, -1);
+    int xmn[4] = {xm[0], xm[1], xm[2], xm[3]};
+    step(g, xmn, NU, -1);
+    const i64 s0 = (i64)par * g.sv + cb, s1 = site_of(g, xm), s2 = site_of(g, xmn), s3 = site_of(g, xn);
+    M3 Q = mul<false, true>(load_h(Hb, st, s0, 0), load_h(Hb, st, s0, 1));
+    {
+      const M3 r = mul<false, false>(mul<false, true>(load_u(g, U, x, NU), load_h(Hb, st, s1, 1)), load_u(g, U, xm, MU));
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
     }
-    const i64 st = 2 * g.sv, s = (i64)par * g.sv + cb;
-    double* o = Fb + (i64)p * 10 * st + s;
+    {
+      const M3 r = mul<true, false>(load_h(Hb, st, s2, 1), load_h(Hb, st, s2, 0));
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
+    }
+    {
+      const M3 r = mul<false, true>(mul<true, false>(load_u(g, U, xn, NU), load_h(Hb, st, s3, 0)), load_u(g, U, x, MU));
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
+    }
+    M3 F;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const cd a = Q.m[3 * i + j], b = Q.m[3 * j + i];
+        F.m[3 * i + j] = mk((a.re - b.re) * 0.125, (a.im + b.im) * 0.125);
+      }
+    const double tr_im = (F.m[0].im + F.m[4].im + F.m[8].im) / 3.0;
+    F.m[0].im -= tr_im;
+    F.m[4].im -= tr_im;
+    F.m[8].im -= tr_im;
+    const double f1 = 0.25 * (sn[s0] + sn[s1] + sn[s2] + sn[s3]);
+    double* o = Fb + (i64)p * 10 * st + s0;
     o[0 * st] = F.m[0].im;
     o[1 * st] = F.m[4].im;
     o[2 * st] = F.m[8].im;
@@ -180,6 +186,9 @@ __global__ void __launch_bounds__(128) k_clover_fs(Geom g, const double2* __rest
   }
 }
 
+// Field strengths per site and plane (written by k_clover_leaves): planes 0..2 = (0,1) (0,2)
+// (0,3), 3 = (2,3), 4 = (1,3), 5 = (1,2); 10 doubles [plane][k][2 sv]: Im F_00, Im F_11, Im F_22,
+// (Re, Im) F_01, F_02, F_12 (the lower triangle is -conj), and fhat.
 __device__ __forceinline__ void load_fs(const double* __restrict__ Fb, i64 st, i64 s, int p, cd F[9], double& f1) {
   const double* o = Fb + (i64)p * 10 * st + s;
   const cd a01 = mk(o[3 * st], o[4 * st]), a02 = mk(o[5 * st], o[6 * st]), a12 = mk(o[7 * st], o[8 * st]);
@@ -439,15 +448,32 @@ qxd_status clover_build(qxd_lattice* lat) {
   const Geom& g = lat->g;
   // field strengths of the six planes (one thread per site and plane), then the blocks; the
   // field-strength buffer (10 doubles per site and plane) is released afterwards
+  // plane by plane: plaquette half-products (and U(1) sines) at every site, then the four leaves
+  // of every site from them (8 3x3 products per site and plane instead of 12)
   double* Fb;
+  double2* Hb;
   QXD_CUDA(lat, cudaMalloc(&Fb, sizeof(double) * 6 * 10 * 2 * g.sv));
-  {
-    dim3 grid((unsigned)grid_cap(2 * g.Vh, 128), 6);
-    k_clover_fs<<<grid, 128, 0, lat->stream>>>(g, lat->U, lat->A, Fb);
+  if (cudaMalloc(&Hb, sizeof(double2) * 19 * 2 * g.sv) != cudaSuccess) {
+    cudaFree(Fb);
+    return fail(lat, QXD_ENOMEM, "clover build scratch");
   }
-  cudaError_t le = cudaGetLastError();
+  cudaError_t le = cudaSuccess;
+  const int gc = grid_cap(2 * g.Vh, 128);
+#define QXD_PLANE(P, M, N)                                                                  \
+  if (le == cudaSuccess) {                                                                  \
+    k_clover_half<M, N><<<gc, 128, 0, lat->stream>>>(g, lat->U, lat->A, Hb);                \
+    k_clover_leaves<M, N><<<gc, 128, 0, lat->stream>>>(g, lat->U, Hb, P, Fb);               \
+    le = cudaGetLastError();                                                                \
+    if (le == cudaSuccess) lat->launches += 2;                                              \
+  }
+  QXD_PLANE(0, 0, 1)
+  QXD_PLANE(1, 0, 2)
+  QXD_PLANE(2, 0, 3)
+  QXD_PLANE(3, 2, 3)
+  QXD_PLANE(4, 1, 3)
+  QXD_PLANE(5, 1, 2)
+#undef QXD_PLANE
   if (le == cudaSuccess) {
-    lat->launches++;
     k_clover_assemble<<<grid_cap(2 * g.Vh, 128), 128, 0, lat->stream>>>(g, Fb, 4.0 + lat->m0, lat->csw,
                                                                         lat->q * lat->csw_qed, lat->C64);
     le = cudaGetLastError();
@@ -455,7 +481,8 @@ qxd_status clover_build(qxd_lattice* lat) {
   }
   cudaStreamSynchronize(lat->stream);
   cudaFree(Fb);
-  if (le != cudaSuccess) return cuda_fail(lat, le, "k_clover_fs / k_clover_assemble");
+  cudaFree(Hb);
+  if (le != cudaSuccess) return cuda_fail(lat, le, "k_clover_half / k_clover_leaves / k_clover_assemble");
   void* w;
   qxd_status st = ensure_work(lat, 30, sizeof(int), &w);  // slot 30: clover singular flag
   if (st) return st;
