@@ -585,7 +585,8 @@ def run_c4(args):
 
 def profile_run(args):
     """One untimed pass of the step (for ncu launch lists and kernel captures).  c4: 40 steps of
-    the learned FGCR with an untrained [1,8,8,1] network at m0 = -0.1; c3b: one batched solve."""
+    the learned FGCR with an untrained [1,8,8,1] network at m0 = -0.1; c3b: one batched solve;
+    c3a: one multi-RHS solve of the 12 point sources."""
     import torch
 
     from paper_2502_02490_gb300 import qxd, synth
@@ -603,6 +604,20 @@ def profile_run(args):
         torch.cuda.synchronize()
         print(f"profile run: learned FGCR, 40 steps, {info}", file=sys.stderr)
         qxd.net_destroy(net)
+        qxd.destroy_lattice(lat)
+        return
+    if args.workload == "c3a":
+        U, A = synth.gauge_field(w["L"], w["gauge_seed"], w["eps"])
+        eta = np.stack([synth.point_source(w["L"], k // 3, k % 3) for k in range(12)])
+        b = torch.from_numpy(eta.view(np.float64)).to(dev)
+        x = torch.empty_like(b)
+        lat = qxd.create_lattice(w["L"], qxd.BC_ANTIPERIODIC, 0, qxd.ORDER_LEXI, stream.cuda_stream)
+        qxd.load_gauge(lat, torch.from_numpy(U.view(np.float64)).to(dev), torch.from_numpy(A).to(dev), w["q"])
+        qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
+        p = qxd.default_params(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=qxd.F32, tol=1e-10)
+        st, infos = qxd.solve_mrhs(lat, x, b, 12, params=p)
+        torch.cuda.synchronize()
+        print(f"profile run: multi-RHS solve, {infos[0]}", file=sys.stderr)
         qxd.destroy_lattice(lat)
         return
     if args.workload == "c3b":

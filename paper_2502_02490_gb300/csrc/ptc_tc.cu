@@ -492,12 +492,10 @@ static qxd_status launch_tc(qxd_lattice* lat, int cin, int cout, int npaths, con
   const size_t base = (size_t)TC_STAGES * TC_ABYTES;
   L.b_resident = base + bchunk * L.nchunks <= TC_SMEM_MAX;
   const size_t smem = base + bchunk * (L.b_resident ? L.nchunks : TC_STAGES);
-  static bool configured = false;
-  if (!configured) {
-    QXD_CUDA(lat, cudaFuncSetAttribute(k_ptc_layer_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX));
-    QXD_CUDA(lat, cudaFuncSetAttribute(k_ptc_layer_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX));
-    configured = true;
-  }
+  // the dynamic shared-memory limit is a per-device function attribute: set it for the kernel
+  // about to run (a cheap host call, no synchronisation)
+  QXD_CUDA(lat, cudaFuncSetAttribute(cin % 8 == 0 ? (const void*)k_ptc_layer_tc<true> : (const void*)k_ptc_layer_tc<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX));
   int dev = 0, sms = 0;
   QXD_CUDA(lat, cudaGetDevice(&dev));
   QXD_CUDA(lat, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
