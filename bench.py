@@ -88,11 +88,11 @@ def hop_source_hash():
     return h.hexdigest()
 
 
-def recorded_traffic(kernel, lattice):
+def recorded_traffic(kernel, lattice, path=None):
     """DRAM bytes per launch from the committed ncu record, or None if the hop sources changed."""
     rec = {}
     try:
-        for line in open(os.path.join(ROOT, "profiles", "roofline_traffic.txt")):
+        for line in open(path or os.path.join(ROOT, "profiles", "roofline_traffic.txt")):
             if "=" in line and not line.startswith("#"):
                 k, v = line.strip().split("=", 1)
                 rec[k] = v

@@ -1,0 +1,33 @@
+"""bench.py host logic on CPU: the DRAM-traffic record is used only for the kernel, lattice and
+hop sources it was captured with."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _write(tmp_path, sha, kernel="hop_f16n", lattice="64,32,32,32"):
+    p = tmp_path / "traffic.txt"
+    p.write_text(f"# comment\nkernel={kernel}\nlattice={lattice}\nbytes_per_launch=123456\nsource_sha256={sha}\n")
+    return str(p)
+
+
+def test_record_matches_current_sources(tmp_path):
+    p = _write(tmp_path, bench.hop_source_hash())
+    assert bench.recorded_traffic("hop_f16n", (64, 32, 32, 32), p) == 123456.0
+
+
+def test_record_rejected_when_sources_kernel_or_lattice_differ(tmp_path):
+    assert bench.recorded_traffic("hop_f16n", (64, 32, 32, 32), _write(tmp_path, "0" * 64)) is None
+    good = _write(tmp_path, bench.hop_source_hash())
+    assert bench.recorded_traffic("hop_f32", (64, 32, 32, 32), good) is None
+    assert bench.recorded_traffic("hop_f16n", (96, 48, 48, 48), good) is None
+    assert bench.recorded_traffic("hop_f16n", (64, 32, 32, 32), str(tmp_path / "missing.txt")) is None
+
+
+def test_hash_covers_every_hop_source():
+    for f in bench.HOP_SOURCES:
+        assert os.path.exists(os.path.join(ROOT, "paper_2502_02490_gb300", "csrc", f))
+    assert bench.hop_source_hash() == bench.hop_source_hash()
