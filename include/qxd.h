@@ -107,12 +107,23 @@ typedef struct {
   int gcr_restart;        /* FGCR restart length (MP_FGCR_NET), 1..32 */
   const qxd_net *net;     /* preconditioner of MP_FGCR_NET, or NULL */
   int gcr_reorth;         /* MP_FGCR_NET: classical Gram-Schmidt passes per step, 1 or 2 */
-  int fallback;           /* MP_FGCR_NET: solver run when the learned solve misses the tolerance
-                             (QXD_SOLVER_CG_EO, MP_CG_EO or MP_BICGSTAB_EO, with the library
-                             defaults except tol, on_device, check_every), or -1 for none */
+  int fallback;           /* solver run when the solve misses the tolerance (QXD_SOLVER_CG_EO,
+                             MP_CG_EO or MP_BICGSTAB_EO, with the library defaults except tol,
+                             on_device, check_every; it continues from the failed solve's x when
+                             that x has a finite residual below ||b||), or -1 for none */
+  /* version 4 */
+  int use_x0;             /* 1: x holds an initial guess on entry (same layout as b) and the
+                             defect correction starts from r = b - D x (resume from a stored
+                             solution); 0: start from x = 0.  qxd_solve only. */
+  int restart_f32;        /* 1: when an MP solve with a 16-bit inner_prec misses the tolerance
+                             (stagnation, breakdown), restart it once from its current x with
+                             FP32 inner precision, a fresh max_outer and the iterations left of
+                             maxiter; before any fallback.  qxd_solve only. */
 } qxd_solve_params;
 
-#define QXD_PARAMS_VERSION 3
+/* Version 4 appended use_x0 and restart_f32.  A version-3 struct (which ends at fallback) is
+ * still accepted and runs with both off. */
+#define QXD_PARAMS_VERSION 4
 
 typedef struct {
   int iters_inner;        /* inner iterations summed over outer rounds */
@@ -121,7 +132,8 @@ typedef struct {
   double true_rel_res;    /* final ||eta - D psi|| / ||eta|| computed in FP64 on the GPU */
   double seconds;         /* wall time of the solve */
   int status;             /* qxd_status of the solve */
-  int fallback_used;      /* 1 if the fallback solver produced x (counts above are its own) */
+  int fallback_used;      /* bit 0 (1): the fallback solver produced x (counts above are then its
+                             own); bit 1 (2): the FP32-inner restart ran (counts above include it) */
 } qxd_solve_info;
 
 /* Create a lattice of extents L = {T, L1, L2, L3} (txyz, Sec. 4.1.1), all even and >= 2.
@@ -184,8 +196,10 @@ qxd_status qxd_apply_Dhat_eo(qxd_lattice *lat, double *out_e, const double *in_e
                              int dagger, int on_device);
 
 /* Solve D x = b to the true relative residual params->tol (x is overwritten; the solve starts
- * from zero).  b, x: [V][4][3][2].  info (may be NULL) receives iteration counts, the final FP64
- * true residual and the wall time.  QXD_ENOCONV when the tolerance is not met. */
+ * from zero, or from x itself with params->use_x0).  b, x: [V][4][3][2].  info (may be NULL)
+ * receives iteration counts, the final FP64 true residual and the wall time.  Recovery when the
+ * tolerance is missed: the FP32-inner restart (restart_f32), then the fallback solver
+ * (fallback).  QXD_ENOCONV when the tolerance is still not met; x then holds the last iterate. */
 qxd_status qxd_solve(qxd_lattice *lat, double *x, const double *b, const qxd_solve_params *params,
                      qxd_solve_info *info);
 
@@ -193,8 +207,9 @@ qxd_status qxd_solve(qxd_lattice *lat, double *x, const double *b, const qxd_sol
  * sources of a propagator): FP64 outer defect correction per right-hand side and one inner
  * FP32 BiCGStab over all of them whose Dhat applications load each site's links and clover once
  * for every right-hand side.  x, b: [nrhs][V][4][3][2]; info: nrhs entries (or NULL).
- * params: solver MP_BICGSTAB_EO, inner_prec F32 (else QXD_EINVAL); the other fields as for
- * qxd_solve.  QXD_ENOCONV if some right-hand side misses the tolerance. */
+ * params: solver MP_BICGSTAB_EO, inner_prec F32, use_x0 0 (else QXD_EINVAL); fallback and
+ * restart_f32 are not used; the other fields as for qxd_solve.  QXD_ENOCONV if some right-hand
+ * side misses the tolerance. */
 qxd_status qxd_solve_mrhs(qxd_lattice *lat, double *x, const double *b, int nrhs,
                           const qxd_solve_params *params, qxd_solve_info *info);
 
@@ -207,7 +222,8 @@ qxd_status qxd_solve_mrhs(qxd_lattice *lat, double *x, const double *b, int nrhs
  * and have their clover built; x[k], b[k] are DEVICE fields [V_k][4][3][2] (params->on_device
  * must be 1); info: n entries (iters_inner per lattice, iters_outer the batch's rounds).  params:
  * tol, maxiter (caps the largest lattice's inner iterations), inner_tol, max_outer as for
- * qxd_solve (solver and inner_prec are implied).  The paper solves one lattice at a time; the
+ * qxd_solve (solver and inner_prec are implied; use_x0 must be 0; fallback and restart_f32 are
+ * not used).  The paper solves one lattice at a time; the
  * batch is a throughput layer over the same even-odd mixed-precision solve (Sec. 3, Sec. 5.1). */
 qxd_status qxd_solve_batch(qxd_lattice *const *lats, int n, double *const *x, const double *const *b,
                            const qxd_solve_params *params, qxd_solve_info *info);
@@ -221,7 +237,7 @@ qxd_status qxd_batch_last_config(int *threads, int *sites_per_thread, int *block
 
 /* Fill *p with the defaults: MP_CG_EO, tol 1e-10, maxiter 100000, inner F32, inner_tol 1e-5,
  * reliable_delta 0.1, max_outer 20, on_device 1, check_every 1, gcr_restart 16, net NULL,
- * gcr_reorth 1, fallback -1. */
+ * gcr_reorth 1, fallback -1, use_x0 0, restart_f32 1. */
 void qxd_default_params(qxd_solve_params *p);
 
 /* Fused BLAS-1 on device vectors of n complex numbers (interleaved re, im), on the lattice's
@@ -319,6 +335,14 @@ qxd_status qxd_set_profiling(qxd_lattice *lat, int on);
 qxd_status qxd_kernel_stats(qxd_lattice *lat, int which, int64_t *launches, double *ms,
                             double *bytes);
 int64_t qxd_launch_count(const qxd_lattice *lat);
+
+/* Guard words, a memory checker for the tests: every device field and work buffer the lattice
+ * allocates carries 256 extra bytes filled with 0xA5 behind its end.  *bad receives the number
+ * of those bytes that have changed (0: no kernel wrote past the end of a library buffer); a
+ * non-zero count is also recorded in qxd_last_error.  Not guarded: buffers the caller owns, the
+ * batch cache of qxd_solve_batch and the buffers of a qxd_net.
+ * Synchronises the lattice stream.  QXD_EINVAL for a NULL lattice or bad. */
+qxd_status qxd_check_guards(qxd_lattice *lat, int64_t *bad);
 
 /* Message of the last failure on this lattice ("" if none); never NULL.  With lat == NULL,
  * the message of the last failed call made without a lattice (qxd_create_lattice,

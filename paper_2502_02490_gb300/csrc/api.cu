@@ -1,8 +1,12 @@
 // C ABI of libqxd (declared in include/qxd.h): argument checks, host/device staging, lattice
 // lifetime, work buffers and kernel timing.
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
+#include <vector>
 
 #include "qxd_internal.cuh"
 
@@ -32,6 +36,39 @@ qxd_status cuda_fail(qxd_lattice* lat, cudaError_t e, const char* where) {
   return fail(lat, e == cudaErrorMemoryAllocation ? QXD_ENOMEM : QXD_ECUDA, m);
 }
 
+// Guard words: every lattice field and work buffer is allocated GUARD_BYTES longer, and that
+// tail is filled with GUARD_FILL.  qxd_check_guards counts tail bytes that changed, so a kernel
+// writing past the end of a buffer shows up in the tests without a memory checker.  The guard
+// addresses live here, keyed by lattice, one per field and one per work slot.
+constexpr size_t GUARD_BYTES = 256;
+constexpr unsigned char GUARD_FILL = 0xA5;
+struct GuardSet {
+  std::vector<unsigned char*> fields;
+  unsigned char* work[QXD_WORK_SLOTS] = {};
+};
+static std::mutex g_guard_mu;
+static std::unordered_map<const qxd_lattice*, GuardSet> g_guards;
+
+// cudaMalloc of bytes plus the guard, zeroed, guard filled; slot < 0 registers a field
+static qxd_status guarded_malloc(qxd_lattice* lat, void** p, size_t bytes, int slot) {
+  QXD_CUDA(lat, cudaMalloc(p, bytes + GUARD_BYTES));
+  unsigned char* tail = (unsigned char*)*p + bytes;
+  QXD_CUDA(lat, cudaMemsetAsync(*p, 0, bytes, lat->stream));
+  QXD_CUDA(lat, cudaMemsetAsync(tail, GUARD_FILL, GUARD_BYTES, lat->stream));
+  std::lock_guard<std::mutex> lk(g_guard_mu);
+  GuardSet& gs = g_guards[lat];
+  if (slot < 0)
+    gs.fields.push_back(tail);
+  else
+    gs.work[slot] = tail;
+  return QXD_OK;
+}
+
+static void guards_forget(const qxd_lattice* lat) {
+  std::lock_guard<std::mutex> lk(g_guard_mu);
+  g_guards.erase(lat);
+}
+
 qxd_status ensure_work(qxd_lattice* lat, int slot, size_t bytes, void** out) {
   if (slot < 0 || slot >= QXD_WORK_SLOTS) return fail(lat, QXD_EINVAL, "bad work slot");
   if (lat->work_bytes[slot] < bytes) {
@@ -40,9 +77,11 @@ qxd_status ensure_work(qxd_lattice* lat, int slot, size_t bytes, void** out) {
       cudaFree(lat->work[slot]);
       lat->work[slot] = nullptr;
       lat->work_bytes[slot] = 0;
+      std::lock_guard<std::mutex> lk(g_guard_mu);
+      g_guards[lat].work[slot] = nullptr;
     }
-    QXD_CUDA(lat, cudaMalloc(&lat->work[slot], bytes));
-    QXD_CUDA(lat, cudaMemsetAsync(lat->work[slot], 0, bytes, lat->stream));
+    const qxd_status st = guarded_malloc(lat, &lat->work[slot], bytes, slot);
+    if (st != QXD_OK) return st;
     lat->work_bytes[slot] = bytes;
   }
   *out = lat->work[slot];
@@ -115,10 +154,25 @@ qxd_status ensure_stage(qxd_lattice* lat, size_t bytes) {
 
 template <typename T>
 static qxd_status alloc(qxd_lattice* lat, T** p, size_t bytes) {
-  QXD_CUDA(lat, cudaMalloc((void**)p, bytes));
-  QXD_CUDA(lat, cudaMemsetAsync(*p, 0, bytes, lat->stream));
+  return guarded_malloc(lat, (void**)p, bytes, -1);
+}
+
+namespace qxd {
+// The caller's params as the current version.  Version 3 ended at `fallback`; version 4 appended
+// use_x0 and restart_f32, which a version-3 caller gets off.
+qxd_status params_current(qxd_lattice* lat, const qxd_solve_params* p, qxd_solve_params* q) {
+  if (p->version == QXD_PARAMS_VERSION) {
+    *q = *p;
+  } else if (p->version == 3) {
+    std::memset(q, 0, sizeof(*q));
+    std::memcpy(q, p, offsetof(qxd_solve_params, use_x0));
+    q->version = QXD_PARAMS_VERSION;
+  } else {
+    return fail(lat, QXD_EINVAL, "qxd_solve_params version mismatch");
+  }
   return QXD_OK;
 }
+}  // namespace qxd
 
 extern "C" {
 
@@ -139,6 +193,8 @@ void qxd_default_params(qxd_solve_params* p) {
   p->gcr_reorth = 1;
   p->fallback = -1;
   p->net = nullptr;
+  p->use_x0 = 0;
+  p->restart_f32 = 1;
 }
 
 qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
@@ -158,7 +214,37 @@ qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
   if (lat->mr_hscal) cudaFreeHost(lat->mr_hscal);
   if (lat->hscal) cudaFreeHost(lat->hscal);
   for (cudaEvent_t e : lat->ev_pool) cudaEventDestroy(e);
+  guards_forget(lat);
   delete lat;
+  return QXD_OK;
+}
+
+qxd_status qxd_check_guards(qxd_lattice* lat, int64_t* bad) {
+  CHECK_LAT(lat);
+  if (!bad) return fail(lat, QXD_EINVAL, "null argument");
+  std::vector<unsigned char*> tails;
+  {
+    std::lock_guard<std::mutex> lk(g_guard_mu);
+    auto it = g_guards.find(lat);
+    if (it != g_guards.end()) {
+      tails = it->second.fields;
+      for (unsigned char* t : it->second.work)
+        if (t) tails.push_back(t);
+    }
+  }
+  std::vector<unsigned char> host(GUARD_BYTES * tails.size());
+  for (size_t i = 0; i < tails.size(); ++i)
+    QXD_CUDA(lat, cudaMemcpyAsync(host.data() + i * GUARD_BYTES, tails[i], GUARD_BYTES, cudaMemcpyDeviceToHost,
+                                  lat->stream));
+  QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  int64_t n = 0;
+  for (unsigned char c : host) n += c != GUARD_FILL;
+  *bad = n;
+  if (n) {
+    char m[96];
+    std::snprintf(m, sizeof(m), "%lld guard bytes overwritten", (long long)n);
+    lat->err = m;
+  }
   return QXD_OK;
 }
 
@@ -430,13 +516,17 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
   CHECK_LAT(lat);
   if (info) std::memset(info, 0, sizeof(*info));
   if (!x || !b || !p) return fail(lat, QXD_EINVAL, "null argument");
-  if (p->version != QXD_PARAMS_VERSION) return fail(lat, QXD_EINVAL, "qxd_solve_params version mismatch");
+  qxd_solve_params pv;
+  TRY(params_current(lat, p, &pv));
+  p = &pv;
   if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO && p->solver != QXD_SOLVER_MP_BICGSTAB_EO &&
       p->solver != QXD_SOLVER_MP_FGCR_NET)
     return fail(lat, QXD_EINVAL, "bad solver");
-  if (p->solver == QXD_SOLVER_MP_FGCR_NET && p->fallback != -1 && p->fallback != QXD_SOLVER_CG_EO &&
-      p->fallback != QXD_SOLVER_MP_CG_EO && p->fallback != QXD_SOLVER_MP_BICGSTAB_EO)
+  if (p->fallback != -1 && p->fallback != QXD_SOLVER_CG_EO && p->fallback != QXD_SOLVER_MP_CG_EO &&
+      p->fallback != QXD_SOLVER_MP_BICGSTAB_EO)
     return fail(lat, QXD_EINVAL, "fallback must be -1, CG_EO, MP_CG_EO or MP_BICGSTAB_EO");
+  if (p->use_x0 != 0 && p->use_x0 != 1) return fail(lat, QXD_EINVAL, "use_x0 must be 0 or 1");
+  if (p->restart_f32 != 0 && p->restart_f32 != 1) return fail(lat, QXD_EINVAL, "restart_f32 must be 0 or 1");
   if (p->solver == QXD_SOLVER_MP_FGCR_NET && (p->gcr_reorth < 1 || p->gcr_reorth > 2))
     return fail(lat, QXD_EINVAL, "gcr_reorth must be 1 or 2");
   if (p->solver == QXD_SOLVER_MP_FGCR_NET && (p->gcr_restart < 1 || p->gcr_restart > 32))
@@ -459,6 +549,14 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
     src = (const double*)bi;
   }
   TRY(pack_spinor64(lat, (const double2*)src, fb_in, 0));
+  if (p->use_x0) {  // the initial guess, in the same boundary layout as b
+    const double* x0 = x;
+    if (!p->on_device) {
+      QXD_CUDA(lat, cudaMemcpyAsync(bo, x, vb, cudaMemcpyHostToDevice, lat->stream));
+      x0 = (const double*)bo;
+    }
+    TRY(pack_spinor64(lat, (const double2*)x0, fx, 0));
+  }
   qxd_status st = solve(lat, fx, fb_in, p, info);
   if (st != QXD_OK && st != QXD_ENOCONV) return st;
   qxd_status st2 = unpack_spinor64(lat, fx, p->on_device ? (double2*)x : (double2*)bo, 0);
@@ -476,7 +574,10 @@ qxd_status qxd_solve_mrhs(qxd_lattice* lat, double* x, const double* b, int nrhs
   if (info && nrhs > 0) std::memset(info, 0, sizeof(*info) * nrhs);
   if (!x || !b || !p) return fail(lat, QXD_EINVAL, "null argument");
   if (nrhs <= 0) return fail(lat, QXD_EINVAL, "nrhs must be positive");
-  if (p->version != QXD_PARAMS_VERSION) return fail(lat, QXD_EINVAL, "qxd_solve_params version mismatch");
+  qxd_solve_params pv;
+  TRY(params_current(lat, p, &pv));
+  p = &pv;
+  if (p->use_x0) return fail(lat, QXD_EINVAL, "use_x0 is supported by qxd_solve only");
   if (p->solver != QXD_SOLVER_MP_BICGSTAB_EO || p->inner_prec != QXD_F32)
     return fail(lat, QXD_EINVAL, "multi-RHS solve: solver must be MP_BICGSTAB_EO with inner_prec F32");
   if (!(p->tol > 0) || p->maxiter <= 0) return fail(lat, QXD_EINVAL, "tol must be > 0 and maxiter > 0");

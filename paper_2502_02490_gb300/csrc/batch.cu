@@ -562,6 +562,7 @@ long long g_spin_limit = 20000000;  // ~1.3 s of 64 ns sleeps: far above any pha
 namespace qxd {
 
 qxd_status apply_D64(qxd_lattice* lat, const double2* in, double2* out);
+qxd_status params_current(qxd_lattice* lat, const qxd_solve_params* p, qxd_solve_params* q);
 
 // Device state of a batch, kept on the batch's first lattice between calls (freed with it or
 // when a call brings another lattice set): fields, reduction and barrier words, the captured
@@ -976,7 +977,10 @@ extern "C" qxd_status qxd_solve_batch(qxd_lattice* const* lats, int n, double* c
   qxd_lattice* l0 = lats[0];
   if (!l0) return QXD_EINVAL;
   if (info) std::memset(info, 0, sizeof(qxd_solve_info) * n);
-  if (prm->version != QXD_PARAMS_VERSION) return fail(l0, QXD_EINVAL, "qxd_solve_params version mismatch");
+  qxd_solve_params pv;
+  if (qxd::params_current(l0, prm, &pv) != QXD_OK) return QXD_EINVAL;
+  prm = &pv;
+  if (prm->use_x0) return fail(l0, QXD_EINVAL, "use_x0 is supported by qxd_solve only");
   if (!prm->on_device) return fail(l0, QXD_EINVAL, "qxd_solve_batch takes device pointers (on_device = 1)");
   for (int k = 0; k < n; ++k) {
     if (!lats[k] || !x[k] || !b[k]) return fail(l0, QXD_EINVAL, "null lattice or field");

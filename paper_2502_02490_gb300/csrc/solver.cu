@@ -370,29 +370,55 @@ qxd_status fgcr32(qxd_lattice* lat, qxd_net* net, int m, int reorth, const float
 static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve_params* prm,
                              qxd_solve_info* info);
 
+// A failed solve leaves x usable as a starting point when its true residual is finite and below
+// that of x = 0.
+static bool usable_iterate(const qxd_solve_info& i) { return std::isfinite(i.true_rel_res) && i.true_rel_res < 1.0; }
+
+// Recovery chain after a missed tolerance (stagnation, breakdown, an expired wait): first the
+// FP32-inner restart of a 16-bit MP solve (restart_f32), then the plain fallback solver
+// (fallback).  Argument errors and CUDA failures are returned as they are.
 qxd_status solve(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve_params* prm, qxd_solve_info* info) {
   auto t0 = std::chrono::steady_clock::now();
-  qxd_status st = solve_impl(lat, x, b, prm, info);
-  if (st != QXD_OK && info && info->status == QXD_OK) info->status = st;  // early failure: record it
-  // the learned solve missed the tolerance (or broke down): the plain solver takes over from scratch
-  if (st != QXD_OK && st != QXD_EINVAL && st != QXD_ESTATE && st != QXD_ECUDA && st != QXD_ENOMEM &&
-      prm->solver == QXD_SOLVER_MP_FGCR_NET && prm->fallback >= 0) {
+  qxd_solve_info own;
+  std::memset(&own, 0, sizeof(own));
+  qxd_solve_info* inf = info ? info : &own;
+  qxd_status st = solve_impl(lat, x, b, prm, inf);
+  if (st != QXD_OK && inf->status == QXD_OK) inf->status = st;  // early failure: record it
+  auto recoverable = [](qxd_status s) { return s == QXD_ENOCONV || s == QXD_ETIMEOUT; };
+  const bool mp16 = (prm->solver == QXD_SOLVER_MP_CG_EO || prm->solver == QXD_SOLVER_MP_BICGSTAB_EO) &&
+                    (prm->inner_prec == QXD_F16N || prm->inner_prec == QXD_BF16N);
+  if (recoverable(st) && prm->restart_f32 && mp16 && prm->maxiter > inf->iters_inner) {
+    qxd_solve_params rp = *prm;
+    rp.inner_prec = QXD_F32;
+    rp.maxiter = prm->maxiter - inf->iters_inner;
+    rp.use_x0 = usable_iterate(*inf);
+    qxd_solve_info ri;
+    std::memset(&ri, 0, sizeof(ri));
+    st = solve_impl(lat, x, b, &rp, &ri);
+    if (st != QXD_OK && ri.status == QXD_OK) ri.status = st;
+    inf->iters_inner += ri.iters_inner;
+    inf->iters_outer += ri.iters_outer;
+    inf->reliable_updates += ri.reliable_updates;
+    inf->true_rel_res = ri.true_rel_res;
+    inf->status = ri.status;
+    inf->fallback_used |= 2;
+  }
+  if (recoverable(st) && prm->fallback >= 0) {
     qxd_solve_params fp;
     qxd_default_params(&fp);
     fp.solver = prm->fallback;
     fp.tol = prm->tol;
     fp.on_device = prm->on_device;
     fp.check_every = prm->check_every;
+    fp.use_x0 = usable_iterate(*inf);
     qxd_solve_info fi;
     std::memset(&fi, 0, sizeof(fi));
     st = solve_impl(lat, x, b, &fp, &fi);
     if (st != QXD_OK && fi.status == QXD_OK) fi.status = st;
-    if (info) {
-      *info = fi;
-      info->fallback_used = 1;
-      info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    }
+    fi.fallback_used = inf->fallback_used | 1;
+    *inf = fi;
   }
+  inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return st;
 }
 
@@ -420,7 +446,9 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
   TRY(blas_norm2_64(lat, b, nf, SC_TMP0));
   TRY(read_scalars(lat, SC_TMP0, 1, &bn2));
   const double bnorm = std::sqrt(bn2);
-  TRY(blas_zero(lat, x, fb));
+  // with an initial guess the first round starts from r = b - D x (b = 0 has the solution 0)
+  const bool from_x0 = prm->use_x0 != 0 && bnorm != 0.0;
+  if (!from_x0) TRY(blas_zero(lat, x, fb));
   int total = 0, outer = 0, nrel_total = 0;
   double rel = 1.0;
   qxd_status result = QXD_ENOCONV;
@@ -431,7 +459,7 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
   const int max_outer = prm->max_outer > 0 ? prm->max_outer : 20;
   for (; result != QXD_OK && outer <= max_outer; ++outer) {
     // r = b - D x (FP64)
-    if (outer == 0) {
+    if (outer == 0 && !from_x0) {
       TRY(blas_copy(lat, r, b, fb));
     } else {
       TRY(apply_D64(lat, x, tf));
@@ -442,7 +470,16 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
     TRY(blas_norm2_64(lat, r, nf, SC_TMP0));
     TRY(read_scalars(lat, SC_TMP0, 1, &rn2));
     rel = std::sqrt(rn2) / bnorm;
-    if (!std::isfinite(rel)) return fail(lat, QXD_ENOCONV, "non-finite residual");
+    if (!std::isfinite(rel)) {
+      if (info) {
+        info->iters_inner = total;
+        info->iters_outer = outer;
+        info->reliable_updates = nrel_total;
+        info->true_rel_res = rel;
+        info->status = QXD_ENOCONV;
+      }
+      return fail(lat, QXD_ENOCONV, "non-finite residual");
+    }
     if (rel <= prm->tol) {
       result = QXD_OK;
       break;

@@ -25,7 +25,7 @@ BC_PERIODIC, BC_ANTIPERIODIC = 0, 1
 ORDER_LEXI, ORDER_IPT = 0, 1
 F64, F32, F16N, BF16N = 0, 1, 2, 3
 SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO, SOLVER_MP_FGCR_NET = 0, 1, 2, 3
-PARAMS_VERSION = 3
+PARAMS_VERSION = 4
 TRAIN_VERSION = 1
 PREC = {"f64": F64, "f32": F32, "f16n": F16N, "bf16n": BF16N}
 
@@ -34,7 +34,8 @@ class SolveParams(C.Structure):
     _fields_ = [("version", C.c_int), ("solver", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int),
                 ("inner_prec", C.c_int), ("inner_tol", C.c_double), ("reliable_delta", C.c_double),
                 ("max_outer", C.c_int), ("on_device", C.c_int), ("check_every", C.c_int),
-                ("gcr_restart", C.c_int), ("net", C.c_void_p), ("gcr_reorth", C.c_int), ("fallback", C.c_int)]
+                ("gcr_restart", C.c_int), ("net", C.c_void_p), ("gcr_reorth", C.c_int), ("fallback", C.c_int),
+                ("use_x0", C.c_int), ("restart_f32", C.c_int)]
 
 
 class TrainParams(C.Structure):
@@ -67,6 +68,7 @@ _SIGS = {
     "qxd_vec_axpy": [_vp, _d, _d, _vp, _vp, _i64],
     "qxd_vec_dot_noalloc": [_vp, _vp, _i64, _vp, _vp],
     "qxd_set_profiling": [_vp, _i],
+    "qxd_check_guards": [_vp, C.POINTER(_i64)],
     "qxd_solve_batch": [_vp, _i, _vp, _vp, C.POINTER(SolveParams), _vp],
     "qxd_batch_last_config": [C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "qxd_batch_set_spin_limit": [C.c_longlong],
@@ -258,6 +260,13 @@ def kernel_stats(lat, which):
 
 def launch_count(lat):
     return int(lib.qxd_launch_count(lat))
+
+
+def check_guards(lat):
+    """qxd_check_guards: the number of guard bytes behind the lattice's buffers that changed."""
+    bad = C.c_int64()
+    _check(lib.qxd_check_guards(lat, C.byref(bad)), lat)
+    return int(bad.value)
 
 
 # ---- learned preconditioner ----

@@ -88,4 +88,9 @@ class Case:
         return as_c128(y, psi_e.shape)
 
     def close(self):
-        self.qxd.destroy_lattice(self.lat)
+        """Destroy the lattice after checking that no kernel wrote past the end of its buffers."""
+        try:
+            bad = self.qxd.check_guards(self.lat)
+        finally:
+            self.qxd.destroy_lattice(self.lat)
+        assert bad == 0, f"{bad} guard bytes overwritten behind the lattice's device buffers"

@@ -51,5 +51,24 @@ def test_default_params(qxd):
     p = qxd.default_params()
     assert p.version == qxd.PARAMS_VERSION and p.tol == 1e-10 and p.solver == qxd.SOLVER_MP_CG_EO
     assert p.gcr_restart == 16 and p.gcr_reorth == 1 and p.check_every == 1 and p.fallback == -1
+    assert p.use_x0 == 0 and p.restart_f32 == 1
     assert qxd.lib.qxd_destroy_lattice(None) == qxd.OK
+    import ctypes as C
+
+    assert qxd.lib.qxd_check_guards(None, C.byref(C.c_int64())) == qxd.EINVAL
     assert qxd.launch_count(None) == 0
+
+
+def test_params_struct_matches_library_layout(qxd):
+    """qxd_default_params writes exactly sizeof(SolveParams) bytes, ending with the version-4 fields."""
+    import ctypes as C
+
+    n = C.sizeof(qxd.SolveParams)
+    buf = (C.c_ubyte * (n + 64))(*([0xA5] * (n + 64)))
+    qxd.lib.qxd_default_params(C.cast(buf, C.POINTER(qxd.SolveParams)))
+    p = qxd.SolveParams.from_buffer(buf)
+    assert p.version == qxd.PARAMS_VERSION and p.restart_f32 == 1 and p.use_x0 == 0 and p.fallback == -1
+    assert bytes(buf[n:]) == bytes([0xA5] * 64)
+    # a version-3 struct ends where use_x0 begins
+    assert qxd.SolveParams.use_x0.offset == qxd.SolveParams.fallback.offset + C.sizeof(C.c_int)
+    assert qxd.SolveParams.use_x0.offset % 8 == 0

@@ -56,8 +56,10 @@ def test_fullsize_operator_clover_and_solve(qxd, name):
         del x, y, psi
         clov = np.empty((lat_o.V, 2, 36))
         qxd.get_clover(lat, clov)
+        bad = qxd.check_guards(lat)  # no kernel of the full-size launches wrote past a buffer
     finally:
         qxd.destroy_lattice(lat)
+    assert bad == 0, f"{bad} guard bytes overwritten"
     # oracle at sampled sites: every boundary class (time wrap, C* mirror crossings) is hit by
     # taking corners as well as random sites
     rng = np.random.default_rng(0)
