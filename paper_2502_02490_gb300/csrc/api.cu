@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "qxd_internal.cuh"
+#include "trace.cuh"
 
 namespace qxd {
 qxd_status apply_dhat_prec(qxd_lattice* lat, int prec, const double2* in64, double2* out64, int dag);
@@ -198,6 +199,7 @@ void qxd_default_params(qxd_solve_params* p) {
 }
 
 qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
+  QXD_TRACE();
   if (!lat) return QXD_OK;
   if (lat->stream) cudaStreamSynchronize(lat->stream);
   if (lat->batch && lat->batch_release) lat->batch_release(lat->batch);
@@ -220,6 +222,7 @@ qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
 }
 
 qxd_status qxd_check_guards(qxd_lattice* lat, int64_t* bad) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (!bad) return fail(lat, QXD_EINVAL, "null argument");
   std::vector<unsigned char*> tails;
@@ -249,6 +252,7 @@ qxd_status qxd_check_guards(qxd_lattice* lat, int64_t* bad) {
 }
 
 qxd_status qxd_create_lattice(const int L[4], int tbc, int cstar, int order, void* cuda_stream, qxd_lattice** out) {
+  QXD_TRACE();
   if (!out || !L) return fail(nullptr, QXD_EINVAL, "null argument");
   *out = nullptr;
   for (int mu = 0; mu < 4; ++mu)
@@ -329,6 +333,7 @@ qxd_status qxd_create_lattice(const int L[4], int tbc, int cstar, int order, voi
 }
 
 qxd_status qxd_load_gauge(qxd_lattice* lat, const double* su3, const double* a_u1, double q, int on_device) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (!su3) return fail(lat, QXD_EINVAL, "su3 is null");
   const i64 Vp = lat->Vphys;
@@ -356,6 +361,7 @@ qxd_status qxd_load_gauge(qxd_lattice* lat, const double* su3, const double* a_u
 }
 
 qxd_status qxd_set_ipt_blocks(qxd_lattice* lat, const int B[4]) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (!B) return fail(lat, QXD_EINVAL, "B is null");
   if (lat->order != QXD_ORDER_IPT) return fail(lat, QXD_EINVAL, "cache blocks need QXD_ORDER_IPT");
@@ -369,6 +375,7 @@ qxd_status qxd_set_ipt_blocks(qxd_lattice* lat, const int B[4]) {
 }
 
 qxd_status qxd_load_gauge_openqxd(qxd_lattice* lat, const double* u8, const double* a8, double q, int on_device) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (!u8) return fail(lat, QXD_EINVAL, "u8 is null");
   if (lat->order != QXD_ORDER_IPT) return fail(lat, QXD_EINVAL, "the openQxD gauge format needs QXD_ORDER_IPT");
@@ -397,6 +404,7 @@ qxd_status qxd_load_gauge_openqxd(qxd_lattice* lat, const double* u8, const doub
 }
 
 qxd_status qxd_build_clover(qxd_lattice* lat, double m0, double csw, double csw_qed) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (!lat->have_gauge) return fail(lat, QXD_ESTATE, "build_clover before load_gauge");
   lat->m0 = m0;
@@ -409,6 +417,7 @@ qxd_status qxd_build_clover(qxd_lattice* lat, double m0, double csw, double csw_
 }
 
 qxd_status qxd_get_clover(qxd_lattice* lat, double* out, int on_device) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (!out) return fail(lat, QXD_EINVAL, "out is null");
   if (!lat->have_clover) return fail(lat, QXD_ESTATE, "get_clover before build_clover");
@@ -423,6 +432,7 @@ qxd_status qxd_get_clover(qxd_lattice* lat, double* out, int on_device) {
 }
 
 qxd_status qxd_apply_D(qxd_lattice* lat, double* out, const double* in, int prec, int nrhs, int on_device) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (!out || !in) return fail(lat, QXD_EINVAL, "null field pointer");
   if (nrhs <= 0) return fail(lat, QXD_EINVAL, "nrhs must be positive");
@@ -484,6 +494,7 @@ qxd_status qxd_apply_D(qxd_lattice* lat, double* out, const double* in, int prec
 
 qxd_status qxd_apply_Dhat_eo(qxd_lattice* lat, double* out_e, const double* in_e, int prec, int dagger,
                              int on_device) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (!out_e || !in_e) return fail(lat, QXD_EINVAL, "null field pointer");
   if (prec < QXD_F64 || prec > QXD_BF16N) return fail(lat, QXD_EINVAL, "bad precision");
@@ -513,6 +524,7 @@ qxd_status qxd_apply_Dhat_eo(qxd_lattice* lat, double* out_e, const double* in_e
 }
 
 qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_solve_params* p, qxd_solve_info* info) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (info) std::memset(info, 0, sizeof(*info));
   if (!x || !b || !p) return fail(lat, QXD_EINVAL, "null argument");
@@ -570,6 +582,7 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
 
 qxd_status qxd_solve_mrhs(qxd_lattice* lat, double* x, const double* b, int nrhs, const qxd_solve_params* p,
                           qxd_solve_info* info) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (info && nrhs > 0) std::memset(info, 0, sizeof(*info) * nrhs);
   if (!x || !b || !p) return fail(lat, QXD_EINVAL, "null argument");
@@ -614,6 +627,7 @@ qxd_status qxd_solve_mrhs(qxd_lattice* lat, double* x, const double* b, int nrhs
 }
 
 qxd_status qxd_vec_dot(qxd_lattice* lat, const double* a, const double* b, int64_t n, double* re, double* im) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (!re || !im || n < 0 || (n > 0 && (!a || !b))) return fail(lat, QXD_EINVAL, "bad argument");
   if (n == 0) {
@@ -629,6 +643,7 @@ qxd_status qxd_vec_dot(qxd_lattice* lat, const double* a, const double* b, int64
 }
 
 qxd_status qxd_vec_norm2(qxd_lattice* lat, const double* a, int64_t n, double* out) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (!out || n < 0 || (n > 0 && !a)) return fail(lat, QXD_EINVAL, "bad argument");
   if (n == 0) {
@@ -640,6 +655,7 @@ qxd_status qxd_vec_norm2(qxd_lattice* lat, const double* a, int64_t n, double* o
 }
 
 qxd_status qxd_vec_axpy(qxd_lattice* lat, double re, double im, const double* x, double* y, int64_t n) {
+  QXD_TRACE();
   CHECK_LAT(lat);
   if (n < 0 || (n > 0 && (!x || !y))) return fail(lat, QXD_EINVAL, "bad argument");
   if (n == 0) return QXD_OK;

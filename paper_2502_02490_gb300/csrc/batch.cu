@@ -29,6 +29,7 @@
 
 #include "hop_site.cuh"
 #include "reduce.cuh"
+#include "trace.cuh"
 
 namespace qxd {
 
@@ -973,6 +974,7 @@ static qxd_status solve_batch_impl(qxd_lattice* const* lats, int n, double* cons
 
 extern "C" qxd_status qxd_solve_batch(qxd_lattice* const* lats, int n, double* const* x, const double* const* b,
                                       const qxd_solve_params* prm, qxd_solve_info* info) {
+  QXD_TRACE();
   if (!lats || n <= 0 || n > BMAX || !x || !b || !prm) return QXD_EINVAL;
   qxd_lattice* l0 = lats[0];
   if (!l0) return QXD_EINVAL;

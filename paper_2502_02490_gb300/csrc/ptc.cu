@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "qxd_internal.cuh"
+#include "trace.cuh"
 
 namespace qxd {
 
@@ -425,6 +426,7 @@ static uint64_t mix64(uint64_t z) {
 extern "C" {
 
 qxd_status qxd_net_create(qxd_lattice* lat, int nlayers, const int* channels, uint64_t seed, qxd_net** out) {
+  QXD_TRACE();
   if (!lat || !channels || !out) return QXD_EINVAL;
   *out = nullptr;
   if (nlayers < 1 || nlayers > 8) return fail(lat, QXD_EINVAL, "nlayers must be 1..8");
@@ -498,6 +500,7 @@ qxd_status qxd_net_create(qxd_lattice* lat, int nlayers, const int* channels, ui
 }
 
 qxd_status qxd_net_destroy(qxd_net* net) {
+  QXD_TRACE();
   if (!net) return QXD_OK;
   if (net->lat) cudaStreamSynchronize(net->lat->stream);
   void* b[] = {net->w, net->wadj, net->grad, net->am, net->av, net->part, net->gbuf[0], net->gbuf[1], net->bp,
@@ -544,6 +547,7 @@ static qxd_status from_internal32(qxd_lattice* lat, const float4* src, int on_de
 }
 
 qxd_status qxd_net_apply(qxd_net* net, double* out, const double* in, int on_device) {
+  QXD_TRACE();
   if (!net || !out || !in) return QXD_EINVAL;
   qxd_lattice* lat = net->lat;
   float4 *a, *b;
@@ -559,6 +563,7 @@ qxd_status qxd_net_apply(qxd_net* net, double* out, const double* in, int on_dev
 
 qxd_status qxd_net_loss_grad(qxd_net* net, const double* v, const double* b, int nsamp, int on_device, double* loss,
                              double* grad) {
+  QXD_TRACE();
   if (!net || !v || !b || nsamp <= 0 || !loss) return QXD_EINVAL;
   qxd_lattice* lat = net->lat;
   const i64 cs = 12 * lat->sv;
@@ -585,6 +590,7 @@ qxd_status qxd_net_loss_grad(qxd_net* net, const double* v, const double* b, int
 
 qxd_status qxd_net_train(qxd_net* net, const double* v, int nsamp, const qxd_train_params* p, double* loss_hist,
                          int on_device) {
+  QXD_TRACE();
   if (!net || !v || !p || nsamp <= 0) return QXD_EINVAL;
   qxd_lattice* lat = net->lat;
   if (p->version != QXD_TRAIN_VERSION) return fail(lat, QXD_EINVAL, "qxd_train_params version mismatch");
@@ -627,6 +633,7 @@ qxd_status qxd_net_train(qxd_net* net, const double* v, int nsamp, const qxd_tra
 
 // file: "QXDNET1\n", then int32 nlayers, int32 channels[nlayers+1], float32 weights (re, im)
 qxd_status qxd_net_save(const qxd_net* net, const char* path) {
+  QXD_TRACE();
   if (!net || !path) return QXD_EINVAL;
   std::vector<double> w(2 * net->nw);
   qxd_status st = qxd_net_get_weights(net, w.data());
@@ -646,6 +653,7 @@ qxd_status qxd_net_save(const qxd_net* net, const char* path) {
 }
 
 qxd_status qxd_net_load(qxd_lattice* lat, const char* path, qxd_net** out) {
+  QXD_TRACE();
   if (!lat || !path || !out) return QXD_EINVAL;
   FILE* f = fopen(path, "rb");
   if (!f) return fail(lat, QXD_EINVAL, "cannot open the net file");
