@@ -227,6 +227,11 @@ qxd_status qxd_solve_mrhs(qxd_lattice *lat, double *x, const double *b, int nrhs
  * batch is a throughput layer over the same even-odd mixed-precision solve (Sec. 3, Sec. 5.1). */
 qxd_status qxd_solve_batch(qxd_lattice *const *lats, int n, double *const *x, const double *const *b,
                            const qxd_solve_params *params, qxd_solve_info *info);
+/* Tuning cache file of qxd_solve_batch (NULL or "" = none, the default).  A set of volumes not
+ * yet tuned in this process is looked up there first; each newly tuned set is appended as the
+ * line "qxd-batch-tune 1 <GPU name, spaces as _> <SM count> <V0,V1,...,> <blocks/SM>
+ * <sites/thread>".  A missing or unreadable file, and malformed lines, are ignored. */
+qxd_status qxd_batch_tune_cache(const char *path);
 /* Iteration limit of the persistent kernel's barrier spin-waits (default 2e7, about 1.3 s);
  * a tiny limit makes the waits run out (QXD_ETIMEOUT), for tests of that path. */
 qxd_status qxd_batch_set_spin_limit(long long limit);

@@ -20,10 +20,12 @@
 // refused); the host reads the lattices' residual norms between rounds.  The sites per thread are
 // picked by a small autotuner that times each candidate once per set of volumes.
 #include <chrono>
+#include <cstdio>
 #include <cstring>
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -557,6 +559,52 @@ std::map<std::string, std::pair<int, int>> g_tuned;  // volumes of a lattice set
 int g_last_spt = 0, g_last_minb = 0;
 bool g_last_graph = false;
 long long g_spin_limit = 20000000;  // ~1.3 s of 64 ns sleeps: far above any phase of these lattices
+std::string g_cache_path;           // tuning cache file ("" = none)
+
+// Tuning cache file: one line per tuned set of volumes,
+//   qxd-batch-tune 1 <GPU name, spaces as _> <SM count> <volumes "V0,V1,...,"> <blocks/SM> <sites/thread>
+// read when a set is not yet tuned in this process, appended to after tuning.  The file only
+// saves tuning time: unreadable files and malformed lines are ignored.
+std::string gpu_tag() {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown 0";
+  std::string name(prop.name);
+  for (char& ch : name)
+    if (ch == ' ' || ch == '\t') ch = '_';
+  return name + " " + std::to_string(prop.multiProcessorCount);
+}
+
+bool cache_lookup(const std::string& key, int* minb, int* spt) {
+  if (g_cache_path.empty()) return false;
+  FILE* f = std::fopen(g_cache_path.c_str(), "r");
+  if (!f) return false;
+  const std::string tag = gpu_tag();
+  char line[1024];
+  bool found = false;
+  while (std::fgets(line, sizeof(line), f)) {
+    std::istringstream is(line);
+    std::string magic, ver, gpu, sms, vols;
+    int mb = 0, sp = 0;
+    if (!(is >> magic >> ver >> gpu >> sms >> vols >> mb >> sp)) continue;
+    if (magic != "qxd-batch-tune" || ver != "1" || gpu + " " + sms != tag || vols != key) continue;
+    if ((mb == 1 || mb == 2) && (sp == 1 || sp == 2 || sp == 4)) {  // the last valid line wins
+      *minb = mb;
+      *spt = sp;
+      found = true;
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void cache_store(const std::string& key, int minb, int spt) {
+  if (g_cache_path.empty()) return;
+  FILE* f = std::fopen(g_cache_path.c_str(), "a");
+  if (!f) return;
+  std::fprintf(f, "qxd-batch-tune 1 %s %s %d %d\n", gpu_tag().c_str(), key.c_str(), minb, spt);
+  std::fclose(f);
+}
 
 }  // namespace
 
@@ -807,6 +855,11 @@ static qxd_status solve_batch_impl(qxd_lattice* const* lats, int n, double* cons
     if (it != g_tuned.end()) {
       minb = it->second.first;
       spt = it->second.second;
+    } else if (cache_lookup(key, &minb, &spt) && c->grid_max[minb - 1] >= 1) {
+      g_tuned[key] = {minb, spt};
+    } else {
+      minb = 1;
+      spt = 0;
     }
   }
   layout_tiles(*c, minb, spt ? spt : 1);
@@ -913,6 +966,7 @@ static qxd_status solve_batch_impl(qxd_lattice* const* lats, int n, double* cons
       layout_tiles(*c, minb, spt);
       std::lock_guard<std::mutex> lock(g_tune_mutex);
       g_tuned[key] = {minb, spt};
+      cache_store(key, minb, spt);
     }
     QXD_CUDA(l0, cudaMemcpyAsync(c->dL, c->hL.data(), sizeof(BLat) * n, cudaMemcpyHostToDevice, S));
     // the inner solve of every lattice: one persistent launch
@@ -1007,6 +1061,12 @@ extern "C" qxd_status qxd_batch_last_config(int* threads, int* sites_per_thread,
   *sites_per_thread = g_last_spt;
   *blocks_per_sm = g_last_minb;
   *graph = g_last_graph ? 1 : 0;
+  return QXD_OK;
+}
+
+extern "C" qxd_status qxd_batch_tune_cache(const char* path) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_cache_path = path ? path : "";
   return QXD_OK;
 }
 

@@ -72,6 +72,7 @@ _SIGS = {
     "qxd_solve_batch": [_vp, _i, _vp, _vp, C.POINTER(SolveParams), _vp],
     "qxd_batch_last_config": [C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "qxd_batch_set_spin_limit": [C.c_longlong],
+    "qxd_batch_tune_cache": [C.c_char_p],
     "qxd_net_create": [_vp, _i, C.POINTER(C.c_int), C.c_uint64, C.POINTER(_vp)],
     "qxd_net_destroy": [_vp],
     "qxd_net_set_weights": [_vp, _vp],
@@ -370,3 +371,8 @@ def batch_last_config():
 
 def batch_set_spin_limit(limit):
     _check(lib.qxd_batch_set_spin_limit(int(limit)))
+
+
+def batch_tune_cache(path):
+    """qxd_batch_tune_cache: the tuning cache file of solve_batch (None = none)."""
+    _check(lib.qxd_batch_tune_cache(None if path is None else os.fsencode(path)))

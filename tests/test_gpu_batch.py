@@ -117,3 +117,37 @@ def test_batch_barrier_timeout_is_reported_and_recoverable(qxd):
     finally:
         for c in cs:
             c.close()
+
+
+def test_batch_tuning_cache_file(qxd, tmp_path):
+    """A newly tuned set is appended to the cache file; an entry in the file is used untuned."""
+    path = tmp_path / "tune.txt"
+    qxd.batch_tune_cache(str(path))
+    cs = []
+    try:
+        # volumes 48 and 48: a set no other test tunes
+        cs = make_cases(qxd, [((6, 2, 2, 2), False, 0.3, -0.1), ((2, 2, 2, 6), False, 0.3, -0.1)])
+        etas = [synth.gaussian_spinor(c.dims, 2400 + k) for k, c in enumerate(cs)]
+        bs = [c.dev_tensor(e) for c, e in zip(cs, etas)]
+        xs = [torch.empty_like(b) for b in bs]
+        st, infos = qxd.solve_batch([c.lat for c in cs], xs, bs, tol=1e-10)
+        assert st == qxd.OK
+        check(cs, xs, etas, infos)
+        lines = path.read_text().splitlines()
+        cfg = qxd.batch_last_config()
+        assert len(lines) == 1, lines
+        f = lines[0].split()
+        assert f[:2] == ["qxd-batch-tune", "1"] and f[4] == "48,48,"
+        assert (int(f[5]), int(f[6])) == (cfg["blocks_per_sm"], cfg["sites_per_thread"])
+        # a hand-written entry for a lone lattice of volume 48 (a set not tuned in this process)
+        path.write_text(lines[0] + "\n" + " ".join(f[:4] + ["48,", "1", "4"]) + "\n")
+        st, infos = qxd.solve_batch([cs[1].lat], [xs[1]], [bs[1]], tol=1e-10)
+        assert st == qxd.OK
+        check([cs[1]], [xs[1]], [etas[1]], infos)
+        cfg = qxd.batch_last_config()
+        assert (cfg["blocks_per_sm"], cfg["sites_per_thread"]) == (1, 4), cfg
+        assert len(path.read_text().splitlines()) == 2  # used, not re-tuned
+    finally:
+        qxd.batch_tune_cache(None)
+        for c in cs:
+            c.close()
