@@ -290,18 +290,33 @@ qxd_status qxd_net_loss_grad(qxd_net *net, const double *v, const double *b, int
                              double *loss, double *grad);
 
 typedef struct {
-  int version;   /* QXD_TRAIN_VERSION */
+  int version;   /* QXD_TRAIN_VERSION (qxd_net_train also takes 1, which ends at eps) */
   int epochs;    /* passes over the training set */
   int batch;     /* samples per Adam step */
   double lr, beta1, beta2, eps; /* Adam */
+  /* version 2: read by qxd_train_precond only */
+  int nlayers;          /* network depth, as qxd_net_create */
+  int channels[9];      /* channels[0..nlayers], as qxd_net_create */
+  int nsamp;            /* training pairs generated on the device */
+  uint64_t net_seed;    /* weight initialisation, as qxd_net_create */
+  uint64_t sample_seed; /* sample i is the Gaussian field of seed sample_seed + i (see below) */
+  double *loss_hist;    /* host [epochs]: mean loss per epoch, or NULL */
 } qxd_train_params;
-#define QXD_TRAIN_VERSION 1
+#define QXD_TRAIN_VERSION 2
 
 /* Train on (b_i = D v_i, v_i), i < nsamp, generated by the lattice's own FP32 operator from the
  * given v ([nsamp][V][4][3][2], e.g. Gaussian): Adam on sum_i ||M(b_i) - v_i||^2 with the
  * network's own forward and backward kernels.  loss_hist (may be NULL): mean loss per epoch. */
 qxd_status qxd_net_train(qxd_net *net, const double *v, int nsamp, const qxd_train_params *p,
                          double *loss_hist, int on_device);
+/* Create and train a network in one call, with the training set generated on the device: sample
+ * i is the Gaussian spinor v_i whose component (alpha, a) at the site of lexicographic index x
+ * (Eq. lexi on the lattice's device extents, x doubled for C*) is re + i im = r (cos th + i sin th)
+ * (Box-Muller), r = sqrt(-2 ln(1 - u_{2j})), th = 2 pi u_{2j+1}, j = 12 x + 3 alpha + a, u_n the top
+ * 53 bits of SplitMix64 output n of seed sample_seed + i (counter style: mix(seed + (n + 1)
+ * 0x9E3779B97F4A7C15)), rounded to FP32; then as qxd_net_train on (D v_i, v_i).  Needs
+ * p->version 2; *out owns the network (qxd_net_destroy).  On failure *out is NULL. */
+qxd_status qxd_train_precond(qxd_lattice *lat, const qxd_train_params *p, qxd_net **out);
 /* Checkpoint: "QXDNET1\n", int32 nlayers, int32 channels[nlayers+1], float32 weights (re, im). */
 qxd_status qxd_net_save(const qxd_net *net, const char *path);
 qxd_status qxd_net_load(qxd_lattice *lat, const char *path, qxd_net **out);

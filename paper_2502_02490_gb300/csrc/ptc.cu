@@ -588,25 +588,12 @@ qxd_status qxd_net_loss_grad(qxd_net* net, const double* v, const double* b, int
   return QXD_OK;
 }
 
-qxd_status qxd_net_train(qxd_net* net, const double* v, int nsamp, const qxd_train_params* p, double* loss_hist,
-                         int on_device) {
-  QXD_TRACE();
-  if (!net || !v || !p || nsamp <= 0) return QXD_EINVAL;
+// Adam epochs over a resident training set set[2i] = v_i, set[2i+1] = b_i (FP32, internal layout)
+static qxd_status train_on_set(qxd_net* net, const float4* set, int nsamp, const qxd_train_params* p,
+                               double* loss_hist) {
   qxd_lattice* lat = net->lat;
-  if (p->version != QXD_TRAIN_VERSION) return fail(lat, QXD_EINVAL, "qxd_train_params version mismatch");
-  if (p->epochs <= 0 || p->batch <= 0 || !(p->lr > 0)) return fail(lat, QXD_EINVAL, "epochs, batch, lr must be > 0");
-  if (!lat->have_clover) return fail(lat, QXD_ESTATE, "train before build_clover");
   const i64 cs = 12 * lat->sv;
-  // training set: v_i and b_i = D v_i (FP32 operator), kept resident in FP32
-  float4* set;
   qxd_status st;
-  if ((st = ensure_work(lat, 31, sizeof(float4) * cs * 2 * nsamp, (void**)&set))) return st;
-  for (int i = 0; i < nsamp; ++i) {
-    float4 *vi = set + (i64)(2 * i) * cs, *bi = vi + cs;
-    if ((st = to_internal32(lat, v + (i64)i * 24 * lat->V, on_device, vi))) return st;
-    if ((st = hop32(lat, 0, EPI_DFULL, 0, vi + 6 * lat->sv, vi, bi, 0.f))) return st;
-    if ((st = hop32(lat, 1, EPI_DFULL, 0, vi, vi + 6 * lat->sv, bi + 6 * lat->sv, 0.f))) return st;
-  }
   const float b1 = (float)p->beta1, b2 = (float)p->beta2, eps = (float)p->eps;
   for (int e = 0; e < p->epochs; ++e) {
     double epoch_loss = 0.0;
@@ -628,6 +615,120 @@ qxd_status qxd_net_train(qxd_net* net, const double* v, int nsamp, const qxd_tra
     if (loss_hist) loss_hist[e] = epoch_loss / nsamp;
   }
   QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  return QXD_OK;
+}
+
+// b_i = D v_i with the FP32 operator, for every sample of a resident training set
+static qxd_status make_targets(qxd_lattice* lat, float4* set, int nsamp) {
+  const i64 cs = 12 * lat->sv;
+  qxd_status st;
+  for (int i = 0; i < nsamp; ++i) {
+    float4 *vi = set + (i64)(2 * i) * cs, *bi = vi + cs;
+    if ((st = hop32(lat, 0, EPI_DFULL, 0, vi + 6 * lat->sv, vi, bi, 0.f))) return st;
+    if ((st = hop32(lat, 1, EPI_DFULL, 0, vi, vi + 6 * lat->sv, bi + 6 * lat->sv, 0.f))) return st;
+  }
+  return QXD_OK;
+}
+
+static qxd_status check_train(qxd_lattice* lat, const qxd_train_params* p) {
+  if (p->version != 1 && p->version != QXD_TRAIN_VERSION) return fail(lat, QXD_EINVAL, "qxd_train_params version mismatch");
+  if (p->epochs <= 0 || p->batch <= 0 || !(p->lr > 0)) return fail(lat, QXD_EINVAL, "epochs, batch, lr must be > 0");
+  if (!lat->have_clover) return fail(lat, QXD_ESTATE, "train before build_clover");
+  return QXD_OK;
+}
+
+qxd_status qxd_net_train(qxd_net* net, const double* v, int nsamp, const qxd_train_params* p, double* loss_hist,
+                         int on_device) {
+  QXD_TRACE();
+  if (!net || !v || !p || nsamp <= 0) return QXD_EINVAL;
+  qxd_lattice* lat = net->lat;
+  qxd_status st;
+  if ((st = check_train(lat, p))) return st;
+  const i64 cs = 12 * lat->sv;
+  // training set: v_i and b_i = D v_i (FP32 operator), kept resident in FP32
+  float4* set;
+  if ((st = ensure_work(lat, 31, sizeof(float4) * cs * 2 * nsamp, (void**)&set))) return st;
+  // the slot is shared with other solvers: clear the padding lanes the kernels below never write
+  QXD_CUDA(lat, cudaMemsetAsync(set, 0, sizeof(float4) * cs * 2 * nsamp, lat->stream));
+  for (int i = 0; i < nsamp; ++i)
+    if ((st = to_internal32(lat, v + (i64)i * 24 * lat->V, on_device, set + (i64)(2 * i) * cs))) return st;
+  if ((st = make_targets(lat, set, nsamp))) return st;
+  return train_on_set(net, set, nsamp, p, loss_hist);
+}
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used counter-style: output i of the stream with
+// seed s is mix64(s + (i + 1) * golden ratio constant); uniforms are the top 53 bits.
+__device__ __forceinline__ double sm64_uniform(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+// Gaussian training sample: component k = 3 alpha + a of the site with lexicographic index x
+// (Eq. lexi, on the device lattice) is (r cos th, r sin th) by Box-Muller from uniforms 2j and
+// 2j + 1 of the stream, j = 12 x + k, r = sqrt(-2 log(1 - u1)), th = 2 pi u2; written in the
+// internal FP32 layout (both parities).
+__global__ void k_gauss_spinor32(Geom g, uint64_t seed, float4* __restrict__ out) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * g.Vh) return;
+  const int par = t >= g.Vh ? 1 : 0;
+  const uint32_t cb = (uint32_t)(t - par * g.Vh);
+  int x[4];
+  cb_coords32(g, cb, par, x);
+  const uint64_t lex = (((uint64_t)x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3];
+  float4* o = out + (i64)par * 6 * g.sv + cb;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    float c[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint64_t pair = 12 * lex + 2 * j + h;
+      const double u1 = sm64_uniform(seed, 2 * pair), u2 = sm64_uniform(seed, 2 * pair + 1);
+      const double r = sqrt(-2.0 * log1p(-u1));
+      double sn, cs;
+      sincos(6.283185307179586 * u2, &sn, &cs);
+      c[2 * h] = (float)(r * cs);
+      c[2 * h + 1] = (float)(r * sn);
+    }
+    o[(i64)j * g.sv] = make_float4(c[0], c[1], c[2], c[3]);
+  }
+}
+
+qxd_status qxd_train_precond(qxd_lattice* lat, const qxd_train_params* p, qxd_net** out) {
+  QXD_TRACE();
+  if (!lat || !p || !out) return QXD_EINVAL;
+  *out = nullptr;
+  if (p->version != QXD_TRAIN_VERSION) return fail(lat, QXD_EINVAL, "qxd_train_precond needs qxd_train_params version 2");
+  qxd_status st;
+  if ((st = check_train(lat, p))) return st;
+  if (p->nsamp <= 0) return fail(lat, QXD_EINVAL, "nsamp must be > 0");
+  qxd_net* net = nullptr;
+  if ((st = qxd_net_create(lat, p->nlayers, p->channels, p->net_seed, &net))) return st;
+  const i64 cs = 12 * lat->sv;
+  float4* set;
+  st = ensure_work(lat, 31, sizeof(float4) * cs * 2 * p->nsamp, (void**)&set);
+  if (st == QXD_OK) {  // padding lanes stay zero, as after to_internal32
+    const cudaError_t e = cudaMemsetAsync(set, 0, sizeof(float4) * cs * 2 * p->nsamp, lat->stream);
+    if (e != cudaSuccess) st = cuda_fail(lat, e, "cudaMemsetAsync");
+  }
+  for (int i = 0; i < p->nsamp && st == QXD_OK; ++i) {
+    const unsigned grid = (unsigned)((2 * lat->g.Vh + 255) / 256);
+    k_gauss_spinor32<<<grid, 256, 0, lat->stream>>>(lat->g, p->sample_seed + (uint64_t)i, set + (i64)(2 * i) * cs);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+      st = cuda_fail(lat, e, "k_gauss_spinor32");
+    else
+      lat->launches++;
+  }
+  if (st == QXD_OK) st = make_targets(lat, set, p->nsamp);
+  if (st == QXD_OK) st = train_on_set(net, set, p->nsamp, p, p->loss_hist);
+  if (st != QXD_OK) {
+    qxd_net_destroy(net);
+    return st;
+  }
+  *out = net;
   return QXD_OK;
 }
 

@@ -26,7 +26,7 @@ ORDER_LEXI, ORDER_IPT = 0, 1
 F64, F32, F16N, BF16N = 0, 1, 2, 3
 SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO, SOLVER_MP_FGCR_NET = 0, 1, 2, 3
 PARAMS_VERSION = 4
-TRAIN_VERSION = 1
+TRAIN_VERSION = 2
 PREC = {"f64": F64, "f32": F32, "f16n": F16N, "bf16n": BF16N}
 
 
@@ -40,7 +40,9 @@ class SolveParams(C.Structure):
 
 class TrainParams(C.Structure):
     _fields_ = [("version", C.c_int), ("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double),
-                ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double)]
+                ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("nlayers", C.c_int), ("channels", C.c_int * 9), ("nsamp", C.c_int), ("net_seed", C.c_uint64),
+                ("sample_seed", C.c_uint64), ("loss_hist", C.c_void_p)]
 
 
 class SolveInfo(C.Structure):
@@ -83,6 +85,7 @@ _SIGS = {
     "qxd_net_set_precision": [_vp, _i],
     "qxd_net_loss_grad": [_vp, _vp, _vp, _i, _i, C.POINTER(_d), _vp],
     "qxd_net_train": [_vp, _vp, _i, C.POINTER(TrainParams), _vp, _i],
+    "qxd_train_precond": [_vp, C.POINTER(TrainParams), C.POINTER(_vp)],
     "qxd_net_save": [_vp, C.c_char_p],
     "qxd_net_load": [_vp, C.c_char_p, C.POINTER(_vp)],
     "qxd_kernel_stats": [_vp, _i, C.POINTER(_i64), C.POINTER(_d), C.POINTER(_d)],
@@ -334,6 +337,21 @@ def net_train(net, v, nsamp, params=None, **kw):
     hist = np.zeros(p.epochs)
     _check(lib.qxd_net_train(net, pv, int(nsamp), C.byref(p), hist.ctypes.data, int(dev)))
     return hist
+
+
+def train_precond(lat, channels, nsamp, sample_seed, net_seed=0, params=None, **kw):
+    """qxd_train_precond: a network trained on nsamp device-generated Gaussian samples.
+    Returns (net handle, mean loss per epoch)."""
+    p = params if params is not None else train_params(**kw)
+    p.nlayers = len(channels) - 1
+    for i, c in enumerate(channels):
+        p.channels[i] = int(c)
+    p.nsamp, p.sample_seed, p.net_seed = int(nsamp), int(sample_seed), int(net_seed)
+    hist = np.zeros(p.epochs)
+    p.loss_hist = hist.ctypes.data
+    out = _vp()
+    _check(lib.qxd_train_precond(lat, C.byref(p), C.byref(out)), lat)
+    return out.value, hist
 
 
 def net_save(net, path):

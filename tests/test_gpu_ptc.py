@@ -148,3 +148,29 @@ def test_learned_solve_falls_back_to_plain_solver(qxd):
     finally:
         qxd.net_destroy(net)
         c.close()
+
+
+@pytest.mark.parametrize("L,cstar", [((4, 4, 4, 4), False), ((4, 2, 2, 4), True)])
+def test_train_precond_matches_host_samples(qxd, L, cstar):
+    """qxd_train_precond draws its samples on the device with the same counter-based recipe as the
+    host generator: training on them gives the loss history and weights of qxd_net_train on the
+    host-drawn fields of the same seeds."""
+    c = Case(qxd, torch, L, cstar=cstar)
+    nets = []
+    try:
+        kw = dict(epochs=3, batch=2, lr=2e-3)
+        net_a, hist_a = qxd.train_precond(c.lat, [1, 4, 1], nsamp=4, sample_seed=500, net_seed=7, **kw)
+        nets.append(net_a)
+        net_b = qxd.net_create(c.lat, [1, 4, 1], seed=7)
+        nets.append(net_b)
+        vs = c.dev_tensor(np.stack([synth.gaussian_spinor(c.dims, 500 + i) for i in range(4)]))
+        hist_b = qxd.net_train(net_b, vs, 4, **kw)
+        print("loss per epoch (device / host samples):", hist_a, hist_b)
+        assert np.all(hist_a > 0)
+        np.testing.assert_allclose(hist_a, hist_b, rtol=1e-6)
+        wa, wb = qxd.net_get_weights(net_a), qxd.net_get_weights(net_b)
+        assert np.linalg.norm(wa - wb) <= 1e-5 * np.linalg.norm(wb)
+    finally:
+        for n in nets:
+            qxd.net_destroy(n)
+        c.close()
