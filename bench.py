@@ -274,11 +274,7 @@ def run_ours(args, rank, world):
         "vs_baseline": None,
         "dtype": {"f16n": "f16+f32norm", "bf16n": "bf16+f32norm", "f32": "f32"}[args.inner] + "/f32/f64",
         "data": "synthetic (seeded SplitMix64 gauge field U=exp(i eps H) exp(i q eps theta), Gaussian source)",
-        "config": {"workload": w["name"],
-                   "lattice": list(w["L"]), "cstar": w["cstar"], "sites": V, "solver": f"mp-{args.solver}", "inner_prec": args.inner,
-                   "inner_tol": args.inner_tol,
-                   "reliable_delta": args.delta, "l2": "inputs larger than L2 (links+clover > 1 GB)",
-                   "parallelism": f"replicas{world}", "step": "load_gauge + build_clover + MP solve"},
+        "config": arm_config(args, world),
         "time_to_solution_s": statistics.mean(i["seconds"] for i in infos),
         "time_to_solution_note": "qxd_solve entry to return, fields resident (ms_per_step adds ingest + clover)",
         "solve": {"iters_inner_per_step": statistics.mean(iters), "iters_outer": infos[-1]["iters_outer"],
@@ -664,13 +660,23 @@ def cpu_sample(sample_slices=1):
     lat = O.Lattice(w["L"], antiperiodic=True)
     n = sample_slices * (w["L"][1] * w["L"][2] * w["L"][3])
     sites = np.arange(n)
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     O.D_at_sites(lat, U, A, w["q"], w["m0"], w["csw"], w["csw_qed"], eta, sites)
-    dt = time.perf_counter() - t0
-    return {"value": n * 2112 / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
+    # threads actually used: the process's CPU time over the wall time of the sample
+    return {"value": n * 2112 / dt / 1e9, "unit": "GB/s", "cores": max(1, round(cpu / dt)), "kind": "oracle",
             "sample": f"oracle D (clover built at the sites + full-spinor hop) on {n} sites "
                       f"({sample_slices} time slice(s) of 32^3x64), 2112 B/site FP64 convention, "
                       f"{dt:.1f} s"}
+
+
+def arm_config(args, world):
+    """The `config` of the default workload's JSON line, shared by both arms."""
+    w = WORKLOAD
+    return {"workload": w["name"], "lattice": list(w["L"]), "cstar": w["cstar"], "sites": int(np.prod(w["L"])) * (2 if w["cstar"] else 1),
+            "solver": f"mp-{args.solver}", "inner_prec": args.inner, "inner_tol": args.inner_tol,
+            "reliable_delta": args.delta, "l2": "inputs larger than L2 (links+clover > 1 GB)",
+            "parallelism": f"replicas{world}", "step": "load_gauge + build_clover + MP solve"}
 
 
 def run_reference(args, rank, world):
@@ -687,8 +693,7 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "32^3x64 clover operator, sampled sites (CPU oracle)"},
-            "cpu_baseline": cb, "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": arm_config(args, world), "cpu_baseline": cb, "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
