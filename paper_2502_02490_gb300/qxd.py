@@ -343,6 +343,8 @@ def train_precond(lat, channels, nsamp, sample_seed, net_seed=0, params=None, **
     """qxd_train_precond: a network trained on nsamp device-generated Gaussian samples.
     Returns (net handle, mean loss per epoch)."""
     p = params if params is not None else train_params(**kw)
+    if not 2 <= len(channels) <= 9:
+        raise ValueError("channels must list 2..9 channel counts (nlayers 1..8)")
     p.nlayers = len(channels) - 1
     for i, c in enumerate(channels):
         p.channels[i] = int(c)

@@ -72,3 +72,16 @@ def test_params_struct_matches_library_layout(qxd):
     # a version-3 struct ends where use_x0 begins
     assert qxd.SolveParams.use_x0.offset == qxd.SolveParams.fallback.offset + C.sizeof(C.c_int)
     assert qxd.SolveParams.use_x0.offset % 8 == 0
+
+
+def test_train_params_layout_and_binding_checks(qxd):
+    """Version-2 training params append the one-call fields after eps; the binding rejects a channel
+    list the library cannot hold before any call."""
+    import ctypes as C
+
+    T = qxd.TrainParams
+    assert qxd.TRAIN_VERSION == 2 and T.nlayers.offset == T.eps.offset + C.sizeof(C.c_double)
+    assert T.channels.size == 9 * C.sizeof(C.c_int)
+    with pytest.raises(ValueError):
+        qxd.train_precond(None, [1] * 10, nsamp=1, sample_seed=0)
+    assert qxd.lib.qxd_train_precond(None, None, None) == qxd.EINVAL

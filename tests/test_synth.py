@@ -38,3 +38,31 @@ def test_links_are_su3_and_chunk_independent():
 def test_eps_zero_is_unit_field():
     U, A = synth.gauge_field((2, 2, 2, 2), 5, 0.0)
     assert np.abs(U - np.eye(3)).max() < 1e-14 and np.abs(A).max() == 0
+
+
+def test_gaussian_spinor_follows_the_documented_recipe():
+    """The Gaussian field recipe that qxd_train_precond also draws on the device (include/qxd.h):
+    component (alpha, a) at lexicographic site x is r (cos th + i sin th) with r = sqrt(-2 ln(1 - u_2j)),
+    th = 2 pi u_(2j+1), j = 12 x + 3 alpha + a and u_n the top 53 bits of SplitMix64 output n.
+    Restated here with Python integers and the math module, independently of numpy."""
+    import math
+
+    mask = (1 << 64) - 1
+
+    def sm64(seed, n):
+        z = (seed + (n + 1) * 0x9E3779B97F4A7C15) & mask
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        return z ^ (z >> 31)
+
+    L, seed = (2, 4, 2, 2), 500
+    psi = synth.gaussian_spinor(L, seed)
+    for x in (0, 1, 17, 31):
+        for alpha in range(4):
+            for a in range(3):
+                j = 12 * x + 3 * alpha + a
+                u1 = (sm64(seed, 2 * j) >> 11) * 2.0 ** -53
+                u2 = (sm64(seed, 2 * j + 1) >> 11) * 2.0 ** -53
+                r = math.sqrt(-2.0 * math.log1p(-u1))
+                want = complex(r * math.cos(2 * math.pi * u2), r * math.sin(2 * math.pi * u2))
+                assert abs(psi[x, alpha, a] - want) <= 1e-15 * max(1.0, abs(want)), (x, alpha, a)
