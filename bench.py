@@ -650,6 +650,23 @@ def profile_run(args):
     qxd.destroy_lattice(lat)
 
 
+def host_cpu():
+    """CPU model and core count of this host, for the CPU baseline's record."""
+    import platform
+
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return f"{platform.machine()} {model or platform.processor() or 'cpu'}, {os.cpu_count()} logical cores"
+
+
 def cpu_sample(sample_slices=1):
     """Time the oracle's D (clover + hop, FP64 numpy) on a bounded sample of the workload's sites:
     every site of the first `sample_slices` time slices of the 32^3 x 64 lattice."""
@@ -665,6 +682,7 @@ def cpu_sample(sample_slices=1):
     dt, cpu = time.perf_counter() - t0, time.process_time() - c0
     # threads actually used: the process's CPU time over the wall time of the sample
     return {"value": n * 2112 / dt / 1e9, "unit": "GB/s", "cores": max(1, round(cpu / dt)), "kind": "oracle",
+            "host": host_cpu(),
             "sample": f"oracle D (clover built at the sites + full-spinor hop) on {n} sites "
                       f"({sample_slices} time slice(s) of 32^3x64), 2112 B/site FP64 convention, "
                       f"{dt:.1f} s"}

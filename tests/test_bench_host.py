@@ -31,3 +31,10 @@ def test_hash_covers_every_hop_source():
     for f in bench.HOP_SOURCES:
         assert os.path.exists(os.path.join(ROOT, "paper_2502_02490_gb300", "csrc", f))
     assert bench.hop_source_hash() == bench.hop_source_hash()
+
+
+def test_host_cpu_record():
+    import bench
+
+    h = bench.host_cpu()
+    assert h and f"{os.cpu_count()} logical cores" in h
