@@ -289,6 +289,7 @@ def run_ours(args, rank, world):
                      "launches": n_l, "avg_launch_us": ms_l / n_l * 1e3 if n_l else None},
         "kernels": {k: {"launches": v[0], "ms": v[1], "GB": v[2] / 1e9} for k, v in stats.items() if v[0]},
         "dslash_kernel_GBps": hop_total / sum(v[1] for v in stats.values()) / 1e6 if world == 1 else None,
+        "dslash_kernel_GFLOPs": dslash_gflops(dom, n_l, ms_l, arm_config(args, world)["sites"] // 2),
         "e2e": {"value": hop_total / e2e_s / 1e9 * (1 if world == 1 else 1), "unit": "GB/s",
                 "seconds_per_step": e2e_s / args.steps,
                 "h2d_bytes_per_step": int(U.nbytes + A.nbytes + eta.nbytes),
@@ -686,6 +687,16 @@ def cpu_sample(sample_slices=1):
             "sample": f"oracle D (clover built at the sites + full-spinor hop) on {n} sites "
                       f"({sample_slices} time slice(s) of 32^3x64), 2112 B/site FP64 convention, "
                       f"{dt:.1f} s"}
+
+
+DSLASH_FLOP_PER_SITE = 1824  # clover dslash: 1320 for the Wilson hop + 504 for the clover term
+
+
+def dslash_gflops(kernel, launches, ms, sites_per_launch):
+    """GFLOP/s of a hop kernel at DSLASH_FLOP_PER_SITE per output site and launch."""
+    value = DSLASH_FLOP_PER_SITE * sites_per_launch * launches / (ms / 1e3) / 1e9 if launches and ms > 0 else None
+    return {"value": value, "unit": "GFLOP/s", "kernel": kernel, "flop_per_site": DSLASH_FLOP_PER_SITE,
+            "sites_per_launch": sites_per_launch}
 
 
 def arm_config(args, world):

@@ -38,3 +38,11 @@ def test_host_cpu_record():
 
     h = bench.host_cpu()
     assert h and f"{os.cpu_count()} logical cores" in h
+
+
+def test_dslash_gflops_convention():
+    import bench
+
+    g = bench.dslash_gflops("hop_f16n", 10, 1.0, 1 << 20)  # 10 launches of 2^20 sites in 1 ms
+    assert g["value"] == 1824 * (1 << 20) * 10 / 1e-3 / 1e9 and g["unit"] == "GFLOP/s"
+    assert bench.dslash_gflops("hop_f16n", 0, 0.0, 8)["value"] is None
