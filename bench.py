@@ -651,20 +651,23 @@ def profile_run(args):
     qxd.destroy_lattice(lat)
 
 
-def host_cpu():
+def host_cpu(cpuinfo="/proc/cpuinfo"):
     """CPU model and core count of this host, for the CPU baseline's record."""
     import platform
 
-    model = ""
+    model, ids = "", {}
     try:
-        with open("/proc/cpuinfo") as f:
+        with open(cpuinfo) as f:
             for line in f:
                 key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu model", "hardware"):
+                if key in ("model name", "cpu model", "hardware") and not model:
                     model = line.split(":", 1)[1].strip()
-                    break
+                elif key in ("cpu implementer", "cpu part") and key not in ids:  # Arm: no model name
+                    ids[key] = line.split(":", 1)[1].strip()
     except OSError:
         pass
+    if not model and ids:
+        model = f"implementer {ids.get('cpu implementer', '?')} part {ids.get('cpu part', '?')}"
     return f"{platform.machine()} {model or platform.processor() or 'cpu'}, {os.cpu_count()} logical cores"
 
 

@@ -46,3 +46,13 @@ def test_dslash_gflops_convention():
     g = bench.dslash_gflops("hop_f16n", 10, 1.0, 1 << 20)  # 10 launches of 2^20 sites in 1 ms
     assert g["value"] == 1824 * (1 << 20) * 10 / 1e-3 / 1e9 and g["unit"] == "GFLOP/s"
     assert bench.dslash_gflops("hop_f16n", 0, 0.0, 8)["value"] is None
+
+
+def test_host_cpu_names_arm_parts(tmp_path):
+    import bench
+
+    f = tmp_path / "cpuinfo"
+    f.write_text("processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n\n"
+                 "processor\t: 1\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n")
+    assert "implementer 0x41 part 0xd4f" in bench.host_cpu(str(f))
+    assert "logical cores" in bench.host_cpu(str(tmp_path / "missing"))
