@@ -162,7 +162,6 @@ qxd_status solve_mrhs(qxd_lattice* lat, double2* x, const double2* b, int n, con
   TRY(blas_zero(lat, x, sizeof(double2) * nf * n));
   int total = 0, outer = 0, nrel = 0;
   const int max_outer = prm->max_outer > 0 ? prm->max_outer : 20;
-  bool all_done = false;
   for (; outer <= max_outer; ++outer) {
     std::vector<char> act(n, 0);
     int nact = 0;
@@ -196,10 +195,7 @@ qxd_status solve_mrhs(qxd_lattice* lat, double2* x, const double2* b, int n, con
       act[i] = 1;
       ++nact;
     }
-    if (nact == 0) {
-      all_done = true;
-      break;
-    }
+    if (nact == 0) break;
     if (outer == max_outer || total >= prm->maxiter) break;
     // the saved odd residuals move out of H_S (the inner solve reuses it)
     float4* ro_save;
