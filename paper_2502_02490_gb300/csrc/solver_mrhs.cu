@@ -233,7 +233,6 @@ qxd_status solve_mrhs(qxd_lattice* lat, double2* x, const double2* b, int n, con
       info[i].status = done[i] ? QXD_OK : QXD_ENOCONV;
     }
   }
-  (void)all_done;
   if (!ok) return fail(lat, QXD_ENOCONV, "some right-hand side did not reach the tolerance");
   return QXD_OK;
 }
