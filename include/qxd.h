@@ -88,9 +88,11 @@ typedef enum {
                               inner_prec with FP32 reliable updates */
   QXD_SOLVER_MP_BICGSTAB_EO = 2, /* as MP_CG_EO with BiCGStab on Dhat as the inner solver (each
                                    reliable update restarts it from the recomputed residual) */
-  QXD_SOLVER_MP_FGCR_NET = 3     /* FP64 outer defect correction around flexible GCR(gcr_restart) on
+  QXD_SOLVER_MP_FGCR_NET = 3,    /* FP64 outer defect correction around flexible GCR(gcr_restart) on
                                    the full D in FP32 with the learned network `net` as right
                                    preconditioner (net NULL: no preconditioner) */
+  QXD_SOLVER_MP_SAP_GCR = 4      /* as MP_FGCR_NET with the Schwarz alternating procedure as the
+                                   preconditioner (sap_block, sap_ncy, sap_nmr; qxd_sap_apply) */
 } qxd_solver;
 
 typedef struct {
@@ -119,11 +121,16 @@ typedef struct {
                              (stagnation, breakdown), restart it once from its current x with
                              FP32 inner precision, a fresh max_outer and the iterations left of
                              maxiter; before any fallback.  qxd_solve only. */
+  /* version 5 */
+  int sap_block[4];       /* MP_SAP_GCR: block extents (see qxd_sap_apply) */
+  int sap_ncy;            /* MP_SAP_GCR: SAP cycles per preconditioner application (>= 1) */
+  int sap_nmr;            /* MP_SAP_GCR: minimal-residual steps per block solve (>= 1) */
 } qxd_solve_params;
 
-/* Version 4 appended use_x0 and restart_f32.  A version-3 struct (which ends at fallback) is
- * still accepted and runs with both off. */
-#define QXD_PARAMS_VERSION 4
+/* Version 4 appended use_x0 and restart_f32, version 5 the SAP fields.  Older structs (version
+ * 3 ends at fallback, version 4 at restart_f32) are still accepted: the fields they lack take
+ * the defaults, except use_x0 and restart_f32, which a version-3 struct runs with off. */
+#define QXD_PARAMS_VERSION 5
 
 typedef struct {
   int iters_inner;        /* inner iterations summed over outer rounds */
@@ -242,8 +249,21 @@ qxd_status qxd_batch_last_config(int *threads, int *sites_per_thread, int *block
 
 /* Fill *p with the defaults: MP_CG_EO, tol 1e-10, maxiter 100000, inner F32, inner_tol 1e-5,
  * reliable_delta 0.1, max_outer 20, on_device 1, check_every 1, gcr_restart 16, net NULL,
- * gcr_reorth 1, fallback -1, use_x0 0, restart_f32 1. */
+ * gcr_reorth 1, fallback -1, use_x0 0, restart_f32 1, sap_block {4, 4, 4, 4}, sap_ncy 2, sap_nmr 4. */
 void qxd_default_params(qxd_solve_params *p);
+
+/* out = M in with M the Schwarz alternating procedure (Sec. 5.1 names it as the preconditioner
+ * of the paper's CPU solves), on full fields [V][4][3][2], FP32 arithmetic.  The lattice is cut
+ * into blocks of extents block[mu] (each divides the lattice extent on the device, x doubled
+ * for C*, with an even number of blocks per direction, and for C* the physical L1 an even number
+ * of x blocks; at most 256 sites per block), so that blocks of one colour never touch.  A block's
+ * colour is the parity of its block coordinates.  Each of ncy cycles sweeps colour 0, then
+ * colour 1.  Every block of the colour takes nmr minimal-residual steps from zero on D
+ * restricted to the block (hops leaving it dropped) for the current residual; the result is
+ * added to the output, and the residual in - D out is recomputed.  QXD_EINVAL for a block shape
+ * outside these rules, ncy < 1 or nmr < 1; QXD_ESTATE before build_clover. */
+qxd_status qxd_sap_apply(qxd_lattice *lat, double *out, const double *in, const int block[4], int ncy,
+                         int nmr, int on_device);
 
 /* Fused BLAS-1 on device vectors of n complex numbers (interleaved re, im), on the lattice's
  * stream, FP64.  Reductions are deterministic (fixed order) and return to host memory.

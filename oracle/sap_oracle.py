@@ -9,8 +9,10 @@ This module writes out the textbook procedure, a multiplicative Schwarz method o
 non-overlapping blocks.  The readings below fill what the paper leaves open:
 
   * Blocks: extents b_mu that divide L_mu.  The block grid n_mu = L_mu / b_mu is 1 or even in
-    every direction, so blocks of one colour never touch, periodic wrap included.  The colour
-    of a block is the parity of the sum of its block coordinates.
+    every direction, so blocks of one colour never touch, periodic wrap included.  With C*, a
+    hop across the y or z boundary also moves x by L1 (Sec. 4.2), so L1 must be an even number
+    of x blocks as well.  The colour of a block is the parity of the sum of its block
+    coordinates.
   * Block operator D_Lambda: the matrix of D restricted to the sites of the block, rows and
     columns both.  Hops that leave the block are dropped (Dirichlet boundary).  A block that
     spans a whole extent keeps its wrap-around links, since both ends lie in the block.
@@ -31,9 +33,15 @@ import numpy as np
 from oracle import qxd_oracle as O
 
 
-def sap_blocks(L, b):
-    """The blocks of extents b on a lattice of extents L: a list of (site mask, colour)."""
+def sap_blocks(L, b, cstar_L1=None):
+    """The blocks of extents b on a lattice of extents L: a list of (site mask, colour).
+
+    cstar_L1: the physical L1 of a C* lattice (L is then the doubled lattice).  A hop across the
+    y or z boundary moves x by L1, so L1 must be an even number of x blocks for blocks that meet
+    there to have opposite colours."""
     L, b = tuple(int(v) for v in L), tuple(int(v) for v in b)
+    if cstar_L1 is not None and int(cstar_L1) % (2 * b[1]):
+        raise ValueError("with C*, the physical L1 must be an even number of x blocks")
     n = []
     for Lm, bm in zip(L, b):
         if bm <= 0 or Lm % bm:

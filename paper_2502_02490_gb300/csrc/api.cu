@@ -159,18 +159,27 @@ static qxd_status alloc(qxd_lattice* lat, T** p, size_t bytes) {
 }
 
 namespace qxd {
+qxd_status sap_check(qxd_lattice* lat, const int b[4]);  // csrc/sap.cu
+
 // The caller's params as the current version.  Version 3 ended at `fallback`; version 4 appended
 // use_x0 and restart_f32, which a version-3 caller gets off.
 qxd_status params_current(qxd_lattice* lat, const qxd_solve_params* p, qxd_solve_params* q) {
-  if (p->version == QXD_PARAMS_VERSION) {
-    *q = *p;
-  } else if (p->version == 3) {
-    std::memset(q, 0, sizeof(*q));
-    std::memcpy(q, p, offsetof(qxd_solve_params, use_x0));
-    q->version = QXD_PARAMS_VERSION;
-  } else {
+  size_t have;
+  if (p->version == QXD_PARAMS_VERSION)
+    have = sizeof(*q);
+  else if (p->version == 4)
+    have = offsetof(qxd_solve_params, sap_block);
+  else if (p->version == 3)
+    have = offsetof(qxd_solve_params, use_x0);
+  else
     return fail(lat, QXD_EINVAL, "qxd_solve_params version mismatch");
+  qxd_default_params(q);
+  std::memcpy(q, p, have);
+  if (p->version == 3) {  // version 3 had no initial guess and no FP32 restart
+    q->use_x0 = 0;
+    q->restart_f32 = 0;
   }
+  q->version = QXD_PARAMS_VERSION;
   return QXD_OK;
 }
 }  // namespace qxd
@@ -196,6 +205,9 @@ void qxd_default_params(qxd_solve_params* p) {
   p->net = nullptr;
   p->use_x0 = 0;
   p->restart_f32 = 1;
+  for (int mu = 0; mu < 4; ++mu) p->sap_block[mu] = 4;
+  p->sap_ncy = 2;
+  p->sap_nmr = 4;
 }
 
 qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
@@ -532,17 +544,20 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
   TRY(params_current(lat, p, &pv));
   p = &pv;
   if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO && p->solver != QXD_SOLVER_MP_BICGSTAB_EO &&
-      p->solver != QXD_SOLVER_MP_FGCR_NET)
+      p->solver != QXD_SOLVER_MP_FGCR_NET && p->solver != QXD_SOLVER_MP_SAP_GCR)
     return fail(lat, QXD_EINVAL, "bad solver");
+  if (p->solver == QXD_SOLVER_MP_SAP_GCR) {
+    TRY(sap_check(lat, p->sap_block));
+    if (p->sap_ncy < 1 || p->sap_nmr < 1) return fail(lat, QXD_EINVAL, "sap_ncy and sap_nmr must be >= 1");
+  }
   if (p->fallback != -1 && p->fallback != QXD_SOLVER_CG_EO && p->fallback != QXD_SOLVER_MP_CG_EO &&
       p->fallback != QXD_SOLVER_MP_BICGSTAB_EO)
     return fail(lat, QXD_EINVAL, "fallback must be -1, CG_EO, MP_CG_EO or MP_BICGSTAB_EO");
   if (p->use_x0 != 0 && p->use_x0 != 1) return fail(lat, QXD_EINVAL, "use_x0 must be 0 or 1");
   if (p->restart_f32 != 0 && p->restart_f32 != 1) return fail(lat, QXD_EINVAL, "restart_f32 must be 0 or 1");
-  if (p->solver == QXD_SOLVER_MP_FGCR_NET && (p->gcr_reorth < 1 || p->gcr_reorth > 2))
-    return fail(lat, QXD_EINVAL, "gcr_reorth must be 1 or 2");
-  if (p->solver == QXD_SOLVER_MP_FGCR_NET && (p->gcr_restart < 1 || p->gcr_restart > 32))
-    return fail(lat, QXD_EINVAL, "gcr_restart must be 1..32");
+  const bool fgcr = p->solver == QXD_SOLVER_MP_FGCR_NET || p->solver == QXD_SOLVER_MP_SAP_GCR;
+  if (fgcr && (p->gcr_reorth < 1 || p->gcr_reorth > 2)) return fail(lat, QXD_EINVAL, "gcr_reorth must be 1 or 2");
+  if (fgcr && (p->gcr_restart < 1 || p->gcr_restart > 32)) return fail(lat, QXD_EINVAL, "gcr_restart must be 1..32");
   if (!(p->tol > 0) || p->maxiter <= 0) return fail(lat, QXD_EINVAL, "tol must be > 0 and maxiter > 0");
   if (p->solver != QXD_SOLVER_CG_EO && (p->inner_prec < QXD_F32 || p->inner_prec > QXD_BF16N))
     return fail(lat, QXD_EINVAL, "inner_prec must be F32, F16N or BF16N");

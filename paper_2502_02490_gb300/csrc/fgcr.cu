@@ -1,5 +1,5 @@
-// Flexible GCR on the full D in FP32 with a right preconditioner M (the learned network, or none),
-// with every coefficient kept on the device.
+// Flexible GCR on the full D in FP32 with a right preconditioner M (the learned network, the
+// Schwarz alternating procedure, or none), with every coefficient kept on the device.
 //
 // Cycle of at most m steps, k = 0, 1, ...:
 //   z_k = M r;  w_k = D z_k;
@@ -14,6 +14,7 @@
 // Reductions: per-block FP64 partials (FP32 products per element), summed in block order by a
 // second small kernel: deterministic for a given grid.
 #include "qxd_internal.cuh"
+#include "sap.cuh"
 #include "reduce.cuh"
 
 namespace qxd {
@@ -212,8 +213,8 @@ __global__ void __launch_bounds__(FG_BLOCK) k_fg_zsum(const float4* __restrict__
   }
 }
 
-qxd_status fgcr32(qxd_lattice* lat, qxd_net* net, int m, int reorth, const float4* rhs, float4* y, double target,
-                  int maxiter, int check_every, int* iters) {
+qxd_status fgcr32(qxd_lattice* lat, qxd_net* net, const SapSpec* sap, int m, int reorth, const float4* rhs, float4* y,
+                  double target, int maxiter, int check_every, int* iters) {
   if (m < 1 || m > FG_MAXM) return fail(lat, QXD_EINVAL, "gcr_restart must be 1..32");
   const i64 sv = lat->sv, n4 = 12 * sv;
   const size_t fb = sizeof(float4) * n4;
@@ -245,7 +246,9 @@ qxd_status fgcr32(qxd_lattice* lat, qxd_net* net, int m, int reorth, const float
   const int every = check_every > 0 ? check_every : 1;
   bool done = !(std::sqrt(rn2) > target);
   while (!done && it < maxiter) {
-    if (net)
+    if (sap)
+      TRY_Q(sap32(lat, sap->block, sap->ncy, sap->nmr, r, z(k)));
+    else if (net)
       TRY_Q(net_apply32(net, r, z(k)));
     else
       QXD_CUDA(lat, cudaMemcpyAsync(z(k), r, fb, cudaMemcpyDeviceToDevice, S));

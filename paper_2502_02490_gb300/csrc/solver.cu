@@ -16,6 +16,7 @@
 #include <cstring>
 
 #include "reduce.cuh"
+#include "sap.cuh"
 
 namespace qxd {
 
@@ -364,8 +365,8 @@ static qxd_status inner_bicg(qxd_lattice* lat, int prec, const float4* bh, float
 }
 
 // The inner flexible GCR of QXD_SOLVER_MP_FGCR_NET lives in fgcr.cu (device-resident coefficients).
-qxd_status fgcr32(qxd_lattice* lat, qxd_net* net, int m, int reorth, const float4* rhs, float4* y, double target,
-                  int maxiter, int check_every, int* iters);
+qxd_status fgcr32(qxd_lattice* lat, qxd_net* net, const SapSpec* sap, int m, int reorth, const float4* rhs, float4* y,
+                  double target, int maxiter, int check_every, int* iters);
 
 static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve_params* prm,
                              qxd_solve_info* info);
@@ -434,7 +435,7 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
   TRY(get(lat, WS_XE64, hb, &xe));
   TRY(get(lat, WS_TO64, hb, &to));
   const bool mp = prm->solver == QXD_SOLVER_MP_CG_EO || prm->solver == QXD_SOLVER_MP_BICGSTAB_EO;
-  const bool gcr = prm->solver == QXD_SOLVER_MP_FGCR_NET;
+  const bool gcr = prm->solver == QXD_SOLVER_MP_FGCR_NET || prm->solver == QXD_SOLVER_MP_SAP_GCR;
   float4 *bh32 = nullptr, *y32 = nullptr, *r32 = nullptr, *to32 = nullptr;
   if (mp) {
     TRY(get(lat, WS_BH32, sizeof(float4) * 12 * sv, &bh32));  // sized for full fields (apply_D_prec shares it)
@@ -488,7 +489,7 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
     int it = 0;
     const double target = 0.5 * prm->tol * bnorm;
     if (gcr) {
-      // the correction D e = r on the full lattice by FGCR with the network, FP32
+      // the correction D e = r on the full lattice by FGCR with the network or SAP, FP32
       float4 *r32f, *e32;
       TRY(get(lat, WS_R32, sizeof(float4) * 12 * sv, &r32f));
       TRY(get(lat, WS_BH32, sizeof(float4) * 12 * sv, &e32));
@@ -496,8 +497,15 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
       TRY(blas_zero(lat, e32, sizeof(float4) * 12 * sv));
       double inner_target = prm->inner_tol * std::sqrt(rn2);
       if (inner_target < target) inner_target = target;
-      TRY(fgcr32(lat, const_cast<qxd_net*>(prm->net), prm->gcr_restart, prm->gcr_reorth, r32f, e32, inner_target,
-                 prm->maxiter - total, prm->check_every, &it));
+      SapSpec sp;
+      const bool with_sap = prm->solver == QXD_SOLVER_MP_SAP_GCR;
+      if (with_sap) {
+        for (int mu = 0; mu < 4; ++mu) sp.block[mu] = prm->sap_block[mu];
+        sp.ncy = prm->sap_ncy;
+        sp.nmr = prm->sap_nmr;
+      }
+      TRY(fgcr32(lat, with_sap ? nullptr : const_cast<qxd_net*>(prm->net), with_sap ? &sp : nullptr, prm->gcr_restart,
+                 prm->gcr_reorth, r32f, e32, inner_target, prm->maxiter - total, prm->check_every, &it));
       TRY(blas_acc_f32_into_f64(lat, e32, x, 12 * sv));
     } else if (!mp) {
       // Schur source bh = r_e + 1/2 H_eo A_oo^-1 r_o, CG, reconstruct x_o += A_oo^-1 (r_o + 1/2 H_oe xe)

@@ -24,8 +24,8 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESINGULAR", "ENOCONV", "ESTA
 BC_PERIODIC, BC_ANTIPERIODIC = 0, 1
 ORDER_LEXI, ORDER_IPT = 0, 1
 F64, F32, F16N, BF16N = 0, 1, 2, 3
-SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO, SOLVER_MP_FGCR_NET = 0, 1, 2, 3
-PARAMS_VERSION = 4
+SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO, SOLVER_MP_FGCR_NET, SOLVER_MP_SAP_GCR = 0, 1, 2, 3, 4
+PARAMS_VERSION = 5
 TRAIN_VERSION = 2
 PREC = {"f64": F64, "f32": F32, "f16n": F16N, "bf16n": BF16N}
 
@@ -35,7 +35,8 @@ class SolveParams(C.Structure):
                 ("inner_prec", C.c_int), ("inner_tol", C.c_double), ("reliable_delta", C.c_double),
                 ("max_outer", C.c_int), ("on_device", C.c_int), ("check_every", C.c_int),
                 ("gcr_restart", C.c_int), ("net", C.c_void_p), ("gcr_reorth", C.c_int), ("fallback", C.c_int),
-                ("use_x0", C.c_int), ("restart_f32", C.c_int)]
+                ("use_x0", C.c_int), ("restart_f32", C.c_int),
+                ("sap_block", C.c_int * 4), ("sap_ncy", C.c_int), ("sap_nmr", C.c_int)]
 
 
 class TrainParams(C.Structure):
@@ -71,6 +72,7 @@ _SIGS = {
     "qxd_vec_dot_noalloc": [_vp, _vp, _i64, _vp, _vp],
     "qxd_set_profiling": [_vp, _i],
     "qxd_check_guards": [_vp, C.POINTER(_i64)],
+    "qxd_sap_apply": [_vp, _vp, _vp, C.POINTER(C.c_int), _i, _i, _i],
     "qxd_solve_batch": [_vp, _i, _vp, _vp, C.POINTER(SolveParams), _vp],
     "qxd_batch_last_config": [C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "qxd_batch_set_spin_limit": [C.c_longlong],
@@ -193,7 +195,8 @@ def default_params(**kw):
     p = SolveParams()
     lib.qxd_default_params(C.byref(p))
     for k, v in kw.items():
-        setattr(p, k, v)
+        cur = getattr(p, k)
+        setattr(p, k, type(cur)(*v) if isinstance(cur, C.Array) else v)
     return p
 
 
@@ -306,6 +309,16 @@ NET_F32, NET_BF16_TC = 0, 1
 
 def net_set_precision(net, prec):
     _check(lib.qxd_net_set_precision(net, int(prec)))
+
+
+def sap_apply(lat, out, inp, block, ncy=2, nmr=4):
+    """qxd_sap_apply: out = M_SAP inp (Schwarz alternating procedure, FP32)."""
+    po, dev = _ptr(out)
+    pi, dev2 = _ptr(inp)
+    if dev != dev2:
+        raise ValueError("out and inp must both be host or both be device buffers")
+    b = (C.c_int * 4)(*[int(v) for v in block])
+    _check(lib.qxd_sap_apply(lat, po, pi, b, int(ncy), int(nmr), int(dev)), lat)
 
 
 def net_apply(net, out, inp):

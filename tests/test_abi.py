@@ -52,6 +52,8 @@ def test_default_params(qxd):
     assert p.version == qxd.PARAMS_VERSION and p.tol == 1e-10 and p.solver == qxd.SOLVER_MP_CG_EO
     assert p.gcr_restart == 16 and p.gcr_reorth == 1 and p.check_every == 1 and p.fallback == -1
     assert p.use_x0 == 0 and p.restart_f32 == 1
+    assert list(p.sap_block) == [4, 4, 4, 4] and p.sap_ncy == 2 and p.sap_nmr == 4
+    assert list(qxd.default_params(sap_block=(2, 2, 2, 4)).sap_block) == [2, 2, 2, 4]
     assert qxd.lib.qxd_destroy_lattice(None) == qxd.OK
     import ctypes as C
 
@@ -69,9 +71,10 @@ def test_params_struct_matches_library_layout(qxd):
     p = qxd.SolveParams.from_buffer(buf)
     assert p.version == qxd.PARAMS_VERSION and p.restart_f32 == 1 and p.use_x0 == 0 and p.fallback == -1
     assert bytes(buf[n:]) == bytes([0xA5] * 64)
-    # a version-3 struct ends where use_x0 begins
+    # a version-3 struct ends where use_x0 begins, a version-4 struct where sap_block begins
     assert qxd.SolveParams.use_x0.offset == qxd.SolveParams.fallback.offset + C.sizeof(C.c_int)
     assert qxd.SolveParams.use_x0.offset % 8 == 0
+    assert qxd.SolveParams.sap_block.offset == qxd.SolveParams.restart_f32.offset + C.sizeof(C.c_int)
 
 
 def test_train_params_layout_and_binding_checks(qxd):

@@ -1,0 +1,107 @@
+"""Schwarz alternating procedure on the GPU (Sec. 5.1 names SAP as the preconditioner of the
+paper's CPU solves) against the oracle's SAP, and SAP-preconditioned GCR solves judged by the
+oracle's true residual."""
+import numpy as np
+import pytest
+
+from oracle import qxd_oracle as O
+from oracle import sap_oracle as S
+from paper_2502_02490_gb300 import synth
+from tests.gpu_util import Case, as_c128
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+# FP32 arithmetic against the FP64 oracle in a nonlinear iteration (the MR step lengths depend on
+# the residual): FP32 unit roundoff 6e-8 times the amplification over the steps and cycles.  A
+# structural mistake (a wrong block, colour or step) gives an O(1) difference.
+SAP_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def qxd():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_02490_gb300 import qxd as q
+
+    return q
+
+
+@pytest.mark.parametrize("L,block,cstar,ncy,nmr", [
+    ((4, 4, 4, 4), (2, 2, 2, 2), False, 2, 4),
+    ((6, 4, 4, 8), (3, 2, 2, 4), False, 1, 6),   # odd block extent
+    ((4, 4, 2, 4), (2, 2, 1, 2), True, 2, 3),    # C*: the device lattice is 4 x 8 x 2 x 4
+])
+def test_sap_matches_oracle(qxd, L, block, cstar, ncy, nmr):
+    c = Case(qxd, torch, L, cstar=cstar)
+    try:
+        eta = synth.gaussian_spinor(c.dims, 2500)
+        x = c.dev_tensor(eta)
+        y = torch.empty_like(x)
+        qxd.sap_apply(c.lat, y, x, block, ncy, nmr)
+        got = as_c128(y, eta.shape)
+        ref = S.sap(c.op, S.sap_blocks(c.dims, block, cstar_L1=L[1] if cstar else None), eta, ncy=ncy, nmr=nmr)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        print(f"{L} block {block} cstar={cstar}: SAP rel err {err:.2e}")
+        assert err < SAP_TOL, err
+        # host buffers give the same result
+        yh = np.zeros_like(eta)
+        qxd.sap_apply(c.lat, yh, np.ascontiguousarray(eta), block, ncy, nmr)
+        assert np.abs(yh - got).max() <= 1e-6 * np.abs(got).max()
+    finally:
+        c.close()
+
+
+def test_sap_rejects_bad_block_shapes(qxd):
+    c = Case(qxd, torch, (4, 4, 4, 4))
+    try:
+        x = c.dev_tensor(synth.gaussian_spinor(c.dims, 1))
+        y = torch.empty_like(x)
+        for block, ncy, nmr in [((3, 2, 2, 2), 1, 1), ((4, 2, 2, 2), 1, 1), ((2, 2, 2, 2), 0, 1),
+                                ((2, 2, 2, 2), 1, 0)]:
+            with pytest.raises(qxd.QxdError) as e:
+                qxd.sap_apply(c.lat, y, x, block, ncy, nmr)
+            assert e.value.status == qxd.EINVAL
+        # C*: the mirror shift L1 = 2 is one x block, so same-coloured blocks would meet
+        cs = Case(qxd, torch, (4, 2, 2, 4), cstar=True)
+        try:
+            w = cs.dev_tensor(synth.gaussian_spinor(cs.dims, 1))
+            with pytest.raises(qxd.QxdError) as e:
+                qxd.sap_apply(cs.lat, torch.empty_like(w), w, (2, 2, 1, 2), 1, 1)
+            assert e.value.status == qxd.EINVAL
+        finally:
+            cs.close()
+        big = Case(qxd, torch, (8, 8, 8, 16))
+        try:
+            z = big.dev_tensor(synth.gaussian_spinor(big.dims, 1))
+            with pytest.raises(qxd.QxdError) as e:
+                qxd.sap_apply(big.lat, torch.empty_like(z), z, (4, 4, 4, 8), 1, 1)  # 512 sites per block
+            assert "256" in qxd.last_error(big.lat)
+        finally:
+            big.close()
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("tol", [1e-10, 1e-12])
+def test_sap_gcr_solves(qxd, tol):
+    c = Case(qxd, torch, (8, 4, 4, 4), m0=0.0)
+    try:
+        eta = synth.gaussian_spinor(c.dims, 2501)
+        b = c.dev_tensor(eta)
+        x = torch.empty_like(b)
+        st, info = qxd.solve(c.lat, x, b, solver=qxd.SOLVER_MP_SAP_GCR, inner_prec=qxd.F32, tol=tol,
+                             sap_block=(2, 2, 2, 2), sap_ncy=2, sap_nmr=4, gcr_restart=16)
+        assert st == qxd.OK
+        res = O.true_rel_residual(c.op, as_c128(x, eta.shape), eta)
+        assert res <= tol, (res, info)
+        x2 = torch.empty_like(b)
+        st, plain = qxd.solve(c.lat, x2, b, solver=qxd.SOLVER_MP_FGCR_NET, inner_prec=qxd.F32, tol=tol,
+                              gcr_restart=16)
+        print(f"tol {tol}: SAP-GCR {info['iters_inner']} steps, plain GCR {plain['iters_inner']}; residual {res:.2e}")
+        assert info["iters_inner"] < plain["iters_inner"]
+    finally:
+        c.close()

@@ -63,6 +63,25 @@ def test_blocks_tile_the_lattice_and_same_colours_never_touch():
         S.sap_blocks((6, 4, 4, 4), (2, 2, 2, 2))  # three blocks in t: same colours would touch
 
 
+def test_cstar_blocks_keep_same_colours_apart():
+    """With C* a hop across the y or z boundary moves x by the physical L1 (Sec. 4.2): blocks of
+    one colour stay apart exactly when L1 is an even number of x blocks."""
+    def touching_same_colour(L, b):
+        lat = O.Lattice(L, cstar=True)
+        blocks = S.sap_blocks(lat.dims, b)
+        owner, colour = np.empty(lat.V, int), np.array([c for _, c in blocks])
+        for k, (mask, _) in enumerate(blocks):
+            owner[mask] = k
+        return any(np.any((owner != owner[lat.fwd(mu)]) & (colour[owner] == colour[owner[lat.fwd(mu)]]))
+                   for mu in range(4))
+
+    assert not touching_same_colour((4, 4, 2, 4), (2, 2, 1, 2))  # L1 = 4: two x blocks
+    assert touching_same_colour((4, 2, 2, 4), (2, 2, 1, 2))      # L1 = 2: one x block
+    S.sap_blocks((4, 8, 2, 4), (2, 2, 1, 2), cstar_L1=4)
+    with pytest.raises(ValueError):
+        S.sap_blocks((4, 4, 2, 4), (2, 2, 1, 2), cstar_L1=2)
+
+
 def test_one_block_with_exact_solves_is_the_inverse():
     L = (2, 2, 2, 2)
     op, _, _ = make_op(L)
