@@ -1,6 +1,7 @@
 """CPU oracle (plain FP64 numpy) for the Wilson-clover operator, its clover term, the
-even-odd Schur complement and the even-odd CG solve (``qxd_oracle``), and for the Schwarz
-alternating procedure with flexible GCR around it (``sap_oracle``).
+even-odd Schur complement and the even-odd CG solve (``qxd_oracle``), for the Schwarz
+alternating procedure with flexible GCR around it (``sap_oracle``), and for inexact deflation
+with a block-local subspace (``dfl_oracle``).
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py``.  It shares no code with the CUDA path.  Every function that
@@ -8,3 +9,4 @@ has no independent pin says "parity unpinned" in its docstring.
 """
 from . import qxd_oracle  # noqa: F401
 from . import sap_oracle  # noqa: F401
+from . import dfl_oracle  # noqa: F401
