@@ -28,8 +28,11 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
+    # the boundary's call list: the operator and solve calls, the batched solve, the one-call
+    # training of the preconditioner, its checkpoint, the clover export and the error message
     for required in ["qxd_create_lattice", "qxd_destroy_lattice", "qxd_load_gauge", "qxd_build_clover",
-                     "qxd_apply_D", "qxd_apply_Dhat_eo", "qxd_solve"]:
+                     "qxd_get_clover", "qxd_apply_D", "qxd_apply_Dhat_eo", "qxd_solve", "qxd_solve_batch",
+                     "qxd_train_precond", "qxd_net_save", "qxd_net_load", "qxd_last_error"]:
         assert required in names
 
 
