@@ -56,3 +56,18 @@ def test_host_cpu_names_arm_parts(tmp_path):
                  "processor\t: 1\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n")
     assert "implementer 0x41 part 0xd4f" in bench.host_cpu(str(f))
     assert "logical cores" in bench.host_cpu(str(tmp_path / "missing"))
+
+
+def test_clock_summary_reports_median_and_throttle_reasons():
+    import bench
+
+    c = bench.Clocks(0)
+    assert c.summary()["reasons"] == ["unsampled"]
+    row = "0, {sm}, 2070, 900.5, 0x0000000000000004, Not Active, Not Active, Not Active, {cap}"
+    c.rows = [[x.strip() for x in row.format(sm=s, cap=cap).split(",")]
+              for s, cap in ((2070, "Not Active"), (1965, "Active"), (2070, "Not Active"))]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.rows[0][5] = "Active"  # a hardware slowdown in one sample is reported
+    assert bench.Clocks.summary(c)["reasons"] == ["hw_slowdown", "sw_power_cap"]
