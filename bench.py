@@ -65,13 +65,17 @@ PREC_NAMES = {"f32": 1, "f16n": 2, "bf16n": 3}
 SOLVERS = {"cg": 1, "bicgstab": 2}  # qxd_solver: MP_CG_EO, MP_BICGSTAB_EO
 
 
-def measured_peaks():
+def measured_peaks(path=None):
+    """(HBM GB/s denominator, "measured" | "fallback"): the machine's measured copy bandwidth, else
+    the 6.8 TB/s fallback of an earlier GB300 measurement."""
     try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            p = json.load(f)
-        return p.get("hbm_gbs", 6800.0), "measured"
-    except OSError:
-        return 6800.0, "fallback"
+        with open(path or os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = json.load(f).get("hbm_gbs")
+        if isinstance(v, (int, float)) and v > 0:
+            return float(v), "measured"
+    except (OSError, ValueError, AttributeError):
+        pass
+    return 6800.0, "fallback"
 
 
 HOP_SOURCES = ("dslash.cu", "hop_site.cuh", "hop_common.cuh", "qxd_internal.cuh")

@@ -71,3 +71,15 @@ def test_clock_summary_reports_median_and_throttle_reasons():
     assert s["reasons"] == ["sw_power_cap"]
     c.rows[0][5] = "Active"  # a hardware slowdown in one sample is reported
     assert bench.Clocks.summary(c)["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_measured_peaks_reads_the_copy_bandwidth_or_falls_back(tmp_path):
+    import bench
+
+    f = tmp_path / "peaks.json"
+    f.write_text('{"hbm_gbs": 6785.9, "bf16_tflops": 1901.2}')
+    assert bench.measured_peaks(str(f)) == (6785.9, "measured")
+    for bad in ('{"bf16_tflops": 1901.2}', "not json", '[1, 2]', '{"hbm_gbs": -1}'):
+        f.write_text(bad)
+        assert bench.measured_peaks(str(f)) == (6800.0, "fallback"), bad
+    assert bench.measured_peaks(str(tmp_path / "missing.json")) == (6800.0, "fallback")
