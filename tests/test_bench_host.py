@@ -1,5 +1,6 @@
 """bench.py host logic on CPU: the DRAM-traffic record is used only for the kernel, lattice and
-hop sources it was captured with."""
+hop sources it was captured with; the host and clock records, the peaks lookup, the GFLOP/s
+convention and the warm-up floor."""
 import os
 import sys
 
@@ -83,3 +84,11 @@ def test_measured_peaks_reads_the_copy_bandwidth_or_falls_back(tmp_path):
         f.write_text(bad)
         assert bench.measured_peaks(str(f)) == (6800.0, "fallback"), bad
     assert bench.measured_peaks(str(tmp_path / "missing.json")) == (6800.0, "fallback")
+
+
+def test_bench_rejects_fewer_than_three_warmup_steps():
+    import subprocess
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--warmup", "2"], capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode != 0 and "--warmup must be >= 3" in r.stderr
