@@ -4,13 +4,14 @@
 // The lattice is cut into non-overlapping blocks of extents b_mu, with a block grid
 // n_mu = L_mu / b_mu that is even in every direction (with C*, the mirror shift L1 is an even
 // number of x blocks too).  So blocks of one colour (the parity of the block coordinates) never
-// touch, and no block wraps around the lattice.  One cycle
-// sweeps colour 0 and then colour 1.  Each block of the colour runs nmr minimal-residual steps
-// on its Dirichlet block operator D_Lambda (D with the hops that leave the block dropped)
-// for the current residual, and adds the result to x.  Blocks of one colour are independent,
-// so a sweep is one launch with one CTA per block, and the residual r = eta - D x is
-// recomputed after the sweep.  That equals updating r block by block, because a block's
-// correction changes r only on the block and on neighbouring blocks of the other colour.
+// touch, and no block wraps around the lattice.
+//
+// One cycle sweeps colour 0 and then colour 1.  Each block of the colour runs nmr
+// minimal-residual steps on its Dirichlet block operator D_Lambda (D with the hops that leave
+// the block dropped) for the current residual, and adds the result to x.  Blocks of one colour
+// are independent, so a sweep is one launch with one CTA per block, and the residual
+// r = eta - D x is recomputed after the sweep.  That equals updating r block by block, because a
+// block's correction changes r only on the block and on neighbouring blocks of the other colour.
 //
 // Kernel: one thread per block site (block volume <= 256).  The block residual lives in
 // shared memory, where the neighbours' hops read it.  Links and the clover come from the FP32
@@ -32,7 +33,7 @@ struct SapGeom {
   int nblocks;    // blocks of both colours
 };
 
-qxd_status sap_geometry(qxd_lattice* lat, const int b[4], SapGeom* sg) {
+static qxd_status sap_geometry(qxd_lattice* lat, const int b[4], SapGeom* sg) {
   const Geom& g = lat->g;
   sg->vb = 1;
   sg->nblocks = 1;
