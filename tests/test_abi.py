@@ -91,3 +91,14 @@ def test_train_params_layout_and_binding_checks(qxd):
     with pytest.raises(ValueError):
         qxd.train_precond(None, [1] * 10, nsamp=1, sample_seed=0)
     assert qxd.lib.qxd_train_precond(None, None, None) == qxd.EINVAL
+
+
+def test_without_a_gpu_calls_fail_with_a_status_not_an_abort(qxd):
+    """Every entry point returns a status: on a machine without a usable GPU, creating a lattice
+    reports QXD_ECUDA with the CUDA message instead of aborting the process."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(qxd.QxdError) as e:
+        qxd.create_lattice((4, 4, 4, 4))
+    assert e.value.status == qxd.ECUDA and "cuda" in qxd.last_error(None).lower()
