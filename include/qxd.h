@@ -267,6 +267,7 @@ qxd_status qxd_sap_apply(qxd_lattice *lat, double *out, const double *in, const 
 
 /* Fused BLAS-1 on device vectors of n complex numbers (interleaved re, im), on the lattice's
  * stream, FP64.  Reductions are deterministic (fixed order) and return to host memory.
+ * Vectors must be device (or managed) memory aligned to 16 bytes, else QXD_EINVAL.
  * n = 0 is allowed (pointers may then be NULL): dot and norm2 give 0, axpy does nothing.
  *   dot:   *re + i *im = sum_k conj(a_k) b_k
  *   norm2: *out = sum_k |a_k|^2
@@ -342,22 +343,23 @@ qxd_status qxd_net_save(const qxd_net *net, const char *path);
 qxd_status qxd_net_load(qxd_lattice *lat, const char *path, qxd_net **out);
 
 /* Dot product for callers that cannot allocate device memory.  The paper has no counterpart:
- * this entry point exists for callers that must not call cudaMalloc -- code running while a
- * stream is being captured into a CUDA graph, code inside a framework whose device memory
- * belongs to its own caching allocator, and latency-critical loops that cannot afford the
- * device synchronisation an allocation can cause.
+ * this entry point exists for callers that must not call cudaMalloc -- code inside a framework
+ * whose device memory belongs to its own caching allocator, and latency-critical loops that
+ * cannot afford the device synchronisation an allocation can cause.
  *   out[0] + i out[1] = sum_k conj(a_k) b_k over n complex numbers (FP64, interleaved re, im).
  * a, b: device vectors; out: DEVICE memory for 2 doubles; cuda_stream: stream to run on (NULL =
  * legacy default stream).  No lattice is needed and the call returns without synchronising.
  * Scratch: a static device array inside the library (64 KiB of per-block partial sums plus a
  * counter), which every GPU that loads the library keeps until process exit.  Limit: n <=
  * QXD_NOALLOC_MAX_N; larger n returns QXD_EINVAL.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress), so make that first call before any stream
- * capture begins.  All calls share the one array: calls that overlap on the GPU (e.g. on two
+ * array's device address (cudaGetSymbolAddress) and keeps it for the life of the process; after
+ * a cudaDeviceReset on that device the kept address is stale, so do not call this entry point
+ * on a device that was reset.  All calls share the one array: calls that overlap on the GPU (e.g. on two
  * streams at once) race and give wrong results; serialise them.  The result is deterministic
  * for a given n (fixed blocking) and agrees with qxd_vec_dot to rounding.  Allocates nothing
- * and calls no allocating routine.  Errors: QXD_EINVAL for n < 0, n > QXD_NOALLOC_MAX_N or a
- * null pointer (a and b may be NULL when n = 0); QXD_ECUDA if a CUDA call fails; the message
+ * and calls no allocating routine.  Errors: QXD_EINVAL for n < 0, n > QXD_NOALLOC_MAX_N, a
+ * null pointer (a and b may be NULL when n = 0), a pointer that is not device (or managed)
+ * memory, a or b not 16-byte aligned, or out not 8-byte aligned; QXD_ECUDA if a CUDA call fails; the message
  * is in qxd_last_error(NULL). */
 #define QXD_NOALLOC_MAX_N 16777216
 qxd_status qxd_vec_dot_noalloc(const double *a, const double *b, int64_t n, double *out,

@@ -305,6 +305,33 @@ def D_at_sites(lat, U, A, q, m0, csw, csw_qed, psi, sites):
     return Cpsi - 0.5 * hop_at(lat, hop_links(U, A, q), psi, sites)
 
 
+def Dhat_at_sites(lat, U, A, q, m0, csw, csw_qed, psi, sites, dagger=False):
+    """(Dhat psi_e)(x) for even sites x in `sites`: D_ee psi - D_eo D_oo^-1 D_oe psi at x only.
+
+    psi is a full-length field whose odd sites are ignored (only psi_e enters).  The Schur
+    complement of the even-odd split, evaluated as its definition reads: D_oe psi_e = -1/2 H
+    psi_e at the odd neighbours y of the sampled x, then D_oo^-1 = A_oo^-1 (the 12x12 clover
+    matrix inverted at each y), then D_ee psi_e - D_eo t = A(x) psi(x) + 1/2 (H t)(x), where t
+    lives on those odd neighbours only (H at x reads nothing else).  dagger: gamma5 Dhat gamma5.
+    """
+    x = np.asarray(sites)
+    if np.any(lat.par[x] != 0):
+        raise ValueError("Dhat_at_sites takes even sites")
+    pe = np.where((lat.par == 0)[:, None, None], psi, 0)
+    if dagger:
+        pe = g5(pe)
+    W = hop_links(U, A, q)
+    ys = np.unique(np.concatenate([lat.neighbour(mu, s)[0][x] for mu in range(4) for s in (+1, -1)]))
+    Doe = -0.5 * hop_at(lat, W, pe, ys)                                    # (D_oe psi_e)(y)
+    Cy = clover_matrix(lat, U, A, q, m0, csw, csw_qed, sites=ys)
+    t = np.zeros_like(pe)
+    t[ys] = np.linalg.solve(Cy, Doe.reshape(-1, 12)[..., None])[..., 0].reshape(-1, 4, 3)
+    Cx = clover_matrix(lat, U, A, q, m0, csw, csw_qed, sites=x)
+    Dee = np.einsum("xij,xj->xi", Cx, pe[x].reshape(-1, 12)).reshape(-1, 4, 3)
+    out = Dee - (-0.5 * hop_at(lat, W, t, x))                              # D_ee psi_e - D_eo t
+    return g5(out) if dagger else out
+
+
 class Operator:
     """The Wilson-clover operator D on a given lattice, gauge field and parameters."""
 

@@ -37,6 +37,20 @@ qxd_status cuda_fail(qxd_lattice* lat, cudaError_t e, const char* where) {
   return fail(lat, e == cudaErrorMemoryAllocation ? QXD_ENOMEM : QXD_ECUDA, m);
 }
 
+qxd_status check_device_vector(qxd_lattice* lat, const void* p, size_t align, const char* what) {
+  if ((uintptr_t)p % align != 0)
+    return fail(lat, QXD_EINVAL, std::string(what) + ": pointer not aligned to " + std::to_string(align) + " bytes");
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // the failed query records a (non-sticky) error: clear it
+    return fail(lat, QXD_EINVAL, std::string(what) + ": not a CUDA pointer");
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(lat, QXD_EINVAL, std::string(what) + ": not device memory");
+  return QXD_OK;
+}
+
 // Guard words: every lattice field and work buffer is allocated GUARD_BYTES longer, and that
 // tail is filled with GUARD_FILL.  qxd_check_guards counts tail bytes that changed, so a kernel
 // writing past the end of a buffer shows up in the tests without a memory checker.  The guard
@@ -649,6 +663,8 @@ qxd_status qxd_vec_dot(qxd_lattice* lat, const double* a, const double* b, int64
     *re = *im = 0.0;
     return QXD_OK;
   }
+  TRY(check_device_vector(lat, a, 16, "qxd_vec_dot: a"));
+  TRY(check_device_vector(lat, b, 16, "qxd_vec_dot: b"));
   TRY(blas_dot_64(lat, (const double2*)a, (const double2*)b, n, SC_TMP2));
   double v[2];
   TRY(read_scalars(lat, SC_TMP2, 2, v));
@@ -665,6 +681,7 @@ qxd_status qxd_vec_norm2(qxd_lattice* lat, const double* a, int64_t n, double* o
     *out = 0.0;
     return QXD_OK;
   }
+  TRY(check_device_vector(lat, a, 16, "qxd_vec_norm2: a"));
   TRY(blas_norm2_64(lat, (const double2*)a, n, SC_TMP1));
   return read_scalars(lat, SC_TMP1, 1, out);
 }
@@ -674,6 +691,8 @@ qxd_status qxd_vec_axpy(qxd_lattice* lat, double re, double im, const double* x,
   CHECK_LAT(lat);
   if (n < 0 || (n > 0 && (!x || !y))) return fail(lat, QXD_EINVAL, "bad argument");
   if (n == 0) return QXD_OK;
+  TRY(check_device_vector(lat, x, 16, "qxd_vec_axpy: x"));
+  TRY(check_device_vector(lat, y, 16, "qxd_vec_axpy: y"));
   return blas_axpy_64(lat, re, im, (const double2*)x, (double2*)y, n);
 }
 

@@ -285,7 +285,10 @@ qxd_status fgcr32(qxd_lattice* lat, qxd_net* net, const SapSpec* sap, int m, int
       QXD_CUDA(lat, cudaMemcpyAsync(lat->hscal, &sc->rn2, sizeof(double), cudaMemcpyDeviceToHost, S));
       QXD_CUDA(lat, cudaStreamSynchronize(S));
       rn2 = lat->hscal[0];
-      if (!std::isfinite(rn2)) return fail(lat, QXD_ENOCONV, "non-finite residual in FGCR");
+      if (!std::isfinite(rn2)) {  // y keeps the cycles completed before this one
+        *iters = it;
+        return fail(lat, QXD_ENOCONV, "non-finite residual in FGCR");
+      }
       done = !(std::sqrt(rn2) > target);
     }
     if (k == m || done || it >= maxiter) {  // end of the cycle: y += Z (I + C)^-1 alpha

@@ -1,12 +1,11 @@
 // qxd_vec_dot_noalloc: the deterministic FP64 dot product for callers that cannot allocate
 // device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being captured into a
-// CUDA graph (allocation is not permitted during global-mode capture), code running inside a
-// framework whose device memory is owned by a caching allocator it must not bypass, and
-// latency-critical loops that cannot afford the implicit device synchronisation cudaMalloc and
-// cudaFree can cause.  Such a caller already owns its input vectors and a 2-double output
-// slot; this entry point needs nothing else.
+// Some callers cannot call cudaMalloc: code running inside a framework whose device memory is
+// owned by a caching allocator it must not bypass, and latency-critical loops that cannot
+// afford the implicit device synchronisation cudaMalloc and cudaFree can cause.  Such a caller
+// already owns its input vectors and a 2-double output slot; this entry point needs nothing
+// else.
 //
 // The kernel is the two-level reduction of qxd_vec_dot (block partial sums, the last block to
 // finish sums the partials in block order), scheduled in fixed chunks of CHUNK entries per
@@ -126,6 +125,12 @@ extern "C" qxd_status qxd_vec_dot_noalloc(const double* a, const double* b, int6
     return qxd::fail(nullptr, QXD_EINVAL,
                      "qxd_vec_dot_noalloc: n exceeds the static scratch capacity of 16777216 complex entries");
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the kernel reads a and b as 16-byte complex words and writes out as doubles: refuse host
+  // pointers and misaligned views here rather than fault on the GPU
+  qxd_status c = qxd::check_device_vector(nullptr, out, 8, "qxd_vec_dot_noalloc: out");
+  if (c == QXD_OK && n > 0) c = qxd::check_device_vector(nullptr, a, 16, "qxd_vec_dot_noalloc: a");
+  if (c == QXD_OK && n > 0) c = qxd::check_device_vector(nullptr, b, 16, "qxd_vec_dot_noalloc: b");
+  if (c != QXD_OK) return c;
   if (n == 0) {
     cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), st);
     return e == cudaSuccess ? QXD_OK : qxd::cuda_fail(nullptr, e, "cudaMemsetAsync(out)");

@@ -684,6 +684,12 @@ qxd_status cuda_fail(qxd_lattice* lat, cudaError_t e, const char* where);
     (lat)->launches++;                                             \
   } while (0)
 
+// A vector argument that kernels read or write directly: it must be memory the current device
+// can address (device or managed memory, not a plain host pointer) and start on an `align`-byte
+// boundary (kernels move it in 8- or 16-byte words).  QXD_EINVAL otherwise, so that a host
+// array or an offset view is refused on the host instead of faulting on the GPU.
+qxd_status check_device_vector(qxd_lattice* lat, const void* p, size_t align, const char* what);
+
 qxd_status ensure_work(qxd_lattice* lat, int slot, size_t bytes, void** out);
 qxd_status ensure_stage(qxd_lattice* lat, size_t bytes);
 

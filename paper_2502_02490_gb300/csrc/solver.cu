@@ -51,6 +51,7 @@ enum {
   // slots 24..27 belong to the API; BiCGStab's extra vectors reuse the CG ones (RR32 = r_hat,
   // Q32 = v, TO32 = t, S32 = s, X32 = x, P32 = p) plus this one:
   WS_R32B = 28, // BiCGStab residual r
+  WS_XB64 = 45, // FP64 copy of x, kept while a failed inner round's progress is tried
 };
 
 #define TRY(x)                      \
@@ -181,7 +182,10 @@ static qxd_status cgls64(qxd_lattice* lat, const double2* bh, double2* xe, doubl
     ++it;
     if (it % check_every == 0) {
       TRY(read_scalars(lat, SC_SS, 1, &ss));
-      if (!std::isfinite(ss)) return fail(lat, QXD_ENOCONV, "non-finite residual in the FP64 CG");
+      if (!std::isfinite(ss)) {
+        *iters = it;
+        return fail(lat, QXD_ENOCONV, "non-finite residual in the FP64 CG");
+      }
     }
   }
   *iters = it;
@@ -249,7 +253,11 @@ static qxd_status inner_mp(qxd_lattice* lat, int prec, const float4* bh, float4*
     ++it;
     if (it % check_every == 0) {
       TRY(read_scalars(lat, SC_SS, 1, &ss));
-      if (!std::isfinite(ss)) return fail(lat, QXD_ENOCONV, "non-finite residual in the inner CG");
+      if (!std::isfinite(ss)) {  // y keeps what the reliable updates folded in; x is dropped
+        *iters = it;
+        *nrel = rel;
+        return fail(lat, QXD_ENOCONV, "non-finite residual in the inner CG");
+      }
       double sn = std::sqrt(ss);
       if (sn > rmax) rmax = sn;
       if (sn < delta * rmax || sn <= target) {
@@ -341,7 +349,11 @@ static qxd_status inner_bicg(qxd_lattice* lat, int prec, const float4* bh, float
     if (it % check_every == 0) {
       TRY(read_scalars(lat, SC_RN, 1, &rn2));
       const bool broke = !std::isfinite(rn2);  // breakdown (e.g. <r_hat, v> = 0): drop x, restart
-      if (broke && ++breakdowns > 10) return fail(lat, QXD_ENOCONV, "repeated breakdown in the inner BiCGStab");
+      if (broke && ++breakdowns > 10) {  // y keeps what the reliable updates folded in
+        *iters = it;
+        *nrel = rel;
+        return fail(lat, QXD_ENOCONV, "repeated breakdown in the inner BiCGStab");
+      }
       double rn = broke ? 0.0 : std::sqrt(rn2);
       if (rn > rmax) rmax = rn;
       if (broke || rn < delta * rmax || rn <= target) {
@@ -372,7 +384,8 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
                              qxd_solve_info* info);
 
 // A failed solve leaves x usable as a starting point when its true residual is finite and below
-// that of x = 0.
+// that of x = 0.  solve_impl reports NaN until it has computed the residual of the x it returns,
+// so a residual that was never computed is never trusted.
 static bool usable_iterate(const qxd_solve_info& i) { return std::isfinite(i.true_rel_res) && i.true_rel_res < 1.0; }
 
 // Recovery chain after a missed tolerance (stagnation, breakdown, an expired wait): first the
@@ -381,8 +394,7 @@ static bool usable_iterate(const qxd_solve_info& i) { return std::isfinite(i.tru
 qxd_status solve(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve_params* prm, qxd_solve_info* info) {
   auto t0 = std::chrono::steady_clock::now();
   qxd_solve_info own;
-  std::memset(&own, 0, sizeof(own));
-  qxd_solve_info* inf = info ? info : &own;
+  qxd_solve_info* inf = info ? info : &own;  // solve_impl fills every field
   qxd_status st = solve_impl(lat, x, b, prm, inf);
   if (st != QXD_OK && inf->status == QXD_OK) inf->status = st;  // early failure: record it
   auto recoverable = [](qxd_status s) { return s == QXD_ENOCONV || s == QXD_ETIMEOUT; };
@@ -426,6 +438,13 @@ qxd_status solve(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve
 static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, const qxd_solve_params* prm,
                              qxd_solve_info* info) {
   auto t0 = std::chrono::steady_clock::now();
+  if (info) {
+    // until a residual is computed for x, none is reported: an early error leaves NaN, which the
+    // recovery chain reads as "x unusable"
+    std::memset(info, 0, sizeof(*info));
+    info->true_rel_res = std::nan("");
+    info->status = QXD_ENOCONV;
+  }
   const i64 sv = lat->sv, nh = 12 * sv, nf = 24 * sv;
   const size_t fb = sizeof(double2) * nf, hb = sizeof(double2) * nh;
   double2 *r, *tf, *bh, *xe, *to;
@@ -453,32 +472,41 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
   int total = 0, outer = 0, nrel_total = 0;
   double rel = 1.0;
   qxd_status result = QXD_ENOCONV;
+  const char* why = "tolerance not reached within maxiter / max_outer";
   if (bnorm == 0.0) {
     rel = 0.0;
     result = QXD_OK;
   }
-  const int max_outer = prm->max_outer > 0 ? prm->max_outer : 20;
-  for (; result != QXD_OK && outer <= max_outer; ++outer) {
-    // r = b - D x (FP64)
-    if (outer == 0 && !from_x0) {
-      TRY(blas_copy(lat, r, b, fb));
-    } else {
-      TRY(apply_D64(lat, x, tf));
-      TRY(blas_copy(lat, r, b, fb));
-      TRY(blas_axpy_64(lat, -1.0, 0.0, tf, r, nf));
-    }
+  auto fill_info = [&](double res, int status) {
+    if (!info) return;
+    info->iters_inner = total;
+    info->iters_outer = outer;
+    info->reliable_updates = nrel_total;
+    info->true_rel_res = res;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->status = status;
+  };
+  // r = b - D x and its relative norm (FP64)
+  auto true_residual = [&](double* out_rel) -> qxd_status {
+    TRY(apply_D64(lat, x, tf));
+    TRY(blas_copy(lat, r, b, fb));
+    TRY(blas_axpy_64(lat, -1.0, 0.0, tf, r, nf));
     double rn2;
     TRY(blas_norm2_64(lat, r, nf, SC_TMP0));
     TRY(read_scalars(lat, SC_TMP0, 1, &rn2));
-    rel = std::sqrt(rn2) / bnorm;
+    *out_rel = std::sqrt(rn2) / bnorm;
+    return QXD_OK;
+  };
+  const int max_outer = prm->max_outer > 0 ? prm->max_outer : 20;
+  for (; result != QXD_OK && outer <= max_outer; ++outer) {
+    if (outer == 0 && !from_x0) {
+      TRY(blas_copy(lat, r, b, fb));
+      rel = 1.0;
+    } else {
+      TRY(true_residual(&rel));
+    }
     if (!std::isfinite(rel)) {
-      if (info) {
-        info->iters_inner = total;
-        info->iters_outer = outer;
-        info->reliable_updates = nrel_total;
-        info->true_rel_res = rel;
-        info->status = QXD_ENOCONV;
-      }
+      fill_info(rel, QXD_ENOCONV);
       return fail(lat, QXD_ENOCONV, "non-finite residual");
     }
     if (rel <= prm->tol) {
@@ -486,7 +514,12 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
       break;
     }
     if (outer == max_outer || total >= prm->maxiter) break;
-    int it = 0;
+    const double rnorm = rel * bnorm;
+    int it = 0, nrel = 0;
+    // status of the inner solve: QXD_ENOCONV means it gave up early (breakdown, non-finite
+    // residual) after `it` iterations; any other failure is returned as it is
+    qxd_status ist = QXD_OK;
+    auto inner_status = [&](qxd_status s) -> bool { ist = s; return s == QXD_OK || s == QXD_ENOCONV; };
     const double target = 0.5 * prm->tol * bnorm;
     if (gcr) {
       // the correction D e = r on the full lattice by FGCR with the network or SAP, FP32
@@ -495,7 +528,7 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
       TRY(get(lat, WS_BH32, sizeof(float4) * 12 * sv, &e32));
       TRY(f64_to_f32(lat, r, r32f, 12 * sv));
       TRY(blas_zero(lat, e32, sizeof(float4) * 12 * sv));
-      double inner_target = prm->inner_tol * std::sqrt(rn2);
+      double inner_target = prm->inner_tol * rnorm;
       if (inner_target < target) inner_target = target;
       SapSpec sp;
       const bool with_sap = prm->solver == QXD_SOLVER_MP_SAP_GCR;
@@ -504,50 +537,69 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
         sp.ncy = prm->sap_ncy;
         sp.nmr = prm->sap_nmr;
       }
-      TRY(fgcr32(lat, with_sap ? nullptr : const_cast<qxd_net*>(prm->net), with_sap ? &sp : nullptr, prm->gcr_restart,
-                 prm->gcr_reorth, r32f, e32, inner_target, prm->maxiter - total, prm->check_every, &it));
+      if (!inner_status(fgcr32(lat, with_sap ? nullptr : const_cast<qxd_net*>(prm->net), with_sap ? &sp : nullptr,
+                               prm->gcr_restart, prm->gcr_reorth, r32f, e32, inner_target, prm->maxiter - total,
+                               prm->check_every, &it)))
+        return ist;
+      if (ist != QXD_OK) TRY(blas_copy(lat, tf, x, fb));
       TRY(blas_acc_f32_into_f64(lat, e32, x, 12 * sv));
     } else if (!mp) {
       // Schur source bh = r_e + 1/2 H_eo A_oo^-1 r_o, CG, reconstruct x_o += A_oo^-1 (r_o + 1/2 H_oe xe)
       TRY(clover_apply64(lat, 1, 1, r + nh, to));
       TRY(hop64(lat, 0, EPI_XPAY, 0, to, r, bh, 0.5));
-      TRY(cgls64(lat, bh, xe, target, prm->maxiter - total, prm->check_every > 0 ? prm->check_every : 1, &it));
+      if (!inner_status(cgls64(lat, bh, xe, target, prm->maxiter - total,
+                               prm->check_every > 0 ? prm->check_every : 1, &it)))
+        return ist;
+      if (ist != QXD_OK) TRY(blas_copy(lat, tf, x, fb));
       TRY(hop64(lat, 1, EPI_INVXPAY, 0, xe, r + nh, to, 0.5));
       TRY(blas_axpy_64(lat, 1.0, 0.0, xe, x, nh));
       TRY(blas_axpy_64(lat, 1.0, 0.0, to, x + nh, nh));
     } else {
       // the correction equation D e = r only needs the inner accuracy, so its Schur source and
       // reconstruction run in FP32; x accumulates in FP64
-      int nrel = 0;
       TRY(f64_to_f32(lat, r, r32, 12 * sv));
       TRY(clover_apply32(lat, 1, 1, r32 + 6 * sv, to32));
       TRY(hop32(lat, 0, EPI_XPAY, 0, to32, r32, bh32, 0.5f));
       TRY(blas_zero(lat, y32, sizeof(float4) * 6 * sv));
-      double inner_target = prm->inner_tol * std::sqrt(rn2);
+      double inner_target = prm->inner_tol * rnorm;
       if (inner_target < target) inner_target = target;
-      if (prm->solver == QXD_SOLVER_MP_BICGSTAB_EO)
-        TRY(inner_bicg(lat, prm->inner_prec, bh32, y32, inner_target, prm->reliable_delta, prm->maxiter - total,
-                       prm->check_every > 0 ? prm->check_every : 1, &it, &nrel));
-      else
-        TRY(inner_mp(lat, prm->inner_prec, bh32, y32, inner_target, prm->reliable_delta, prm->maxiter - total,
-                     prm->check_every > 0 ? prm->check_every : 1, &it, &nrel));
+      const int every = prm->check_every > 0 ? prm->check_every : 1;
+      const bool ok =
+          prm->solver == QXD_SOLVER_MP_BICGSTAB_EO
+              ? inner_status(inner_bicg(lat, prm->inner_prec, bh32, y32, inner_target, prm->reliable_delta,
+                                        prm->maxiter - total, every, &it, &nrel))
+              : inner_status(inner_mp(lat, prm->inner_prec, bh32, y32, inner_target, prm->reliable_delta,
+                                      prm->maxiter - total, every, &it, &nrel));
+      if (!ok) return ist;
+      if (ist != QXD_OK) TRY(blas_copy(lat, tf, x, fb));
       TRY(hop32(lat, 1, EPI_INVXPAY, 0, y32, r32 + 6 * sv, to32, 0.5f));
       TRY(blas_acc_f32_into_f64(lat, y32, x, 6 * sv));
       TRY(blas_acc_f32_into_f64(lat, to32, x + nh, 6 * sv));
-      nrel_total += nrel;
     }
     total += it;
+    nrel_total += nrel;
+    if (ist != QXD_OK) {
+      // The inner solve gave up early.  Keep what it folded in if that lowers the true
+      // residual, else return to the x of this round (saved in tf, copied to XB64 first since
+      // the residual below overwrites tf); either way true_rel_res is that of the x returned.
+      double2* xb;
+      TRY(get(lat, WS_XB64, fb, &xb));
+      TRY(blas_copy(lat, xb, tf, fb));
+      double rel_new;
+      TRY(true_residual(&rel_new));
+      if (std::isfinite(rel_new) && rel_new < rel) {
+        rel = rel_new;
+      } else {
+        TRY(blas_copy(lat, x, xb, fb));
+      }
+      why = "the inner solver gave up (breakdown or non-finite residual)";
+      ++outer;
+      break;
+    }
   }
   QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
-  if (info) {
-    info->iters_inner = total;
-    info->iters_outer = outer;
-    info->reliable_updates = nrel_total;
-    info->true_rel_res = rel;
-    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    info->status = result;
-  }
-  if (result != QXD_OK) return fail(lat, QXD_ENOCONV, "tolerance not reached within maxiter / max_outer");
+  fill_info(rel, result);
+  if (result != QXD_OK) return fail(lat, QXD_ENOCONV, why);
   return QXD_OK;
 }
 

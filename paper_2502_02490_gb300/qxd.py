@@ -232,27 +232,40 @@ def solve_mrhs(lat, x, b, nrhs, params=None, check=True, **kw):
 
 def vec_dot(lat, a, b, n):
     re, im = C.c_double(), C.c_double()
-    _check(lib.qxd_vec_dot(lat, _ptr(a)[0], _ptr(b)[0], int(n), C.byref(re), C.byref(im)), lat)
+    _check(lib.qxd_vec_dot(lat, _device_ptr(a, "a"), _device_ptr(b, "b"), int(n), C.byref(re), C.byref(im)), lat)
     return complex(re.value, im.value)
 
 
 def vec_norm2(lat, a, n):
     out = C.c_double()
-    _check(lib.qxd_vec_norm2(lat, _ptr(a)[0], int(n), C.byref(out)), lat)
+    _check(lib.qxd_vec_norm2(lat, _device_ptr(a, "a"), int(n), C.byref(out)), lat)
     return out.value
 
 
 def vec_axpy(lat, alpha, x, y, n):
-    _check(lib.qxd_vec_axpy(lat, float(np.real(alpha)), float(np.imag(alpha)), _ptr(x)[0], _ptr(y)[0], int(n)), lat)
+    _check(lib.qxd_vec_axpy(lat, float(np.real(alpha)), float(np.imag(alpha)), _device_ptr(x, "x"),
+                            _device_ptr(y, "y"), int(n)), lat)
 
 
 NOALLOC_MAX_N = 16777216
 
 
+def _device_ptr(t, what):
+    """Address of a CUDA tensor (None passes through); anything in host memory is refused."""
+    if t is None:
+        return None
+    p, dev = _ptr(t)
+    if not dev:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    return p
+
+
 def vec_dot_noalloc(a, b, n, out, stream=None):
     """qxd_vec_dot_noalloc: <a, b> of n complex entries into the 2 doubles of device memory `out`,
-    with scratch in a static device array (no allocation).  stream: a cudaStream_t address or None."""
-    _check(lib.qxd_vec_dot_noalloc(_ptr(a)[0], _ptr(b)[0], int(n), _ptr(out)[0], stream))
+    with scratch in a static device array (no allocation).  stream: a cudaStream_t address or None.
+    a, b and out must be CUDA tensors; the library also refuses misaligned addresses."""
+    _check(lib.qxd_vec_dot_noalloc(_device_ptr(a, "a"), _device_ptr(b, "b"), int(n), _device_ptr(out, "out"),
+                                   stream))
 
 
 def set_profiling(lat, on):

@@ -77,3 +77,87 @@ def test_fullsize_operator_clover_and_solve(qxd, name):
     # the sampled residual must be consistent with a full residual <= 1e-10 ||eta||
     assert np.sqrt((np.abs(r) ** 2).sum() * lat_o.V / len(sites)) <= 3e-10 * np.linalg.norm(eta)
     print(f"{name}: apply_D rel err {err:.2e}, solve {info}")
+
+
+# unit roundoff of the 16-bit storage formats (round to nearest): FP16 has an 11-bit
+# significand, BF16 an 8-bit one
+UNIT = {"f16n": 2.0 ** -11, "bf16n": 2.0 ** -8}
+C_SITE = 8  # per-site bound: max_i |gpu_i - ref_i| <= C_SITE * u * max_i |ref_i| over one site's 12 entries
+
+
+def _sample_sites(lat_o, n, parity, seed):
+    """n random sites of the given parity (None: any) plus corners that cross the time and C*
+    mirror boundaries (moved by one step in x3 where the corner has the other parity)."""
+    d = lat_o.dims
+    rng = np.random.default_rng(seed)
+    pool = np.arange(lat_o.V) if parity is None else np.flatnonzero(lat_o.par == parity)
+    corners = []
+    for c in [(0, 0, 0, 0), (d[0] - 1, d[1] - 1, d[2] - 1, d[3] - 1), (0, d[1] // 2, d[2] - 1, 0),
+              (d[0] - 1, 0, 0, d[3] - 1), (d[0] - 1, d[1] // 2 - 1, d[2] - 1, 0)]:
+        c = np.array(c)
+        if parity is not None and int(c.sum()) % 2 != parity:
+            c[3] = (c[3] + 1) % d[3]
+        corners.append(O.lexi(c, d))
+    return np.unique(np.concatenate([rng.choice(pool, n, replace=False), corners]))
+
+
+def _site_ratio(got, ref):
+    """Per site: max |got - ref| / max |ref| over the site's 12 complex entries."""
+    e = np.abs(got - ref).reshape(len(ref), -1).max(axis=1)
+    m = np.abs(ref).reshape(len(ref), -1).max(axis=1)
+    return e / m
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_fullsize_16bit_dslash_per_site(qxd, name):
+    """The 16-bit operators the mixed-precision solve runs (D and the Dhat the bench times, in the
+    INV and DHAT2 hop instantiations and the launch configuration of the full-size lattice),
+    site by site against the FP64 oracle at sampled sites."""
+    w = WORKLOADS[name]
+    L = w["L"]
+    lat_o = O.Lattice(L, antiperiodic=True, cstar=w["cstar"])
+    U, A = synth.gauge_field(L, w["gseed"], w["eps"])
+    Uf, Af = (O.cstar_double_gauge(U, A, L) if w["cstar"] else (U, A))
+    eta = synth.gaussian_spinor(lat_o.dims, w["sseed"])
+    sites = _sample_sites(lat_o, 120, None, 0)
+    esites = _sample_sites(lat_o, 120, 0, 1)
+    erank = np.searchsorted(np.flatnonzero(lat_o.par == 0), esites)
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    lat = qxd.create_lattice(L, qxd.BC_ANTIPERIODIC, int(w["cstar"]), qxd.ORDER_LEXI, stream.cuda_stream)
+    got = {}
+    try:
+        qxd.load_gauge(lat, torch.from_numpy(U.view(np.float64)).to(dev), torch.from_numpy(A).to(dev), w["q"])
+        qxd.build_clover(lat, w["m0"], CSW, CQ)
+        x = torch.from_numpy(eta.view(np.float64)).to(dev)
+        y = torch.empty_like(x)
+        st_idx = torch.from_numpy(sites).to(dev)
+        for prec in ("f16n", "bf16n"):
+            qxd.apply_D(lat, y, x, qxd.PREC[prec])
+            got[("D", prec, 0)] = as_c128(y.view(lat_o.V, 24)[st_idx], (len(sites), 4, 3))
+        del y
+        even_idx = torch.from_numpy(np.flatnonzero(lat_o.par == 0)).to(dev)
+        xe = x.view(lat_o.V, 24)[even_idx].contiguous()
+        del x
+        ye = torch.empty_like(xe)
+        er_idx = torch.from_numpy(erank).to(dev)
+        for prec, dag in (("f16n", 0), ("f16n", 1), ("bf16n", 0)):
+            qxd.apply_Dhat_eo(lat, ye, xe, qxd.PREC[prec], dag)
+            got[("Dhat", prec, dag)] = as_c128(ye.view(-1, 24)[er_idx], (len(esites), 4, 3))
+        del xe, ye
+        torch.cuda.synchronize()
+        bad = qxd.check_guards(lat)
+    finally:
+        qxd.destroy_lattice(lat)
+    assert bad == 0, f"{bad} guard bytes overwritten"
+    args = (w["q"], w["m0"], CSW, CQ)
+    ref_D = O.D_at_sites(lat_o, Uf, Af, *args, eta, sites)
+    ref_Dh = {dag: O.Dhat_at_sites(lat_o, Uf, Af, *args, eta, esites, dagger=bool(dag)) for dag in (0, 1)}
+    worst = {}
+    for (op, prec, dag), g in got.items():
+        ref = ref_D if op == "D" else ref_Dh[dag]
+        ratio = _site_ratio(g, ref) / UNIT[prec]
+        worst[(op, prec, dag)] = float(ratio.max())
+        assert ratio.max() <= C_SITE, (op, prec, dag, float(ratio.max()))
+    print(f"{name}: worst per-site error in units of roundoff: " +
+          ", ".join(f"{op}{'^+' if d else ''} {p} {v:.2f}" for (op, p, d), v in worst.items()))

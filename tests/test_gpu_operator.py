@@ -121,6 +121,28 @@ def test_vector_ops(qxd):
         c.close()
 
 
+def test_vector_ops_refuse_host_and_misaligned_pointers(qxd):
+    import ctypes
+
+    c = Case(qxd, torch, (2, 2, 2, 2), build=False)
+    try:
+        t = torch.zeros(2 * 100 + 1, dtype=torch.float64, device="cuda:0")
+        host = np.zeros(200)
+        re, im = ctypes.c_double(), ctypes.c_double()
+        vp = ctypes.c_void_p
+        for pa, pb in [(host.ctypes.data, t.data_ptr()), (t.data_ptr(), t.data_ptr() + 8)]:
+            st = qxd.lib.qxd_vec_dot(vp(c.lat), vp(pa), vp(pb), 100, ctypes.byref(re), ctypes.byref(im))
+            assert st == qxd.EINVAL
+            st = qxd.lib.qxd_vec_axpy(vp(c.lat), 1.0, 0.0, vp(pa), vp(pb), 100)
+            assert st == qxd.EINVAL
+        assert qxd.lib.qxd_vec_norm2(vp(c.lat), vp(t.data_ptr() + 8), 100, ctypes.byref(re)) == qxd.EINVAL
+        with pytest.raises(ValueError):
+            qxd.vec_dot(c.lat, host, host, 100)
+        assert qxd.vec_norm2(c.lat, t[:200], 100) == 0.0
+    finally:
+        c.close()
+
+
 def test_reductions_are_deterministic(qxd):
     c = Case(qxd, torch, (2, 2, 2, 2), build=False)
     try:

@@ -145,3 +145,40 @@ def test_version3_params_are_accepted(qxd):
         assert st == qxd.EINVAL
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("solver,prec", [(s, p) for s in (2, 1) for p in (2, 1)])
+def test_breakdown_exit_fills_the_solve_info(qxd, solver, prec):
+    """An inner solver that gives up early still reports what it did.
+
+    With U = 1, A = 0, m0 = 0, no clover term and periodic time, the constant spinor is a zero
+    mode of D (the free operator at p = 0 is m0).  For a constant source the Schur source is
+    constant too and Dhat maps it to exactly zero, so BiCGStab divides by <r_hat, Dhat p> = 0 at
+    every step and CG on the normal equations by <p, Dhat^+ Dhat p> = 0: every inner solve breaks
+    down.  The solve must return ENOCONV with the iterations it spent, the true residual of the x
+    it returns (judged by the oracle), and a 16-bit solve's FP32 restart must only get the
+    iterations left of maxiter.
+    """
+    c = Case(qxd, torch, (4, 4, 4, 4), anti=False, eps=0.0, m0=0.0, csw=0.0, csw_qed=0.0)
+    try:
+        eta = np.ones((c.V, 4, 3), dtype=np.complex128)
+        b = c.dev_tensor(eta)
+        maxiter = 15
+        for restart in (0, 1):
+            x = torch.empty_like(b)
+            st, info = qxd.solve(c.lat, x, b, check=False, solver=solver, inner_prec=prec, tol=1e-10,
+                                 maxiter=maxiter, check_every=1, fallback=-1, restart_f32=restart)
+            assert st == qxd.ENOCONV and info["status"] == qxd.ENOCONV, info
+            assert info["iters_inner"] > 0, info
+            assert info["iters_inner"] <= maxiter, info
+            xh = as_c128(x, eta.shape)
+            assert np.isfinite(xh).all()
+            ref = O.true_rel_residual(c.op, xh, eta)
+            assert abs(info["true_rel_res"] - ref) <= 1e-12, (info, ref)
+            restarted = restart and prec == qxd.F16N
+            assert bool(info["fallback_used"] & 2) == bool(restarted), info
+            if solver == qxd.SOLVER_MP_BICGSTAB_EO:
+                # BiCGStab gives up after 11 breakdowns; the FP32 restart then gets the 4 left
+                assert info["iters_inner"] == (maxiter if restarted else 11), info
+    finally:
+        c.close()

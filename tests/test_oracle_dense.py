@@ -81,3 +81,29 @@ def test_schur_block_structure_against_dense():
     psi[lat.par == 1] = 0
     got = op.Dhat(psi)[lat.par == 0].ravel()
     assert np.abs(got - Dh @ psi[lat.par == 0].ravel()).max() < 1e-13 * np.abs(got).max()
+
+
+@pytest.mark.parametrize("L,cstar", [((2, 4, 2, 2), False), ((4, 2, 2, 4), False), ((2, 2, 2, 2), True)])
+def test_sampled_site_schur_complement_against_dense(L, cstar):
+    """Dhat_at_sites (and its gamma5 dagger) at sampled even sites equals the dense Schur
+    complement D_ee - D_eo D_oo^-1 D_oe built from the edge-loop matrix; odd entries of the
+    input field are ignored."""
+    lat, op, Dd = build(L, cstar=cstar)
+    U, A = synth.gauge_field(lat.dims, 1000, 0.3)  # the field build() used
+    idx = np.arange(12 * lat.V).reshape(lat.V, 12)
+    e = idx[lat.par == 0].ravel()
+    o = idx[lat.par == 1].ravel()
+    Dh = Dd[np.ix_(e, e)] - Dd[np.ix_(e, o)] @ np.linalg.solve(Dd[np.ix_(o, o)], Dd[np.ix_(o, e)])
+    psi = synth.gaussian_spinor(lat.dims, 6)
+    g5 = np.kron(np.eye(len(e) // 12), np.kron(np.diag([1, 1, -1, -1]), np.eye(3)))
+    even_sites = np.flatnonzero(lat.par == 0)
+    sites = even_sites[np.random.default_rng(1).choice(len(even_sites), 5, replace=False)]
+    rank = np.searchsorted(even_sites, sites)
+    for dagger, M in ((False, Dh), (True, g5 @ Dh @ g5)):
+        ref = (M @ psi[lat.par == 0].ravel()).reshape(-1, 4, 3)[rank]
+        got = O.Dhat_at_sites(lat, U, A, PARAMS["q"], PARAMS["m0"],
+                              PARAMS["csw"], PARAMS["csw_qed"], psi, sites, dagger=dagger)
+        assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max(), dagger
+    with pytest.raises(ValueError):
+        O.Dhat_at_sites(lat, U, A, PARAMS["q"], PARAMS["m0"],
+                        PARAMS["csw"], PARAMS["csw_qed"], psi, np.flatnonzero(lat.par == 1)[:1])

@@ -1,8 +1,8 @@
 """The dot product entry point that allocates no device memory (qxd_vec_dot_noalloc).
 
-It serves callers that cannot call cudaMalloc: code running during CUDA-graph stream capture,
-code whose device memory belongs to a framework's caching allocator, and latency-critical
-loops that cannot afford the synchronisation an allocation may cause.  Its scratch is a static
+It serves callers that cannot call cudaMalloc: code whose device memory belongs to a
+framework's caching allocator, and latency-critical loops that cannot afford the
+synchronisation an allocation may cause.  Its scratch is a static
 array inside the library.  This file is collected last so that a run stopping at the first
 failure has already run every other test.
 """
@@ -42,7 +42,16 @@ def test_noalloc_dot_matches_the_allocating_entry_point_twice(qxd):
                 ref = qxd.vec_dot(lat, ta, tb, n)
                 torch.cuda.synchronize()
                 got = complex(out[0].item(), out[1].item())
-                assert abs(got - ref) < 1e-12 * n, (n, call, got, ref)
+                # FP64 summation error bound: a few units of roundoff times sum |a_k| |b_k|
+                za, zb = a.view(np.complex128), b.view(np.complex128)
+                scale = float(np.sum(np.abs(za) * np.abs(zb)))
+                assert abs(got - np.vdot(za, zb)) <= 1e-13 * scale, (n, call, got)
+                assert abs(got - ref) <= 1e-13 * scale, (n, call, got, ref)
+                # the same inputs again give the same bits (fixed blocking and summation order)
+                out2 = torch.zeros(2, dtype=torch.float64, device=dev)
+                qxd.vec_dot_noalloc(ta, tb, n, out2, stream.cuda_stream)
+                torch.cuda.synchronize()
+                assert torch.equal(out, out2), (n, call)
     finally:
         qxd.destroy_lattice(lat)
 
@@ -56,3 +65,28 @@ def test_noalloc_dot_limits(qxd):
     with pytest.raises(qxd.QxdError) as e:
         qxd.vec_dot_noalloc(out, out, qxd.NOALLOC_MAX_N + 1, out)
     assert e.value.status == qxd.EINVAL and "capacity" in qxd.last_error(None)
+
+
+def test_noalloc_dot_refuses_host_and_misaligned_pointers(qxd):
+    """Pointers the kernel cannot use are refused on the host with QXD_EINVAL, before any launch."""
+    import ctypes
+
+    dev = torch.device("cuda:0")
+    out = torch.zeros(2, dtype=torch.float64, device=dev)
+    t = torch.zeros(2 * 64 + 1, dtype=torch.float64, device=dev)
+    host = np.zeros(2 * 64)
+    cases = [
+        (host.ctypes.data, t.data_ptr(), out.data_ptr()),                 # a in host memory
+        (t.data_ptr(), t.data_ptr() + 8, out.data_ptr()),                 # b only 8-byte aligned
+        (t.data_ptr(), t.data_ptr(), host.ctypes.data),                   # out in host memory
+        (t.data_ptr(), t.data_ptr(), out.data_ptr() + 4),                 # out not 8-byte aligned
+    ]
+    for pa, pb, po in cases:
+        st = qxd.lib.qxd_vec_dot_noalloc(ctypes.c_void_p(pa), ctypes.c_void_p(pb), 64, ctypes.c_void_p(po), None)
+        assert st == qxd.EINVAL, (pa, pb, po)
+    with pytest.raises(ValueError):
+        qxd.vec_dot_noalloc(host, host, 64, out)
+    # the context is intact: a valid call still works
+    qxd.vec_dot_noalloc(t[:128], t[:128], 64, out)
+    torch.cuda.synchronize()
+    assert out.tolist() == [0.0, 0.0]
