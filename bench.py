@@ -62,6 +62,12 @@ WORKLOAD = dict(WORKLOADS["c2"])
 KSTAT = {0: "hop_f64", 1: "hop_f32", 2: "hop_f16n", 3: "hop_bf16n", 4: "hop_f32_mrhs", 5: "batch_f32",
          6: "ptc_layer_bf16_tc", 7: "ptc_layer_f32"}
 PREC_NAMES = {"f32": 1, "f16n": 2, "bf16n": 3}
+FP64_REPEATS = 3
+# Algorithmic bytes of one Dhat application per even site: 2 hops (4 spinors of the precision,
+# 2 x 8 links), A_oo^-1 and A_ee (2 clover blocks pairs), one extra read of psi_e.  16-bit with
+# per-site FP32 norms: 4 x 52 + 2 x 288 + 2 x 148 + 52 = 1132; FP32: 4 x 96 + 2 x 576 + 2 x 288
+# + 96 = 2208; FP64: 4416.
+DHAT_BYTES_PER_EVEN_SITE = {"hop_f16n": 1132, "hop_bf16n": 1132, "hop_f32": 2208, "hop_f64": 4416}
 SOLVERS = {"cg": 1, "bicgstab": 2}  # qxd_solver: MP_CG_EO, MP_BICGSTAB_EO
 
 
@@ -187,7 +193,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     w = WORKLOAD
-    U, A, eta = make_inputs(rank)
+    # rank 0 reuses the inputs the CPU baseline's pool was set up with (the same seeded fields)
+    U, A, eta = (_CPU["U"], _CPU["A"], _CPU["eta"]) if (_CPU and rank == 0) else make_inputs(rank)
     V = eta.shape[0]
     su3_h = torch.from_numpy(U.view(np.float64)).pin_memory()
     a_h = torch.from_numpy(A).pin_memory()
@@ -219,8 +226,7 @@ def run_ours(args, rank, world):
 
     for _ in range(args.warmup):
         info = step()
-    # ---- timed region (device-resident inputs) ----
-    qxd.set_profiling(lat, 1)
+    # ---- timed region (device-resident inputs; library profiling off: the production path) ----
     n0 = qxd.launch_count(lat)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -233,9 +239,15 @@ def run_ours(args, rank, world):
         barrier()
     ms_total = e0.elapsed_time(e1)
     launches = qxd.launch_count(lat) - n0
+    # ---- per-kernel figures in a separate pass: CUDA events around every hop launch ----
+    prof_steps = min(args.steps, 3)
+    qxd.set_profiling(lat, 1)
+    prof_infos = [step() for _ in range(prof_steps)]
     stats = {KSTAT[k]: qxd.kernel_stats(lat, k) for k in KSTAT}
     qxd.set_profiling(lat, 0)
-    hop_bytes = sum(b for (_, _, b) in stats.values())
+    # the solve is deterministic (fixed-order reductions), so every step repeats the same launches
+    same_work = all(i["iters_inner"] == infos[0]["iters_inner"] for i in infos + prof_infos)
+    hop_bytes = sum(b for (_, _, b) in stats.values()) / prof_steps * args.steps
     # ---- end-to-end through host buffers ----
     barrier()
     t0 = time.perf_counter()
@@ -243,18 +255,25 @@ def run_ours(args, rank, world):
         step(host=True)
     barrier()
     e2e_s = time.perf_counter() - t0
-    # ---- plain FP64 eo-CG on the same field and source (the comparison baseline) ----
+    # ---- plain FP64 eo-CG on the same field and source (the comparison baseline): one warm-up
+    # solve, then the median of FP64_REPEATS solves, as for the mixed-precision arm ----
     fp64 = None
     if not args.skip_fp64:
         p64 = qxd.default_params(solver=qxd.SOLVER_CG_EO, tol=1e-10, check_every=args.check_every)
         qxd.load_gauge(lat, su3_d, a_d, w["q"])
         qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
-        barrier()
-        t0 = time.perf_counter()
-        st, info64 = qxd.solve(lat, x_d, b_d, params=p64)
-        barrier()
-        fp64 = {"seconds": info64["seconds"], "wall_s": time.perf_counter() - t0, "iterations": info64["iters_inner"],
-                "true_rel_res": info64["true_rel_res"]}
+        runs = []
+        for k in range(1 + FP64_REPEATS):
+            barrier()
+            t0 = time.perf_counter()
+            st, info64 = qxd.solve(lat, x_d, b_d, params=p64)
+            barrier()
+            if k:
+                runs.append((info64["seconds"], time.perf_counter() - t0, info64))
+        med = sorted(runs, key=lambda r: r[0])[len(runs) // 2]
+        fp64 = {"seconds": med[0], "wall_s": med[1], "iterations": med[2]["iters_inner"],
+                "true_rel_res": med[2]["true_rel_res"], "runs_s": [r[0] for r in runs],
+                "timing": f"median of {FP64_REPEATS} solves after one warm-up solve"}
     qxd.destroy_lattice(lat)
 
     # ---- aggregate over ranks ----
@@ -262,7 +281,14 @@ def run_ours(args, rank, world):
     dom = max(stats, key=lambda k: stats[k][1])
     n_l, ms_l, b_l = stats[dom]
     peak, peak_kind = measured_peaks()
-    achieved = (b_l / n_l) / (ms_l / n_l / 1e3) / 1e9 if n_l else 0.0
+    sites = arm_config(args, world)["sites"]
+    # one Dhat application = two hop launches (A_oo^-1 H and the A_ee - 1/4 H epilogue); its
+    # algorithmic bytes per even site are the minimum the method moves in this precision
+    dhat_bytes = DHAT_BYTES_PER_EVEN_SITE.get(dom)
+    if dhat_bytes and n_l:
+        achieved = dhat_bytes * (sites // 2) / (2 * ms_l / n_l / 1e3) / 1e9
+    else:
+        achieved = (b_l / n_l) / (ms_l / n_l / 1e3) / 1e9 if n_l else 0.0
     tts = t_s / args.steps
     iters = [i["iters_inner"] for i in infos]
     out = {
@@ -289,8 +315,13 @@ def run_ours(args, rank, world):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "traffic": recorded_traffic(dom, w["L"]),
-                     "algorithmic_bytes_per_launch": b_l / n_l if n_l else None,
-                     "launches": n_l, "avg_launch_us": ms_l / n_l * 1e3 if n_l else None},
+                     "bytes_convention": (f"{dhat_bytes} B per even site per Dhat application (two launches)"
+                                          if dhat_bytes else "the kernel's own algorithmic bytes per launch"),
+                     "kernel_bytes_per_launch": b_l / n_l if n_l else None,
+                     "launches": n_l, "avg_launch_us": ms_l / n_l * 1e3 if n_l else None,
+                     "timing": f"CUDA events around every launch of {prof_steps} profiled steps after the "
+                               "timed steps"},
+        "profiled_steps_same_work": same_work,
         "kernels": {k: {"launches": v[0], "ms": v[1], "GB": v[2] / 1e9} for k, v in stats.items() if v[0]},
         "dslash_kernel_GBps": hop_total / sum(v[1] for v in stats.values()) / 1e6 if world == 1 else None,
         "dslash_kernel_GFLOPs": dslash_gflops(dom, n_l, ms_l, arm_config(args, world)["sites"] // 2),
@@ -496,11 +527,17 @@ def tune_m0():
             lo = m0
         else:
             hi = m0
+    # the physical branch in steps of 0.01 on [-0.3, 0]: its slowest point
+    scan = {round(v, 2): iters(round(v, 2)) for v in np.arange(-0.30, 0.001, 0.01)}
+    slow = max(scan, key=scan.get)
     qxd.destroy_lattice(lat)
     with open(C4_M0_FILE, "w") as f:
         f.write(f"# m0 of the 16^3x32 near-critical workload: FP64 eo-CG iterations {n} (bench.py --tune-m0)\n")
+        f.write("# physical-branch scan, m0: eo-CG iterations: " +
+                ", ".join(f"{k:+.2f}: {v}" for k, v in scan.items()) + "\n")
         f.write(f"m0={m0!r}\n")
-    print(json.dumps({"m0": m0, "eo_cg_iterations": n}))
+        f.write(f"m0_physical={slow!r}\n")
+    print(json.dumps({"m0": m0, "eo_cg_iterations": n, "physical_scan": scan, "m0_physical": slow}))
 
 
 def c4_m0(key="m0"):
@@ -675,25 +712,74 @@ def host_cpu(cpuinfo="/proc/cpuinfo"):
     return f"{platform.machine()} {model or platform.processor() or 'cpu'}, {os.cpu_count()} logical cores"
 
 
-def cpu_sample(sample_slices=1):
-    """Time the oracle's D (clover + hop, FP64 numpy) on a bounded sample of the workload's sites:
-    every site of the first `sample_slices` time slices of the 32^3 x 64 lattice."""
+# The oracle's inputs and lattice, set in the parent before the worker pool forks, so that every
+# worker inherits them (copy on write) instead of receiving GB-sized arrays.
+_CPU = {}
+CPU_SAMPLE_SITES = 65536  # two time slices of 32^3x64 per step, split evenly over the workers
+
+
+def cpu_pool_start(nproc=None):
+    """Fork the pool of oracle workers (one per host core).  Called before the first GPU call of
+    the process: a pool forked after CUDA is initialised can hang."""
+    import multiprocessing as mp
+
     from oracle import qxd_oracle as O
 
     w = WORKLOAD
     U, A, eta = make_inputs(0)
     lat = O.Lattice(w["L"], antiperiodic=True)
-    n = sample_slices * (w["L"][1] * w["L"][2] * w["L"][3])
-    sites = np.arange(n)
+    for mu in range(4):
+        for step in (+1, -1):
+            lat.neighbour(mu, step)  # neighbour tables built once, shared by the workers
+    _CPU.update(U=U, A=A, eta=eta, lat=lat)
+    n = int(nproc or os.cpu_count() or 1)
+    return mp.get_context("fork").Pool(n), n
+
+
+def _cpu_worker(chunk):
+    """One worker's share of a step: the oracle's D at sites [lo, hi); its wall and CPU time."""
+    from oracle import qxd_oracle as O
+
+    lo, hi = chunk
+    w = WORKLOAD
     t0, c0 = time.perf_counter(), time.process_time()
-    O.D_at_sites(lat, U, A, w["q"], w["m0"], w["csw"], w["csw_qed"], eta, sites)
-    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
-    # threads actually used: the process's CPU time over the wall time of the sample
+    O.D_at_sites(_CPU["lat"], _CPU["U"], _CPU["A"], w["q"], w["m0"], w["csw"], w["csw_qed"], _CPU["eta"],
+                 np.arange(lo, hi))
+    return time.perf_counter() - t0, time.process_time() - c0
+
+
+def cpu_sample(pool, nworkers):
+    """Time the oracle's D (clover + hop, FP64 numpy) on a bounded sample of the workload's sites,
+    process-parallel over the host cores: CPU_SAMPLE_SITES consecutive sites of the 32^3 x 64
+    lattice, an equal run of them per worker."""
+    per = CPU_SAMPLE_SITES // nworkers
+    chunks = [(k * per, (k + 1) * per) for k in range(nworkers)]
+    n = per * nworkers
+    t0 = time.perf_counter()
+    res = pool.map(_cpu_worker, chunks, chunksize=1)
+    dt = time.perf_counter() - t0
+    cpu = sum(r[1] for r in res)
+    # cores actually used: the workers' CPU time over the wall time of the sample
     return {"value": n * 2112 / dt / 1e9, "unit": "GB/s", "cores": max(1, round(cpu / dt)), "kind": "oracle",
-            "host": host_cpu(),
-            "sample": f"oracle D (clover built at the sites + full-spinor hop) on {n} sites "
-                      f"({sample_slices} time slice(s) of 32^3x64), 2112 B/site FP64 convention, "
-                      f"{dt:.1f} s"}
+            "workers": nworkers, "host": host_cpu(),
+            "sample": f"oracle D (clover built at the sites + full-spinor hop) on {n} sites of 32^3x64 "
+                      f"({nworkers} processes x {per} sites), 2112 B/site FP64 convention, "
+                      f"{dt:.1f} s wall, {cpu:.1f} s CPU"}
+
+
+def cpu_eocg_c1():
+    """The oracle's FP64 even-odd CG to 1e-10 on the 4^4 workload (one process): seconds, iterations."""
+    from oracle import qxd_oracle as O
+    from paper_2502_02490_gb300 import synth
+
+    L = (4, 4, 4, 4)
+    U, A = synth.gauge_field(L, 1000, 0.3)
+    eta = synth.gaussian_spinor(L, 2000)
+    t0 = time.perf_counter()
+    op = O.Operator(O.Lattice(L, antiperiodic=True), U, A, -1 / 3, -0.1, 1.9, 1.0)
+    psi, info = O.solve_eo_cg(op, eta, tol=1e-10)
+    return {"lattice": "4^4 (eps=0.3, q=-1/3, m0=-0.1, c_sw=1.9, c_sw^QED=1.0)", "seconds": time.perf_counter() - t0,
+            "iterations": info["iterations"], "true_rel_res": info["true_rel_residual"], "processes": 1}
 
 
 DSLASH_FLOP_PER_SITE = 1824  # clover dslash: 1320 for the Wilson hop + 504 for the clover term
@@ -718,14 +804,20 @@ def arm_config(args, world):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    vals = []
-    for _ in range(args.warmup):
-        cpu_sample()
-    for _ in range(args.steps):
-        vals.append(cpu_sample())
+    pool, nw = cpu_pool_start()
+    try:
+        vals = []
+        for _ in range(args.warmup):
+            cpu_sample(pool, nw)
+        for _ in range(args.steps):
+            vals.append(cpu_sample(pool, nw))
+    finally:
+        pool.close()
+        pool.join()
     v = statistics.mean(x["value"] for x in vals)
     cb = dict(vals[-1])
     cb["value"] = v
+    cb["eocg_c1"] = cpu_eocg_c1()
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -777,6 +869,10 @@ def main():
         if out is not None:
             print(json.dumps(out))
         return
+    # the CPU baseline's worker pool forks now, before this process makes its first GPU call
+    pool, nworkers = None, 0
+    if world == 1 and rank == 0 and not args.no_cpu_baseline and args.workload == "c2" and not args.tune_m0:
+        pool, nworkers = cpu_pool_start()
     if world > 1:
         import torch
 
@@ -799,8 +895,14 @@ def main():
         return
     out = run_ours(args, rank, world)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline and args.workload == "c2":
-            out["cpu_baseline"] = cpu_sample()
+        if pool is not None:
+            try:
+                cpu_sample(pool, nworkers)  # warm-up
+                out["cpu_baseline"] = cpu_sample(pool, nworkers)
+                out["cpu_baseline"]["eocg_c1"] = cpu_eocg_c1()
+            finally:
+                pool.close()
+                pool.join()
         print(json.dumps(out))
     if world > 1:
         import torch
