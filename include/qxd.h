@@ -192,8 +192,9 @@ qxd_status qxd_get_clover(qxd_lattice *lat, double *out, int on_device);
 
 /* out = D in for nrhs right-hand sides: in, out are [nrhs][V][4][3][2] in the lattice's site
  * order.  prec selects the operator's precision (inputs are rounded to it, outputs widened
- * back to FP64).  With prec F32 and nrhs > 1 the multi-RHS kernel applies D to up to 12
- * right-hand sides per link and clover load.  QXD_ESTATE before build_clover; QXD_EINVAL for nrhs <= 0 or a null pointer. */
+ * back to FP64).  With nrhs > 1 and prec F32 the multi-RHS kernel applies D to up to 12
+ * right-hand sides per link and clover load; with F16N or BF16N the 16-bit multi-RHS kernel
+ * stages each tile's links and clover once for a group of right-hand sides.  QXD_ESTATE before build_clover; QXD_EINVAL for nrhs <= 0 or a null pointer. */
 qxd_status qxd_apply_D(qxd_lattice *lat, double *out, const double *in, int prec, int nrhs,
                        int on_device);
 
@@ -212,9 +213,11 @@ qxd_status qxd_solve(qxd_lattice *lat, double *x, const double *b, const qxd_sol
 
 /* Solve D x_r = b_r for nrhs right-hand sides in lock step (e.g. the 12 spin-colour point
  * sources of a propagator): FP64 outer defect correction per right-hand side and one inner
- * FP32 BiCGStab over all of them whose Dhat applications load each site's links and clover once
- * for every right-hand side.  x, b: [nrhs][V][4][3][2]; info: nrhs entries (or NULL).
- * params: solver MP_BICGSTAB_EO, inner_prec F32, use_x0 0 (else QXD_EINVAL); fallback and
+ * BiCGStab (FP32 vectors) over all of them whose Dhat applications load each site's links and
+ * clover once for every right-hand side (inner_prec F32: FP32 fields; F16N / BF16N: 16-bit
+ * spinors, links and clover with per-site norms, FP32 reliable updates).
+ * x, b: [nrhs][V][4][3][2]; info: nrhs entries (or NULL).
+ * params: solver MP_BICGSTAB_EO, inner_prec F32, F16N or BF16N, use_x0 0 (else QXD_EINVAL); fallback and
  * restart_f32 are not used; the other fields as for qxd_solve.  QXD_ENOCONV if some right-hand
  * side misses the tolerance. */
 qxd_status qxd_solve_mrhs(qxd_lattice *lat, double *x, const double *b, int nrhs,
@@ -370,7 +373,7 @@ qxd_status qxd_vec_dot_noalloc(const double *a, const double *b, int64_t n, doub
  * (0 = FP64 hop, 1 = FP32 hop, 2 = FP16N hop, 3 = BF16N hop, 4 = FP32 multi-RHS hop, 5 = the
  * persistent batch kernel of qxd_solve_batch, counted on the batch's first lattice, 6 = tensor-core
  * PTC layer, 7 = FP32 PTC layer; bytes of a PTC layer: input channels, links and output channels
- * once per site), the number of timed launches, their
+ * once per site; 8 = 16-bit multi-RHS hop), the number of timed launches, their
  * summed device time in ms and the summed algorithmic bytes they moved.  Reading the stats
  * synchronises the stream.  qxd_launch_count is the number of kernels the library launched. */
 qxd_status qxd_set_profiling(qxd_lattice *lat, int on);

@@ -502,6 +502,44 @@ qxd_status qxd_apply_D(qxd_lattice* lat, double* out, const double* in, int prec
     }
     return QXD_OK;
   }
+  if ((prec == QXD_F16N || prec == QXD_BF16N) && nrhs > 1) {
+    // multi-RHS 16-bit path: per parity, the right-hand sides' 16-bit copies (with per-site
+    // norms) sit one after another, [rhs][6][sv]; one link/clover tile load serves all of them
+    const int bf = prec == QXD_BF16N;
+    const i64 h = 6 * sv * nrhs;  // float4 (or uint2) entries of one parity of all RHS
+    float4* m32;
+    uint2* m16;
+    TRY(ensure_work(lat, 37, sizeof(float4) * 2 * h, (void**)&m32));
+    TRY(ensure_work(lat, 38, sizeof(uint2) * 2 * h + sizeof(float) * 2 * sv * nrhs, (void**)&m16));
+    float* n16 = (float*)(m16 + 2 * h);
+    for (int r = 0; r < nrhs; ++r) {
+      const double* src = in + (i64)r * 24 * lat->V;
+      if (!on_device) {
+        QXD_CUDA(lat, cudaMemcpyAsync(bi, src, vb, cudaMemcpyHostToDevice, lat->stream));
+        src = (const double*)bi;
+      }
+      TRY(pack_spinor64(lat, (const double2*)src, fin, 0));
+      for (int par = 0; par < 2; ++par) {
+        float4* f = m32 + par * h + (i64)r * 6 * sv;
+        TRY(f64_to_f32(lat, fin + (i64)par * 12 * sv, f, 6 * sv));
+        TRY(f32_to_n16(lat, f, m16 + par * h + (i64)r * 6 * sv, n16 + (par * nrhs + r) * sv, bf));
+      }
+    }
+    for (int par = 0; par < 2; ++par)
+      TRY(hop16_mrhs(lat, bf, par, EPI_DFULL, 0, m16 + (1 - par) * h, n16 + (i64)(1 - par) * nrhs * sv,
+                     m16 + par * h, n16 + (i64)par * nrhs * sv, nullptr, nullptr, m32 + par * h, 0.f, nrhs));
+    for (int r = 0; r < nrhs; ++r) {
+      double* dst = out + (i64)r * 24 * lat->V;
+      for (int par = 0; par < 2; ++par)
+        TRY(f32_to_f64(lat, m32 + par * h + (i64)r * 6 * sv, fout + (i64)par * 12 * sv, 6 * sv));
+      TRY(unpack_spinor64(lat, fout, on_device ? (double2*)dst : (double2*)bo, 0));
+      if (!on_device) {
+        QXD_CUDA(lat, cudaMemcpyAsync(dst, bo, vb, cudaMemcpyDeviceToHost, lat->stream));
+        QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+      }
+    }
+    return QXD_OK;
+  }
   for (int r = 0; r < nrhs; ++r) {
     const double* src = in + (i64)r * 24 * lat->V;
     double* dst = out + (i64)r * 24 * lat->V;
@@ -620,8 +658,9 @@ qxd_status qxd_solve_mrhs(qxd_lattice* lat, double* x, const double* b, int nrhs
   TRY(params_current(lat, p, &pv));
   p = &pv;
   if (p->use_x0) return fail(lat, QXD_EINVAL, "use_x0 is supported by qxd_solve only");
-  if (p->solver != QXD_SOLVER_MP_BICGSTAB_EO || p->inner_prec != QXD_F32)
-    return fail(lat, QXD_EINVAL, "multi-RHS solve: solver must be MP_BICGSTAB_EO with inner_prec F32");
+  if (p->solver != QXD_SOLVER_MP_BICGSTAB_EO ||
+      (p->inner_prec != QXD_F32 && p->inner_prec != QXD_F16N && p->inner_prec != QXD_BF16N))
+    return fail(lat, QXD_EINVAL, "multi-RHS solve: solver must be MP_BICGSTAB_EO with inner_prec F32, F16N or BF16N");
   if (!(p->tol > 0) || p->maxiter <= 0) return fail(lat, QXD_EINVAL, "tol must be > 0 and maxiter > 0");
   if (!lat->have_clover) return fail(lat, QXD_ESTATE, "solve before build_clover");
   const i64 sv = lat->sv;

@@ -114,6 +114,10 @@ __global__ void __launch_bounds__(BB) k_bicg_s(const float4* __restrict__ r, con
   r += (i64)blockIdx.y * rs;
   v += (i64)blockIdx.y * rs;
   s += (i64)blockIdx.y * rs;
+  if (WR16) {  // 16-bit copies of a multi-RHS field: [rhs][6][sv] values, [rhs][sv] norms
+    s16 += (i64)blockIdx.y * rs;
+    s16n += (i64)blockIdx.y * sv;
+  }
   const cd2 alpha = cdiv({scal[SC_RHO], scal[SC_RHO + 1]}, {scal[SC_RV], scal[SC_RV + 1]});
   const float ar = (float)-alpha.re, ai = (float)-alpha.im;
   for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
@@ -205,6 +209,10 @@ __global__ void __launch_bounds__(BB) k_bicg_p(const float4* __restrict__ r, con
   r += (i64)blockIdx.y * rs;
   v += (i64)blockIdx.y * rs;
   p += (i64)blockIdx.y * rs;
+  if (WR16) {  // as in k_bicg_s
+    p16 += (i64)blockIdx.y * rs;
+    p16n += (i64)blockIdx.y * sv;
+  }
   const cd2 rho = {scal[SC_RHO], scal[SC_RHO + 1]};
   const cd2 alpha = cdiv(rho, {scal[SC_RV], scal[SC_RV + 1]});
   const cd2 omega = {scal[SC_TS] / scal[SC_TT], scal[SC_TS + 1] / scal[SC_TT]};

@@ -8,7 +8,9 @@
 // (site, rhs) with links and clover from shared memory and its neighbour spinors from global
 // memory (L1/L2 serve the reuse).  Per site and RHS the algorithmic traffic is the spinors
 // (in, out, diagonal in) plus (8 links + clover) / R.
-#include "hop_common.cuh"
+#include <cstdlib>
+
+#include "hop_site.cuh"
 
 namespace qxd {
 
@@ -210,6 +212,228 @@ qxd_status hop32_mrhs(qxd_lattice* lat, int par, int epi, int g5, const float4* 
     QXD_CHECK_LAUNCH(lat, "k_hop_mrhs");
   }
   return QXD_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// 16-bit multi-RHS hop.  Spinors of each right-hand side in 16 bits with a per-site FP32 norm
+// (as the single-RHS 16-bit hop); links and the clover block pair of a tile of MR16_SITES
+// sites are staged once in shared memory (16-bit, as stored) and serve the NRB right-hand
+// sides of the block.  A block is MR16_SITES sites (threadIdx.x, one warp per right-hand side)
+// times NRB right-hand sides (threadIdx.y); blockIdx.y selects a group of NRB right-hand sides.
+// Each thread runs the software-pipelined hop of the single-RHS kernel (neighbour spinors
+// fetched PF legs ahead) with its link and clover reads served by shared memory.  Per site and
+// RHS the algorithmic bytes are the spinors (52 B each: in, out, diagonal in) plus
+// (8 x 36 B links + 152 B clover) / NRB.
+// ------------------------------------------------------------------------------------------
+constexpr int MR16_SITES = 32;
+
+template <int S>
+struct Mr16Shared {
+  uint32_t nbb[4][S];      // backward neighbours (cb in the other parity) of the tile's sites
+  uint32_t link[8][9][S];  // leg 2 mu: W_mu(x); leg 2 mu + 1: W_mu(x - mu) (16-bit pairs)
+  uint2 clov[2][9][S];     // clover block pair (16-bit) and its per-block norms
+  float cn[2][S];
+};
+
+// Link accessor over the staged tile: a "raw" link is only the leg; decode reads shared memory.
+template <class FMT, int S>
+struct LinkTile16 {
+  typedef float real;
+  struct Raw {
+    int leg;
+  };
+  const Mr16Shared<S>* sh;
+  int s, par;
+  __device__ __forceinline__ Raw fetch(int lp, int mu, uint32_t) const { return Raw{2 * mu + (lp != par ? 1 : 0)}; }
+  __device__ __forceinline__ void decode(const Raw& r, cplx<float> u[9]) const {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const uint32_t w = sh->link[r.leg][k][s];
+      u[k] = mk(FMT::lo(w), FMT::hi(w));
+    }
+  }
+};
+
+// Clover accessor over the staged tile (the epilogue reads it when it needs it).
+template <class FMT, int S>
+struct CloverTile16 {
+  typedef float real;
+  struct Raw {};
+  const Mr16Shared<S>* sh;
+  int s;
+  __device__ __forceinline__ Raw fetch(int, uint32_t) const { return Raw{}; }
+  __device__ __forceinline__ void decode(const Raw&, int blk, float o[36]) const {
+    const float n = sh->cn[blk][s];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const uint2 v = sh->clov[blk][k][s];
+      o[4 * k] = n * FMT::lo(v.x);
+      o[4 * k + 1] = n * FMT::hi(v.x);
+      o[4 * k + 2] = n * FMT::lo(v.y);
+      o[4 * k + 3] = n * FMT::hi(v.y);
+    }
+  }
+};
+template <class F, int S>
+struct is16<CloverTile16<F, S>> {
+  static constexpr bool value = true;  // epilogue data prefetched like the 16-bit single-RHS hop
+};
+
+template <class FMT, int NRB, int MINB, bool OUT16, int EPI, bool G5>
+__global__ void __launch_bounds__(MR16_SITES* NRB, MINB)
+    k_hop_mrhs16(Geom g, int par, int nr, const uint2* __restrict__ in, const float* __restrict__ in_n,
+                 const uint2* __restrict__ same, const float* __restrict__ same_n, uint2* __restrict__ out,
+                 float* __restrict__ out_n, float4* __restrict__ out32, const uint32_t* __restrict__ W,
+                 const uint2* __restrict__ C, const float* __restrict__ Cn, float coef) {
+  constexpr int S = MR16_SITES;
+  __shared__ Mr16Shared<S> sh;
+  const int s = threadIdx.x, rb = threadIdx.y;
+  const int tid = rb * S + s, nthr = S * NRB;
+  const uint32_t cb0 = blockIdx.x * S;
+  const i64 sv = g.sv;
+  // phase 1: backward neighbours of the tile (directions unrolled: register-only index math)
+  for (int ss = tid; ss < S; ss += nthr) {
+    const uint32_t cb = cb0 + ss;
+    int x[4] = {0, 0, 0, 0};
+    const bool live = cb < (uint32_t)g.Vh;
+    if (live) cb_coords32(g, cb, par, x);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      bool cr;
+      sh.nbb[mu][ss] = live ? nbr_cb32(g, x, mu, -1, cr) : 0u;
+    }
+  }
+  __syncthreads();
+  // phase 2: the tile's links and clover (coalesced across sites)
+  for (int e = tid; e < 8 * 9 * S; e += nthr) {
+    const int ss = e % S, rest = e / S, leg = rest / 9, k = rest % 9;
+    const uint32_t cb = cb0 + ss;
+    uint32_t w = 0u;
+    if (cb < (uint32_t)g.Vh) {
+      const int mu = leg >> 1;
+      const bool fwd = (leg & 1) == 0;
+      const int lp = fwd ? par : 1 - par;
+      w = __ldg(W + ((i64)(lp * 4 + mu) * 9 + k) * sv + (fwd ? cb : sh.nbb[mu][ss]));
+    }
+    sh.link[leg][k][ss] = w;
+  }
+  constexpr bool NEEDC = EPI != EPI_HOP && EPI != EPI_XPAY;
+  if (NEEDC) {
+    for (int e = tid; e < 2 * 9 * S; e += nthr) {
+      const int ss = e % S, rest = e / S, blk = rest / 9, k = rest % 9;
+      const uint32_t cb = cb0 + ss;
+      sh.clov[blk][k][ss] = cb < (uint32_t)g.Vh ? __ldg(C + ((i64)(par * 2 + blk) * 9 + k) * sv + cb) : make_uint2(0u, 0u);
+    }
+    for (int e = tid; e < 2 * S; e += nthr) {
+      const int ss = e % S, blk = e / S;
+      const uint32_t cb = cb0 + ss;
+      sh.cn[blk][ss] = cb < (uint32_t)g.Vh ? __ldg(Cn + (i64)(par * 2 + blk) * sv + cb) : 0.f;
+    }
+  }
+  __syncthreads();
+  const uint32_t cb = cb0 + s;
+  const int r = blockIdx.y * NRB + rb;
+  if (cb >= (uint32_t)g.Vh || r >= nr) return;
+  const i64 o16 = (i64)r * 6 * sv, on = (i64)r * sv;
+  SpinorN16<FMT> si{const_cast<uint2*>(in) + o16, const_cast<float*>(in_n) + on, sv};
+  SpinorN16<FMT> ssame{const_cast<uint2*>(same) + (same ? o16 : 0), const_cast<float*>(same_n) + (same_n ? on : 0), sv};
+  LinkTile16<FMT, S> lk{&sh, s, par};
+  CloverTile16<FMT, S> cl{&sh, s};
+  if constexpr (OUT16) {
+    SpinorN16<FMT> so{out + o16, out_n + on, sv};
+    hop_site<float, SpinorN16<FMT>, SpinorN16<FMT>, SpinorN16<FMT>, LinkTile16<FMT, S>, CloverTile16<FMT, S>, EPI, G5,
+             QXD_HOP_PF16>(g, par, cb, si, ssame, so, lk, cl, coef);
+  } else {
+    SpinorF32 so{out32 + o16, sv};
+    hop_site<float, SpinorN16<FMT>, SpinorN16<FMT>, SpinorF32, LinkTile16<FMT, S>, CloverTile16<FMT, S>, EPI, G5,
+             QXD_HOP_PF16>(g, par, cb, si, ssame, so, lk, cl, coef);
+  }
+}
+
+// Right-hand sides per block of the 16-bit multi-RHS hop: 12, 6 or 4 (the environment variable
+// QXD_MRHS16_NRB overrides the default, for shape sweeps).
+static int mrhs16_nrb() {
+  static int nrb = [] {
+    const char* e = std::getenv("QXD_MRHS16_NRB");
+    int v = e ? std::atoi(e) : 6;
+    return (v == 12 || v == 6 || v == 4) ? v : 6;
+  }();
+  return nrb;
+}
+
+template <class FMT, int NRB, int MINB, bool OUT16>
+static qxd_status launch_mrhs16(qxd_lattice* lat, int par, int epi, int g5, const uint2* in, const float* in_n,
+                                const uint2* same, const float* same_n, uint2* out, float* out_n, float4* out32,
+                                const uint32_t* W, const uint2* C, const float* Cn, float coef, int nrhs) {
+  const Geom& g = lat->g;
+  dim3 grid((unsigned)((g.Vh + MR16_SITES - 1) / MR16_SITES), (unsigned)((nrhs + NRB - 1) / NRB)),
+      block(MR16_SITES, NRB);
+#define QXD_MR16_CASE(E, G)                                                                                        \
+  if (epi == E && (g5 != 0) == G)                                                                                  \
+    k_hop_mrhs16<FMT, NRB, MINB, OUT16, E, G><<<grid, block, 0, lat->stream>>>(g, par, nrhs, in, in_n, same, same_n, \
+                                                                              out, out_n, out32, W, C, Cn, coef);   \
+  else
+  QXD_MR16_CASE(EPI_INV, false)
+  QXD_MR16_CASE(EPI_INV, true)
+  QXD_MR16_CASE(EPI_DHAT2, false)
+  QXD_MR16_CASE(EPI_DHAT2, true)
+  QXD_MR16_CASE(EPI_DFULL, false) { return fail(lat, QXD_EINVAL, "unsupported 16-bit multi-RHS epilogue"); }
+#undef QXD_MR16_CASE
+  QXD_CHECK_LAUNCH(lat, "k_hop_mrhs16");
+  return QXD_OK;
+}
+
+template <class FMT, bool OUT16>
+static qxd_status mrhs16_shape(qxd_lattice* lat, int par, int epi, int g5, const uint2* in, const float* in_n,
+                               const uint2* same, const float* same_n, uint2* out, float* out_n, float4* out32,
+                               const uint32_t* W, const uint2* C, const float* Cn, float coef, int nrhs) {
+  switch (mrhs16_nrb()) {
+    case 12:
+      return launch_mrhs16<FMT, 12, 2, OUT16>(lat, par, epi, g5, in, in_n, same, same_n, out, out_n, out32, W, C, Cn,
+                                              coef, nrhs);
+    case 4:
+      return launch_mrhs16<FMT, 4, 5, OUT16>(lat, par, epi, g5, in, in_n, same, same_n, out, out_n, out32, W, C, Cn,
+                                             coef, nrhs);
+    default:
+      return launch_mrhs16<FMT, 6, 3, OUT16>(lat, par, epi, g5, in, in_n, same, same_n, out, out_n, out32, W, C, Cn,
+                                             coef, nrhs);
+  }
+}
+
+qxd_status hop16_mrhs(qxd_lattice* lat, int bf16, int par, int epi, int g5, const uint2* in, const float* in_nrm,
+                      const uint2* same, const float* same_nrm, uint2* out, float* out_nrm, float4* out32, float coef,
+                      int nrhs) {
+  if (nrhs < 1) return fail(lat, QXD_EINVAL, "nrhs must be positive");
+  if (!out32 && !(out && out_nrm)) return fail(lat, QXD_EINVAL, "16-bit multi-RHS hop: no output");
+  const bool inv = epi == EPI_INV || epi == EPI_INVXPAY;
+  const bool needs_same = epi == EPI_DFULL || epi == EPI_DHAT2;
+  if (needs_same && !(same && same_nrm)) return fail(lat, QXD_EINVAL, "16-bit multi-RHS hop: epilogue needs same");
+  const Geom& g = lat->g;
+  const int nrb = mrhs16_nrb();
+  // bytes: per site and RHS the spinors; links and clover once per site and block of nrb RHS
+  const double sp = 52.0 + (out32 ? 96.0 : 52.0) + (needs_same ? 52.0 : 0.0);
+  const double groups = (double)((nrhs + nrb - 1) / nrb);
+  prof_begin(lat, KSTAT_N16_MRHS, (sp * nrhs + groups * (8 * 36.0 + 152.0)) * (double)g.Vh);
+  qxd_status st;
+  if (bf16) {
+    const uint32_t* W = lat->WB16;
+    const uint2* C = inv ? lat->CiB16 : lat->CB16;
+    const float* Cn = inv ? lat->CiB16n : lat->CB16n;
+    st = out32 ? mrhs16_shape<B16, false>(lat, par, epi, g5, in, in_nrm, same, same_nrm, out, out_nrm, out32, W, C, Cn,
+                                          coef, nrhs)
+               : mrhs16_shape<B16, true>(lat, par, epi, g5, in, in_nrm, same, same_nrm, out, out_nrm, out32, W, C, Cn,
+                                         coef, nrhs);
+  } else {
+    const uint32_t* W = lat->W16;
+    const uint2* C = inv ? lat->Ci16 : lat->C16;
+    const float* Cn = inv ? lat->Ci16n : lat->C16n;
+    st = out32 ? mrhs16_shape<H16, false>(lat, par, epi, g5, in, in_nrm, same, same_nrm, out, out_nrm, out32, W, C, Cn,
+                                          coef, nrhs)
+               : mrhs16_shape<H16, true>(lat, par, epi, g5, in, in_nrm, same, same_nrm, out, out_nrm, out32, W, C, Cn,
+                                         coef, nrhs);
+  }
+  prof_end(lat);
+  return st;
 }
 
 }  // namespace qxd

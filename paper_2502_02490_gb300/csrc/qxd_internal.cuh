@@ -570,7 +570,8 @@ enum {
   KSTAT_BATCH = 5,
   KSTAT_PTC_TC = 6,   // tensor-core PTC layer
   KSTAT_PTC_F32 = 7,  // FP32 CUDA-core PTC layer
-  KSTAT_N = 8
+  KSTAT_N16_MRHS = 8, // 16-bit multi-RHS hop
+  KSTAT_N = 9
 };
 
 // Device scalar slots used by the solvers and reductions.
@@ -733,6 +734,11 @@ qxd_status hop16(qxd_lattice* lat, int bf16, int par, int epi, int g5, const uin
                  float coef);
 
 // ---- mrhs.cu: FP32 hop on nrhs right-hand sides (fields at base + r * rs float4s) ----
+// 16-bit multi-RHS hop: right-hand side r of a 16-bit field at base + r * 6 sv (uint2) with its
+// norms at base + r * sv; FP32 output (out32, RHS r at + r * 6 sv float4s) or 16-bit output.
+qxd_status hop16_mrhs(qxd_lattice* lat, int bf16, int par, int epi, int g5, const uint2* in, const float* in_nrm,
+                      const uint2* same, const float* same_nrm, uint2* out, float* out_nrm, float4* out32, float coef,
+                      int nrhs);
 qxd_status hop32_mrhs(qxd_lattice* lat, int par, int epi, int g5, const float4* in, const float4* same, float4* out,
                       float coef, int nrhs, i64 rs);
 

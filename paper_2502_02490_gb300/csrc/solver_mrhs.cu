@@ -3,8 +3,9 @@
 //
 // Outer: per right-hand side, the FP64 defect correction of the single-RHS solver (FP64 D and
 // norms, Schur source and reconstruction in FP32).  Inner: BiCGStab on Dhat for all right-hand
-// sides at once in FP32, its Dhat applications by the multi-RHS hop (one link and clover load
-// per site serves every right-hand side), its vector updates and FP64 reductions by the
+// sides at once with FP32 vectors, its Dhat applications by the multi-RHS hop (one link and
+// clover load per site serves every right-hand side; FP32, or 16-bit spinors, links and clover
+// with per-site norms), its vector updates and FP64 reductions by the
 // BiCGStab kernels launched over (site blocks x right-hand sides) with per-RHS scalars.  A
 // right-hand side that reaches its inner target is frozen (SC_ACTIVE = 0) while the others go
 // on; each gets its own FP32 reliable updates (recompute s, restart).
@@ -24,7 +25,7 @@ qxd_status apply_D64(qxd_lattice* lat, const double2* in, double2* out);
     if (_s != QXD_OK) return _s; \
   } while (0)
 
-enum { MW_HALVES = 32, MW_R32 = 33, MW_R64 = 34, MW_T64 = 35, MW_RO = 36 };
+enum { MW_HALVES = 32, MW_R32 = 33, MW_R64 = 34, MW_T64 = 35, MW_RO = 36, MW_H16 = 46, MW_H16N = 47 };
 enum { H_BH = 0, H_Y, H_X, H_R, H_RH, H_P, H_V, H_S, H_T, H_TMP, H_N };
 
 // Dhat on all n right-hand sides (FP32, multi-RHS hop): out = Dhat in, tmp odd-half scratch
@@ -41,8 +42,10 @@ static qxd_status read_mr(qxd_lattice* lat, int n) {
   return QXD_OK;
 }
 
-// Inner lock-step BiCGStab for the active right-hand sides (act[i]); targets per RHS.
-static qxd_status inner_mr(qxd_lattice* lat, float4* H, int n, const std::vector<char>& act,
+// Inner lock-step BiCGStab for the active right-hand sides (act[i]); targets per RHS.  With a
+// 16-bit inner precision the Dhat applications read 16-bit copies of p and s (with per-site
+// norms) that the vector kernels write as they update p and s, as in the single-RHS solver.
+static qxd_status inner_mr(qxd_lattice* lat, float4* H, int n, int prec, const std::vector<char>& act,
                            const std::vector<double>& target, double delta, int maxiter, int check_every, int* iters,
                            int* nrel) {
   const i64 sv = lat->sv, n4 = 6 * sv, rs = n4;
@@ -50,6 +53,22 @@ static qxd_status inner_mr(qxd_lattice* lat, float4* H, int n, const std::vector
   float4 *bh = half(H_BH, 0), *y = half(H_Y, 0), *x = half(H_X, 0), *r = half(H_R, 0), *rh = half(H_RH, 0),
          *p = half(H_P, 0), *v = half(H_V, 0), *s = half(H_S, 0), *t = half(H_T, 0), *tmp = half(H_TMP, 0);
   const size_t all = sizeof(float4) * n4 * n;
+  const bool low = prec == QXD_F16N || prec == QXD_BF16N;
+  const int bf = prec == QXD_BF16N;
+  uint2* h16 = nullptr;
+  float* h16n = nullptr;
+  if (low) {  // [P, S, T][rhs][6][sv] 16-bit values and [P, S, T][rhs][sv] norms
+    TRY(ensure_work(lat, MW_H16, sizeof(uint2) * 3 * n4 * n, (void**)&h16));
+    TRY(ensure_work(lat, MW_H16N, sizeof(float) * 3 * sv * n, (void**)&h16n));
+  }
+  uint2 *p16 = h16, *s16 = h16 ? h16 + n4 * n : nullptr, *t16 = h16 ? h16 + 2 * n4 * n : nullptr;
+  float *p16n = h16n, *s16n = h16n ? h16n + sv * n : nullptr, *t16n = h16n ? h16n + 2 * sv * n : nullptr;
+  // out = Dhat in for every right-hand side (FP32 out)
+  auto dhat_all = [&](const float4* in32, const uint2* in16, const float* in16n, float4* out) -> qxd_status {
+    if (!low) return dhat_mr(lat, in32, out, tmp, n, rs);
+    TRY(hop16_mrhs(lat, bf, 1, EPI_INV, 0, in16, in16n, nullptr, nullptr, t16, t16n, nullptr, 1.0f, n));
+    return hop16_mrhs(lat, bf, 0, EPI_DHAT2, 0, t16, t16n, in16, in16n, nullptr, nullptr, out, -0.25f, n);
+  };
   Rhs R;
   R.nrhs = n;
   R.rs = rs;
@@ -69,6 +88,8 @@ static qxd_status inner_mr(qxd_lattice* lat, float4* H, int n, const std::vector
   TRY(blas_copy(lat, r, bh, all));
   TRY(blas_copy(lat, rh, r, all));
   TRY(blas_copy(lat, p, r, all));
+  if (low)
+    for (int i = 0; i < n; ++i) TRY(f32_to_n16(lat, half(H_P, i), p16 + (i64)i * n4, p16n + (i64)i * sv, bf));
   TRY(bicg_cdot(lat, rh, r, SC_RHO, R));
   TRY(bicg_cdot(lat, r, r, SC_RN, R));
   TRY(read_mr(lat, n));
@@ -84,13 +105,13 @@ static qxd_status inner_mr(qxd_lattice* lat, float4* H, int n, const std::vector
   }
   int it = 0, rel = 0;
   while (nact > 0 && it < maxiter) {
-    TRY(dhat_mr(lat, p, v, tmp, n, rs));
+    TRY(dhat_all(p, p16, p16n, v));
     TRY(bicg_cdot(lat, rh, v, SC_RV, R));
-    TRY(bicg_s(lat, r, v, s, nullptr, nullptr, 0, R));
-    TRY(dhat_mr(lat, s, t, tmp, n, rs));
+    TRY(bicg_s(lat, r, v, s, s16, s16n, bf, R));
+    TRY(dhat_all(s, s16, s16n, t));
     TRY(bicg_ts(lat, t, s, R));
     TRY(bicg_xr(lat, x, p, s, t, rh, r, R));
-    TRY(bicg_p(lat, r, v, p, nullptr, nullptr, 0, R));
+    TRY(bicg_p(lat, r, v, p, p16, p16n, bf, R));
     ++it;
     if (it % check_every) continue;
     TRY(read_mr(lat, n));
@@ -122,7 +143,8 @@ static qxd_status inner_mr(qxd_lattice* lat, float4* H, int n, const std::vector
           TRY(set_scalar_at(lat, lat->mr_scal + (i64)i * SC_N + SC_ACTIVE, 0.0));
         } else {
           TRY(blas_copy(lat, half(H_RH, i), ri, sizeof(float4) * n4));
-          TRY(blas_copy(lat, half(H_P, i), ri, sizeof(float4) * n4));
+          TRY(bicg_copy(lat, ri, half(H_P, i), low ? p16 + (i64)i * n4 : nullptr, low ? p16n + (i64)i * sv : nullptr,
+                        bf));
           TRY(bicg_cdot(lat, ri, ri, SC_RHO, one(i)));
         }
       }
@@ -206,7 +228,7 @@ qxd_status solve_mrhs(qxd_lattice* lat, double2* x, const double2* b, int n, con
       if (!act[i]) TRY(blas_zero(lat, half(H_BH, i), sizeof(float4) * 6 * sv));
     TRY(blas_zero(lat, half(H_Y, 0), sizeof(float4) * 6 * sv * n));
     int it = 0, nr = 0;
-    TRY(inner_mr(lat, H, n, act, target, prm->reliable_delta, prm->maxiter - total,
+    TRY(inner_mr(lat, H, n, prm->inner_prec, act, target, prm->reliable_delta, prm->maxiter - total,
                  prm->check_every > 0 ? prm->check_every : 1, &it, &nr));
     total += it;
     nrel += nr;

@@ -79,3 +79,55 @@ def test_mrhs_solve_with_a_zero_source(qxd):
             assert O.true_rel_residual(c.op, psi[k], eta[k]) <= 1e-10
     finally:
         c.close()
+
+
+UNIT16 = {"f16n": 2.0 ** -11, "bf16n": 2.0 ** -8}
+
+
+@pytest.mark.parametrize("prec", ["f16n", "bf16n"])
+@pytest.mark.parametrize("L,nrhs,cstar", [((6, 6, 6, 6), 12, False), ((4, 2, 2, 6), 13, False),
+                                          ((2, 2, 4, 2), 5, True), ((8, 6, 4, 6), 7, False)])
+def test_mrhs16_apply_per_site(qxd, prec, L, nrhs, cstar):
+    """The 16-bit multi-RHS hop (tile-staged links and clover, groups of right-hand sides) against
+    the FP64 oracle site by site: max error over a site's 12 entries <= 8 u max |ref| there, and
+    equal to the single-RHS 16-bit operator up to FP32 rounding of the accumulation order."""
+    c = Case(qxd, torch, L, cstar=cstar)
+    try:
+        psis = np.stack([synth.gaussian_spinor(c.dims, 3100 + k) for k in range(nrhs)])
+        x = c.dev_tensor(psis)
+        y = torch.empty_like(x)
+        qxd.apply_D(c.lat, y, x, qxd.PREC[prec], nrhs=nrhs)
+        got = as_c128(y, psis.shape)
+        worst = 0.0
+        for k in range(nrhs):
+            ref = c.op.D(psis[k])
+            e = np.abs(got[k] - ref).reshape(c.V, -1).max(axis=1) / np.abs(ref).reshape(c.V, -1).max(axis=1)
+            worst = max(worst, float(e.max()) / UNIT16[prec])
+            single = c.apply_D(psis[k], qxd.PREC[prec])
+            assert np.abs(got[k] - single).max() <= 1e-5 * np.abs(single).max(), k
+        assert worst <= 8, worst
+        print(f"{L} nrhs={nrhs} {prec}: worst per-site error {worst:.2f} u")
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("prec", ["f16n", "bf16n"])
+@pytest.mark.parametrize("L,cstar", [((4, 4, 4, 4), False), ((4, 2, 2, 4), True), ((8, 4, 6, 4), False)])
+def test_mrhs16_solve_point_sources(qxd, prec, L, cstar):
+    """The multi-RHS solve with the 16-bit inner operator: every right-hand side judged by the
+    oracle's FP64 true residual."""
+    c = Case(qxd, torch, L, cstar=cstar)
+    try:
+        eta = point_sources(c.dims)
+        b = c.dev_tensor(eta)
+        x = torch.empty_like(b)
+        st, infos = qxd.solve_mrhs(c.lat, x, b, 12, solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=qxd.PREC[prec],
+                                   tol=1e-10)
+        assert st == qxd.OK, infos[0]
+        psi = as_c128(x, eta.shape)
+        for k in range(12):
+            res = O.true_rel_residual(c.op, psi[k], eta[k])
+            assert res <= 1e-10, (k, res, infos[k])
+        print(f"{L} cstar={cstar} {prec}: {infos[0]}")
+    finally:
+        c.close()
