@@ -323,7 +323,8 @@ def run_ours(args, rank, world):
                                "timed steps"},
         "profiled_steps_same_work": same_work,
         "kernels": {k: {"launches": v[0], "ms": v[1], "GB": v[2] / 1e9} for k, v in stats.items() if v[0]},
-        "dslash_kernel_GBps": hop_total / sum(v[1] for v in stats.values()) / 1e6 if world == 1 else None,
+        "dslash_kernel_GBps": (sum(v[2] for v in stats.values()) / sum(v[1] for v in stats.values()) / 1e6
+                               if world == 1 else None),
         "dslash_kernel_GFLOPs": dslash_gflops(dom, n_l, ms_l, arm_config(args, world)["sites"] // 2),
         "e2e": {"value": hop_total / e2e_s / 1e9 * (1 if world == 1 else 1), "unit": "GB/s",
                 "seconds_per_step": e2e_s / args.steps,
