@@ -557,7 +557,7 @@ def tune_m0():
         else:
             hi = m0
     # the physical branch in steps of 0.01 on [-0.3, 0]: its slowest point
-    scan = {round(v, 2): iters(round(v, 2)) for v in np.arange(-0.30, 0.001, 0.01)}
+    scan = {round(float(v), 2): iters(round(float(v), 2)) for v in np.arange(-0.30, 0.001, 0.01)}
     slow = max(scan, key=scan.get)
     qxd.destroy_lattice(lat)
     with open(C4_M0_FILE, "w") as f:
