@@ -274,6 +274,36 @@ def run_ours(args, rank, world):
         fp64 = {"seconds": med[0], "wall_s": med[1], "iterations": med[2]["iters_inner"],
                 "true_rel_res": med[2]["true_rel_res"], "runs_s": [r[0] for r in runs],
                 "timing": f"median of {FP64_REPEATS} solves after one warm-up solve"}
+    # ---- resident-field link update: k links replaced on the device (clover rebuilt around them)
+    # against reloading the whole field and rebuilding the clover term ----
+    link_update = None
+    if world == 1:
+        from paper_2502_02490_gb300 import synth
+
+        qxd.load_gauge(lat, su3_d, a_d, w["q"])
+        qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
+        upd = {}
+        for k in (1, 1000, 100000):
+            idx = torch.from_numpy(np.random.default_rng(k).choice(4 * V, size=k, replace=False)
+                                   .astype(np.int64)).to(dev)
+            newu = torch.from_numpy(synth.random_su3(k, 17, eps=w["eps"]).view(np.float64)).to(dev)
+            newa = torch.from_numpy(synth.random_angles(k, 18, scale=w["eps"])).to(dev)
+            qxd.update_links(lat, idx, newu, newa)  # warm-up (scratch allocation)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                qxd.update_links(lat, idx, newu, newa)
+            torch.cuda.synchronize()
+            upd[str(k)] = (time.perf_counter() - t0) / 3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            qxd.load_gauge(lat, su3_d, a_d, w["q"])
+            qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
+        torch.cuda.synchronize()
+        link_update = {"update_links_s": upd, "full_load_gauge_build_clover_s": (time.perf_counter() - t0) / 3,
+                       "note": "k random links replaced on the device (qxd_update_links, clover rebuilt at the "
+                               "sites around them); mean of 3 calls after one warm-up"}
     qxd.destroy_lattice(lat)
 
     # ---- aggregate over ranks ----
@@ -332,6 +362,7 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": int(eta.nbytes)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
+        "link_update": link_update,
     }
     return out
 

@@ -162,6 +162,25 @@ qxd_status qxd_destroy_lattice(qxd_lattice *lat);
 qxd_status qxd_load_gauge(qxd_lattice *lat, const double *su3, const double *a_u1, double q,
                           int on_device);
 
+/* Update n links of the resident gauge field on the device, without reloading it (the Markov
+ * chain changes the field in place; Sec. 6 asks for fields kept on the GPU and updated there).
+ *   idx[j]: the link's entry 4 s + mu of the canonical arrays qxd_load_gauge takes (s: the
+ *           site on the physical lattice, in the lattice's site order), 0 <= idx[j] < 4 V;
+ *   su3:    [n][3][3][2] its new SU(3) (or U(3)) matrix; a_u1: [n] its new U(1) angle, or NULL
+ *           for 0.  All three are device pointers with on_device = 1, else host memory.
+ * Each link's device copies (two with C*: the mirror one conjugated, angle negated) and its hop
+ * link W = exp(i q A) U in every precision are replaced.  If the clover term was built, it is
+ * rebuilt (with the m0, c_sw and c_sw^QED of the last qxd_build_clover) at the sites whose
+ * plaquettes hold an updated link -- the link's two end points and their +-nu neighbours -- or in
+ * full when that is most of the lattice.  Entries of idx must be distinct (with a repeated link
+ * it is unspecified which value wins).  Synchronises the lattice stream.  Errors: QXD_ESTATE
+ * before load_gauge; QXD_EINVAL for n < 0, a null pointer or an index outside the range (the
+ * other links are updated; the clover is then marked unbuilt, so applies return QXD_ESTATE until
+ * qxd_build_clover); QXD_ESINGULAR if a rebuilt odd-site
+ * block is not invertible (the clover must then be rebuilt before the next apply). */
+qxd_status qxd_update_links(qxd_lattice *lat, int64_t n, const int64_t *idx, const double *su3,
+                            const double *a_u1, int on_device);
+
 /* Cache blocks of QXD_ORDER_IPT (Eq. ipt, Sec. 4.1.1): B[mu] must divide the lattice extent L[mu]
  * (for C* both the physical and the doubled x extent); default B = L.  Applies to every field
  * exchanged afterwards (spinors, gauge field, clover export).  QXD_EINVAL for a LEXI lattice or

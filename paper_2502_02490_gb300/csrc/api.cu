@@ -386,6 +386,80 @@ qxd_status qxd_load_gauge(qxd_lattice* lat, const double* su3, const double* a_u
   return QXD_OK;
 }
 
+qxd_status qxd_update_links(qxd_lattice* lat, int64_t n, const int64_t* idx, const double* su3, const double* a_u1,
+                            int on_device) {
+  QXD_TRACE();
+  CHECK_LAT(lat);
+  if (!lat->have_gauge) return fail(lat, QXD_ESTATE, "update_links before load_gauge");
+  if (n < 0) return fail(lat, QXD_EINVAL, "n must be >= 0");
+  if (n == 0) return QXD_OK;
+  if (!idx || !su3) return fail(lat, QXD_EINVAL, "idx and su3 must not be null");
+  const Geom& g = lat->g;
+  const int64_t* d_idx = idx;
+  const double2* d_su3 = (const double2*)su3;
+  const double* d_a = a_u1;
+  if (!on_device) {  // stage the host arrays: idx, then su3, then the angles
+    unsigned char* st;
+    TRY(ensure_work(lat, 49, (size_t)n * (sizeof(int64_t) + sizeof(double2) * 9 + sizeof(double)), (void**)&st));
+    QXD_CUDA(lat, cudaMemcpyAsync(st, idx, sizeof(int64_t) * n, cudaMemcpyHostToDevice, lat->stream));
+    QXD_CUDA(lat, cudaMemcpyAsync(st + sizeof(int64_t) * n, su3, sizeof(double2) * 9 * n, cudaMemcpyHostToDevice,
+                                  lat->stream));
+    d_idx = (const int64_t*)st;
+    d_su3 = (const double2*)(st + sizeof(int64_t) * n);
+    if (a_u1) {
+      double* da = (double*)(st + (sizeof(int64_t) + sizeof(double2) * 9) * n);
+      QXD_CUDA(lat, cudaMemcpyAsync(da, a_u1, sizeof(double) * n, cudaMemcpyHostToDevice, lat->stream));
+      d_a = da;
+    }
+  }
+  // slot 48: the clover-site mask [2 Vh] bytes, then the list count and the bad-index flag
+  const i64 nsite = 2 * g.Vh;
+  const size_t mask_bytes = ((size_t)nsite + 255) / 256 * 256;
+  unsigned char* mask;
+  TRY(ensure_work(lat, 48, mask_bytes + 2 * sizeof(int), (void**)&mask));
+  unsigned int* count = (unsigned int*)(mask + mask_bytes);
+  int* bad = (int*)(count + 1);
+  QXD_CUDA(lat, cudaMemsetAsync(mask, 0, mask_bytes + 2 * sizeof(int), lat->stream));
+  TRY(update_links(lat, n, d_idx, d_su3, d_a, mask, bad));
+  int hbad[2] = {0, 0};
+  if (lat->have_clover) {
+    // slot 50: the site list [2 Vh] and the field strengths of the listed sites (60 doubles each)
+    uint32_t* list;
+    TRY(ensure_work(lat, 50, sizeof(uint32_t) * nsite, (void**)&list));
+    TRY(compact_mask(lat, mask, list, count));
+    QXD_CUDA(lat, cudaMemcpyAsync(hbad, count, 2 * sizeof(int), cudaMemcpyDeviceToHost, lat->stream));
+    QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    const i64 nl = (i64)(unsigned int)hbad[0];
+    if (hbad[1]) {
+      lat->have_clover = false;  // stale at the updated links: build_clover must run before the next apply
+      return fail(lat, QXD_EINVAL, "update_links: a link index is outside 0 .. 4 V - 1 (skipped)");
+    }
+    if (nl > nsite / 4) {
+      // most of the lattice changed: the full build (shared plaquette half-products) is cheaper
+      lat->have_clover = false;
+      TRY(clover_build(lat));
+      lat->have_clover = true;
+      return QXD_OK;
+    }
+    double* Fc;
+    TRY(ensure_work(lat, 51, sizeof(double) * 60 * (size_t)(nl > 0 ? nl : 1), (void**)&Fc));
+    int* sbad = bad;  // reused as the singular-block flag
+    QXD_CUDA(lat, cudaMemsetAsync(sbad, 0, sizeof(int), lat->stream));
+    TRY(clover_rebuild_sites(lat, list, nl, Fc, sbad));
+    QXD_CUDA(lat, cudaMemcpyAsync(hbad + 1, sbad, sizeof(int), cudaMemcpyDeviceToHost, lat->stream));
+    QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    if (hbad[1]) {
+      lat->have_clover = false;
+      return fail(lat, QXD_ESINGULAR, "update_links: a rebuilt clover block on an odd site is not invertible");
+    }
+    return QXD_OK;
+  }
+  QXD_CUDA(lat, cudaMemcpyAsync(hbad + 1, bad, sizeof(int), cudaMemcpyDeviceToHost, lat->stream));
+  QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  if (hbad[1]) return fail(lat, QXD_EINVAL, "update_links: a link index is outside 0 .. 4 V - 1 (skipped)");
+  return QXD_OK;
+}
+
 qxd_status qxd_set_ipt_blocks(qxd_lattice* lat, const int B[4]) {
   QXD_TRACE();
   CHECK_LAT(lat);

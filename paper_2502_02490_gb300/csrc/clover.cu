@@ -122,6 +122,33 @@ __device__ __forceinline__ i64 site_of(const Geom& g, const int y[4]) {
   return (i64)par * g.sv + (lexi(g, y) >> 1);
 }
 
+// Fhat = (Q - Q^+)/8 made traceless, and fhat, stored as 10 doubles of stride st at o: Im F_00,
+// Im F_11, Im F_22, (Re, Im) F_01, F_02, F_12 (the rest follows from anti-Hermiticity), fhat.
+__device__ __forceinline__ void store_fs(const M3& Q, double f1, double* __restrict__ o, i64 st) {
+  M3 F;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const cd a = Q.m[3 * i + j], b = Q.m[3 * j + i];
+      F.m[3 * i + j] = mk((a.re - b.re) * 0.125, (a.im + b.im) * 0.125);
+    }
+  const double tr_im = (F.m[0].im + F.m[4].im + F.m[8].im) / 3.0;
+  F.m[0].im -= tr_im;
+  F.m[4].im -= tr_im;
+  F.m[8].im -= tr_im;
+  o[0 * st] = F.m[0].im;
+  o[1 * st] = F.m[4].im;
+  o[2 * st] = F.m[8].im;
+  o[3 * st] = F.m[1].re;
+  o[4 * st] = F.m[1].im;
+  o[5 * st] = F.m[2].re;
+  o[6 * st] = F.m[2].im;
+  o[7 * st] = F.m[5].re;
+  o[8 * st] = F.m[5].im;
+  o[9 * st] = f1;
+}
+
 // The four leaves of the plane (MU, NU) at x from the half-products of the plaquettes around it:
 //   leaf 1 = A(x) B(x)^+,  leaf 2 = U_nu(x) B(x-mu)^+ U_mu(x-mu),  leaf 3 = B(x-mu-nu)^+ A(x-mu-nu),
 //   leaf 4 = U_nu(x-nu)^+ A(x-nu) U_mu(x)^+
@@ -159,30 +186,69 @@ __global__ void __launch_bounds__(128) k_clover_leaves(Geom g, const double2* __
 #pragma unroll
       for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
     }
-    M3 F;
+    store_fs(Q, 0.25 * (sn[s0] + sn[s1] + sn[s2] + sn[s3]), Fb + (i64)p * 10 * st + s0, st);
+  }
+}
+
+// The link-update path: the field strength of the plane (MU, NU) at listed sites only (list
+// entries par * Vh + cb), each leaf multiplied out from the links (3 products per leaf) and the
+// U(1) part from the four plaquette angles; written in the layout of k_clover_leaves at list
+// position e with stride nl.
+template <int MU, int NU>
+__global__ void __launch_bounds__(128) k_fs_sites(Geom g, const double2* __restrict__ U, const double* __restrict__ A,
+                                                  const uint32_t* __restrict__ list, i64 nl, int p,
+                                                  double* __restrict__ Fc) {
+  for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < nl; e += (i64)gridDim.x * blockDim.x) {
+    const i64 t = list[e];
+    const int par = t >= g.Vh ? 1 : 0;
+    int x[4];
+    cb_coords(g, t - (i64)par * g.Vh, par, x);
+    int xpm[4] = {x[0], x[1], x[2], x[3]}, xpn[4] = {x[0], x[1], x[2], x[3]};
+    int xm[4] = {x[0], x[1], x[2], x[3]}, xn[4] = {x[0], x[1], x[2], x[3]};
+    step(g, xpm, MU, +1);
+    step(g, xpn, NU, +1);
+    step(g, xm, MU, -1);
+    step(g, xn, NU, -1);
+    int xmn[4] = {xm[0], xm[1], xm[2], xm[3]}, xmpn[4] = {xm[0], xm[1], xm[2], xm[3]};
+    int xnpm[4] = {xn[0], xn[1], xn[2], xn[3]};
+    step(g, xmn, NU, -1);
+    step(g, xmpn, NU, +1);
+    step(g, xnpm, MU, +1);
+    // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+    M3 Q = mul<false, true>(mul<false, true>(mul<false, false>(load_u(g, U, x, MU), load_u(g, U, xpm, NU)),
+                                             load_u(g, U, xpn, MU)),
+                            load_u(g, U, x, NU));
+    // leaf 2: U_nu(x) U_mu(x-mu+nu)^+ U_nu(x-mu)^+ U_mu(x-mu)
+    {
+      const M3 r = mul<false, false>(mul<false, true>(mul<false, true>(load_u(g, U, x, NU), load_u(g, U, xmpn, MU)),
+                                                      load_u(g, U, xm, NU)),
+                                     load_u(g, U, xm, MU));
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
+    }
+    // leaf 3: U_mu(x-mu)^+ U_nu(x-mu-nu)^+ U_mu(x-mu-nu) U_nu(x-nu)
+    {
+      const M3 r = mul<false, false>(mul<false, false>(mul<true, true>(load_u(g, U, xm, MU), load_u(g, U, xmn, NU)),
+                                                       load_u(g, U, xmn, MU)),
+                                     load_u(g, U, xn, NU));
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const cd a = Q.m[3 * i + j], b = Q.m[3 * j + i];
-        F.m[3 * i + j] = mk((a.re - b.re) * 0.125, (a.im + b.im) * 0.125);
-      }
-    const double tr_im = (F.m[0].im + F.m[4].im + F.m[8].im) / 3.0;
-    F.m[0].im -= tr_im;
-    F.m[4].im -= tr_im;
-    F.m[8].im -= tr_im;
-    const double f1 = 0.25 * (sn[s0] + sn[s1] + sn[s2] + sn[s3]);
-    double* o = Fb + (i64)p * 10 * st + s0;
-    o[0 * st] = F.m[0].im;
-    o[1 * st] = F.m[4].im;
-    o[2 * st] = F.m[8].im;
-    o[3 * st] = F.m[1].re;
-    o[4 * st] = F.m[1].im;
-    o[5 * st] = F.m[2].re;
-    o[6 * st] = F.m[2].im;
-    o[7 * st] = F.m[5].re;
-    o[8 * st] = F.m[5].im;
-    o[9 * st] = f1;
+      for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
+    }
+    // leaf 4: U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^+
+    {
+      const M3 r = mul<false, true>(mul<false, false>(mul<true, false>(load_u(g, U, xn, NU), load_u(g, U, xn, MU)),
+                                                      load_u(g, U, xnpm, NU)),
+                                    load_u(g, U, x, MU));
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
+    }
+    // U(1): plaquette angle th(c) = A_mu(c) + A_nu(c+mu) - A_mu(c+nu) - A_nu(c) at the corners
+    // x, x-mu, x-mu-nu, x-nu of the four leaves
+    const double s0 = sin(load_a(g, A, x, MU) + load_a(g, A, xpm, NU) - load_a(g, A, xpn, MU) - load_a(g, A, x, NU));
+    const double s1 = sin(load_a(g, A, xm, MU) + load_a(g, A, x, NU) - load_a(g, A, xmpn, MU) - load_a(g, A, xm, NU));
+    const double s2 = sin(load_a(g, A, xmn, MU) + load_a(g, A, xn, NU) - load_a(g, A, xm, MU) - load_a(g, A, xmn, NU));
+    const double s3 = sin(load_a(g, A, xn, MU) + load_a(g, A, xnpm, NU) - load_a(g, A, x, MU) - load_a(g, A, xn, NU));
+    store_fs(Q, 0.25 * (s0 + s1 + s2 + s3), Fc + (i64)p * 10 * nl + e, nl);
   }
 }
 
@@ -242,13 +308,17 @@ __device__ __forceinline__ void pack_block(const cd blk[36], double r[36]) {
 
 // A_+- of every site from the stored field strengths: G^{+-}_l = F_{0l} -+ sgn_l F_mag(l) with the
 // magnetic planes (2,3), (1,3), (1,2) of sign +1, -1, +1; one chiral block at a time.
+// With a list (link-update path) only the listed sites, their field strengths at list position e
+// with stride nl.
 __global__ void __launch_bounds__(128) k_clover_assemble(Geom g, const double* __restrict__ Fb, double diag, double csw,
-                                                         double cq, double2* __restrict__ C) {
-  const i64 n = 2 * g.Vh, st = 2 * g.sv;
+                                                         double cq, double2* __restrict__ C,
+                                                         const uint32_t* __restrict__ list, i64 nl) {
+  const i64 n = list ? nl : 2 * g.Vh, st = list ? nl : 2 * g.sv;
   for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x) {
-    const int par = e >= g.Vh ? 1 : 0;
-    const i64 cb = e - (i64)par * g.Vh;
-    const i64 s = (i64)par * g.sv + cb;
+    const i64 t = list ? (i64)list[e] : e;
+    const int par = t >= g.Vh ? 1 : 0;
+    const i64 cb = t - (i64)par * g.Vh;
+    const i64 s = list ? e : (i64)par * g.sv + cb;
 #pragma unroll
     for (int blkid = 0; blkid < 2; ++blkid) {
       cd blk[36];
@@ -343,12 +413,20 @@ __device__ __forceinline__ void gj_unswap(cd a[6][6], const int piv[6]) {
 // predicated; the row permutation is undone as column swaps at the end).  A block whose pivot
 // falls below 1e-14 times its largest entry sets *bad.  Only the odd-site inverse is used
 // (A_oo^-1 of the Schur complement and of the reconstruction).
+// With a list (link-update path): the odd listed sites only.
 __global__ void __launch_bounds__(128) k_clover_invert(Geom g, const double2* __restrict__ C,
-                                                       double2* __restrict__ Ci, int* __restrict__ bad) {
-  const i64 n = 2 * g.Vh;  // (odd site, block)
+                                                       double2* __restrict__ Ci, int* __restrict__ bad,
+                                                       const uint32_t* __restrict__ list, i64 nl) {
+  const i64 nsites = list ? nl : g.Vh;
+  const i64 n = 2 * nsites;  // (odd site, block)
   for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
-    const int blkid = (int)(t / g.Vh);
-    const i64 cb = t - (i64)blkid * g.Vh;
+    const int blkid = (int)(t / nsites);
+    i64 cb = t - (i64)blkid * nsites;
+    if (list) {
+      const i64 v = list[cb];
+      if (v < g.Vh) continue;  // even site: no inverse needed
+      cb = v - g.Vh;
+    }
     const double2* in = C + (i64)((2 + blkid) * 18) * g.sv + cb;
     // packed: pairs 0..2 the six real diagonal entries, pairs 3..17 the strict upper triangle
     cd a[6][6];
@@ -406,12 +484,22 @@ __global__ void __launch_bounds__(128) k_clover_invert(Geom g, const double2* __
   }
 }
 
+// With a list (link-update path): the two blocks of each listed site.
 __global__ void k_clover_low(Geom g, const double2* __restrict__ C, float4* __restrict__ C32,
                              uint2* __restrict__ C16, float* __restrict__ C16n, uint2* __restrict__ CB,
-                             float* __restrict__ CBn) {
-  i64 n = 4 * g.sv;  // (parity, block, site incl. padding)
+                             float* __restrict__ CBn, const uint32_t* __restrict__ list, i64 nl) {
+  i64 n = list ? 2 * nl : 4 * g.sv;  // (parity, block, site incl. padding) or (listed site, block)
   for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
-    i64 pb = t / g.sv, cb = t - pb * g.sv;
+    i64 pb, cb;
+    if (list) {
+      const i64 v = list[t >> 1];
+      const int par = v >= g.Vh ? 1 : 0;
+      pb = 2 * par + (t & 1);
+      cb = v - (i64)par * g.Vh;
+    } else {
+      pb = t / g.sv;
+      cb = t - pb * g.sv;
+    }
     const double2* in = C + pb * 18 * g.sv + cb;
     float r[36];
     float m = 0.f;
@@ -475,7 +563,7 @@ qxd_status clover_build(qxd_lattice* lat) {
 #undef QXD_PLANE
   if (le == cudaSuccess) {
     k_clover_assemble<<<grid_cap(2 * g.Vh, 128), 128, 0, lat->stream>>>(g, Fb, 4.0 + lat->m0, lat->csw,
-                                                                        lat->q * lat->csw_qed, lat->C64);
+                                                                        lat->q * lat->csw_qed, lat->C64, nullptr, 0);
     le = cudaGetLastError();
     if (le == cudaSuccess) lat->launches++;
   }
@@ -488,18 +576,50 @@ qxd_status clover_build(qxd_lattice* lat) {
   if (st) return st;
   int* bad = (int*)w;
   QXD_CUDA(lat, cudaMemsetAsync(bad, 0, sizeof(int), lat->stream));
-  k_clover_invert<<<grid_cap(2 * g.Vh, 128), 128, 0, lat->stream>>>(g, lat->C64, lat->Ci64, bad);
+  k_clover_invert<<<grid_cap(2 * g.Vh, 128), 128, 0, lat->stream>>>(g, lat->C64, lat->Ci64, bad, nullptr, 0);
   QXD_CHECK_LAUNCH(lat, "k_clover_invert");
   k_clover_low<<<grid_cap(4 * g.sv, 128), 128, 0, lat->stream>>>(g, lat->C64, lat->C32, lat->C16, lat->C16n,
-                                                                 lat->CB16, lat->CB16n);
+                                                                 lat->CB16, lat->CB16n, nullptr, 0);
   QXD_CHECK_LAUNCH(lat, "k_clover_low");
   k_clover_low<<<grid_cap(4 * g.sv, 128), 128, 0, lat->stream>>>(g, lat->Ci64, lat->Ci32, lat->Ci16, lat->Ci16n,
-                                                                 lat->CiB16, lat->CiB16n);
+                                                                 lat->CiB16, lat->CiB16n, nullptr, 0);
   QXD_CHECK_LAUNCH(lat, "k_clover_low");
   int hbad = 0;
   QXD_CUDA(lat, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, lat->stream));
   QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
   if (hbad) return fail(lat, QXD_ESINGULAR, "a clover block on an odd site is not invertible");
+  return QXD_OK;
+}
+
+// Rebuild the clover blocks (A, the odd-site inverse and the FP32 / 16-bit copies) at the nl
+// listed sites only (list entries par * Vh + cb, on the device), after a link update changed the
+// plaquettes around them.  Same arithmetic as clover_build, with each leaf multiplied out from the
+// links (12 products per site and plane) since the listed sites share no half-products.
+qxd_status clover_rebuild_sites(qxd_lattice* lat, const uint32_t* list, i64 nl, double* Fc, int* bad) {
+  const Geom& g = lat->g;
+  if (nl <= 0) return QXD_OK;
+  const int gc = grid_cap(nl, 128);
+#define QXD_PLANE_SITES(P, M, N)                                                                \
+  k_fs_sites<M, N><<<gc, 128, 0, lat->stream>>>(g, lat->U, lat->A, list, nl, P, Fc);            \
+  QXD_CHECK_LAUNCH(lat, "k_fs_sites");
+  QXD_PLANE_SITES(0, 0, 1)
+  QXD_PLANE_SITES(1, 0, 2)
+  QXD_PLANE_SITES(2, 0, 3)
+  QXD_PLANE_SITES(3, 2, 3)
+  QXD_PLANE_SITES(4, 1, 3)
+  QXD_PLANE_SITES(5, 1, 2)
+#undef QXD_PLANE_SITES
+  k_clover_assemble<<<gc, 128, 0, lat->stream>>>(g, Fc, 4.0 + lat->m0, lat->csw, lat->q * lat->csw_qed, lat->C64,
+                                                 list, nl);
+  QXD_CHECK_LAUNCH(lat, "k_clover_assemble");
+  k_clover_invert<<<grid_cap(2 * nl, 128), 128, 0, lat->stream>>>(g, lat->C64, lat->Ci64, bad, list, nl);
+  QXD_CHECK_LAUNCH(lat, "k_clover_invert");
+  k_clover_low<<<grid_cap(2 * nl, 128), 128, 0, lat->stream>>>(g, lat->C64, lat->C32, lat->C16, lat->C16n, lat->CB16,
+                                                               lat->CB16n, list, nl);
+  QXD_CHECK_LAUNCH(lat, "k_clover_low");
+  k_clover_low<<<grid_cap(2 * nl, 128), 128, 0, lat->stream>>>(g, lat->Ci64, lat->Ci32, lat->Ci16, lat->Ci16n,
+                                                               lat->CiB16, lat->CiB16n, list, nl);
+  QXD_CHECK_LAUNCH(lat, "k_clover_low");
   return QXD_OK;
 }
 

@@ -187,6 +187,126 @@ qxd_status ingest_gauge(qxd_lattice* lat, const double2* su3, const double* a) {
   return QXD_OK;
 }
 
+// Link update on the device (the resident field changes in place, no host transfer).  Link j is
+// entry idx[j] = 4 s + mu of the canonical arrays load_gauge took (s: the physical site in the
+// lattice's site order); its new value is su3[j] (3x3 row-major) and a[j] (or 0 without angles).
+// Every device copy of the link (two with C*: the site and its mirror, conjugated with the angle
+// negated) gets U, A and the hop link W = exp(i q A) U in FP64, FP32 and both 16-bit formats, and
+// the clover sites whose plaquettes hold the link are marked in mask[par * Vh + cb]: the link's
+// two end points x and x + mu, each also shifted by +-nu for every nu != mu.  An index outside
+// the lattice sets *bad and is skipped.
+__device__ __forceinline__ void mark_site(const Geom& g, int y[4], unsigned char* mask) {
+  const int par = (y[0] + y[1] + y[2] + y[3]) & 1;
+  mask[(i64)par * g.Vh + (lexi(g, y) >> 1)] = 1;
+}
+
+__device__ __forceinline__ void shift_site(const Geom& g, int y[4], int mu, int dir) {
+  y[mu] += dir;
+  bool crossed = false;
+  if (y[mu] >= g.L[mu]) {
+    y[mu] = 0;
+    crossed = true;
+  } else if (y[mu] < 0) {
+    y[mu] = g.L[mu] - 1;
+    crossed = true;
+  }
+  if (crossed && g.shift && mu >= 2) {
+    y[1] += g.shift;
+    if (y[1] >= g.L[1]) y[1] -= g.L[1];
+  }
+}
+
+__global__ void k_update_links(Geom g, int order, int Lp1, int Lp2, int Lp3, i64 n, const int64_t* __restrict__ idx,
+                               const double2* __restrict__ su3, const double* __restrict__ a, double q,
+                               double2* __restrict__ U, double* __restrict__ A, double2* __restrict__ W,
+                               float2* __restrict__ W32, uint32_t* __restrict__ W16, uint32_t* __restrict__ WB16,
+                               unsigned char* __restrict__ mask, int* __restrict__ bad) {
+  const int Lp[4] = {g.L[0], Lp1, Lp2, Lp3};
+  const i64 Vp = (i64)Lp[0] * Lp1 * Lp2 * Lp3;
+  for (i64 j = blockIdx.x * (i64)blockDim.x + threadIdx.x; j < n; j += (i64)gridDim.x * blockDim.x) {
+    const int64_t e = idx[j];
+    if (e < 0 || e >= 4 * Vp) {
+      atomicOr(bad, 1);
+      continue;
+    }
+    const int mu = (int)(e & 3);
+    const i64 src = e >> 2;
+    int x[4];
+    if (order == QXD_ORDER_IPT) {
+      int Bp[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) Bp[m] = g.B[m] == g.L[m] ? Lp[m] : g.B[m];
+      ipt_coords(Lp, Bp, src, x);
+    } else {
+      i64 t = src;
+      x[3] = (int)(t % Lp3);
+      t /= Lp3;
+      x[2] = (int)(t % Lp2);
+      t /= Lp2;
+      x[1] = (int)(t % Lp1);
+      x[0] = (int)(t / Lp1);
+    }
+    const double ang0 = a ? a[j] : 0.0;
+    for (int copy = 0; copy < (g.shift ? 2 : 1); ++copy) {
+      int y[4] = {x[0], x[1] + copy * g.shift, x[2], x[3]};  // copy 1: the C* mirror
+      const double ang = copy ? -ang0 : ang0;
+      double sn, cs;
+      sincos(q * ang, &sn, &cs);
+      const int par = (y[0] + y[1] + y[2] + y[3]) & 1;
+      const i64 cb = lexi(g, y) >> 1;
+      const i64 base = ((i64)(par * 4 + mu) * 9) * g.sv + cb;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        double2 u = su3[j * 9 + k];
+        if (copy) u.y = -u.y;
+        const double2 w = make_double2(cs * u.x - sn * u.y, cs * u.y + sn * u.x);
+        U[base + k * g.sv] = u;
+        W[base + k * g.sv] = w;
+        W32[base + k * g.sv] = make_float2((float)w.x, (float)w.y);
+        W16[base + k * g.sv] = H16::pack((float)w.x, (float)w.y);
+        WB16[base + k * g.sv] = B16::pack((float)w.x, (float)w.y);
+      }
+      A[(i64)(par * 4 + mu) * g.sv + cb] = ang;
+      for (int end = 0; end < 2; ++end) {
+        int z[4] = {y[0], y[1], y[2], y[3]};
+        if (end) shift_site(g, z, mu, +1);
+        mark_site(g, z, mask);
+        for (int nu = 0; nu < 4; ++nu) {
+          if (nu == mu) continue;
+          int zp[4] = {z[0], z[1], z[2], z[3]}, zm[4] = {z[0], z[1], z[2], z[3]};
+          shift_site(g, zp, nu, +1);
+          shift_site(g, zm, nu, -1);
+          mark_site(g, zp, mask);
+          mark_site(g, zm, mask);
+        }
+      }
+    }
+  }
+}
+
+// Marked sites -> a list of par * Vh + cb (order immaterial); *count must start at 0.
+__global__ void k_compact_mask(i64 n, const unsigned char* __restrict__ mask, uint32_t* __restrict__ list,
+                               unsigned int* __restrict__ count) {
+  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x)
+    if (mask[t]) list[atomicAdd(count, 1u)] = (uint32_t)t;
+}
+
+qxd_status update_links(qxd_lattice* lat, i64 n, const int64_t* idx, const double2* su3, const double* a,
+                        unsigned char* mask, int* bad) {
+  k_update_links<<<grid_cap(n, 128), 128, 0, lat->stream>>>(lat->g, lat->order, lat->Lphys[1], lat->Lphys[2],
+                                                            lat->Lphys[3], n, idx, su3, a, lat->q, lat->U, lat->A,
+                                                            lat->W64, lat->W32, lat->W16, lat->WB16, mask, bad);
+  QXD_CHECK_LAUNCH(lat, "k_update_links");
+  return QXD_OK;
+}
+
+qxd_status compact_mask(qxd_lattice* lat, const unsigned char* mask, uint32_t* list, unsigned int* count) {
+  const i64 n = 2 * lat->Vh;
+  k_compact_mask<<<grid_cap(n, 256), 256, 0, lat->stream>>>(n, mask, list, count);
+  QXD_CHECK_LAUNCH(lat, "k_compact_mask");
+  return QXD_OK;
+}
+
 // FP64 hop links -> FP32 and the two 16-bit formats (unitary links need no scale).
 __global__ void k_links_low(i64 n, const double2* __restrict__ W, float2* __restrict__ W32,
                             uint32_t* __restrict__ W16, uint32_t* __restrict__ WB16) {

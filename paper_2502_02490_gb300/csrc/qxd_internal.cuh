@@ -593,7 +593,7 @@ struct Field64 {  // FP64 full field: two parities of double2 [12][sv]
 // device work buffers owned by a lattice (allocated on first use, grown on demand): slots 0..28 the
 // single-RHS solvers, 24..27 API staging, 29 and 31 FGCR vectors (31 also the training set), 30 the
 // clover singular flag, 32..38 multi-RHS, 39 network application, 40 FGCR coefficients
-#define QXD_WORK_SLOTS 48
+#define QXD_WORK_SLOTS 52
 struct qxd_lattice {
   qxd::Geom g;
   // device state of qxd_solve_batch when this lattice leads a batch (freed with the lattice)
@@ -709,6 +709,11 @@ qxd_status n16_to_f32(qxd_lattice* lat, const uint2* in, const float* nrm, float
 
 // ---- clover.cu ----
 qxd_status clover_build(qxd_lattice* lat);
+qxd_status clover_rebuild_sites(qxd_lattice* lat, const uint32_t* list, i64 nl, double* Fc, int* bad);
+// link update on the device (layout.cu): scatter, re-derive W, mark the clover sites it touches
+qxd_status update_links(qxd_lattice* lat, i64 n, const int64_t* idx, const double2* su3, const double* a,
+                        unsigned char* mask, int* bad);
+qxd_status compact_mask(qxd_lattice* lat, const unsigned char* mask, uint32_t* list, unsigned int* count);
 qxd_status clover_export(qxd_lattice* lat, double* bnd);
 // out = C in on one parity (site-local); which = 0 clover, 1 inverse
 qxd_status clover_apply64(qxd_lattice* lat, int par, int which, const double2* in, double2* out);

@@ -60,6 +60,7 @@ _SIGS = {
     "qxd_create_lattice": [C.POINTER(C.c_int), _i, _i, _i, _vp, C.POINTER(_vp)],
     "qxd_destroy_lattice": [_vp],
     "qxd_load_gauge": [_vp, _vp, _vp, _d, _i],
+    "qxd_update_links": [_vp, _i64, _vp, _vp, _vp, _i],
     "qxd_build_clover": [_vp, _d, _d, _d],
     "qxd_get_clover": [_vp, _vp, _i],
     "qxd_apply_D": [_vp, _vp, _vp, _i, _i, _i],
@@ -152,6 +153,18 @@ def load_gauge(lat, su3, a_u1, q):
     p, dev = _ptr(su3)
     pa, _ = _ptr(a_u1)
     _check(lib.qxd_load_gauge(lat, p, pa, float(q), int(dev)), lat)
+
+
+def update_links(lat, idx, su3, a_u1=None):
+    """qxd_update_links: replace the links idx (int64 entries 4 s + mu) with su3 [n][3][3] complex
+    (and angles a_u1 [n]); host arrays or CUDA tensors, all of the same kind."""
+    pi, dev = _ptr(idx)
+    pu, dev2 = _ptr(su3)
+    pa, dev3 = _ptr(a_u1)
+    if dev != dev2 or (a_u1 is not None and dev3 != dev):
+        raise ValueError("idx, su3 and a_u1 must all be host or all be device buffers")
+    n = idx.shape[0] if hasattr(idx, "shape") else len(idx)
+    _check(lib.qxd_update_links(lat, int(n), pi, pu, pa, int(dev)), lat)
 
 
 def set_ipt_blocks(lat, B):
