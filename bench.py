@@ -60,7 +60,7 @@ WORKLOADS = {
 }
 WORKLOAD = dict(WORKLOADS["c2"])
 KSTAT = {0: "hop_f64", 1: "hop_f32", 2: "hop_f16n", 3: "hop_bf16n", 4: "hop_f32_mrhs", 5: "batch_f32",
-         6: "ptc_layer_bf16_tc", 7: "ptc_layer_f32", 8: "hop_n16_mrhs"}
+         6: "ptc_layer_bf16_tc", 7: "ptc_layer_f32", 8: "hop_n16_mrhs", 9: "sap_block_mr"}
 PREC_NAMES = {"f32": 1, "f16n": 2, "bf16n": 3}
 FP64_REPEATS = 3
 # Algorithmic bytes of one Dhat application per even site: 2 hops (4 spinors of the precision,
@@ -643,8 +643,12 @@ def run_c4(args):
 
         res = {"m0": m0,
                "fp64_eocg": timed_solve(solver=qxd.SOLVER_CG_EO, tol=1e-10, maxiter=20000),
-               "mp_bicgstab_f16n": timed_solve(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=qxd.F16N, tol=1e-10),
+               "mp_cg_eo_f32": timed_solve(solver=qxd.SOLVER_MP_CG_EO, inner_prec=qxd.F32, tol=1e-10,
+                                           maxiter=20000),
+               "mp_bicgstab_f16n": timed_solve(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=qxd.F16N, tol=1e-10,
+                                               restart_f32=0),
                "mp_bicgstab_f32": timed_solve(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=qxd.F32, tol=1e-10),
+               "mp_cgnr_no_net": timed_solve(solver=qxd.SOLVER_MP_CGNR, tol=1e-10, net=None, maxiter=20000),
                "fgcr_no_net": timed_solve(solver=qxd.SOLVER_MP_FGCR_NET, inner_prec=qxd.F32, tol=1e-10,
                                           gcr_restart=32, net=None, maxiter=args.fgcr_maxiter)}
         qxd.apply_D(lat, bte, vte, qxd.F32, nrhs=ntest)
@@ -663,7 +667,8 @@ def run_c4(args):
                 "heldout_loss_before": l0 / ntest / V, "heldout_loss_after": l1 / ntest / V,
                 "heldout_rel_err_after": float(np.sqrt(l1 / ntest / (24.0 * V))),
                 "fgcr": timed_solve(solver=qxd.SOLVER_MP_FGCR_NET, inner_prec=qxd.F32, tol=1e-10, gcr_restart=32,
-                                    net=net, maxiter=args.fgcr_maxiter)}
+                                    net=net, maxiter=args.fgcr_maxiter),
+                "cgnr": timed_solve(solver=qxd.SOLVER_MP_CGNR, tol=1e-10, net=net, maxiter=20000)}
             # the same network with its channel mix in FP32 on the CUDA cores
             qxd.net_set_precision(net, qxd.NET_F32)
             nets["x".join(map(str, chans))]["fgcr_net_f32"] = timed_solve(
@@ -671,14 +676,19 @@ def run_c4(args):
                 maxiter=args.fgcr_maxiter)
             qxd.net_destroy(net)
         res["nets"] = nets
-        ok = [d["fgcr"]["seconds"] for d in nets.values() if d["fgcr"]["status"] == "OK"]
+        ok = [d[k]["seconds"] for d in nets.values() for k in ("fgcr", "cgnr") if d[k]["status"] == "OK"]
         res["learned_vs_fp64_eocg_speedup"] = (res["fp64_eocg"]["seconds"] / min(ok)) if ok else None
+        plain = [v["seconds"] for k, v in res.items() if isinstance(v, dict) and v.get("status") == "OK"
+                 and k != "fp64_eocg"]
+        res["fastest_plain_solver_s"] = min(plain) if plain else None
         results[point] = res
         qxd.destroy_lattice(lat)
     return {"metric": METRIC, "workload": w["name"], "sites": V, "points": results,
             "note": "losses per site; held-out set of 16 (D v, v) pairs not used in training; "
                     "heldout_rel_err = sqrt(loss / ||v||^2); fgcr: network channel mix in BF16 on the tensor "
-                    "cores (default), fgcr_net_f32: the same network in FP32 on the CUDA cores"}
+                    "cores (default), fgcr_net_f32: the same network in FP32 on the CUDA cores; cgnr: CG on the "
+                    "normal equations of D M on the full lattice (M the network in BF16, M^+ its adjoint "
+                    "network); mp_cgnr_no_net: the same with M = 1; seconds: one solve after a short warm-up"}
 
 
 def profile_run(args):

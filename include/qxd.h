@@ -91,8 +91,14 @@ typedef enum {
   QXD_SOLVER_MP_FGCR_NET = 3,    /* FP64 outer defect correction around flexible GCR(gcr_restart) on
                                    the full D in FP32 with the learned network `net` as right
                                    preconditioner (net NULL: no preconditioner) */
-  QXD_SOLVER_MP_SAP_GCR = 4      /* as MP_FGCR_NET with the Schwarz alternating procedure as the
+  QXD_SOLVER_MP_SAP_GCR = 4,     /* as MP_FGCR_NET with the Schwarz alternating procedure as the
                                    preconditioner (sap_block, sap_ncy, sap_nmr; qxd_sap_apply) */
+  QXD_SOLVER_MP_CGNR = 5         /* FP64 outer defect correction around CG on the normal equations
+                                   (D M)^+ D M y = (D M)^+ r of the full lattice in FP32, x += M y,
+                                   with the learned network `net` as M (NULL: M = 1) and its adjoint
+                                   network as M^+; FP32 reliable updates (reliable_delta).  Converges
+                                   for any invertible D, also where D is indefinite and GCR or
+                                   BiCGStab stagnate or break down; inner_prec is not used */
 } qxd_solver;
 
 typedef struct {
@@ -316,6 +322,12 @@ qxd_status qxd_net_destroy(qxd_net *net);
 int64_t qxd_net_num_weights(const qxd_net *net); /* complex weights */
 qxd_status qxd_net_set_weights(qxd_net *net, const double *w); /* host [n][2] */
 qxd_status qxd_net_get_weights(const qxd_net *net, double *w);
+/* out = M^+ in, the adjoint network: the layers last to first, each with the weights
+ * Omega[c][c'][p] -> Omega[c][c'][p']^+ of the opposite path p' (the adjoint of the transport along
+ * p is the transport along -p, and it commutes with the spin matrices), in the net's precision.
+ * <phi, M psi> = <M^+ phi, psi> up to rounding.  Layout and errors as qxd_net_apply. */
+qxd_status qxd_net_apply_adjoint(qxd_net *net, double *out, const double *in, int on_device);
+
 /* Inference precision of qxd_net_apply and of the network inside QXD_SOLVER_MP_FGCR_NET:
  * QXD_NET_BF16_TC (default): each layer's channel mix on the tensor cores (tcgen05), BF16
  *   transported activations and weights, FP32 accumulation and FP32 activations between layers;
@@ -392,7 +404,8 @@ qxd_status qxd_vec_dot_noalloc(const double *a, const double *b, int64_t n, doub
  * (0 = FP64 hop, 1 = FP32 hop, 2 = FP16N hop, 3 = BF16N hop, 4 = FP32 multi-RHS hop, 5 = the
  * persistent batch kernel of qxd_solve_batch, counted on the batch's first lattice, 6 = tensor-core
  * PTC layer, 7 = FP32 PTC layer; bytes of a PTC layer: input channels, links and output channels
- * once per site; 8 = 16-bit multi-RHS hop), the number of timed launches, their
+ * once per site; 8 = 16-bit multi-RHS hop; 9 = SAP block sweep, bytes: residual, x read and
+ * written, links and clover once per site of the colour), the number of timed launches, their
  * summed device time in ms and the summed algorithmic bytes they moved.  Reading the stats
  * synchronises the stream.  qxd_launch_count is the number of kernels the library launched. */
 qxd_status qxd_set_profiling(qxd_lattice *lat, int on);

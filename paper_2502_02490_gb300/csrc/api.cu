@@ -670,7 +670,7 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
   TRY(params_current(lat, p, &pv));
   p = &pv;
   if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO && p->solver != QXD_SOLVER_MP_BICGSTAB_EO &&
-      p->solver != QXD_SOLVER_MP_FGCR_NET && p->solver != QXD_SOLVER_MP_SAP_GCR)
+      p->solver != QXD_SOLVER_MP_FGCR_NET && p->solver != QXD_SOLVER_MP_SAP_GCR && p->solver != QXD_SOLVER_MP_CGNR)
     return fail(lat, QXD_EINVAL, "bad solver");
   if (p->solver == QXD_SOLVER_MP_SAP_GCR) {
     TRY(sap_check(lat, p->sap_block));

@@ -281,6 +281,20 @@ qxd_status cg_update_xs_32(qxd_lattice* lat, float4* x, const float4* p, float4*
   QXD_CHECK_LAUNCH(lat, "k_cg_xs_32");
   return QXD_OK;
 }
+// The same updates on full fields [2][6][sv]: the kernels walk 6 planes of stride 2 sv, which
+// visits every float4 of the field once (the update is elementwise, the norm a plain sum).
+qxd_status cg_update_xs_32_full(qxd_lattice* lat, float4* x, const float4* p, float4* s, const float4* q) {
+  const i64 st = 2 * lat->sv;
+  k_cg_xs_32<H16, false><<<site_grid(lat, st), RB, 0, lat->stream>>>(x, p, s, q, st, nullptr, nullptr, RED_ARGS);
+  QXD_CHECK_LAUNCH(lat, "k_cg_xs_32");
+  return QXD_OK;
+}
+qxd_status cg_update_p_32_full(qxd_lattice* lat, const float4* r, float4* p) {
+  const i64 st = 2 * lat->sv;
+  k_cg_p_32<H16, false><<<site_grid(lat, st), RB, 0, lat->stream>>>(r, p, st, nullptr, nullptr, lat->ticket, lat->scal);
+  QXD_CHECK_LAUNCH(lat, "k_cg_p_32");
+  return QXD_OK;
+}
 qxd_status cg_update_p_64(qxd_lattice* lat, const double2* r, double2* p, i64 n) {
   k_cg_p_64<<<site_grid(lat, n), RB, 0, lat->stream>>>(r, p, n, lat->ticket, lat->scal);
   QXD_CHECK_LAUNCH(lat, "k_cg_p_64");

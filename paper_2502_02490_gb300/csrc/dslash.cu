@@ -46,6 +46,7 @@ static qxd_status launch_hop(qxd_lattice* lat, int par, int epi, int g5, SIN in,
   } else
   QXD_HOP_CASE(EPI_HOP, false)
   QXD_HOP_CASE(EPI_DFULL, false)
+  QXD_HOP_CASE(EPI_DFULL, true)
   QXD_HOP_CASE(EPI_INV, false)
   QXD_HOP_CASE(EPI_INV, true)
   QXD_HOP_CASE(EPI_DHAT2, false)

@@ -1,7 +1,8 @@
 // The hop at one output site with its fused epilogue, shared by the hop kernels and the batched
 // persistent solver.  (H psi)(x) = sum_mu [(1 - gamma_mu) W_mu(x) psi(x+mu)
 //                                       + (1 + gamma_mu) W_mu(x-mu)^dag psi(x-mu)]
-// Epilogues: HOP: out = coef H in;  DFULL: out = A same - 1/2 H in;  INV: out = A^-1 (coef H g5? in);
+// Epilogues: HOP: out = coef H in;  DFULL: out = A same - 1/2 g5? H g5? in (with g5: the parity block
+//            of D^+ = gamma5 D gamma5, since A commutes with gamma5);  INV: out = A^-1 (coef H g5? in);
 //            DHAT2: out = A same + coef g5? H in;  XPAY: out = same + coef H in;
 //            INVXPAY: out = A^-1 (same + coef H in).
 #pragma once
@@ -114,7 +115,7 @@ __device__ __forceinline__ void hop_site(const Geom& g, int par, uint32_t cb, co
   cplx<R> acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = mk((R)0, (R)0);
-  constexpr bool G5IN = G5 && (EPI == EPI_INV);
+  constexpr bool G5IN = G5 && (EPI == EPI_INV || EPI == EPI_DFULL);
   leg_step<0, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
   leg_step<1, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
   leg_step<2, PF, R, SIN, LNK, G5IN>(g, par, cb, nb, cr_f, cr_b, in, lk, sr, lr, acc);
@@ -159,7 +160,7 @@ __device__ __forceinline__ void hop_site(const Geom& g, int par, uint32_t cb, co
     load_same(v);
     cmul(v, y);
     R c = EPI == EPI_DFULL ? (R)-0.5 : coef;
-    if (EPI == EPI_DHAT2 && G5) {
+    if ((EPI == EPI_DHAT2 || EPI == EPI_DFULL) && G5) {  // DFULL: A same - 1/2 gamma5 H gamma5 in
 #pragma unroll
       for (int k = 6; k < 12; ++k) acc[k] = neg(acc[k]);
     }

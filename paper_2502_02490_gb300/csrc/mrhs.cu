@@ -1,8 +1,8 @@
 // Multi-right-hand-side hop (FP32): one link and clover load serves R right-hand sides.
 //
-// A block covers 32 consecutive output sites (threadIdx.x) times R right-hand sides
-// (threadIdx.y).  Phase 1: 256 threads compute the 8 neighbour indices of the 32 sites into
-// shared memory.  Phase 2: the block loads the 32 sites' 8 links (forward links of the sites,
+// A block covers 32 consecutive output sites (threadIdx.x) times up to 12 right-hand sides
+// (threadIdx.y; rows beyond the launch's count only help load).  Phase 1: 256 threads compute the
+// 8 neighbour indices of the 32 sites into shared memory.  Phase 2: the block loads the 32 sites' 8 links (forward links of the sites,
 // backward links of their neighbours) and, when the epilogue needs it, the clover block pair
 // into shared memory, coalesced across sites.  Phase 3: every thread applies the hop for its
 // (site, rhs) with links and clover from shared memory and its neighbour spinors from global
@@ -79,46 +79,62 @@ __global__ void __launch_bounds__(MR_SITES* MR_MAXR, 2) k_hop_mrhs(Geom g, int p
                                                                const float4* __restrict__ C, float coef) {
   __shared__ MrShared sh;
   const int s = threadIdx.x, r = threadIdx.y;
-  const int tid = r * MR_SITES + s, nthr = MR_SITES * nr;
+  constexpr int NTHR = MR_SITES * MR_MAXR;  // the block always has MR_MAXR rows; rows >= nr only load
+  const int tid = r * MR_SITES + s, nthr = NTHR;
   const uint32_t cb0 = blockIdx.x * MR_SITES;
-  // phase 1: neighbour table
-  for (int e = tid; e < 8 * MR_SITES; e += nthr) {
-    const int ss = e % MR_SITES, leg = e / MR_SITES;
+  // phase 1: neighbour table (legs unrolled: register-only index math)
+  for (int ss = tid; ss < MR_SITES; ss += nthr) {
     const uint32_t cb = cb0 + ss;
-    uint32_t nbv = 0;
-    bool cr = false;
-    if (cb < (uint32_t)g.Vh) {
-      int x[4];
-      cb_coords32(g, cb, par, x);
-      nbv = nbr_cb32(g, x, leg >> 1, (leg & 1) ? -1 : +1, cr);
+    const bool live = cb < (uint32_t)g.Vh;
+    int x[4] = {0, 0, 0, 0};
+    if (live) cb_coords32(g, cb, par, x);
+#pragma unroll
+    for (int leg = 0; leg < 8; ++leg) {
+      bool cr = false;
+      const uint32_t nbv = live ? nbr_cb32(g, x, leg >> 1, (leg & 1) ? -1 : +1, cr) : 0u;
+      sh.nb[leg][ss] = nbv;
+      if (leg < 2) sh.cross[leg][ss] = cr && live;
     }
-    sh.nb[leg][ss] = nbv;
-    if (leg == 0) sh.cross[0][ss] = cr;
-    if (leg == 1) sh.cross[1][ss] = cr;
   }
   __syncthreads();
-  // phase 2: links (and clover)
-  for (int e = tid; e < 8 * 9 * MR_SITES; e += nthr) {
+  // phase 2: links (and clover), every load of a thread issued before its first shared store
+  // (compile-time trip counts): one memory round trip per block
+  constexpr int NL = (8 * 9 * MR_SITES + NTHR - 1) / NTHR;
+  constexpr bool NEEDC = EPI != EPI_HOP && EPI != EPI_XPAY;
+  constexpr int NC = NEEDC ? (2 * 9 * MR_SITES + NTHR - 1) / NTHR : 0;
+  float2 wl[NL];
+  float4 cvl[NC > 0 ? NC : 1];
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    const int e = tid + i * NTHR;
     const int ss = e % MR_SITES, rest = e / MR_SITES, leg = rest / 9, k = rest % 9;
     const uint32_t cb = cb0 + ss;
-    float2 w = make_float2(0.f, 0.f);
-    if (cb < (uint32_t)g.Vh) {
+    wl[i] = make_float2(0.f, 0.f);
+    if (e < 8 * 9 * MR_SITES && cb < (uint32_t)g.Vh) {
       const int mu = leg >> 1;
       const bool fwd = (leg & 1) == 0;
       const int lp = fwd ? par : 1 - par;
       const uint32_t site = fwd ? cb : sh.nb[leg][ss];
-      w = __ldg(W + ((i64)(lp * 4 + mu) * 9 + k) * g.sv + site);
+      wl[i] = __ldg(W + ((i64)(lp * 4 + mu) * 9 + k) * g.sv + site);
     }
-    sh.link[leg][k][ss] = w;
   }
-  constexpr bool NEEDC = EPI != EPI_HOP && EPI != EPI_XPAY;
-  if (NEEDC) {
-    for (int e = tid; e < 2 * 9 * MR_SITES; e += nthr) {
-      const int ss = e % MR_SITES, rest = e / MR_SITES, blk = rest / 9, k = rest % 9;
-      const uint32_t cb = cb0 + ss;
-      sh.clov[blk][k][ss] =
-          cb < (uint32_t)g.Vh ? __ldg(C + ((i64)(par * 2 + blk) * 9 + k) * g.sv + cb) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    const int e = tid + i * NTHR;
+    const int ss = e % MR_SITES, rest = e / MR_SITES, blk = rest / 9, k = rest % 9;
+    const uint32_t cb = cb0 + ss;
+    cvl[i] = (e < 2 * 9 * MR_SITES && cb < (uint32_t)g.Vh) ? __ldg(C + ((i64)(par * 2 + blk) * 9 + k) * g.sv + cb)
+                                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    const int e = tid + i * NTHR;
+    if (e < 8 * 9 * MR_SITES) sh.link[(e / MR_SITES) / 9][(e / MR_SITES) % 9][e % MR_SITES] = wl[i];
+  }
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    const int e = tid + i * NTHR;
+    if (e < 2 * 9 * MR_SITES) sh.clov[(e / MR_SITES) / 9][(e / MR_SITES) % 9][e % MR_SITES] = cvl[i];
   }
   __syncthreads();
   const uint32_t cb = cb0 + s;
@@ -185,7 +201,7 @@ qxd_status hop32_mrhs(qxd_lattice* lat, int par, int epi, int g5, const float4* 
   const Geom& g = lat->g;
   for (int r0 = 0; r0 < nrhs; r0 += MR_MAXR) {
     const int nr = nrhs - r0 < MR_MAXR ? nrhs - r0 : MR_MAXR;
-    dim3 grid((unsigned)((g.Vh + MR_SITES - 1) / MR_SITES)), block(MR_SITES, nr);
+    dim3 grid((unsigned)((g.Vh + MR_SITES - 1) / MR_SITES)), block(MR_SITES, MR_MAXR);  // rows >= nr only load
     const float4* i0 = in + r0 * rs;
     const float4* s0 = same ? same + r0 * rs : nullptr;
     float4* o0 = out + r0 * rs;
@@ -291,6 +307,7 @@ __global__ void __launch_bounds__(MR16_SITES* NRB, MINB)
   const int tid = rb * S + s, nthr = S * NRB;
   const uint32_t cb0 = blockIdx.x * S;
   const i64 sv = g.sv;
+  (void)nthr;
   // phase 1: backward neighbours of the tile (directions unrolled: register-only index math)
   for (int ss = tid; ss < S; ss += nthr) {
     const uint32_t cb = cb0 + ss;
@@ -304,31 +321,59 @@ __global__ void __launch_bounds__(MR16_SITES* NRB, MINB)
     }
   }
   __syncthreads();
-  // phase 2: the tile's links and clover (coalesced across sites)
-  for (int e = tid; e < 8 * 9 * S; e += nthr) {
+  // phase 2: the tile's links and clover (coalesced across sites).  The trip counts are compile-
+  // time constants so that every load of a thread is issued before the first store to shared
+  // memory: one memory round trip per block instead of one per loop iteration.
+  constexpr int NTHR = S * NRB;
+  constexpr int NL = (8 * 9 * S + NTHR - 1) / NTHR;
+  constexpr bool NEEDC = EPI != EPI_HOP && EPI != EPI_XPAY;
+  constexpr int NC = NEEDC ? (2 * 9 * S + NTHR - 1) / NTHR : 0;
+  constexpr int NN = NEEDC ? (2 * S + NTHR - 1) / NTHR : 0;
+  uint32_t wl[NL];
+  uint2 cvl[NC > 0 ? NC : 1];
+  float cnl[NN > 0 ? NN : 1];
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    const int e = tid + i * NTHR;
     const int ss = e % S, rest = e / S, leg = rest / 9, k = rest % 9;
     const uint32_t cb = cb0 + ss;
-    uint32_t w = 0u;
-    if (cb < (uint32_t)g.Vh) {
+    wl[i] = 0u;
+    if (e < 8 * 9 * S && cb < (uint32_t)g.Vh) {
       const int mu = leg >> 1;
       const bool fwd = (leg & 1) == 0;
       const int lp = fwd ? par : 1 - par;
-      w = __ldg(W + ((i64)(lp * 4 + mu) * 9 + k) * sv + (fwd ? cb : sh.nbb[mu][ss]));
+      wl[i] = __ldg(W + ((i64)(lp * 4 + mu) * 9 + k) * sv + (fwd ? cb : sh.nbb[mu][ss]));
     }
-    sh.link[leg][k][ss] = w;
   }
-  constexpr bool NEEDC = EPI != EPI_HOP && EPI != EPI_XPAY;
-  if (NEEDC) {
-    for (int e = tid; e < 2 * 9 * S; e += nthr) {
-      const int ss = e % S, rest = e / S, blk = rest / 9, k = rest % 9;
-      const uint32_t cb = cb0 + ss;
-      sh.clov[blk][k][ss] = cb < (uint32_t)g.Vh ? __ldg(C + ((i64)(par * 2 + blk) * 9 + k) * sv + cb) : make_uint2(0u, 0u);
-    }
-    for (int e = tid; e < 2 * S; e += nthr) {
-      const int ss = e % S, blk = e / S;
-      const uint32_t cb = cb0 + ss;
-      sh.cn[blk][ss] = cb < (uint32_t)g.Vh ? __ldg(Cn + (i64)(par * 2 + blk) * sv + cb) : 0.f;
-    }
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    const int e = tid + i * NTHR;
+    const int ss = e % S, rest = e / S, blk = rest / 9, k = rest % 9;
+    const uint32_t cb = cb0 + ss;
+    cvl[i] = (e < 2 * 9 * S && cb < (uint32_t)g.Vh) ? __ldg(C + ((i64)(par * 2 + blk) * 9 + k) * sv + cb)
+                                                 : make_uint2(0u, 0u);
+  }
+#pragma unroll
+  for (int i = 0; i < NN; ++i) {
+    const int e = tid + i * NTHR;
+    const int ss = e % S, blk = e / S;
+    const uint32_t cb = cb0 + ss;
+    cnl[i] = (e < 2 * S && cb < (uint32_t)g.Vh) ? __ldg(Cn + (i64)(par * 2 + blk) * sv + cb) : 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    const int e = tid + i * NTHR;
+    if (e < 8 * 9 * S) sh.link[(e / S) / 9][(e / S) % 9][e % S] = wl[i];
+  }
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    const int e = tid + i * NTHR;
+    if (e < 2 * 9 * S) sh.clov[(e / S) / 9][(e / S) % 9][e % S] = cvl[i];
+  }
+#pragma unroll
+  for (int i = 0; i < NN; ++i) {
+    const int e = tid + i * NTHR;
+    if (e < 2 * S) sh.cn[e / S][e % S] = cnl[i];
   }
   __syncthreads();
   const uint32_t cb = cb0 + s;

@@ -318,6 +318,12 @@ struct qxd_net {
   bool bp_valid = false;        // packed weights match w
   int* tc_err = nullptr;        // error word of the tensor-core kernel
   float4* tc_scratch = nullptr; // virtual channels of pull-form layers
+  // the adjoint network M^+ (layers in reverse, each the adjoint layer): its FP32 weights and
+  // their tensor-core packing, rebuilt from w when adj_valid is false
+  float2* wadj_all = nullptr;
+  unsigned char* bpadj = nullptr;
+  i64 bpadjoff[9] = {0};
+  bool adj_valid = false;
 };
 
 namespace qxd {
@@ -363,6 +369,45 @@ qxd_status net_apply32(qxd_net* net, const float4* in, float4* out) {
                         net->tc_err);
     else
       st = layer_fwd(net, l, h, o, false);
+    if (st) return st;
+    h = o;
+  }
+  return QXD_OK;
+}
+
+// M^+(in): the adjoint network, for the normal-equation solver that uses M as a right
+// preconditioner.  The adjoint of a layer with weights Omega[c][c'][p] is the layer from the c
+// channels to the c' channels with weights Omega[c][c'][swap p]^+ (the transport of path p has
+// the transport of the opposite path as adjoint, and it commutes with the spin matrices); the
+// adjoint network runs those layers last to first.  Same precision as net_apply32.
+qxd_status net_apply_adj32(qxd_net* net, const float4* in, float4* out) {
+  qxd_lattice* lat = net->lat;
+  qxd_status st;
+  if (!net->adj_valid) {
+    for (int l = 0; l < net->nlayers; ++l) {
+      const int ci = net->ch[l], co = net->ch[l + 1];
+      k_ptc_adjoint_weights<<<ew_grid(ci * co * 9), 256, 0, lat->stream>>>(ci, co, net->w + net->woff[l],
+                                                                           net->wadj_all + net->woff[l]);
+      QXD_CHECK_LAUNCH(lat, "k_ptc_adjoint_weights");
+      if ((st = ptc_pack_weights(lat, co, ci, net->wadj_all + net->woff[l], net->bpadj + net->bpadjoff[l]))) return st;
+    }
+    net->adj_valid = true;
+  }
+  const float4* h = in;
+  for (int i = 0; i < net->nlayers; ++i) {
+    const int l = net->nlayers - 1 - i;
+    const int ci = net->ch[l + 1], co = net->ch[l];
+    float4* o = (l == 0) ? out : net->act[l];
+    if (net->prec == QXD_NET_BF16_TC) {
+      st = ptc_layer_tc(lat, ci, co, h, net->bpadj + net->bpadjoff[l], o, net->tc_scratch, net->tc_err);
+    } else {
+      dim3 grid((unsigned)((lat->Vh + PT_SITES - 1) / PT_SITES), 2), block(PT_SITES, co);
+      prof_begin(lat, KSTAT_PTC_F32, (96.0 * (ci + co) + 576.0) * (double)lat->V);
+      k_ptc_layer<<<grid, block, 0, lat->stream>>>(lat->g, ci, co, h, net->wadj_all + net->woff[l], lat->W32, o);
+      prof_end(lat);
+      QXD_CHECK_LAUNCH(lat, "k_ptc_layer");
+      st = QXD_OK;
+    }
     if (st) return st;
     h = o;
   }
@@ -461,8 +506,17 @@ qxd_status qxd_net_create(qxd_lattice* lat, int nlayers, const int* channels, ui
     bpb += (i64)ptc_tc_packed_bytes(channels[l], channels[l + 1]);
   }
   ok = ok && cudaMalloc(&net->bp, (size_t)bpb) == cudaSuccess;
+  i64 bpa = 0;  // the adjoint layers (c -> c') packed
+  for (int l = 0; l < nlayers; ++l) {
+    net->bpadjoff[l] = bpa;
+    bpa += (i64)ptc_tc_packed_bytes(channels[l + 1], channels[l]);
+  }
+  ok = ok && cudaMalloc(&net->bpadj, (size_t)bpa) == cudaSuccess &&
+       cudaMalloc(&net->wadj_all, sizeof(float2) * off) == cudaSuccess;
   size_t scr = 0;
-  for (int l = 0; l < nlayers; ++l) scr = std::max(scr, ptc_tc_pull_scratch(channels[l], channels[l + 1], lat->sv));
+  for (int l = 0; l < nlayers; ++l)
+    scr = std::max(scr, std::max(ptc_tc_pull_scratch(channels[l], channels[l + 1], lat->sv),
+                                 ptc_tc_pull_scratch(channels[l + 1], channels[l], lat->sv)));
   if (scr) ok = ok && cudaMalloc(&net->tc_scratch, sizeof(float4) * scr) == cudaSuccess;
   if (ok) cudaMemsetAsync(net->tc_err, 0, sizeof(int), lat->stream);
   for (int l = 1; l <= nlayers && ok; ++l) ok = cudaMalloc(&net->act[l], sizeof(float4) * cs * channels[l]) == cudaSuccess;
@@ -503,8 +557,8 @@ qxd_status qxd_net_destroy(qxd_net* net) {
   QXD_TRACE();
   if (!net) return QXD_OK;
   if (net->lat) cudaStreamSynchronize(net->lat->stream);
-  void* b[] = {net->w, net->wadj, net->grad, net->am, net->av, net->part, net->gbuf[0], net->gbuf[1], net->bp,
-               net->tc_err, net->tc_scratch};
+  void* b[] = {net->w,     net->wadj,       net->grad,   net->am,     net->av,     net->part,    net->gbuf[0],
+               net->gbuf[1], net->bp,        net->tc_err, net->tc_scratch, net->bpadj, net->wadj_all};
   for (void* p : b)
     if (p) cudaFree(p);
   for (int l = 1; l <= net->nlayers; ++l)
@@ -544,6 +598,21 @@ static qxd_status from_internal32(qxd_lattice* lat, const float4* src, int on_de
   QXD_CUDA(lat, cudaMemcpyAsync(dst, bo, vb, cudaMemcpyDeviceToHost, lat->stream));
   QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
   return QXD_OK;
+}
+
+qxd_status qxd_net_apply_adjoint(qxd_net* net, double* out, const double* in, int on_device) {
+  QXD_TRACE();
+  if (!net || !out || !in) return QXD_EINVAL;
+  qxd_lattice* lat = net->lat;
+  float4 *a, *b;
+  const size_t fb = sizeof(float4) * 12 * lat->sv;
+  qxd_status st;
+  if ((st = ensure_work(lat, 39, 2 * fb, (void**)&a))) return st;
+  b = a + 12 * lat->sv;
+  if ((st = to_internal32(lat, in, on_device, a))) return st;
+  if ((st = net_apply_adj32(net, a, b))) return st;
+  if ((st = net_check(net))) return st;
+  return from_internal32(lat, b, on_device, out);
 }
 
 qxd_status qxd_net_apply(qxd_net* net, double* out, const double* in, int on_device) {
@@ -611,6 +680,7 @@ static qxd_status train_on_set(qxd_net* net, const float4* set, int nsamp, const
                                                         (float)p->lr, b1, b2, eps, c1, c2, 1.f / (float)(s1 - s0));
       QXD_CHECK_LAUNCH(lat, "k_adam");
       net->bp_valid = false;
+      net->adj_valid = false;
     }
     if (loss_hist) loss_hist[e] = epoch_loss / nsamp;
   }
@@ -795,6 +865,7 @@ qxd_status qxd_net_set_weights(qxd_net* net, const double* w) {
   QXD_CUDA(net->lat, cudaMemcpyAsync(net->w, h.data(), sizeof(float2) * net->nw, cudaMemcpyHostToDevice, net->lat->stream));
   QXD_CUDA(net->lat, cudaStreamSynchronize(net->lat->stream));
   net->bp_valid = false;
+  net->adj_valid = false;
   return QXD_OK;
 }
 

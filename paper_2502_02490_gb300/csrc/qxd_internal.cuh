@@ -571,7 +571,8 @@ enum {
   KSTAT_PTC_TC = 6,   // tensor-core PTC layer
   KSTAT_PTC_F32 = 7,  // FP32 CUDA-core PTC layer
   KSTAT_N16_MRHS = 8, // 16-bit multi-RHS hop
-  KSTAT_N = 9
+  KSTAT_SAP = 9,      // SAP block minimal-residual sweep
+  KSTAT_N = 10
 };
 
 // Device scalar slots used by the solvers and reductions.
@@ -593,7 +594,7 @@ struct Field64 {  // FP64 full field: two parities of double2 [12][sv]
 // device work buffers owned by a lattice (allocated on first use, grown on demand): slots 0..28 the
 // single-RHS solvers, 24..27 API staging, 29 and 31 FGCR vectors (31 also the training set), 30 the
 // clover singular flag, 32..38 multi-RHS, 39 network application, 40 FGCR coefficients
-#define QXD_WORK_SLOTS 52
+#define QXD_WORK_SLOTS 58
 struct qxd_lattice {
   qxd::Geom g;
   // device state of qxd_solve_batch when this lattice leads a batch (freed with the lattice)
@@ -765,6 +766,8 @@ qxd_status cg_update_xs_32(qxd_lattice* lat, float4* x, const float4* p, float4*
 //   p = r + (scal[SC_GAMMA_NEW] / scal[SC_GAMMA]) p; then scal[SC_GAMMA] = scal[SC_GAMMA_NEW]
 qxd_status cg_update_p_64(qxd_lattice* lat, const double2* r, double2* p, i64 n);
 qxd_status cg_update_p_32(qxd_lattice* lat, const float4* r, float4* p, uint2* p16, float* p16n, int bf16);
+qxd_status cg_update_xs_32_full(qxd_lattice* lat, float4* x, const float4* p, float4* s, const float4* q);
+qxd_status cg_update_p_32_full(qxd_lattice* lat, const float4* r, float4* p);
 qxd_status read_scalars(qxd_lattice* lat, int first, int count, double* out);
 qxd_status set_scalar(qxd_lattice* lat, int slot, double v);
 // y += x (FP32 x widened into FP64 y), n = complex entries of y
@@ -807,6 +810,7 @@ qxd_status solve(qxd_lattice* lat, double2* x_field, const double2* b_field, con
 qxd_status apply_D64(qxd_lattice* lat, const double2* in, double2* out);
 // ---- ptc.cu ----
 qxd_status net_apply32(qxd_net* net, const float4* in, float4* out);  // full FP32 fields
+qxd_status net_apply_adj32(qxd_net* net, const float4* in, float4* out);  // the adjoint network M^+
 qxd_status net_check(qxd_net* net);  // error word of the tensor-core layers (synchronises)
 size_t ptc_tc_packed_bytes(int cin, int cout);
 qxd_status ptc_pack_weights(qxd_lattice* lat, int cin, int cout, const float2* Om, void* Bp);

@@ -24,6 +24,9 @@
 namespace qxd {
 
 constexpr int SAP_MAXVB = 256;
+#ifndef QXD_SAP_MINB
+#define QXD_SAP_MINB 2  // resident CTAs of 256 threads per SM: caps the block kernel at 128 registers
+#endif
 
 struct SapGeom {
   int b[4];       // block extents
@@ -96,7 +99,7 @@ __device__ __forceinline__ void sap_leg(const Geom& g, const SapGeom& sg, const 
 // nmr minimal-residual steps on every block of one colour: e = 0, rr = r on the block;
 // each step: a = D_Lambda rr, alpha = <a, rr> / <a, a>, e += alpha rr, rr -= alpha a.
 // Then x += e.  r and x are full FP32 fields (parity planes [2][6][sv]).
-__global__ void __launch_bounds__(SAP_MAXVB) k_sap_block_mr(Geom g, SapGeom sg, int colour, int nmr,
+__global__ void __launch_bounds__(SAP_MAXVB, QXD_SAP_MINB) k_sap_block_mr(Geom g, SapGeom sg, int colour, int nmr,
                                                             const float4* __restrict__ r, float4* __restrict__ x,
                                                             const float2* __restrict__ W,
                                                             const float4* __restrict__ C) {
@@ -120,20 +123,24 @@ __global__ void __launch_bounds__(SAP_MAXVB) k_sap_block_mr(Geom g, SapGeom sg, 
   const int par = (xg[0] + xg[1] + xg[2] + xg[3]) & 1;
   const i64 cb = lexi(g, xg) >> 1;
   const i64 base = (i64)par * 6 * g.sv + cb;
-  cplx<float> e[12], me[12];
+  // this site's residual lives only in shared memory (rr), where the neighbours read it too
+  auto my_rr = [&](cplx<float> v[12]) {
 #pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    const float4 q = __ldg(r + base + (i64)j * g.sv);
-    rr[j * sg.vb + s] = q;
-    me[2 * j] = mk(q.x, q.y);
-    me[2 * j + 1] = mk(q.z, q.w);
-  }
+    for (int j = 0; j < 6; ++j) {
+      const float4 q = rr[j * sg.vb + s];
+      v[2 * j] = mk(q.x, q.y);
+      v[2 * j + 1] = mk(q.z, q.w);
+    }
+  };
+  cplx<float> e[12];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) rr[j * sg.vb + s] = __ldg(r + base + (i64)j * g.sv);
 #pragma unroll
   for (int k = 0; k < 12; ++k) e[k] = mk(0.f, 0.f);
   __syncthreads();
   for (int it = 0; it < nmr; ++it) {
-    // a = D_Lambda rr at this site: A rr - 1/2 (the hops inside the block)
-    cplx<float> acc[12], a[12];
+    // a = D_Lambda rr at this site: A rr - 1/2 (the hops inside the block), built in acc
+    cplx<float> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = mk(0.f, 0.f);
     sap_leg<0>(g, sg, W, rr, s, lc, xg, par, acc);
@@ -144,6 +151,8 @@ __global__ void __launch_bounds__(SAP_MAXVB) k_sap_block_mr(Geom g, SapGeom sg, 
     sap_leg<5>(g, sg, W, rr, s, lc, xg, par, acc);
     sap_leg<6>(g, sg, W, rr, s, lc, xg, par, acc);
     sap_leg<7>(g, sg, W, rr, s, lc, xg, par, acc);
+    cplx<float> me[12];
+    my_rr(me);
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk) {
       float cl[36];
@@ -155,16 +164,19 @@ __global__ void __launch_bounds__(SAP_MAXVB) k_sap_block_mr(Geom g, SapGeom sg, 
         cl[4 * k + 2] = c.z;
         cl[4 * k + 3] = c.w;
       }
-      herm6_apply<float>(cl, me + 6 * blk, a + 6 * blk);
+      cplx<float> y[6];
+      herm6_apply<float>(cl, me + 6 * blk, y);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[6 * blk + k] = y[k] + (-0.5f) * acc[6 * blk + k];
     }
     float p_re = 0.f, p_im = 0.f, p_nn = 0.f;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      a[k] = a[k] + (-0.5f) * acc[k];
+      const cplx<float> a = acc[k];
       // <a, rr> = sum conj(a) rr and ||a||^2
-      p_re = fmaf(a[k].re, me[k].re, fmaf(a[k].im, me[k].im, p_re));
-      p_im = fmaf(a[k].re, me[k].im, fmaf(-a[k].im, me[k].re, p_im));
-      p_nn = fmaf(a[k].re, a[k].re, fmaf(a[k].im, a[k].im, p_nn));
+      p_re = fmaf(a.re, me[k].re, fmaf(a.im, me[k].im, p_re));
+      p_im = fmaf(a.re, me[k].im, fmaf(-a.im, me[k].re, p_im));
+      p_nn = fmaf(a.re, a.re, fmaf(a.im, a.im, p_nn));
     }
     part[s] = p_re;
     part[SAP_MAXVB + s] = p_im;
@@ -186,10 +198,11 @@ __global__ void __launch_bounds__(SAP_MAXVB) k_sap_block_mr(Geom g, SapGeom sg, 
     }
     __syncthreads();
     const cplx<float> alpha = mk(alpha_sm[0], alpha_sm[1]);
+    my_rr(me);  // reloaded: fewer live registers across the reduction
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       e[k] = cmac(e[k], alpha, me[k]);
-      me[k] = me[k] - cmul(alpha, a[k]);
+      me[k] = me[k] - cmul(alpha, acc[k]);
     }
 #pragma unroll
     for (int j = 0; j < 6; ++j)
@@ -228,8 +241,12 @@ qxd_status sap32(qxd_lattice* lat, const int b[4], int ncy, int nmr, const float
   const float4* rcur = rin;
   for (int cy = 0; cy < ncy; ++cy) {
     for (int colour = 0; colour < 2; ++colour) {
+      // algorithmic bytes of a sweep, per site of the colour: the residual read, x read and
+      // written, 8 links and the clover pair once (the MR steps re-read them through L1/L2)
+      prof_begin(lat, KSTAT_SAP, (3 * 96.0 + 8 * 72.0 + 288.0) * (double)lat->Vh);
       k_sap_block_mr<<<sg.nblocks, sg.vb, smem, lat->stream>>>(lat->g, sg, colour, nmr, rcur, z, lat->W32,
                                                                 lat->C32);
+      prof_end(lat);
       QXD_CHECK_LAUNCH(lat, "k_sap_block_mr");
       if (cy == ncy - 1 && colour == 1) break;  // the last sweep needs no new residual
       // r = rin - D z with the full FP32 operator

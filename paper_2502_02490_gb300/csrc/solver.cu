@@ -5,6 +5,8 @@
 //
 // CG_EO     : CG on Dhat^+ Dhat psi_e = Dhat^+ eta_hat_e (tracking s = eta_hat - Dhat psi_e), all FP64,
 //             the plain FP64 even-odd CG baseline.  Judged by the full FP64 true residual.
+// MP_CGNR   : FP64 outer defect correction around an inner full-lattice CGNR on D M in FP32 (M the
+//             learned network or 1), robust where D is indefinite (below).
 // MP_CG_EO  : FP64 outer defect correction r = eta - D psi (FP64 D, FP64 norms), around an inner
 //             CG whose iteration runs in FP32 vectors with the Dhat applications in inner_prec
 //             (FP32, or 16-bit spinors/links/clover with per-site norms), with FP32 reliable
@@ -376,6 +378,92 @@ static qxd_status inner_bicg(qxd_lattice* lat, int prec, const float4* bh, float
   return QXD_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Inner CGNR on the full lattice, FP32, right-preconditioned by the network M (or M = 1):
+// CG on (D M)^+ (D M) y = (D M)^+ rhs, accumulating the correction e = M y directly (e += alpha
+// M p, since M is linear), s = rhs - D e tracked, FP32 reliable updates recompute s = rhs - D e
+// when ||s|| has fallen by delta.  The normal equations are Hermitian positive definite whatever
+// the spectrum of D, so the iteration converges where GCR and BiCGStab stagnate on an indefinite
+// D; M^+ is the adjoint network and D^+ = gamma5 D gamma5.
+// ------------------------------------------------------------------------------------------
+enum { WS_NR_S = 52, WS_NR_Z, WS_NR_P, WS_NR_W, WS_NR_Q, WS_NR_T };
+
+static qxd_status cgnr32(qxd_lattice* lat, qxd_net* net, const float4* rhs, float4* e, double target, double delta,
+                         int maxiter, int check_every, int* iters, int* nrel) {
+  const i64 sv = lat->sv, n4 = 12 * sv;
+  const size_t fb = sizeof(float4) * n4;
+  float4 *s, *z, *p, *w, *q, *t;
+  TRY(get(lat, WS_NR_S, fb, &s));
+  TRY(get(lat, WS_NR_Z, fb, &z));
+  TRY(get(lat, WS_NR_P, fb, &p));
+  TRY(get(lat, WS_NR_W, fb, &w));
+  TRY(get(lat, WS_NR_Q, fb, &q));
+  TRY(get(lat, WS_NR_T, fb, &t));
+  // out = D in (dag: D^+ = gamma5 D gamma5), full FP32 fields
+  auto dfull = [&](const float4* in, float4* out, int dag) -> qxd_status {
+    TRY(hop32(lat, 0, EPI_DFULL, dag, in + 6 * sv, in, out, 0.f));
+    return hop32(lat, 1, EPI_DFULL, dag, in, in + 6 * sv, out + 6 * sv, 0.f);
+  };
+  // out = M^+ D^+ in
+  auto normal_rhs = [&](const float4* in, float4* out) -> qxd_status {
+    if (!net) return dfull(in, out, 1);
+    TRY(dfull(in, t, 1));
+    return net_apply_adj32(net, t, out);
+  };
+  TRY(blas_copy(lat, s, rhs, fb));
+  TRY(blas_zero(lat, e, fb));
+  TRY(normal_rhs(s, z));
+  TRY(blas_copy(lat, p, z, fb));
+  TRY(blas_norm2_32(lat, z, n4, SC_GAMMA));
+  TRY(blas_norm2_32(lat, s, n4, SC_SS));
+  double ss;
+  TRY(read_scalars(lat, SC_SS, 1, &ss));
+  double rmax = std::sqrt(ss);
+  int it = 0, rel = 0;
+  while (std::sqrt(ss) > target && it < maxiter) {
+    const float4* wp = p;
+    if (net) {
+      TRY(net_apply32(net, p, w));  // w = M p
+      wp = w;
+    }
+    TRY(dfull(wp, q, 0));                                     // q = D M p
+    TRY(blas_norm2_32(lat, q, n4, SC_QQ));
+    TRY(cg_update_xs_32_full(lat, e, wp, s, q));              // e += alpha M p, s -= alpha q, ||s||^2
+    TRY(normal_rhs(s, z));                                    // z = M^+ D^+ s
+    TRY(blas_norm2_32(lat, z, n4, SC_GAMMA_NEW));
+    TRY(cg_update_p_32_full(lat, z, p));                      // p = z + beta p
+    ++it;
+    if (it % check_every == 0) {
+      TRY(read_scalars(lat, SC_SS, 1, &ss));
+      if (!std::isfinite(ss)) {  // e keeps what it had before this check
+        *iters = it;
+        *nrel = rel;
+        return fail(lat, QXD_ENOCONV, "non-finite residual in the inner CGNR");
+      }
+      const double sn = std::sqrt(ss);
+      if (sn > rmax) rmax = sn;
+      if (sn < delta * rmax || sn <= target) {
+        // reliable update: s = rhs - D e in FP32; keep p, refresh z and gamma
+        TRY(dfull(e, q, 0));
+        TRY(blas_copy(lat, s, rhs, fb));
+        TRY(blas_axpy_32(lat, -1.0f, q, s, n4));
+        TRY(blas_norm2_32(lat, s, n4, SC_SS));
+        TRY(read_scalars(lat, SC_SS, 1, &ss));
+        rmax = std::sqrt(ss);
+        ++rel;
+        if (std::sqrt(ss) > target) {
+          TRY(normal_rhs(s, z));
+          TRY(blas_norm2_32(lat, z, n4, SC_GAMMA));
+        }
+      }
+    }
+  }
+  *iters = it;
+  *nrel = rel;
+  if (net) TRY(net_check(net));
+  return QXD_OK;
+}
+
 // The inner flexible GCR of QXD_SOLVER_MP_FGCR_NET lives in fgcr.cu (device-resident coefficients).
 qxd_status fgcr32(qxd_lattice* lat, qxd_net* net, const SapSpec* sap, int m, int reorth, const float4* rhs, float4* y,
                   double target, int maxiter, int check_every, int* iters);
@@ -455,6 +543,7 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
   TRY(get(lat, WS_TO64, hb, &to));
   const bool mp = prm->solver == QXD_SOLVER_MP_CG_EO || prm->solver == QXD_SOLVER_MP_BICGSTAB_EO;
   const bool gcr = prm->solver == QXD_SOLVER_MP_FGCR_NET || prm->solver == QXD_SOLVER_MP_SAP_GCR;
+  const bool cgnr = prm->solver == QXD_SOLVER_MP_CGNR;
   float4 *bh32 = nullptr, *y32 = nullptr, *r32 = nullptr, *to32 = nullptr;
   if (mp) {
     TRY(get(lat, WS_BH32, sizeof(float4) * 12 * sv, &bh32));  // sized for full fields (apply_D_prec shares it)
@@ -521,7 +610,20 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
     qxd_status ist = QXD_OK;
     auto inner_status = [&](qxd_status s) -> bool { ist = s; return s == QXD_OK || s == QXD_ENOCONV; };
     const double target = 0.5 * prm->tol * bnorm;
-    if (gcr) {
+    if (cgnr) {
+      // the correction D e = r on the full lattice by CGNR on D M (M the network, or 1), FP32
+      float4 *r32f, *e32;
+      TRY(get(lat, WS_R32, sizeof(float4) * 12 * sv, &r32f));
+      TRY(get(lat, WS_BH32, sizeof(float4) * 12 * sv, &e32));
+      TRY(f64_to_f32(lat, r, r32f, 12 * sv));
+      double inner_target = prm->inner_tol * rnorm;
+      if (inner_target < target) inner_target = target;
+      if (!inner_status(cgnr32(lat, const_cast<qxd_net*>(prm->net), r32f, e32, inner_target, prm->reliable_delta,
+                               prm->maxiter - total, prm->check_every > 0 ? prm->check_every : 1, &it, &nrel)))
+        return ist;
+      if (ist != QXD_OK) TRY(blas_copy(lat, tf, x, fb));
+      TRY(blas_acc_f32_into_f64(lat, e32, x, 12 * sv));
+    } else if (gcr) {
       // the correction D e = r on the full lattice by FGCR with the network or SAP, FP32
       float4 *r32f, *e32;
       TRY(get(lat, WS_R32, sizeof(float4) * 12 * sv, &r32f));

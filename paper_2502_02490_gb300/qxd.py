@@ -24,7 +24,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESINGULAR", "ENOCONV", "ESTA
 BC_PERIODIC, BC_ANTIPERIODIC = 0, 1
 ORDER_LEXI, ORDER_IPT = 0, 1
 F64, F32, F16N, BF16N = 0, 1, 2, 3
-SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO, SOLVER_MP_FGCR_NET, SOLVER_MP_SAP_GCR = 0, 1, 2, 3, 4
+SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO, SOLVER_MP_FGCR_NET, SOLVER_MP_SAP_GCR, SOLVER_MP_CGNR = range(6)
 PARAMS_VERSION = 5
 TRAIN_VERSION = 2
 PREC = {"f64": F64, "f32": F32, "f16n": F16N, "bf16n": BF16N}
@@ -83,6 +83,7 @@ _SIGS = {
     "qxd_net_set_weights": [_vp, _vp],
     "qxd_net_get_weights": [_vp, _vp],
     "qxd_net_apply": [_vp, _vp, _vp, _i],
+    "qxd_net_apply_adjoint": [_vp, _vp, _vp, _i],
     "qxd_set_ipt_blocks": [_vp, C.POINTER(C.c_int)],
     "qxd_load_gauge_openqxd": [_vp, _vp, _vp, _d, _i],
     "qxd_net_set_precision": [_vp, _i],
@@ -351,6 +352,13 @@ def net_apply(net, out, inp):
     po, dev = _ptr(out)
     pi, _ = _ptr(inp)
     _check(lib.qxd_net_apply(net, po, pi, int(dev)))
+
+
+def net_apply_adjoint(net, out, inp):
+    """qxd_net_apply_adjoint: out = M^+ inp."""
+    po, dev = _ptr(out)
+    pi, _ = _ptr(inp)
+    _check(lib.qxd_net_apply_adjoint(net, po, pi, int(dev)))
 
 
 def net_loss_grad(net, v, b, nsamp, want_grad=True):

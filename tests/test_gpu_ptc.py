@@ -174,3 +174,69 @@ def test_train_precond_matches_host_samples(qxd, L, cstar):
         for n in nets:
             qxd.net_destroy(n)
         c.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16_tc"])
+@pytest.mark.parametrize("L,cstar,chans", [((4, 2, 2, 4), False, [1, 3, 2, 1]), ((2, 2, 4, 2), True, [1, 4, 1]),
+                                           ((6, 4, 4, 6), False, [1, 16, 16, 1]),
+                                           ((8, 6, 6, 4), False, [1, 8, 5, 1])])
+def test_net_adjoint_matches_oracle(qxd, L, cstar, chans, prec):
+    """qxd_net_apply_adjoint against the oracle's adjoint layers run last to first, and
+    <phi, M psi> = <M^+ phi, psi> for the GPU's own forward and adjoint networks."""
+    c = Case(qxd, torch, L, cstar=cstar)
+    net = qxd.net_create(c.lat, chans, seed=1)
+    try:
+        qxd.net_set_precision(net, qxd.NET_F32 if prec == "f32" else qxd.NET_BF16_TC)
+        w = random_flat(qxd.net_num_weights(net), 13)
+        qxd.net_set_weights(net, w)
+        w32 = w.real.astype(np.float32) + 1j * w.imag.astype(np.float32)
+        W = O.hop_links(c.U, c.A, c.q)
+        phi = synth.gaussian_spinor(c.dims, 21)
+        psi = synth.gaussian_spinor(c.dims, 22)
+        x = c.dev_tensor(phi)
+        y = torch.empty_like(x)
+        qxd.net_apply_adjoint(net, y, x)
+        got = as_c128(y, phi.shape)
+        g = phi[None]
+        for om in reversed(layer_weights(w32, chans)):
+            g = O.ptc_layer_adjoint(c.lat_o, W, om, g)
+        ref = g[0]
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        tol = 2e-6 if prec == "f32" else TC_TOL_PER_LAYER * (len(chans) - 1)
+        assert err < tol, err
+        # the adjoint identity with the GPU's forward network
+        xp = c.dev_tensor(psi)
+        yp = torch.empty_like(xp)
+        qxd.net_apply(net, yp, xp)
+        lhs = np.vdot(phi, as_c128(yp, psi.shape))
+        rhs = np.vdot(got, psi)
+        assert abs(lhs - rhs) <= 2 * tol * np.linalg.norm(phi) * np.linalg.norm(as_c128(yp, psi.shape)) + 1e-12
+        print(f"adjoint {chans} {prec}: rel err {err:.2e}, <phi, M psi> - <M+ phi, psi> = {abs(lhs - rhs):.2e}")
+    finally:
+        qxd.net_destroy(net)
+        c.close()
+
+
+@pytest.mark.parametrize("use_net", [False, True])
+@pytest.mark.parametrize("L,cstar,m0", [((4, 4, 4, 4), False, -0.1), ((4, 2, 2, 4), True, -0.1),
+                                        ((6, 4, 4, 8), False, -2.6)])
+def test_cgnr_solve(qxd, use_net, L, cstar, m0):
+    """QXD_SOLVER_MP_CGNR (CG on the normal equations of D M on the full lattice, FP32 inner,
+    FP64 defect correction), with and without the network as M, judged by the oracle's true
+    residual; m0 = -2.6 puts the spectrum of D around the origin (indefinite)."""
+    c = Case(qxd, torch, L, cstar=cstar, m0=m0)
+    net = qxd.net_create(c.lat, [1, 4, 1], seed=5) if use_net else None
+    try:
+        eta = synth.gaussian_spinor(c.dims, 2300)
+        b = c.dev_tensor(eta)
+        x = torch.empty_like(b)
+        st, info = qxd.solve(c.lat, x, b, solver=qxd.SOLVER_MP_CGNR, net=net, tol=1e-10, maxiter=20000)
+        assert st == qxd.OK, info
+        res = O.true_rel_residual(c.op, as_c128(x, eta.shape), eta)
+        assert res <= 1e-10, (res, info)
+        assert abs(info["true_rel_res"] - res) <= 1e-12 + 1e-3 * res
+        print(f"CGNR {L} cstar={cstar} m0={m0} net={use_net}: {info}")
+    finally:
+        if net:
+            qxd.net_destroy(net)
+        c.close()

@@ -13,9 +13,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 # FP32 arithmetic against the FP64 oracle in a nonlinear iteration (the MR step lengths depend on
-# the residual): FP32 unit roundoff 6e-8 times the amplification over the steps and cycles.  A
-# structural mistake (a wrong block, colour or step) gives an O(1) difference.
-SAP_TOL = 1e-4
+# the residual): FP32 unit roundoff 6e-8 times the amplification over the steps and cycles; the
+# measured differences are 1.3e-7 .. 1.4e-7, and the bound sits within 10x of them.  A structural
+# mistake (a wrong block, colour or step) gives an O(1) difference.
+SAP_TOL = 1e-6
 
 
 @pytest.fixture(scope="module")
