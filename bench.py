@@ -722,10 +722,10 @@ def profile_run(args):
         lat = qxd.create_lattice(w["L"], qxd.BC_ANTIPERIODIC, 0, qxd.ORDER_LEXI, stream.cuda_stream)
         qxd.load_gauge(lat, torch.from_numpy(U.view(np.float64)).to(dev), torch.from_numpy(A).to(dev), w["q"])
         qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
-        p = qxd.default_params(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=qxd.F32, tol=1e-10)
+        p = qxd.default_params(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=PREC_NAMES[args.inner], tol=1e-10)
         st, infos = qxd.solve_mrhs(lat, x, b, 12, params=p)
         torch.cuda.synchronize()
-        print(f"profile run: multi-RHS solve, {infos[0]}", file=sys.stderr)
+        print(f"profile run: multi-RHS solve ({args.inner} inner), {infos[0]}", file=sys.stderr)
         qxd.destroy_lattice(lat)
         return
     if args.workload == "c3b":
