@@ -93,12 +93,16 @@ typedef enum {
                                    preconditioner (net NULL: no preconditioner) */
   QXD_SOLVER_MP_SAP_GCR = 4,     /* as MP_FGCR_NET with the Schwarz alternating procedure as the
                                    preconditioner (sap_block, sap_ncy, sap_nmr; qxd_sap_apply) */
-  QXD_SOLVER_MP_CGNR = 5         /* FP64 outer defect correction around CG on the normal equations
+  QXD_SOLVER_MP_CGNR = 5,        /* FP64 outer defect correction around CG on the normal equations
                                    (D M)^+ D M y = (D M)^+ r of the full lattice in FP32, x += M y,
                                    with the learned network `net` as M (NULL: M = 1) and its adjoint
                                    network as M^+; FP32 reliable updates (reliable_delta).  Converges
                                    for any invertible D, also where D is indefinite and GCR or
                                    BiCGStab stagnate or break down; inner_prec is not used */
+  QXD_SOLVER_MP_DFL_SAP_GCR = 6  /* as MP_SAP_GCR with the two-level preconditioner of inexact
+                                   deflation: z = P A^-1 P^+ r on the subspace of qxd_dfl_setup
+                                   (coarse GCR to its coarse_tol), then z += M_SAP (r - D z)
+                                   (QXD_ESTATE without a subspace set up on the current field) */
 } qxd_solver;
 
 typedef struct {
@@ -375,6 +379,34 @@ qxd_status qxd_train_precond(qxd_lattice *lat, const qxd_train_params *p, qxd_ne
 /* Checkpoint: "QXDNET1\n", int32 nlayers, int32 channels[nlayers+1], float32 weights (re, im). */
 qxd_status qxd_net_save(const qxd_net *net, const char *path);
 qxd_status qxd_net_load(qxd_lattice *lat, const char *path, qxd_net **out);
+
+/* ---- Inexact deflation (the "DFL" of the DFL_SAP_GCR solver of Sec. 5.1; the paper names it
+ * without detail, so this is the textbook two-level method) ----
+ * qxd_dfl_generate: approximate low modes from ns start fields (the caller draws them): each is
+ *   normalised and then improved by n_it normalised SAP inverse iterations v <- M_SAP v / ||.||
+ *   (FP32 SAP with blocks sap_block, ncy cycles, nmr MR steps).  start, out: [ns][V][4][3][2].
+ * qxd_dfl_setup: the deflation subspace of ns fields `vectors` ([ns][V][4][3][2], host or device
+ *   per on_device) on blocks of extents block[4]: restricted to each block and orthonormalised
+ *   there (modified Gram-Schmidt in vector order, FP64), and the little Dirac operator
+ *   A = P^+ D P (FP64), which couples a block to itself and its eight face neighbours.  Blocks:
+ *   each extent divides L, the block grid is 1 or even per direction, extents >= 2 where the grid
+ *   has more than one block, at most 256 sites; with C* the physical L1 is an even number of x
+ *   blocks.  The coarse solve of the preconditioner (GCR(16) on A, FP64) stops at
+ *   ||f - A c|| <= coarse_tol ||f|| or after coarse_maxiter steps.  Replaces an earlier subspace;
+ *   a later load_gauge, build_clover or update_links makes it stale (QXD_ESTATE from the solve).
+ *   QXD_EINVAL for a bad block shape, ns outside 1..64 or vectors that are linearly dependent on a
+ *   block; QXD_ESTATE before build_clover.
+ * qxd_dfl_get_little: A as [nb][9][ns][ns][2] doubles (entry (b, slot, k, k') couples basis vector
+ *   k of block b with vector k' of block nbr[b][slot]; slot 0 the block itself, 1 + 2 mu the
+ *   neighbour in +mu, 2 + 2 mu in -mu) and nbr [nb][9]; host arrays.  Blocks are numbered
+ *   lexicographically by block coordinates (direction 3 fastest).
+ * qxd_dfl_info: the number of blocks, ns, and the coarse iterations and coarse solves so far. */
+qxd_status qxd_dfl_generate(qxd_lattice *lat, const int sap_block[4], int ncy, int nmr, int ns, int n_it,
+                            const double *start, double *out, int on_device);
+qxd_status qxd_dfl_setup(qxd_lattice *lat, const int block[4], int ns, const double *vectors, int on_device,
+                         double coarse_tol, int coarse_maxiter);
+qxd_status qxd_dfl_get_little(qxd_lattice *lat, double *A, int *nbr);
+qxd_status qxd_dfl_info(qxd_lattice *lat, int *nblocks, int *ns, int64_t *coarse_iters, int64_t *coarse_calls);
 
 /* Dot product for callers that cannot allocate device memory.  The paper has no counterpart:
  * this entry point exists for callers that must not call cudaMalloc -- code inside a framework

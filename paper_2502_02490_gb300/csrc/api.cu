@@ -174,6 +174,7 @@ static qxd_status alloc(qxd_lattice* lat, T** p, size_t bytes) {
 
 namespace qxd {
 qxd_status sap_check(qxd_lattice* lat, const int b[4]);  // csrc/sap.cu
+bool dfl_ready(const qxd_lattice* lat);                  // csrc/dfl.cu
 
 // The caller's params as the current version.  Version 3 ended at `fallback`; version 4 appended
 // use_x0 and restart_f32, which a version-3 caller gets off.
@@ -229,6 +230,7 @@ qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
   if (!lat) return QXD_OK;
   if (lat->stream) cudaStreamSynchronize(lat->stream);
   if (lat->batch && lat->batch_release) lat->batch_release(lat->batch);
+  if (lat->dfl && lat->dfl_release) lat->dfl_release(lat->dfl);
   void* bufs[] = {lat->U,    lat->A,     lat->W64,   lat->W32,   lat->W16,   lat->WB16,  lat->C64,
                   lat->Ci64, lat->C32,   lat->Ci32,  lat->C16,   lat->Ci16,  lat->C16n,  lat->Ci16n,
                   lat->CB16, lat->CiB16, lat->CB16n, lat->CiB16n, lat->red,  lat->ticket, lat->scal};
@@ -383,6 +385,7 @@ qxd_status qxd_load_gauge(qxd_lattice* lat, const double* su3, const double* a_u
   QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
   lat->have_gauge = true;
   lat->have_clover = false;
+  lat->epoch++;
   return QXD_OK;
 }
 
@@ -420,6 +423,7 @@ qxd_status qxd_update_links(qxd_lattice* lat, int64_t n, const int64_t* idx, con
   unsigned int* count = (unsigned int*)(mask + mask_bytes);
   int* bad = (int*)(count + 1);
   QXD_CUDA(lat, cudaMemsetAsync(mask, 0, mask_bytes + 2 * sizeof(int), lat->stream));
+  lat->epoch++;
   TRY(update_links(lat, n, d_idx, d_su3, d_a, mask, bad));
   int hbad[2] = {0, 0};
   if (lat->have_clover) {
@@ -500,6 +504,7 @@ qxd_status qxd_load_gauge_openqxd(qxd_lattice* lat, const double* u8, const doub
   QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
   lat->have_gauge = true;
   lat->have_clover = false;
+  lat->epoch++;
   return QXD_OK;
 }
 
@@ -511,6 +516,7 @@ qxd_status qxd_build_clover(qxd_lattice* lat, double m0, double csw, double csw_
   lat->csw = csw;
   lat->csw_qed = csw_qed;
   lat->have_clover = false;
+  lat->epoch++;
   TRY(clover_build(lat));
   lat->have_clover = true;
   return QXD_OK;
@@ -670,9 +676,12 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
   TRY(params_current(lat, p, &pv));
   p = &pv;
   if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO && p->solver != QXD_SOLVER_MP_BICGSTAB_EO &&
-      p->solver != QXD_SOLVER_MP_FGCR_NET && p->solver != QXD_SOLVER_MP_SAP_GCR && p->solver != QXD_SOLVER_MP_CGNR)
+      p->solver != QXD_SOLVER_MP_FGCR_NET && p->solver != QXD_SOLVER_MP_SAP_GCR && p->solver != QXD_SOLVER_MP_CGNR &&
+      p->solver != QXD_SOLVER_MP_DFL_SAP_GCR)
     return fail(lat, QXD_EINVAL, "bad solver");
-  if (p->solver == QXD_SOLVER_MP_SAP_GCR) {
+  if (p->solver == QXD_SOLVER_MP_DFL_SAP_GCR && !dfl_ready(lat))
+    return fail(lat, QXD_ESTATE, "DFL_SAP_GCR needs a deflation subspace set up on the current field (qxd_dfl_setup)");
+  if (p->solver == QXD_SOLVER_MP_SAP_GCR || p->solver == QXD_SOLVER_MP_DFL_SAP_GCR) {
     TRY(sap_check(lat, p->sap_block));
     if (p->sap_ncy < 1 || p->sap_nmr < 1) return fail(lat, QXD_EINVAL, "sap_ncy and sap_nmr must be >= 1");
   }
@@ -681,7 +690,8 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
     return fail(lat, QXD_EINVAL, "fallback must be -1, CG_EO, MP_CG_EO or MP_BICGSTAB_EO");
   if (p->use_x0 != 0 && p->use_x0 != 1) return fail(lat, QXD_EINVAL, "use_x0 must be 0 or 1");
   if (p->restart_f32 != 0 && p->restart_f32 != 1) return fail(lat, QXD_EINVAL, "restart_f32 must be 0 or 1");
-  const bool fgcr = p->solver == QXD_SOLVER_MP_FGCR_NET || p->solver == QXD_SOLVER_MP_SAP_GCR;
+  const bool fgcr = p->solver == QXD_SOLVER_MP_FGCR_NET || p->solver == QXD_SOLVER_MP_SAP_GCR ||
+                    p->solver == QXD_SOLVER_MP_DFL_SAP_GCR;
   if (fgcr && (p->gcr_reorth < 1 || p->gcr_reorth > 2)) return fail(lat, QXD_EINVAL, "gcr_reorth must be 1 or 2");
   if (fgcr && (p->gcr_restart < 1 || p->gcr_restart > 32)) return fail(lat, QXD_EINVAL, "gcr_restart must be 1..32");
   if (!(p->tol > 0) || p->maxiter <= 0) return fail(lat, QXD_EINVAL, "tol must be > 0 and maxiter > 0");

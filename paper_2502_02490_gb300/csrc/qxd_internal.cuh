@@ -594,12 +594,16 @@ struct Field64 {  // FP64 full field: two parities of double2 [12][sv]
 // device work buffers owned by a lattice (allocated on first use, grown on demand): slots 0..28 the
 // single-RHS solvers, 24..27 API staging, 29 and 31 FGCR vectors (31 also the training set), 30 the
 // clover singular flag, 32..38 multi-RHS, 39 network application, 40 FGCR coefficients
-#define QXD_WORK_SLOTS 58
+#define QXD_WORK_SLOTS 60
 struct qxd_lattice {
   qxd::Geom g;
   // device state of qxd_solve_batch when this lattice leads a batch (freed with the lattice)
   void* batch = nullptr;
   void (*batch_release)(void*) = nullptr;
+  // deflation subspace and little Dirac operator (qxd_dfl_setup; freed with the lattice)
+  void* dfl = nullptr;
+  void (*dfl_release)(void*) = nullptr;
+  qxd::i64 epoch = 0;  // counts changes of the gauge field or the clover term
   int Lphys[4];
   int tbc, cstar, order;
   qxd::i64 V, Vh, sv, Vphys;

@@ -9,9 +9,16 @@ struct SapSpec {
   int block[4];  // block extents (each divides the lattice; an even number of blocks per direction)
   int ncy;       // cycles from zero
   int nmr;       // minimal-residual steps per block solve
+  int dfl = 0;   // 1: two-level preconditioner (deflation coarse solve, then SAP), csrc/dfl.cu
 };
 
 // z = M_SAP r on full FP32 fields in the internal layout (work slots 41, 42)
 qxd_status sap32(qxd_lattice* lat, const int b[4], int ncy, int nmr, const float4* rin, float4* z);
+qxd_status sap_check(qxd_lattice* lat, const int b[4]);
+
+// Two-level preconditioner of DFL_SAP_GCR (csrc/dfl.cu): z = P A^-1 P^+ r (coarse solve on the
+// deflation subspace set up by qxd_dfl_setup), then z += M_SAP (r - D z).  Full FP32 fields.
+qxd_status dfl_precond32(qxd_lattice* lat, const SapSpec& sap, const float4* r, float4* z);
+bool dfl_ready(const qxd_lattice* lat);
 
 }  // namespace qxd

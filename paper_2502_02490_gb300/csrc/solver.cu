@@ -271,6 +271,11 @@ static qxd_status inner_mp(qxd_lattice* lat, int prec, const float4* bh, float4*
         TRY(blas_axpy_32(lat, -1.0f, q, s, n4));
         TRY(blas_norm2_32(lat, s, n4, SC_SS));
         TRY(read_scalars(lat, SC_SS, 1, &ss));
+        if (!std::isfinite(ss)) {  // a non-finite update reached y itself
+          *iters = it;
+          *nrel = rel;
+          return fail(lat, QXD_ENOCONV, "non-finite residual in the inner CG");
+        }
         rmax = std::sqrt(ss);
         ++rel;
         if (std::sqrt(ss) > target) {
@@ -366,6 +371,11 @@ static qxd_status inner_bicg(qxd_lattice* lat, int prec, const float4* bh, float
         TRY(blas_axpy_32(lat, -1.0f, v, r, n4));
         TRY(blas_norm2_32(lat, r, n4, SC_RN));
         TRY(read_scalars(lat, SC_RN, 1, &rn2));
+        if (!std::isfinite(rn2)) {  // a non-finite update reached y itself
+          *iters = it;
+          *nrel = rel;
+          return fail(lat, QXD_ENOCONV, "non-finite residual in the inner BiCGStab");
+        }
         rmax = std::sqrt(rn2);
         ++rel;
         if (std::sqrt(rn2) > target) TRY(restart());
@@ -449,6 +459,11 @@ static qxd_status cgnr32(qxd_lattice* lat, qxd_net* net, const float4* rhs, floa
         TRY(blas_axpy_32(lat, -1.0f, q, s, n4));
         TRY(blas_norm2_32(lat, s, n4, SC_SS));
         TRY(read_scalars(lat, SC_SS, 1, &ss));
+        if (!std::isfinite(ss)) {  // a non-finite update reached e itself
+          *iters = it;
+          *nrel = rel;
+          return fail(lat, QXD_ENOCONV, "non-finite residual in the inner CGNR");
+        }
         rmax = std::sqrt(ss);
         ++rel;
         if (std::sqrt(ss) > target) {
@@ -542,7 +557,8 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
   TRY(get(lat, WS_XE64, hb, &xe));
   TRY(get(lat, WS_TO64, hb, &to));
   const bool mp = prm->solver == QXD_SOLVER_MP_CG_EO || prm->solver == QXD_SOLVER_MP_BICGSTAB_EO;
-  const bool gcr = prm->solver == QXD_SOLVER_MP_FGCR_NET || prm->solver == QXD_SOLVER_MP_SAP_GCR;
+  const bool gcr = prm->solver == QXD_SOLVER_MP_FGCR_NET || prm->solver == QXD_SOLVER_MP_SAP_GCR ||
+                   prm->solver == QXD_SOLVER_MP_DFL_SAP_GCR;
   const bool cgnr = prm->solver == QXD_SOLVER_MP_CGNR;
   float4 *bh32 = nullptr, *y32 = nullptr, *r32 = nullptr, *to32 = nullptr;
   if (mp) {
@@ -633,11 +649,12 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
       double inner_target = prm->inner_tol * rnorm;
       if (inner_target < target) inner_target = target;
       SapSpec sp;
-      const bool with_sap = prm->solver == QXD_SOLVER_MP_SAP_GCR;
+      const bool with_sap = prm->solver == QXD_SOLVER_MP_SAP_GCR || prm->solver == QXD_SOLVER_MP_DFL_SAP_GCR;
       if (with_sap) {
         for (int mu = 0; mu < 4; ++mu) sp.block[mu] = prm->sap_block[mu];
         sp.ncy = prm->sap_ncy;
         sp.nmr = prm->sap_nmr;
+        sp.dfl = prm->solver == QXD_SOLVER_MP_DFL_SAP_GCR;
       }
       if (!inner_status(fgcr32(lat, with_sap ? nullptr : const_cast<qxd_net*>(prm->net), with_sap ? &sp : nullptr,
                                prm->gcr_restart, prm->gcr_reorth, r32f, e32, inner_target, prm->maxiter - total,

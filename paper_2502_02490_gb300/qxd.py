@@ -24,7 +24,8 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESINGULAR", "ENOCONV", "ESTA
 BC_PERIODIC, BC_ANTIPERIODIC = 0, 1
 ORDER_LEXI, ORDER_IPT = 0, 1
 F64, F32, F16N, BF16N = 0, 1, 2, 3
-SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO, SOLVER_MP_FGCR_NET, SOLVER_MP_SAP_GCR, SOLVER_MP_CGNR = range(6)
+(SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO, SOLVER_MP_FGCR_NET, SOLVER_MP_SAP_GCR, SOLVER_MP_CGNR,
+ SOLVER_MP_DFL_SAP_GCR) = range(7)
 PARAMS_VERSION = 5
 TRAIN_VERSION = 2
 PREC = {"f64": F64, "f32": F32, "f16n": F16N, "bf16n": BF16N}
@@ -93,6 +94,10 @@ _SIGS = {
     "qxd_net_save": [_vp, C.c_char_p],
     "qxd_net_load": [_vp, C.c_char_p, C.POINTER(_vp)],
     "qxd_kernel_stats": [_vp, _i, C.POINTER(_i64), C.POINTER(_d), C.POINTER(_d)],
+    "qxd_dfl_generate": [_vp, C.POINTER(C.c_int), _i, _i, _i, _i, _vp, _vp, _i],
+    "qxd_dfl_setup": [_vp, C.POINTER(C.c_int), _i, _vp, _i, _d, _i],
+    "qxd_dfl_get_little": [_vp, _vp, _vp],
+    "qxd_dfl_info": [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i64), C.POINTER(_i64)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -346,6 +351,41 @@ def sap_apply(lat, out, inp, block, ncy=2, nmr=4):
         raise ValueError("out and inp must both be host or both be device buffers")
     b = (C.c_int * 4)(*[int(v) for v in block])
     _check(lib.qxd_sap_apply(lat, po, pi, b, int(ncy), int(nmr), int(dev)), lat)
+
+
+# ---- inexact deflation ----
+def dfl_generate(lat, sap_block, start, out, n_it, ncy=1, nmr=4):
+    """qxd_dfl_generate: ns = len(start) approximate low modes into out (same shape), by n_it
+    normalised SAP inverse iterations of each start field."""
+    ps, dev = _ptr(start)
+    po, dev2 = _ptr(out)
+    if dev != dev2:
+        raise ValueError("start and out must both be host or both be device buffers")
+    b = (C.c_int * 4)(*[int(v) for v in sap_block])
+    _check(lib.qxd_dfl_generate(lat, b, int(ncy), int(nmr), int(start.shape[0]), int(n_it), ps, po, int(dev)), lat)
+
+
+def dfl_setup(lat, block, vectors, coarse_tol=1e-2, coarse_maxiter=64):
+    """qxd_dfl_setup with ns = len(vectors) fields [ns][V][4][3] (host array or CUDA tensor)."""
+    pv, dev = _ptr(vectors)
+    b = (C.c_int * 4)(*[int(v) for v in block])
+    _check(lib.qxd_dfl_setup(lat, b, int(vectors.shape[0]), pv, int(dev), float(coarse_tol), int(coarse_maxiter)), lat)
+
+
+def dfl_info(lat):
+    nb, ns, it, calls = C.c_int(), C.c_int(), C.c_int64(), C.c_int64()
+    _check(lib.qxd_dfl_info(lat, C.byref(nb), C.byref(ns), C.byref(it), C.byref(calls)), lat)
+    return {"nblocks": nb.value, "ns": ns.value, "coarse_iters": it.value, "coarse_calls": calls.value}
+
+
+def dfl_get_little(lat):
+    """(A [nb][9][ns][ns] complex, nbr [nb][9] int) of the current deflation subspace."""
+    info = dfl_info(lat)
+    nb, ns = info["nblocks"], info["ns"]
+    A = np.empty((nb, 9, ns, ns), dtype=np.complex128)
+    nbr = np.empty((nb, 9), dtype=np.int32)
+    _check(lib.qxd_dfl_get_little(lat, A.ctypes.data, nbr.ctypes.data), lat)
+    return A, nbr
 
 
 def net_apply(net, out, inp):
