@@ -391,7 +391,7 @@ qxd_status qxd_net_load(qxd_lattice *lat, const char *path, qxd_net **out);
  *   A = P^+ D P (FP64), which couples a block to itself and its eight face neighbours.  Blocks:
  *   each extent divides L, the block grid is 1 or even per direction, extents >= 2 where the grid
  *   has more than one block, at most 256 sites; with C* the physical L1 is an even number of x
- *   blocks.  The coarse solve of the preconditioner (GCR(16) on A, FP64) stops at
+ *   blocks and the grid has at least two blocks in y and in z.  The coarse solve of the preconditioner (GCR(16) on A, FP64) stops at
  *   ||f - A c|| <= coarse_tol ||f|| or after coarse_maxiter steps.  Replaces an earlier subspace;
  *   a later load_gauge, build_clover or update_links makes it stale (QXD_ESTATE from the solve).
  *   QXD_EINVAL for a bad block shape, ns outside 1..64 or vectors that are linearly dependent on a

@@ -14,7 +14,7 @@
 //
 // Blocks: extents b_mu dividing L_mu, a block grid n_mu that is 1 or even, b_mu >= 2 where
 // n_mu > 1 (the two faces of a block in direction mu must be different site layers), and with C*
-// the physical L1 an even number of x blocks.  A block's colour is the 4-bit pattern of its block
+// the physical L1 an even number of x blocks and at least two blocks in y and in z.  A block's colour is the 4-bit pattern of its block
 // coordinates' parities; a block's face neighbour in direction mu has the colour with bit mu
 // flipped, and no other block of that colour touches it.  So for each colour c and vector k', the
 // field F = sum over blocks of colour c of psi_{b',k'} gives D F, whose inner products with the
@@ -90,6 +90,11 @@ static qxd_status dfl_geometry(qxd_lattice* lat, const int b[4], DflGeom* dg) {
   }
   if (g.shift && g.shift % (2 * b[1]))
     return fail(lat, QXD_EINVAL, "deflation with C*: the physical L1 must be an even number of x blocks");
+  // with C*, a hop across the y or z boundary lands on the x-shifted copy; with a single block in
+  // that direction it would reach another block of the same colour, which the colour classes
+  // cannot tell apart from the block itself
+  if (g.shift && (dg->n[2] < 2 || dg->n[3] < 2))
+    return fail(lat, QXD_EINVAL, "deflation with C*: at least two blocks in y and in z");
   if (dg->vb > DFL_MAXVB) return fail(lat, QXD_EINVAL, "deflation block volume must be at most 256 sites");
   dg->stride[3] = 1;
   for (int mu = 2; mu >= 0; --mu) dg->stride[mu] = dg->stride[mu + 1] * b[mu + 1];

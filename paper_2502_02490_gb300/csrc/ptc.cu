@@ -364,9 +364,9 @@ qxd_status net_apply32(qxd_net* net, const float4* in, float4* out) {
   const float4* h = in;
   for (int l = 0; l < net->nlayers; ++l) {
     float4* o = (l == net->nlayers - 1) ? out : net->act[l + 1];
-    if (net->prec == QXD_NET_BF16_TC)
-      st = ptc_layer_tc(net->lat, net->ch[l], net->ch[l + 1], h, net->bp + net->bpoff[l], o, net->tc_scratch,
-                        net->tc_err);
+    if (net->prec == QXD_NET_BF16_TC)  // activations between layers in BF16
+      st = ptc_layer_tc(net->lat, net->ch[l], net->ch[l + 1], h, l > 0, net->bp + net->bpoff[l], o,
+                        l < net->nlayers - 1, net->tc_scratch, net->tc_err);
     else
       st = layer_fwd(net, l, h, o, false);
     if (st) return st;
@@ -399,7 +399,7 @@ qxd_status net_apply_adj32(qxd_net* net, const float4* in, float4* out) {
     const int ci = net->ch[l + 1], co = net->ch[l];
     float4* o = (l == 0) ? out : net->act[l];
     if (net->prec == QXD_NET_BF16_TC) {
-      st = ptc_layer_tc(lat, ci, co, h, net->bpadj + net->bpadjoff[l], o, net->tc_scratch, net->tc_err);
+      st = ptc_layer_tc(lat, ci, co, h, i > 0, net->bpadj + net->bpadjoff[l], o, l > 0, net->tc_scratch, net->tc_err);
     } else {
       dim3 grid((unsigned)((lat->Vh + PT_SITES - 1) / PT_SITES), 2), block(PT_SITES, co);
       prof_begin(lat, KSTAT_PTC_F32, (96.0 * (ci + co) + 576.0) * (double)lat->V);

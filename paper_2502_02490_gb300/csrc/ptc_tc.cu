@@ -40,8 +40,8 @@ struct TcLayer {
   Geom g;
   int cin, cout, np, nchunks;  // np = 8 cout rounded up to 16; nchunks = ceil(npaths cin / 8)
   int npaths;                  // 9: transport then mix; 1: mix only (first stage of the pull form)
-  const float4* in;            // [cin][2][6][sv]
-  float4* out;                 // [cout][2][6][sv]
+  const void* in;              // [cin][2][6][sv] float4 (FP32) or uint2 (BF16 activations)
+  void* out;                   // [cout][2][6][sv] float4 (FP32) or uint2 (BF16 activations)
   const float2* W;             // FP32 hop links
   const unsigned char* Bp;     // packed weights: [nchunks][np x 64 BF16, K-major core-matrix layout]
   int ntiles, tiles_per_par;   // tiles over both parities
@@ -138,6 +138,30 @@ __device__ __forceinline__ void put_transported_m(unsigned char* a0, int s, int 
   }
 }
 
+// Activations between layers are BF16 (four values per uint2, the float4 layout halved): the
+// MMA operands are BF16 anyway, and half the bytes per load lets a producer keep both of its
+// channels' loads in flight.  The network's input and output fields stay FP32.
+template <bool IN16>
+struct ActRaw {
+  typedef float4 T;
+};
+template <>
+struct ActRaw<true> {
+  typedef uint2 T;
+};
+
+template <bool IN16>
+__device__ __forceinline__ void act_load(const void* base, i64 off, i64 sv, typename ActRaw<IN16>::T raw[6]) {
+  const typename ActRaw<IN16>::T* p = (const typename ActRaw<IN16>::T*)base + off;
+#pragma unroll
+  for (int jj = 0; jj < 6; ++jj) raw[jj] = __ldg(p + jj * sv);
+}
+
+__device__ __forceinline__ float4 act_f4(const float4 v) { return v; }
+__device__ __forceinline__ float4 act_f4(const uint2 v) {
+  return make_float4(B16::lo(v.x), B16::hi(v.x), B16::lo(v.y), B16::hi(v.y));
+}
+
 // The transported spinor of one input channel at one site (link u already carries the time sign):
 // forward path t = u h, backward path t = u^+ h, path 0 t = h, written as BF16 into the three
 // colour tiles of the stage, k = 8 slot + 2 beta + re/im (one 16-byte core-matrix row each).
@@ -180,6 +204,7 @@ __device__ __forceinline__ void path_setup(const TcLayer& L, int p, int par, uin
 // C_in a multiple of 8: chunk j is path j / (C_in / 8) and input channels 8 (j % (C_in / 8)) + 0..7;
 // thread (s, grp) transports channels + 2 grp + 0..1 of its site.  (Seventeen warps per SM leave
 // each thread 96 registers: four SM sub-partitions of 16K registers, five warps on one of them.)
+template <bool IN16>
 __device__ __forceinline__ void transport_chunk_path(const TcLayer& L, unsigned char* a0, int j, int s, int grp,
                                                      bool live, int par, uint32_t cb, const int x[4], i64 cs) {
   const int G = L.cin >> 3;
@@ -188,21 +213,35 @@ __device__ __forceinline__ void transport_chunk_path(const TcLayer& L, unsigned 
   int spar;
   cplx<float> u[9];
   if (live) path_setup(L, p, par, cb, x, src, spar, u);
-  const float4* hp = L.in + (i64)c0 * cs + (i64)spar * 6 * L.g.sv + src;
-  // one channel's six loads in flight at a time: 16 producer warps keep ~48 KB in flight per SM
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    float4 raw[6];
+  const i64 off = (i64)c0 * cs + (i64)spar * 6 * L.g.sv + src;
+  if constexpr (IN16) {
+    // BF16 activations: both channels' loads in flight at once (12 registers each)
+    uint2 raw16[2][6];
     if (live) {
-#pragma unroll
-      for (int jj = 0; jj < 6; ++jj) raw[jj] = __ldg(hp + i * cs + jj * L.g.sv);
+      act_load<true>(L.in, off, L.g.sv, raw16[0]);
+      act_load<true>(L.in, off + cs, L.g.sv, raw16[1]);
     }
-    put_transported(a0, s, 2 * grp + i, p, p < 5, u, raw, !live);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      float4 raw[6];
+#pragma unroll
+      for (int jj = 0; jj < 6; ++jj) raw[jj] = live ? act_f4(raw16[i][jj]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      put_transported(a0, s, 2 * grp + i, p, p < 5, u, raw, !live);
+    }
+  } else {
+    // FP32 input: one channel's six loads in flight at a time (register budget)
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      float4 raw[6];
+      if (live) act_load<false>(L.in, off + i * cs, L.g.sv, raw);
+      put_transported(a0, s, 2 * grp + i, p, p < 5, u, raw, !live);
+    }
   }
 }
 
 // general C_in: chunk j holds the pairs q = 8 j .. 8 j + 7 (q = p C_in + c', path-major); thread
 // (s, grp) transports pairs 8 j + 2 grp + 0..1 (zero beyond npaths C_in)
+template <bool IN16>
 __device__ __forceinline__ void transport_chunk_pairs(const TcLayer& L, unsigned char* a0, int j, int s, int grp,
                                                       bool live, int par, uint32_t cb, const int x[4], i64 cs) {
   int last_p = -1;
@@ -220,16 +259,18 @@ __device__ __forceinline__ void transport_chunk_pairs(const TcLayer& L, unsigned
         path_setup(L, p, par, cb, x, src, spar, u);
         last_p = p;
       }
-      const float4* hp = L.in + (i64)ci * cs + (i64)spar * 6 * L.g.sv + src;
+      typename ActRaw<IN16>::T r16[6];
+      act_load<IN16>(L.in, (i64)ci * cs + (i64)spar * 6 * L.g.sv + src, L.g.sv, r16);
 #pragma unroll
-      for (int jj = 0; jj < 6; ++jj) raw[jj] = __ldg(hp + jj * L.g.sv);
+      for (int jj = 0; jj < 6; ++jj) raw[jj] = act_f4(r16[jj]);
     }
     put_transported(a0, s, 2 * grp + i, p, p < 5, u, raw, !ok);
   }
 }
 
-// FAST: C_in a multiple of 8 (one path per chunk); else the general pair enumeration
-template <bool FAST>
+// FAST: C_in a multiple of 8 (one path per chunk); else the general pair enumeration.  IN16 /
+// OUT16: BF16 input / output activations.
+template <bool FAST, bool IN16, bool OUT16>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_ptc_layer_tc(TcLayer L) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], tile_bar, bload;
@@ -321,9 +362,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ptc_layer_tc(TcLayer L) {
         }
         unsigned char* a0 = sA + st * TC_ABYTES;
         if constexpr (FAST)
-          transport_chunk_path(L, a0, j, s, grp, live, par, cb, x, cs);
+          transport_chunk_path<IN16>(L, a0, j, s, grp, live, par, cb, x, cs);
         else
-          transport_chunk_pairs(L, a0, j, s, grp, live, par, cb, x, cs);
+          transport_chunk_pairs<IN16>(L, a0, j, s, grp, live, par, cb, x, cs);
         tc::fence_async_smem();
         mbar_arrive(&full[st]);
       }
@@ -346,13 +387,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ptc_layer_tc(TcLayer L) {
           for (int a = 0; a < 3; ++a)
             tc::tmem_ld8(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(a * L.np + c * 8), v[a]);
           if (olive) {
-            float4* o = L.out + c * cs + (i64)par * 6 * g.sv;
-            // complex index 3 alpha + a; float4 jj holds complex 2 jj, 2 jj + 1
+            // complex index 3 alpha + a; float4 (or uint2) jj holds complex 2 jj, 2 jj + 1
 #pragma unroll
             for (int jj = 0; jj < 6; ++jj) {
               const int k0 = 2 * jj, k1 = 2 * jj + 1;
-              o[jj * g.sv + ocb] = make_float4(v[k0 % 3][2 * (k0 / 3)], v[k0 % 3][2 * (k0 / 3) + 1],
-                                               v[k1 % 3][2 * (k1 / 3)], v[k1 % 3][2 * (k1 / 3) + 1]);
+              const float a = v[k0 % 3][2 * (k0 / 3)], b = v[k0 % 3][2 * (k0 / 3) + 1];
+              const float cc = v[k1 % 3][2 * (k1 / 3)], d = v[k1 % 3][2 * (k1 / 3) + 1];
+              if constexpr (OUT16)
+                ((uint2*)L.out)[c * cs + (i64)par * 6 * g.sv + jj * g.sv + ocb] = make_uint2(B16::pack(a, b), B16::pack(cc, d));
+              else
+                ((float4*)L.out)[c * cs + (i64)par * 6 * g.sv + jj * g.sv + ocb] = make_float4(a, b, cc, d);
             }
           }
         }
@@ -368,8 +412,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ptc_layer_tc(TcLayer L) {
 
 // Second stage of the pull form: out_c(x) = G_{0,c}(x) + sum_{p=1..8} (T_p G_{p,c})(x), with
 // G_{p,c} the virtual channel p cout + c of the mix-only stage.  One thread per (site, channel).
-__global__ void __launch_bounds__(256) k_ptc_pull(Geom g, int cout, const float4* __restrict__ G,
-                                                 const float2* __restrict__ W, float4* __restrict__ out) {
+template <bool IN16, bool OUT16>
+__global__ void __launch_bounds__(256) k_ptc_pull(Geom g, int cout, const void* __restrict__ G,
+                                                 const float2* __restrict__ W, void* __restrict__ out) {
   const i64 cs = 12 * g.sv;
   const i64 n = (i64)2 * g.Vh * cout;
   for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x) {
@@ -377,10 +422,11 @@ __global__ void __launch_bounds__(256) k_ptc_pull(Geom g, int cout, const float4
     const int par = (int)((e / g.Vh) & 1), c = (int)(e / (2 * g.Vh));
     cplx<float> acc[12];
     {
-      const float4* gp = G + (i64)c * cs + (i64)par * 6 * g.sv + cb;
+      typename ActRaw<IN16>::T r[6];
+      act_load<IN16>(G, (i64)c * cs + (i64)par * 6 * g.sv + cb, g.sv, r);
 #pragma unroll
       for (int jj = 0; jj < 6; ++jj) {
-        const float4 q = __ldg(gp + jj * g.sv);
+        const float4 q = act_f4(r[jj]);
         acc[2 * jj] = mk(q.x, q.y);
         acc[2 * jj + 1] = mk(q.z, q.w);
       }
@@ -402,10 +448,11 @@ __global__ void __launch_bounds__(256) k_ptc_pull(Geom g, int cout, const float4
         const float2 w = __ldg(W + ((i64)(lpar * 4 + mu) * 9 + k) * g.sv + ls);
         u[k] = mk(sign * w.x, sign * w.y);
       }
-      const float4* gp = G + (i64)(p * cout + c) * cs + (i64)(1 - par) * 6 * g.sv + src;
+      typename ActRaw<IN16>::T r[6];
+      act_load<IN16>(G, (i64)(p * cout + c) * cs + (i64)(1 - par) * 6 * g.sv + src, g.sv, r);
 #pragma unroll
       for (int jj = 0; jj < 6; ++jj) {
-        const float4 q = __ldg(gp + jj * g.sv);
+        const float4 q = act_f4(r[jj]);
         sp[2 * jj] = mk(q.x, q.y);
         sp[2 * jj + 1] = mk(q.z, q.w);
       }
@@ -425,10 +472,16 @@ __global__ void __launch_bounds__(256) k_ptc_pull(Geom g, int cout, const float4
             for (int b = 0; b < 3; ++b) acc[3 * be + a] = cjmac(acc[3 * be + a], u[3 * b + a], sp[3 * be + b]);
       }
     }
-    float4* o = out + (i64)c * cs + (i64)par * 6 * g.sv + cb;
+    const i64 ob = (i64)c * cs + (i64)par * 6 * g.sv + cb;
 #pragma unroll
-    for (int jj = 0; jj < 6; ++jj)
-      o[jj * g.sv] = make_float4(acc[2 * jj].re, acc[2 * jj].im, acc[2 * jj + 1].re, acc[2 * jj + 1].im);
+    for (int jj = 0; jj < 6; ++jj) {
+      if constexpr (OUT16)
+        ((uint2*)out)[ob + jj * g.sv] =
+            make_uint2(B16::pack(acc[2 * jj].re, acc[2 * jj].im), B16::pack(acc[2 * jj + 1].re, acc[2 * jj + 1].im));
+      else
+        ((float4*)out)[ob + jj * g.sv] =
+            make_float4(acc[2 * jj].re, acc[2 * jj].im, acc[2 * jj + 1].re, acc[2 * jj + 1].im);
+    }
   }
 }
 
@@ -452,25 +505,35 @@ qxd_status ptc_pack_weights(qxd_lattice* lat, int cin, int cout, const float2* O
   return QXD_OK;
 }
 
-static qxd_status launch_tc(qxd_lattice* lat, int cin, int cout, int npaths, const float4* in, const void* Bp,
-                            float4* out, int* err);
+static qxd_status launch_tc(qxd_lattice* lat, int cin, int cout, int npaths, const void* in, int in16, const void* Bp,
+                            void* out, int out16, int* err);
 
-// one layer: push form (transport then mix) or pull form (mix, then transport the outputs)
-qxd_status ptc_layer_tc(qxd_lattice* lat, int cin, int cout, const float4* in, const void* Bp, float4* out, float4* scratch,
-                        int* err) {
-  if (!tc_pull(cin, cout)) return launch_tc(lat, cin, cout, 9, in, Bp, out, err);
-  qxd_status st = launch_tc(lat, cin, 9 * cout, 1, in, Bp, scratch, err);
+// one layer: push form (transport then mix) or pull form (mix, then transport the outputs); the
+// pull form's virtual channels are BF16 activations in `scratch`
+qxd_status ptc_layer_tc(qxd_lattice* lat, int cin, int cout, const void* in, int in16, const void* Bp, void* out,
+                        int out16, void* scratch, int* err) {
+  if (!tc_pull(cin, cout)) return launch_tc(lat, cin, cout, 9, in, in16, Bp, out, out16, err);
+  qxd_status st = launch_tc(lat, cin, 9 * cout, 1, in, in16, Bp, scratch, 1, err);
   if (st) return st;
   const i64 n = (i64)2 * lat->Vh * cout;
-  prof_begin(lat, KSTAT_PTC_TC, (96.0 * 9 * cout + 96.0 * cout + 576.0) * (double)lat->V);
-  k_ptc_pull<<<(int)std::min<i64>((n + 255) / 256, 152 * 16), 256, 0, lat->stream>>>(lat->g, cout, scratch, lat->W32, out);
+  const int grid = (int)std::min<i64>((n + 255) / 256, 152 * 16);
+  prof_begin(lat, KSTAT_PTC_TC, (48.0 * 9 * cout + (out16 ? 48.0 : 96.0) * cout + 576.0) * (double)lat->V);
+  if (out16)
+    k_ptc_pull<true, true><<<grid, 256, 0, lat->stream>>>(lat->g, cout, scratch, lat->W32, out);
+  else
+    k_ptc_pull<true, false><<<grid, 256, 0, lat->stream>>>(lat->g, cout, scratch, lat->W32, out);
   prof_end(lat);
   QXD_CHECK_LAUNCH(lat, "k_ptc_pull");
   return QXD_OK;
 }
 
-static qxd_status launch_tc(qxd_lattice* lat, int cin, int cout, int npaths, const float4* in, const void* Bp,
-                            float4* out, int* err) {
+template <bool FAST, bool IN16, bool OUT16>
+static const void* tc_kernel() {
+  return (const void*)k_ptc_layer_tc<FAST, IN16, OUT16>;
+}
+
+static qxd_status launch_tc(qxd_lattice* lat, int cin, int cout, int npaths, const void* in, int in16, const void* Bp,
+                            void* out, int out16, int* err) {
   TcLayer L;
   L.g = lat->g;
   L.cin = cin;
@@ -494,20 +557,25 @@ static qxd_status launch_tc(qxd_lattice* lat, int cin, int cout, int npaths, con
   const size_t smem = base + bchunk * (L.b_resident ? L.nchunks : TC_STAGES);
   // the dynamic shared-memory limit is a per-device function attribute: set it for the kernel
   // about to run (a cheap host call, no synchronisation)
-  QXD_CUDA(lat, cudaFuncSetAttribute(cin % 8 == 0 ? (const void*)k_ptc_layer_tc<true> : (const void*)k_ptc_layer_tc<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX));
+  const bool fast = cin % 8 == 0;
+  const int variant = (fast ? 4 : 0) + (in16 ? 2 : 0) + (out16 ? 1 : 0);
+  static const void* kernels[8] = {tc_kernel<false, false, false>(), tc_kernel<false, false, true>(),
+                                   tc_kernel<false, true, false>(),  tc_kernel<false, true, true>(),
+                                   tc_kernel<true, false, false>(),  tc_kernel<true, false, true>(),
+                                   tc_kernel<true, true, false>(),   tc_kernel<true, true, true>()};
+  QXD_CUDA(lat, cudaFuncSetAttribute(kernels[variant], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX));
   int dev = 0, sms = 0;
   QXD_CUDA(lat, cudaGetDevice(&dev));
   QXD_CUDA(lat, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = L.ntiles < sms ? L.ntiles : sms;
   // algorithmic bytes: each input channel, the 8 links (when transporting) and each output channel
   // once per site
-  prof_begin(lat, KSTAT_PTC_TC, (96.0 * (cin + cout) + (npaths == 9 ? 576.0 : 0.0)) * (double)lat->V);
-  if (cin % 8 == 0)
-    k_ptc_layer_tc<true><<<grid, TC_THREADS, smem, lat->stream>>>(L);
-  else
-    k_ptc_layer_tc<false><<<grid, TC_THREADS, smem, lat->stream>>>(L);
+  prof_begin(lat, KSTAT_PTC_TC,
+             ((in16 ? 48.0 : 96.0) * cin + (out16 ? 48.0 : 96.0) * cout + (npaths == 9 ? 576.0 : 0.0)) * (double)lat->V);
+  void* args[] = {&L};
+  const cudaError_t le = cudaLaunchKernel(kernels[variant], dim3(grid), dim3(TC_THREADS), args, smem, lat->stream);
   prof_end(lat);
+  if (le != cudaSuccess) return cuda_fail(lat, le, "k_ptc_layer_tc");
   QXD_CHECK_LAUNCH(lat, "k_ptc_layer_tc");
   return QXD_OK;
 }

@@ -819,8 +819,8 @@ qxd_status net_check(qxd_net* net);  // error word of the tensor-core layers (sy
 size_t ptc_tc_packed_bytes(int cin, int cout);
 qxd_status ptc_pack_weights(qxd_lattice* lat, int cin, int cout, const float2* Om, void* Bp);
 size_t ptc_tc_pull_scratch(int cin, int cout, i64 sv);  // float4s of the pull form's virtual channels
-qxd_status ptc_layer_tc(qxd_lattice* lat, int cin, int cout, const float4* in, const void* Bp, float4* out,
-                        float4* scratch, int* err);
+qxd_status ptc_layer_tc(qxd_lattice* lat, int cin, int cout, const void* in, int in16, const void* Bp, void* out,
+                        int out16, void* scratch, int* err);
 // ---- solver_mrhs.cu ----
 qxd_status solve_mrhs(qxd_lattice* lat, double2* x, const double2* b, int n, const qxd_solve_params* p,
                       qxd_solve_info* info);

@@ -40,7 +40,7 @@ def dense_little(A, nbr):
 @pytest.mark.parametrize("L,block,cstar,ns", [
     ((4, 4, 4, 4), (2, 2, 2, 2), False, 3),
     ((6, 4, 4, 8), (3, 2, 2, 4), False, 2),
-    ((4, 4, 2, 4), (2, 2, 2, 2), True, 3),   # C*: the device lattice is 4 x 8 x 2 x 4
+    ((4, 4, 4, 4), (2, 2, 2, 2), True, 3),   # C*: the device lattice is 4 x 8 x 4 x 4
     ((4, 4, 4, 4), (4, 2, 4, 2), False, 4),  # a grid of one block in two directions
 ])
 def test_little_operator_matches_oracle(qxd, L, block, cstar, ns):
@@ -121,5 +121,14 @@ def test_dfl_rejects_bad_input(qxd):
             with pytest.raises(qxd.QxdError) as e:
                 qxd.dfl_setup(c.lat, blk, w)
             assert e.value.status == qxd.EINVAL, blk
+    finally:
+        c.close()
+    # C* with a single block in z: the z wrap reaches the x-shifted copy, another block
+    c = Case(qxd, torch, (4, 4, 2, 4), cstar=True)
+    try:
+        w = c.dev_tensor(np.stack([synth.gaussian_spinor(c.dims, 2)]))
+        with pytest.raises(qxd.QxdError) as e:
+            qxd.dfl_setup(c.lat, (2, 2, 2, 2), w)
+        assert e.value.status == qxd.EINVAL
     finally:
         c.close()
