@@ -173,7 +173,7 @@ __device__ __forceinline__ void cta_sum(double v[NV], double* sh /* [NV][8 warps
 
 // Modified Gram-Schmidt of the ns vectors on every block (one CTA per block, one thread per
 // block site): w_k -= <u_j, w_k> u_j for j < k in order, then u_k = w_k / ||w_k||.  A vector
-// with zero norm on a block sets *bad.
+// that the projections reduce to rounding (||w_k|| <= 1e-12 of its norm before them) sets *bad.
 __global__ void __launch_bounds__(DFL_MAXVB) k_dfl_orthonormalise(Geom g, DflGeom dg, int ns, double2* __restrict__ V,
                                                                   int* __restrict__ bad) {
   __shared__ double sh[2 * 8];
@@ -186,6 +186,13 @@ __global__ void __launch_bounds__(DFL_MAXVB) k_dfl_orthonormalise(Geom g, DflGeo
   const i64 base = (i64)par * 12 * g.sv + cb;
   for (int k = 0; k < ns; ++k) {
     double2* wk = V + (i64)k * fs + base;
+    double n0[1] = {0.0};  // ||w_k||^2 before the projections
+    if (act)
+      for (int c = 0; c < 12; ++c) {
+        const double2 b = wk[c * g.sv];
+        n0[0] += b.x * b.x + b.y * b.y;
+      }
+    cta_sum<1>(n0, sh);
     for (int j = 0; j < k; ++j) {
       const double2* uj = V + (i64)j * fs + base;
       double v[2] = {0.0, 0.0};
@@ -212,7 +219,8 @@ __global__ void __launch_bounds__(DFL_MAXVB) k_dfl_orthonormalise(Geom g, DflGeo
         nn[0] += b.x * b.x + b.y * b.y;
       }
     cta_sum<1>(nn, sh);
-    if (!(nn[0] > 0.0)) {
+    // dependent on this block: what the projections leave is rounding (relative 1e-12 or less)
+    if (!(nn[0] > 1e-24 * n0[0])) {
       if (s == 0) atomicOr(bad, 1);
       return;  // uniform over the CTA
     }

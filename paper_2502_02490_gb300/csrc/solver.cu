@@ -392,7 +392,7 @@ static qxd_status inner_bicg(qxd_lattice* lat, int prec, const float4* bh, float
 // Inner CGNR on the full lattice, FP32, right-preconditioned by the network M (or M = 1):
 // CG on (D M)^+ (D M) y = (D M)^+ rhs, accumulating the correction e = M y directly (e += alpha
 // M p, since M is linear), s = rhs - D e tracked, FP32 reliable updates recompute s = rhs - D e
-// when ||s|| has fallen by delta.  The normal equations are Hermitian positive definite whatever
+// when ||s|| has fallen by delta and restart the CG there.  The normal equations are Hermitian positive definite whatever
 // the spectrum of D, so the iteration converges where GCR and BiCGStab stagnate on an indefinite
 // D; M^+ is the adjoint network and D^+ = gamma5 D gamma5.
 // ------------------------------------------------------------------------------------------
@@ -453,7 +453,9 @@ static qxd_status cgnr32(qxd_lattice* lat, qxd_net* net, const float4* rhs, floa
       const double sn = std::sqrt(ss);
       if (sn > rmax) rmax = sn;
       if (sn < delta * rmax || sn <= target) {
-        // reliable update: s = rhs - D e in FP32; keep p, refresh z and gamma
+        // reliable update: s = rhs - D e in FP32, then restart from it (p = z).  Keeping the old
+        // p here lets FP32 rounding steer it into near-null directions of D on ill-conditioned
+        // fields, where the iteration then diverges (measured: 16^3x32 at m0 = -0.12).
         TRY(dfull(e, q, 0));
         TRY(blas_copy(lat, s, rhs, fb));
         TRY(blas_axpy_32(lat, -1.0f, q, s, n4));
@@ -468,6 +470,7 @@ static qxd_status cgnr32(qxd_lattice* lat, qxd_net* net, const float4* rhs, floa
         ++rel;
         if (std::sqrt(ss) > target) {
           TRY(normal_rhs(s, z));
+          TRY(blas_copy(lat, p, z, fb));
           TRY(blas_norm2_32(lat, z, n4, SC_GAMMA));
         }
       }
