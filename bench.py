@@ -50,6 +50,9 @@ WORKLOADS = {
                 source_seed=2002,
                 name="24^3x48 multi-RHS solve of the 12 spin-colour point sources to 1e-10 (FP32 inner, "
                      "eps=0.3, q=-1/3, m0=-0.1, c_sw=1.9, c_sw^QED=1.0, antiperiodic t)"),
+    # the paper's solver family (SAP-GCR, DFL-SAP-GCR) on the 32^3x64 field (extra line)
+    "sap": dict(L=(64, 32, 32, 32), cstar=0, eps=0.4, q=2 / 3, m0=-0.2, csw=1.9, csw_qed=1.0, gauge_seed=1001,
+                source_seed=2001, name="32^3x64 SAP-GCR and DFL-SAP-GCR"),
     # 8 independent lattices of uneven volume in one persistent batched solve (extra line)
     "c3b": dict(L=None, cstar=0, eps=None, q=-1 / 3, m0=-0.1, csw=1.9, csw_qed=1.0, gauge_seed=1010, source_seed=2010,
                 lattices=[(16, 8, 8, 8), (20, 10, 10, 10), (16, 12, 12, 12), (24, 12, 12, 12), (28, 14, 14, 14),
@@ -532,6 +535,73 @@ def run_batch(args):
             "gpu_launches": int(launches), "clocks": clk.summary()}
 
 
+def run_sap(args):
+    """The paper's CPU solver family on the 32^3x64 field: SAP-preconditioned flexible GCR and the
+    deflated two-level version (DFL_SAP_GCR) to the paper's 1e-12, against MP BiCGStab; SAP block
+    kernel time and bytes from a profiled pass."""
+    import torch
+
+    from paper_2502_02490_gb300 import qxd, synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    w = WORKLOADS["c2"]
+    U, A = synth.gauge_field(w["L"], w["gauge_seed"], w["eps"])
+    eta = torch.from_numpy(synth.gaussian_spinor(w["L"], w["source_seed"]).view(np.float64)).to(dev)
+    x = torch.empty_like(eta)
+    lat = qxd.create_lattice(w["L"], qxd.BC_ANTIPERIODIC, 0, qxd.ORDER_LEXI, stream.cuda_stream)
+    qxd.load_gauge(lat, torch.from_numpy(U.view(np.float64)).to(dev), torch.from_numpy(A).to(dev), w["q"])
+    qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
+    blk, ncy, nmr, ns = (4, 4, 4, 4), 2, 4, 8
+    sap = dict(sap_block=blk, sap_ncy=ncy, sap_nmr=nmr, gcr_restart=16, tol=1e-12, maxiter=5000)
+
+    def timed(profile=False, **kw):
+        qxd.solve(lat, x, eta, check=False, **dict(kw, maxiter=20))
+        if profile:
+            qxd.set_profiling(lat, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = qxd.solve(lat, x, eta, check=False, **kw)
+        torch.cuda.synchronize()
+        out = {"status": qxd.STATUS_NAMES[st], "seconds": time.perf_counter() - t0, "iterations": info["iters_inner"],
+               "true_rel_res": info["true_rel_res"]}
+        if profile:
+            n, ms, by = qxd.kernel_stats(lat, 9)
+            qxd.set_profiling(lat, 0)
+            out["sap_kernel"] = {"launches": n, "ms": ms, "avg_us": ms / n * 1e3 if n else None,
+                                 "GBps_convention": by / (ms / 1e3) / 1e9 if ms else None}
+        return out
+
+    res = {"sap_gcr": timed(solver=qxd.SOLVER_MP_SAP_GCR, **sap),
+           "mp_bicgstab_f16n": timed(solver=qxd.SOLVER_MP_BICGSTAB_EO, inner_prec=qxd.F16N, tol=1e-12)}
+    res["sap_gcr_profiled"] = timed(profile=True, solver=qxd.SOLVER_MP_SAP_GCR, **sap)
+    start = torch.from_numpy(np.stack([synth.gaussian_spinor(w["L"], 7000 + k) for k in range(ns)])
+                             .view(np.float64)).to(dev)
+    vecs = torch.empty_like(start)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qxd.dfl_generate(lat, blk, start, vecs, n_it=4, ncy=1, nmr=nmr)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    qxd.dfl_setup(lat, blk, vecs, coarse_tol=1e-2, coarse_maxiter=64)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    res["dfl_sap_gcr"] = timed(solver=qxd.SOLVER_MP_DFL_SAP_GCR, **sap)
+    res["dfl"] = {"ns": ns, "block": list(blk), "generate_s": t_gen, "setup_s": t_setup, **qxd.dfl_info(lat)}
+    qxd.destroy_lattice(lat)
+    peak, kind = measured_peaks()
+    k = res["sap_gcr_profiled"]["sap_kernel"]
+    return {"metric": METRIC, "workload": w["name"] + "; SAP blocks 4^4, 2 cycles x 4 MR steps, GCR(16), to 1e-12",
+            "results": res,
+            "sap_kernel_roofline": {"bound": "latency / L2 (block-local MR iterations)",
+                                    "achieved_GBps_convention": k["GBps_convention"], "peak": peak,
+                                    "frac": (k["GBps_convention"] or 0) / peak,
+                                    "bytes": "per site of the colour and sweep: residual, x read and written, 8 links "
+                                             "and the clover pair once (1152 B)"},
+            "note": "seconds: one solve after a short warm-up; DFL generate/setup timed separately"}
+
+
 C4_M0_FILE = os.path.join(ROOT, "profiles", "c4_m0.txt")
 
 
@@ -916,7 +986,7 @@ def main():
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS),
                     help="c2: 32^3x64 (the metric's workload, default); c5: 48^3x96 C* doubled; "
                          "c3a: 12 point sources on 24^3x48 (multi-RHS); c3b: 8 uneven lattices in one batched solve; "
-                         "c4: learned preconditioner on 16^3x32")
+                         "c4: learned preconditioner on 16^3x32; sap: SAP-GCR and DFL-SAP-GCR on 32^3x64")
     args = ap.parse_args()
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[args.workload])
@@ -962,6 +1032,9 @@ def main():
         return
     if args.workload == "c3b":
         print(json.dumps(run_batch(args)))
+        return
+    if args.workload == "sap":
+        print(json.dumps(run_sap(args)))
         return
     out = run_ours(args, rank, world)
     if rank == 0:

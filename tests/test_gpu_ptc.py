@@ -240,3 +240,49 @@ def test_cgnr_solve(qxd, use_net, L, cstar, m0):
         if net:
             qxd.net_destroy(net)
         c.close()
+
+
+def test_learned_preconditioner_at_a_scaled_down_near_critical_point(qxd):
+    """8^4 with the workload's field recipe at m0 = -2.63, where D is indefinite (the odd clover
+    blocks nearly singular, eo-CG slow): flexible GCR without a network stagnates, with a small
+    trained network it reaches the inner target; at the physical branch's slowest point the
+    network cuts the iterations of CG on the normal equations.  Judged by the oracle's residual."""
+    L = (8, 8, 8, 8)
+    c = Case(qxd, torch, L, eps=0.3, seed=1003, m0=-2.63)
+    try:
+        eta = synth.gaussian_spinor(c.dims, 2003)
+        b = c.dev_tensor(eta)
+        x = torch.empty_like(b)
+        vs = c.dev_tensor(np.stack([synth.gaussian_spinor(c.dims, 5000 + k) for k in range(32)]))
+        net = qxd.net_create(c.lat, [1, 4, 4, 1], seed=7)
+        try:
+            qxd.net_train(net, vs, 32, epochs=20, batch=8, lr=2e-3)
+            kw = dict(solver=qxd.SOLVER_MP_FGCR_NET, tol=1e-10, gcr_restart=32, maxiter=400, max_outer=1, check=False)
+            st0, plain = qxd.solve(c.lat, x, b, net=None, **kw)
+            st1, learned = qxd.solve(c.lat, x, b, net=net, **kw)
+            res = O.true_rel_residual(c.op, as_c128(x, eta.shape), eta)  # x of the learned solve
+            print(f"m0=-2.63 FGCR: plain {plain['true_rel_res']:.2e} after {plain['iters_inner']}, learned "
+                  f"{learned['true_rel_res']:.2e} after {learned['iters_inner']}")
+            assert plain["true_rel_res"] > 0.1 and plain["iters_inner"] == 400, plain
+            assert learned["iters_inner"] < 400 and res < 2e-5, (learned, res)
+            # the full solve to 1e-10 with the network as right preconditioner
+            st, full = qxd.solve(c.lat, x, b, solver=qxd.SOLVER_MP_FGCR_NET, tol=1e-10, gcr_restart=32, net=net,
+                                 maxiter=3000)
+            assert st == qxd.OK and O.true_rel_residual(c.op, as_c128(x, eta.shape), eta) <= 1e-10, full
+        finally:
+            qxd.net_destroy(net)
+        # physical branch: the network reduces the iterations of the normal-equation solve
+        qxd.build_clover(c.lat, -0.12, c.csw, c.csw_qed)
+        op = O.Operator(c.lat_o, c.U, c.A, c.q, -0.12, c.csw, c.csw_qed)
+        net = qxd.net_create(c.lat, [1, 4, 4, 1], seed=7)
+        try:
+            qxd.net_train(net, vs, 32, epochs=20, batch=8, lr=2e-3)
+            st0, plain = qxd.solve(c.lat, x, b, solver=qxd.SOLVER_MP_CGNR, tol=1e-10, net=None, maxiter=5000)
+            st1, learned = qxd.solve(c.lat, x, b, solver=qxd.SOLVER_MP_CGNR, tol=1e-10, net=net, maxiter=5000)
+            assert st1 == qxd.OK and O.true_rel_residual(op, as_c128(x, eta.shape), eta) <= 1e-10
+            print(f"m0=-0.12 CGNR: {plain['iters_inner']} iterations without the network, {learned['iters_inner']} with")
+            assert learned["iters_inner"] * 2 < plain["iters_inner"], (plain, learned)
+        finally:
+            qxd.net_destroy(net)
+    finally:
+        c.close()
