@@ -286,8 +286,9 @@ def run_ours(args, rank, world):
         qxd.load_gauge(lat, su3_d, a_d, w["q"])
         qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
         upd = {}
+        Vp = synth.volume(w["L"])  # links are indexed on the physical lattice (C*: not the doubled one)
         for k in (1, 1000, 100000):
-            idx = torch.from_numpy(np.random.default_rng(k).choice(4 * V, size=k, replace=False)
+            idx = torch.from_numpy(np.random.default_rng(k).choice(4 * Vp, size=k, replace=False)
                                    .astype(np.int64)).to(dev)
             newu = torch.from_numpy(synth.random_su3(k, 17, eps=w["eps"]).view(np.float64)).to(dev)
             newa = torch.from_numpy(synth.random_angles(k, 18, scale=w["eps"])).to(dev)
