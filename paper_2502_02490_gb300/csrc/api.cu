@@ -231,8 +231,7 @@ qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
   if (lat->stream) cudaStreamSynchronize(lat->stream);
   if (lat->batch && lat->batch_release) lat->batch_release(lat->batch);
   if (lat->dfl && lat->dfl_release) lat->dfl_release(lat->dfl);
-  void* bufs[] = {lat->W16C, lat->WB16C,
-                  lat->U,    lat->A,     lat->W64,   lat->W32,   lat->W16,   lat->WB16,  lat->C64,
+  void* bufs[] = {lat->U,    lat->A,     lat->W64,   lat->W32,   lat->W16,   lat->WB16,  lat->C64,
                   lat->Ci64, lat->C32,   lat->Ci32,  lat->C16,   lat->Ci16,  lat->C16n,  lat->Ci16n,
                   lat->CB16, lat->CiB16, lat->CB16n, lat->CiB16n, lat->red,  lat->ticket, lat->scal};
   for (void* b : bufs)
@@ -330,8 +329,6 @@ qxd_status qxd_create_lattice(const int L[4], int tbc, int cstar, int order, voi
   ALLOC(W32, sizeof(float2) * 72 * sv);
   ALLOC(W16, sizeof(uint32_t) * 72 * sv);
   ALLOC(WB16, sizeof(uint32_t) * 72 * sv);
-  ALLOC(W16C, sizeof(uint32_t) * 56 * sv);
-  ALLOC(WB16C, sizeof(uint32_t) * 56 * sv);
   ALLOC(C64, sizeof(double2) * 72 * sv);
   ALLOC(Ci64, sizeof(double2) * 72 * sv);
   ALLOC(C32, sizeof(float4) * 36 * sv);

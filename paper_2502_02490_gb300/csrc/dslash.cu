@@ -91,18 +91,18 @@ static qxd_status hop16_t(qxd_lattice* lat, int kind, int par, int epi, int g5, 
   const i64 sv = lat->sv;
   SpinorN16<FMT> si{const_cast<uint2*>(in), const_cast<float*>(in_nrm), sv};
   SpinorN16<FMT> ss{const_cast<uint2*>(same), const_cast<float*>(same_nrm), sv};
-  Link16C<FMT> lk{W, sv};  // two rows and det(W): 28 B per link
+  Link16<FMT> lk{W, sv};
   Clover16<FMT> cl{C, Cn, sv};
   double bytes;
   qxd_status st;
   if (out32) {
     SpinorF32 so{out32, sv};
-    bytes = hop_bytes(lat, epi, 52, 96, 28, 152);
+    bytes = hop_bytes(lat, epi, 52, 96, 36, 152);
     prof_begin(lat, kind, bytes);
     st = launch_hop<float, QXD_HOP_PF16>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
   } else {
     SpinorN16<FMT> so{out, out_nrm, sv};
-    bytes = hop_bytes(lat, epi, 52, 52, 28, 152);
+    bytes = hop_bytes(lat, epi, 52, 52, 36, 152);
     prof_begin(lat, kind, bytes);
     st = launch_hop<float, QXD_HOP_PF16>(lat, par, epi, g5, si, ss, so, lk, cl, coef);
   }
@@ -115,9 +115,9 @@ qxd_status hop16(qxd_lattice* lat, int bf16, int par, int epi, int g5, const uin
   bool inv = epi == EPI_INV || epi == EPI_INVXPAY;
   if (bf16)
     return hop16_t<B16>(lat, KSTAT_BF16N, par, epi, g5, in, in_nrm, same, same_nrm, out, out_nrm, out32, coef,
-                        lat->WB16C, inv ? lat->CiB16 : lat->CB16, inv ? lat->CiB16n : lat->CB16n);
+                        lat->WB16, inv ? lat->CiB16 : lat->CB16, inv ? lat->CiB16n : lat->CB16n);
   return hop16_t<H16>(lat, KSTAT_F16N, par, epi, g5, in, in_nrm, same, same_nrm, out, out_nrm, out32, coef,
-                      lat->W16C, inv ? lat->Ci16 : lat->C16, inv ? lat->Ci16n : lat->C16n);
+                      lat->W16, inv ? lat->Ci16 : lat->C16, inv ? lat->Ci16n : lat->C16n);
 }
 
 }  // namespace qxd

@@ -187,34 +187,6 @@ qxd_status ingest_gauge(qxd_lattice* lat, const double2* su3, const double* a) {
   return QXD_OK;
 }
 
-// Compressed 16-bit copy of one hop link (Link16C): rows 1 and 2 and det(W), computed in FP64.
-__device__ __forceinline__ void compress_link(const double2 w[9], uint32_t* h, uint32_t* b, i64 stride) {
-  auto m = [&](int i) { return mk(w[i].x, w[i].y); };
-  const cplx<double> d = cmul(m(0), cmul(m(4), m(8)) - cmul(m(5), m(7))) -
-                         cmul(m(1), cmul(m(3), m(8)) - cmul(m(5), m(6))) +
-                         cmul(m(2), cmul(m(3), m(7)) - cmul(m(4), m(6)));
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    h[k * stride] = H16::pack((float)w[k].x, (float)w[k].y);
-    b[k * stride] = B16::pack((float)w[k].x, (float)w[k].y);
-  }
-  h[6 * stride] = H16::pack((float)d.re, (float)d.im);
-  b[6 * stride] = B16::pack((float)d.re, (float)d.im);
-}
-
-// one thread per (parity, mu, site): the compressed copies of every link
-__global__ void k_links_compress(i64 sv, const double2* __restrict__ W, uint32_t* __restrict__ WC,
-                                 uint32_t* __restrict__ WBC) {
-  const i64 n = 8 * sv;
-  for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
-    const i64 pm = t / sv, cb = t - pm * sv;  // pm = par * 4 + mu
-    double2 w[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) w[k] = W[(pm * 9 + k) * sv + cb];
-    compress_link(w, WC + pm * 7 * sv + cb, WBC + pm * 7 * sv + cb, sv);
-  }
-}
-
 // Link update on the device (the resident field changes in place, no host transfer).  Link j is
 // entry idx[j] = 4 s + mu of the canonical arrays load_gauge took (s: the physical site in the
 // lattice's site order); its new value is su3[j] (3x3 row-major) and a[j] (or 0 without angles).
@@ -248,7 +220,6 @@ __global__ void k_update_links(Geom g, int order, int Lp1, int Lp2, int Lp3, i64
                                const double2* __restrict__ su3, const double* __restrict__ a, double q,
                                double2* __restrict__ U, double* __restrict__ A, double2* __restrict__ W,
                                float2* __restrict__ W32, uint32_t* __restrict__ W16, uint32_t* __restrict__ WB16,
-                               uint32_t* __restrict__ W16C, uint32_t* __restrict__ WB16C,
                                unsigned char* __restrict__ mask, int* __restrict__ bad) {
   const int Lp[4] = {g.L[0], Lp1, Lp2, Lp3};
   const i64 Vp = (i64)Lp[0] * Lp1 * Lp2 * Lp3;
@@ -284,21 +255,17 @@ __global__ void k_update_links(Geom g, int order, int Lp1, int Lp2, int Lp3, i64
       const int par = (y[0] + y[1] + y[2] + y[3]) & 1;
       const i64 cb = lexi(g, y) >> 1;
       const i64 base = ((i64)(par * 4 + mu) * 9) * g.sv + cb;
-      double2 wl[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         double2 u = su3[j * 9 + k];
         if (copy) u.y = -u.y;
         const double2 w = make_double2(cs * u.x - sn * u.y, cs * u.y + sn * u.x);
-        wl[k] = w;
         U[base + k * g.sv] = u;
         W[base + k * g.sv] = w;
         W32[base + k * g.sv] = make_float2((float)w.x, (float)w.y);
         W16[base + k * g.sv] = H16::pack((float)w.x, (float)w.y);
         WB16[base + k * g.sv] = B16::pack((float)w.x, (float)w.y);
       }
-      const i64 cbase = ((i64)(par * 4 + mu) * 7) * g.sv + cb;
-      compress_link(wl, W16C + cbase, WB16C + cbase, g.sv);
       A[(i64)(par * 4 + mu) * g.sv + cb] = ang;
       for (int end = 0; end < 2; ++end) {
         int z[4] = {y[0], y[1], y[2], y[3]};
@@ -328,8 +295,7 @@ qxd_status update_links(qxd_lattice* lat, i64 n, const int64_t* idx, const doubl
                         unsigned char* mask, int* bad) {
   k_update_links<<<grid_cap(n, 128), 128, 0, lat->stream>>>(lat->g, lat->order, lat->Lphys[1], lat->Lphys[2],
                                                             lat->Lphys[3], n, idx, su3, a, lat->q, lat->U, lat->A,
-                                                            lat->W64, lat->W32, lat->W16, lat->WB16, lat->W16C,
-                                                            lat->WB16C, mask, bad);
+                                                            lat->W64, lat->W32, lat->W16, lat->WB16, mask, bad);
   QXD_CHECK_LAUNCH(lat, "k_update_links");
   return QXD_OK;
 }
@@ -356,8 +322,6 @@ qxd_status convert_links_low(qxd_lattice* lat) {
   i64 n = 2 * 4 * 9 * lat->sv;
   k_links_low<<<grid_cap(n, 256), 256, 0, lat->stream>>>(n, lat->W64, lat->W32, lat->W16, lat->WB16);
   QXD_CHECK_LAUNCH(lat, "k_links_low");
-  k_links_compress<<<grid_cap(8 * lat->sv, 256), 256, 0, lat->stream>>>(lat->sv, lat->W64, lat->W16C, lat->WB16C);
-  QXD_CHECK_LAUNCH(lat, "k_links_compress");
   return QXD_OK;
 }
 

@@ -459,41 +459,6 @@ struct Link16 {
   }
 };
 
-// Compressed 16-bit links [parity][mu][7][sv]: the first two rows (6 complex) and det(W) of the
-// unitary hop link W = exp(iqA) U.  For any unitary 3x3 matrix the third row is
-// det(W) conj(row1 x row2), so 7 of the 9 entries carry the link (28 B instead of 36 B).
-template <class FMT>
-struct Link16C {
-  typedef float real;
-  struct Raw {
-    uint32_t w[7];
-  };
-  const uint32_t* p;
-  i64 sv;
-  __device__ __forceinline__ Raw fetch(int par, int mu, uint32_t cb) const {
-    const uint32_t* b = p + (i64)((par * 4 + mu) * 7) * sv + cb;
-    Raw r;
-#pragma unroll
-    for (int k = 0; k < 7; ++k) r.w[k] = __ldg(b + k * sv);
-    return r;
-  }
-  __device__ __forceinline__ void decode(const Raw& r, cplx<float> u[9]) const {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) u[k] = mk(FMT::lo(r.w[k]), FMT::hi(r.w[k]));
-    const cplx<float> d = mk(FMT::lo(r.w[6]), FMT::hi(r.w[6]));
-    // row 3 = det(W) conj(row1 x row2)
-    const cplx<float> c0 = cmul(u[1], u[5]) - cmul(u[2], u[4]);
-    const cplx<float> c1 = cmul(u[2], u[3]) - cmul(u[0], u[5]);
-    const cplx<float> c2 = cmul(u[0], u[4]) - cmul(u[1], u[3]);
-    u[6] = cmul(d, mk(c0.re, -c0.im));
-    u[7] = cmul(d, mk(c1.re, -c1.im));
-    u[8] = cmul(d, mk(c2.re, -c2.im));
-  }
-  __device__ __forceinline__ void load(int par, int mu, i64 cb, cplx<float> u[9]) const {
-    decode(fetch(par, mu, (uint32_t)cb), u);
-  }
-};
-
 // ------------------------------------------------------------------------------------------
 // Clover accessors: 36 reals per (parity, block, site)
 // ------------------------------------------------------------------------------------------
@@ -652,8 +617,6 @@ struct qxd_lattice {
   float2* W32 = nullptr;
   uint32_t* W16 = nullptr;   // FP16 pairs
   uint32_t* WB16 = nullptr;  // BF16 pairs
-  uint32_t* W16C = nullptr;  // compressed FP16 links [2][4][7][sv] (Link16C)
-  uint32_t* WB16C = nullptr; // compressed BF16 links
   double q = 0;
   bool have_gauge = false;
 
