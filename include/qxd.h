@@ -437,7 +437,8 @@ qxd_status qxd_vec_dot_noalloc(const double *a, const double *b, int64_t n, doub
  * persistent batch kernel of qxd_solve_batch, counted on the batch's first lattice, 6 = tensor-core
  * PTC layer, 7 = FP32 PTC layer; bytes of a PTC layer: input channels, links and output channels
  * once per site; 8 = 16-bit multi-RHS hop; 9 = SAP block sweep, bytes: residual, x read and
- * written, links and clover once per site of the colour), the number of timed launches, their
+ * written, links and clover once per site of the colour; 10 = the vector kernels of the multi-RHS
+ * BiCGStab, bytes: the FP32 vectors each reads and writes), the number of timed launches, their
  * summed device time in ms and the summed algorithmic bytes they moved.  Reading the stats
  * synchronises the stream.  qxd_launch_count is the number of kernels the library launched. */
 qxd_status qxd_set_profiling(qxd_lattice *lat, int on);

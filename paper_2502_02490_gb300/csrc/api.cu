@@ -571,6 +571,7 @@ qxd_status qxd_apply_D(qxd_lattice* lat, double* out, const double* in, int prec
     const i64 rs = 12 * sv;
     TRY(hop32_mrhs(lat, 0, EPI_DFULL, 0, mi + 6 * sv, mi, mo, 0.f, nrhs, rs));
     TRY(hop32_mrhs(lat, 1, EPI_DFULL, 0, mi, mi + 6 * sv, mo + 6 * sv, 0.f, nrhs, rs));
+    TRY(mrhs_tile_status(lat));
     for (int r = 0; r < nrhs; ++r) {
       double* dst = out + (i64)r * 24 * lat->V;
       TRY(f32_to_f64(lat, mo + (i64)r * 12 * sv, fout, 12 * sv));

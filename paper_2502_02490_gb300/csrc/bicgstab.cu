@@ -7,8 +7,8 @@
 // The complex scalars live in device slots (SC_RHO, SC_RV, SC_TS, SC_TT, SC_RR, SC_RN); each
 // kernel recomputes alpha, omega, beta from them, so an iteration needs no host round trip.
 // Kernels work site by site (one thread per site, six float4 per site) so they can also write
-// the 16-bit copies (with per-site scale) that the next 16-bit Dhat reads; per-site products
-// are summed in FP32 and everything beyond in FP64.
+// the 16-bit copies (with per-site scale) that the next 16-bit Dhat reads; products are summed in
+// FP32 within a thread and a warp and in FP64 beyond, and the coefficients are formed once per block.
 //
 // Multi-RHS: blockIdx.y selects the right-hand side.  Its vectors sit at base + rhs * rs
 // (float4s), its scalars at scal + rhs * SC_N, its ticket at ticket + rhs and its partial sums
@@ -32,7 +32,6 @@ struct RhsView {
   unsigned int* ticket;
   double* scal;
   i64 off;  // float4 offset of this RHS's vectors
-  bool active;
 };
 
 __device__ __forceinline__ RhsView rhs_view(double* red, unsigned int* ticket, double* scal, i64 rs) {
@@ -42,7 +41,6 @@ __device__ __forceinline__ RhsView rhs_view(double* red, unsigned int* ticket, d
   v.ticket = ticket + r;
   v.scal = scal + (i64)r * SC_N;
   v.off = (i64)r * rs;
-  v.active = v.scal[SC_ACTIVE] != 0.0;
   return v;
 }
 
@@ -54,6 +52,36 @@ __device__ __forceinline__ cd2 cdiv(cd2 a, cd2 b) {
   return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
 }
 __device__ __forceinline__ cd2 cmul2(cd2 a, cd2 b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+// The BiCGStab coefficients of a block, formed once in FP64 by thread 0 from the device slots and
+// shared as FP32 (FP64 runs at 1/64 of the FP32 rate on GB300: a complex division per thread
+// would make these bandwidth-bound kernels ALU-bound).  KIND 0: -alpha; 1: alpha, omega;
+// 2: beta, omega.  Returns false, uniformly over the block, for a frozen right-hand side.
+template <int KIND>
+__device__ __forceinline__ bool block_coefs(const double* scal, float c[4]) {
+  __shared__ float sc[4];
+  __shared__ int act;
+  if (threadIdx.x == 0) {
+    act = scal[SC_ACTIVE] != 0.0;
+    const cd2 rho = {scal[SC_RHO], scal[SC_RHO + 1]};
+    const cd2 alpha = cdiv(rho, {scal[SC_RV], scal[SC_RV + 1]});
+    if (KIND == 0) {
+      sc[0] = (float)-alpha.re;
+      sc[1] = (float)-alpha.im;
+    } else {
+      const cd2 omega = {scal[SC_TS] / scal[SC_TT], scal[SC_TS + 1] / scal[SC_TT]};
+      const cd2 a = KIND == 1 ? alpha : cmul2(cdiv({scal[SC_RR], scal[SC_RR + 1]}, rho), cdiv(alpha, omega));
+      sc[0] = (float)a.re;
+      sc[1] = (float)a.im;
+      sc[2] = (float)omega.re;
+      sc[3] = (float)omega.im;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) c[k] = sc[k];
+  return act != 0;
+}
 
 __device__ __forceinline__ float4 caxpy4(float ar, float ai, float4 x, float4 y) {  // y + a x (two complex)
   return make_float4(y.x + ar * x.x - ai * x.y, y.y + ar * x.y + ai * x.x, y.z + ar * x.z - ai * x.w,
@@ -83,25 +111,23 @@ __device__ __forceinline__ void cdot4(float4 a, float4 b, float& re, float& im) 
   im += a.x * b.y - a.y * b.x + a.z * b.w - a.w * b.z;
 }
 
+// Per-thread sums (over the thread's sites) and warp sums are FP32, block and grid sums FP64
+// (block_sum_f32).
+
 // scal[slot..slot+1] = <a, b>
 __global__ void __launch_bounds__(BB) k_cdot_32(const float4* __restrict__ a, const float4* __restrict__ b, i64 sv,
                                                 i64 rs, double* red0, unsigned int* ticket0, double* scal0, int slot) {
   const RhsView rv = rhs_view(red0, ticket0, scal0, rs);
   a += rv.off;
   b += rv.off;
-  double* red = rv.red;
-  unsigned int* ticket = rv.ticket;
-  double* scal = rv.scal;
-  double v[2] = {0.0, 0.0};
+  float f[2] = {0.f, 0.f};
   for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
-    float re = 0.f, im = 0.f;
 #pragma unroll
-    for (int j = 0; j < 6; ++j) cdot4(a[j * sv + cb], b[j * sv + cb], re, im);
-    v[0] += re;
-    v[1] += im;
+    for (int j = 0; j < 6; ++j) cdot4(a[j * sv + cb], b[j * sv + cb], f[0], f[1]);
   }
-  block_sum<2, BB>(v);
-  finish_reduce<2, BB>(v, red, ticket, scal, slot);
+  double v[2] = {0.0, 0.0};
+  block_sum_f32<2, BB>(f, v);
+  finish_reduce<2, BB>(v, rv.red, rv.ticket, rv.scal, slot);
 }
 
 // s = r - alpha v, alpha = rho / <r_hat, v>; optional 16-bit s
@@ -109,8 +135,8 @@ template <class FMT, bool WR16>
 __global__ void __launch_bounds__(BB) k_bicg_s(const float4* __restrict__ r, const float4* __restrict__ v,
                                                float4* __restrict__ s, uint2* __restrict__ s16, float* __restrict__ s16n,
                                                i64 sv, i64 rs, double* scal0) {
-  const double* scal = scal0 + (i64)blockIdx.y * SC_N;
-  if (scal[SC_ACTIVE] == 0.0) return;
+  float c[4];
+  if (!block_coefs<0>(scal0 + (i64)blockIdx.y * SC_N, c)) return;
   r += (i64)blockIdx.y * rs;
   v += (i64)blockIdx.y * rs;
   s += (i64)blockIdx.y * rs;
@@ -118,8 +144,7 @@ __global__ void __launch_bounds__(BB) k_bicg_s(const float4* __restrict__ r, con
     s16 += (i64)blockIdx.y * rs;
     s16n += (i64)blockIdx.y * sv;
   }
-  const cd2 alpha = cdiv({scal[SC_RHO], scal[SC_RHO + 1]}, {scal[SC_RV], scal[SC_RV + 1]});
-  const float ar = (float)-alpha.re, ai = (float)-alpha.im;
+  const float ar = c[0], ai = c[1];
   for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
     float4 o[6];
 #pragma unroll
@@ -137,24 +162,18 @@ __global__ void __launch_bounds__(BB) k_bicg_ts(const float4* __restrict__ t, co
   const RhsView rv = rhs_view(red0, ticket0, scal0, rs);
   t += rv.off;
   s += rv.off;
-  double* red = rv.red;
-  unsigned int* ticket = rv.ticket;
-  double* scal = rv.scal;
-  double v[3] = {0.0, 0.0, 0.0};
+  float f[3] = {0.f, 0.f, 0.f};
   for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
-    float re = 0.f, im = 0.f, tt = 0.f;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       float4 a = t[j * sv + cb];
-      cdot4(a, s[j * sv + cb], re, im);
-      tt += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+      cdot4(a, s[j * sv + cb], f[0], f[1]);
+      f[2] += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
     }
-    v[0] += re;
-    v[1] += im;
-    v[2] += tt;
   }
-  block_sum<3, BB>(v);
-  finish_reduce<3, BB>(v, red, ticket, scal, SC_TS);  // SC_TS, SC_TS + 1, SC_TT = SC_TS + 2
+  double v[3] = {0.0, 0.0, 0.0};
+  block_sum_f32<3, BB>(f, v);
+  finish_reduce<3, BB>(v, rv.red, rv.ticket, rv.scal, SC_TS);  // SC_TS, SC_TS + 1, SC_TT = SC_TS + 2
 }
 
 // x += alpha p + omega s;  r = s - omega t;  scal[SC_RR..] = <r_hat, r>, scal[SC_RN] = ||r||^2
@@ -163,22 +182,17 @@ __global__ void __launch_bounds__(BB) k_bicg_xr(float4* __restrict__ x, const fl
                                                 const float4* __restrict__ rh, float4* __restrict__ r, i64 sv,
                                                 i64 rs, double* red0, unsigned int* ticket0, double* scal0) {
   const RhsView rv = rhs_view(red0, ticket0, scal0, rs);
-  if (!rv.active) return;  // uniform over the RHS's blocks: none of them takes part
+  float c[4];
+  if (!block_coefs<1>(rv.scal, c)) return;  // uniform over the RHS's blocks: none of them takes part
   x += rv.off;
   p += rv.off;
   s += rv.off;
   t += rv.off;
   rh += rv.off;
   r += rv.off;
-  double* red = rv.red;
-  unsigned int* ticket = rv.ticket;
-  double* scal = rv.scal;
-  const cd2 alpha = cdiv({scal[SC_RHO], scal[SC_RHO + 1]}, {scal[SC_RV], scal[SC_RV + 1]});
-  const cd2 omega = {scal[SC_TS] / scal[SC_TT], scal[SC_TS + 1] / scal[SC_TT]};
-  const float a_r = (float)alpha.re, a_i = (float)alpha.im, w_r = (float)omega.re, w_i = (float)omega.im;
-  double v[3] = {0.0, 0.0, 0.0};
+  const float a_r = c[0], a_i = c[1], w_r = c[2], w_i = c[3];
+  float f[3] = {0.f, 0.f, 0.f};
   for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
-    float re = 0.f, im = 0.f, rn = 0.f;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const i64 i = j * sv + cb;
@@ -186,15 +200,13 @@ __global__ void __launch_bounds__(BB) k_bicg_xr(float4* __restrict__ x, const fl
       x[i] = caxpy4(w_r, w_i, sj, caxpy4(a_r, a_i, p[i], x[i]));
       float4 rj = caxpy4(-w_r, -w_i, t[i], sj);
       r[i] = rj;
-      cdot4(rh[i], rj, re, im);
-      rn += rj.x * rj.x + rj.y * rj.y + rj.z * rj.z + rj.w * rj.w;
+      cdot4(rh[i], rj, f[0], f[1]);
+      f[2] += rj.x * rj.x + rj.y * rj.y + rj.z * rj.z + rj.w * rj.w;
     }
-    v[0] += re;
-    v[1] += im;
-    v[2] += rn;
   }
-  block_sum<3, BB>(v);
-  finish_reduce<3, BB>(v, red, ticket, scal, SC_RR);  // SC_RR, SC_RR + 1, SC_RN = SC_RR + 2
+  double v[3] = {0.0, 0.0, 0.0};
+  block_sum_f32<3, BB>(f, v);
+  finish_reduce<3, BB>(v, rv.red, rv.ticket, rv.scal, SC_RR);  // SC_RR, SC_RR + 1, SC_RN = SC_RR + 2
 }
 
 // p = r + beta (p - omega v), beta = (<r_hat,r> / rho)(alpha / omega); optional 16-bit p; the
@@ -205,7 +217,8 @@ __global__ void __launch_bounds__(BB) k_bicg_p(const float4* __restrict__ r, con
                                                i64 sv, i64 rs, unsigned int* ticket0, double* scal0) {
   double* scal = scal0 + (i64)blockIdx.y * SC_N;
   unsigned int* ticket = ticket0 + blockIdx.y;
-  if (scal[SC_ACTIVE] == 0.0) return;
+  float c[4];
+  if (!block_coefs<2>(scal, c)) return;
   r += (i64)blockIdx.y * rs;
   v += (i64)blockIdx.y * rs;
   p += (i64)blockIdx.y * rs;
@@ -213,11 +226,7 @@ __global__ void __launch_bounds__(BB) k_bicg_p(const float4* __restrict__ r, con
     p16 += (i64)blockIdx.y * rs;
     p16n += (i64)blockIdx.y * sv;
   }
-  const cd2 rho = {scal[SC_RHO], scal[SC_RHO + 1]};
-  const cd2 alpha = cdiv(rho, {scal[SC_RV], scal[SC_RV + 1]});
-  const cd2 omega = {scal[SC_TS] / scal[SC_TT], scal[SC_TS + 1] / scal[SC_TT]};
-  const cd2 beta = cmul2(cdiv({scal[SC_RR], scal[SC_RR + 1]}, rho), cdiv(alpha, omega));
-  const float b_r = (float)beta.re, b_i = (float)beta.im, w_r = (float)omega.re, w_i = (float)omega.im;
+  const float b_r = c[0], b_i = c[1], w_r = c[2], w_i = c[3];
   for (i64 cb = blockIdx.x * (i64)BB + threadIdx.x; cb < sv; cb += (i64)gridDim.x * BB) {
     float4 o[6];
 #pragma unroll

@@ -5,9 +5,10 @@
 // vector precision (global inner products and norms stay FP64).  Solver scalars (alpha, beta)
 // are read from device slots, so a solver iteration needs no host round trip.  Each thread
 // keeps UNROLL independent loads in flight.  For FP32 vectors the squares of one site (or of
-// one unrolled group of 16 values) are summed in FP32 and all further accumulation is FP64:
-// FP64 arithmetic on GB300 runs at 1/64 of the FP32 rate, so an FP64 operation per element would
-// make these bandwidth-bound kernels ALU-bound.  The CG updates work site by site so that they can
+// one unrolled group of 16 values) are summed in FP32 and all further accumulation is FP64; in
+// the CG updates the sums within a thread and a warp are FP32 too, and the update coefficient is
+// formed once per block.  FP64 arithmetic on GB300 runs at 1/64 of the FP32 rate, so FP64 work per
+// element would make these bandwidth-bound kernels ALU-bound.  The CG updates work site by site so that they can
 // also write the 16-bit copy (with its per-site scale) that the next 16-bit hop reads.
 #include "reduce.cuh"
 
@@ -147,6 +148,15 @@ __global__ void __launch_bounds__(RB) k_cg_xs_64(double2* __restrict__ x, const 
   finish_reduce<1, RB>(v, red, ticket, scal, SC_SS);
 }
 
+// scal[num] / scal[den] in FP64, formed once per block by thread 0 and shared as FP32 (an FP64
+// division per thread would make a bandwidth-bound update ALU-bound on GB300)
+__device__ __forceinline__ float block_ratio(const double* scal, int num, int den) {
+  __shared__ float q;
+  if (threadIdx.x == 0) q = (float)(scal[num] / scal[den]);
+  __syncthreads();
+  return q;
+}
+
 // x += alpha p; s -= alpha q; scal[SC_SS] = ||s||^2; optionally s16 = 16-bit copy of s.
 // alpha = scal[SC_GAMMA] / scal[SC_QQ].  One thread per site (sv sites incl. zero padding).
 template <class FMT, bool WR16>
@@ -154,11 +164,11 @@ __global__ void __launch_bounds__(RB) k_cg_xs_32(float4* __restrict__ x, const f
                                                  float4* __restrict__ s, const float4* __restrict__ q, i64 sv,
                                                  uint2* __restrict__ s16, float* __restrict__ s16n, double* red,
                                                  unsigned int* ticket, double* scal) {
-  const float alpha = (float)(scal[SC_GAMMA] / scal[SC_QQ]);
-  double v[1] = {0.0};
+  const float alpha = block_ratio(scal, SC_GAMMA, SC_QQ);
+  float f[1] = {0.f};  // FP32 within the thread and the warp, FP64 beyond (block_sum_f32)
   for (i64 cb = blockIdx.x * (i64)blockDim.x + threadIdx.x; cb < sv; cb += (i64)gridDim.x * blockDim.x) {
     float4 sn[6];
-    float g = 0.f;  // the 24 squares of one site in FP32, the sum over sites in FP64
+    float g = 0.f;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const i64 i = j * sv + cb;
@@ -176,10 +186,11 @@ __global__ void __launch_bounds__(RB) k_cg_xs_32(float4* __restrict__ x, const f
       sn[j] = si;
       g += (si.x * si.x + si.y * si.y) + (si.z * si.z + si.w * si.w);
     }
-    v[0] += (double)g;
+    f[0] += g;
     if (WR16) store_n16<FMT>(sn, s16, s16n, sv, cb);
   }
-  block_sum<1, RB>(v);
+  double v[1] = {0.0};
+  block_sum_f32<1, RB>(f, v);
   finish_reduce<1, RB>(v, red, ticket, scal, SC_SS);
 }
 
@@ -213,7 +224,7 @@ template <class FMT, bool WR16>
 __global__ void __launch_bounds__(RB) k_cg_p_32(const float4* __restrict__ r, float4* __restrict__ p, i64 sv,
                                                 uint2* __restrict__ p16, float* __restrict__ p16n,
                                                 unsigned int* ticket, double* scal) {
-  const float beta = (float)(scal[SC_GAMMA_NEW] / scal[SC_GAMMA]);
+  const float beta = block_ratio(scal, SC_GAMMA_NEW, SC_GAMMA);
   for (i64 cb = blockIdx.x * (i64)blockDim.x + threadIdx.x; cb < sv; cb += (i64)gridDim.x * blockDim.x) {
     float4 pn[6];
 #pragma unroll

@@ -1,35 +1,83 @@
-// Multi-right-hand-side hop (FP32): one link and clover load serves R right-hand sides.
+// Multi-right-hand-side hops: one link and clover load serves up to 12 right-hand sides.
 //
-// A block covers 32 consecutive output sites (threadIdx.x) times up to 12 right-hand sides
-// (threadIdx.y; rows beyond the launch's count only help load).  Phase 1: 256 threads compute the
-// 8 neighbour indices of the 32 sites into shared memory.  Phase 2: the block loads the 32 sites' 8 links (forward links of the sites,
-// backward links of their neighbours) and, when the epilogue needs it, the clover block pair
-// into shared memory, coalesced across sites.  Phase 3: every thread applies the hop for its
-// (site, rhs) with links and clover from shared memory and its neighbour spinors from global
-// memory (L1/L2 serve the reuse).  Per site and RHS the algorithmic traffic is the spinors
-// (in, out, diagonal in) plus (8 links + clover) / R.
+// FP32: a persistent kernel over tile records (32 consecutive checkerboard sites with their 8
+// neighbour indices, 8 links and clover block pair, stored contiguously); one bulk copy per tile
+// stages the record in shared memory while the block computes the previous tile.  Every thread
+// applies the hop for its (site, rhs) with links and clover from shared memory and its neighbour
+// spinors from global memory (L1/L2 serve the reuse).  Per site and RHS the algorithmic traffic
+// is the spinors (in, out, diagonal in) plus (8 links + clover) / R.
+//
+// 16 bits: spinors, links and clover with per-site FP32 norms (below).
 #include <cstdlib>
 
 #include "hop_site.cuh"
+#include "tc_common.cuh"
 
 namespace qxd {
 
-constexpr int MR_SITES = 32;
 constexpr int MR_MAXR = 12;
 
-struct MrShared {
-  uint32_t nb[8][MR_SITES];
-  unsigned char cross[2][MR_SITES];  // time-boundary crossing of the forward / backward t hop
-  float2 link[8][9][MR_SITES];
-  float4 clov[2][9][MR_SITES];
-};
+// ------------------------------------------------------------------------------------------
+// Tile records of the FP32 multi-RHS hop.  For each parity and each tile of MT_S consecutive
+// checkerboard sites one contiguous record holds everything the hop reads once per site:
+//     [clover A: 2 x 9 x MT_S float4][neighbours: 8 x MT_S uint32][links: 8 x 9 x MT_S float2]
+//     [A^-1: 2 x 9 x MT_S float4]
+// Leg 2 mu holds W_mu(x) (applied as W), leg 2 mu + 1 holds W_mu(x - mu) (applied as W^+), so the
+// backward links sit beside the site instead of at its neighbour.  A neighbour entry is the
+// checkerboard index of x +- mu; bit 31 marks a time hop across the antiperiodic boundary.  A
+// kernel stages the part it needs, [clover][neighbours][links] or [neighbours][links][A^-1], with
+// one bulk copy.  Sites beyond Vh in the last tile are zero.  The records are rebuilt whenever
+// the gauge field or the clover term changes (the lattice's epoch).
+// ------------------------------------------------------------------------------------------
+constexpr int MT_S = 32;
+constexpr uint32_t MT_CLOV = 2 * 9 * MT_S * 16;
+constexpr uint32_t MT_NB = 8 * MT_S * 4;
+constexpr uint32_t MT_W = 8 * 9 * MT_S * 8;
+constexpr uint32_t MT_OFF_NB = MT_CLOV, MT_OFF_W = MT_CLOV + MT_NB, MT_OFF_CI = MT_CLOV + MT_NB + MT_W;
+constexpr uint32_t MT_REC = 2 * MT_CLOV + MT_NB + MT_W;
+constexpr long long MT_WAIT = 1ll << 24;  // polls of a tile's mbarrier before the kernel gives up
+enum { MW_TILES = 60, MW_TILE_ERR = 61 };
+
+__global__ void k_mr_tiles(Geom g, int par, const float2* __restrict__ W, const float4* __restrict__ C,
+                           const float4* __restrict__ Ci, unsigned char* __restrict__ rec0, i64 ntiles) {
+  const i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x;
+  if (e >= ntiles * MT_S) return;
+  const i64 tile = e / MT_S, cb = e;
+  const int s = (int)(e % MT_S);
+  unsigned char* rec = rec0 + tile * MT_REC;
+  float4* cl = (float4*)rec;
+  uint32_t* nb = (uint32_t*)(rec + MT_OFF_NB);
+  float2* wl = (float2*)(rec + MT_OFF_W);
+  float4* ci = (float4*)(rec + MT_OFF_CI);
+  const bool live = cb < g.Vh;
+  int x[4] = {0, 0, 0, 0};
+  if (live) cb_coords32(g, (uint32_t)cb, par, x);
+#pragma unroll
+  for (int leg = 0; leg < 8; ++leg) {
+    const int mu = leg >> 1;
+    const bool fwd = (leg & 1) == 0;
+    bool cr = false;
+    const uint32_t n = live ? nbr_cb32(g, x, mu, fwd ? +1 : -1, cr) : 0u;
+    nb[leg * MT_S + s] = n | ((live && mu == 0 && g.anti && cr) ? 0x80000000u : 0u);
+    const int lp = fwd ? par : 1 - par;
+    const i64 site = fwd ? cb : (i64)n;
+    for (int k = 0; k < 9; ++k)
+      wl[(leg * 9 + k) * MT_S + s] = live ? W[((i64)(lp * 4 + mu) * 9 + k) * g.sv + site] : make_float2(0.f, 0.f);
+  }
+  for (int bk = 0; bk < 18; ++bk) {  // bk = blk * 9 + k
+    const i64 src = ((i64)par * 18 + bk) * g.sv + cb;
+    cl[bk * MT_S + s] = (live && C) ? C[src] : make_float4(0.f, 0.f, 0.f, 0.f);
+    ci[bk * MT_S + s] = (live && Ci) ? Ci[src] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
 
 template <int LEG, bool G5IN>
-__device__ __forceinline__ void mr_leg(const Geom& g, const MrShared& sh, int s, const float4* __restrict__ in,
-                                       i64 sv, cplx<float> acc[12]) {
+__device__ __forceinline__ void mt_leg(const uint32_t* __restrict__ nbt, const float2* __restrict__ wt, int s,
+                                       const float4* __restrict__ in, i64 sv, cplx<float> acc[12]) {
   constexpr int MU = LEG >> 1;
   constexpr bool FWD = (LEG & 1) == 0;
-  const uint32_t n = sh.nb[LEG][s];
+  const uint32_t e = nbt[LEG * MT_S + s];
+  const uint32_t n = e & 0x7fffffffu;
   cplx<float> v[12], h[6], u[9], t[6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
@@ -42,190 +90,240 @@ __device__ __forceinline__ void mr_leg(const Geom& g, const MrShared& sh, int s,
     for (int k = 6; k < 12; ++k) v[k] = neg(v[k]);
   }
   project<float, MU, FWD>(v, h);
-  if (MU == 0 && g.anti && sh.cross[FWD ? 0 : 1][s]) {
+  if (MU == 0 && (e >> 31)) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) h[k] = neg(h[k]);
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    float2 w = sh.link[LEG][k][s];
+    float2 w = wt[(LEG * 9 + k) * MT_S + s];
     u[k] = mk(w.x, w.y);
   }
   link_mul<float, !FWD>(u, h, t);
   accumulate<float, MU, FWD>(acc, t);
 }
 
-__device__ __forceinline__ void mr_clover(const MrShared& sh, int s, const cplx<float> v[12], cplx<float> y[12]) {
+// Persistent FP32 multi-RHS hop over tile records.  A block of MT_S x nr threads (site x RHS)
+// loops over tiles blockIdx.x, + gridDim.x, ...; thread 0 stages the next tile's record into the
+// other of two shared-memory buffers with one bulk copy while the block computes the current
+// tile, so the record's latency hides behind the work.  A wait that does not end within MT_WAIT
+// polls sets *err; the block then stops after its current tile and waits (bounded) for its
+// copies in flight.
+template <int EPI, bool G5>
+__global__ void __launch_bounds__(MT_S* MR_MAXR, 2)
+    k_hop_mrhs_t(Geom g, int nr, const float4* __restrict__ in, const float4* __restrict__ same,
+                 float4* __restrict__ out, i64 rs, const unsigned char* __restrict__ rec0, int ntiles, float coef,
+                 int* err) {
+  constexpr bool NEEDC = EPI != EPI_HOP && EPI != EPI_XPAY;
+  constexpr bool CI = EPI == EPI_INV || EPI == EPI_INVXPAY;
+  // staged part of a record: its offset in the record, its size, and where each piece lands
+  constexpr uint32_t SRC = (NEEDC && !CI) ? 0u : MT_OFF_NB;
+  constexpr uint32_t BYTES = NEEDC ? MT_CLOV + MT_NB + MT_W : MT_NB + MT_W;
+  constexpr uint32_t S_NB = (NEEDC && !CI) ? MT_CLOV : 0u, S_W = S_NB + MT_NB, S_CL = CI ? MT_NB + MT_W : 0u;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = (uint64_t*)(smem + 2 * BYTES);
+  volatile int* failed = (volatile int*)(bar + 2);
+  const int s = threadIdx.x, r = threadIdx.y, tid = r * MT_S + s;
+  const i64 sv = g.sv;
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    *failed = 0;
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int tile, int b) {
+    tc::mbar_expect_tx(&bar[b], BYTES);
+    tc::bulk_g2s(smem + b * BYTES, rec0 + (i64)tile * MT_REC + SRC, BYTES, &bar[b]);
+  };
+  if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  int i = 0;
+  bool pending_next = false;  // a copy into the other buffer is in flight (thread 0's view)
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+    const int b = i & 1;
+    pending_next = tile + (int)gridDim.x < ntiles;
+    if (tid == 0 && pending_next) issue(tile + gridDim.x, b ^ 1);
+    const bool ok = !*failed && tc::mbar_wait(&bar[b], (uint32_t)(i >> 1) & 1u, MT_WAIT);
+    if (!ok) *failed = 1;
+    const uint32_t cb = (uint32_t)tile * MT_S + s;
+    if (ok && r < nr && cb < (uint32_t)g.Vh) {
+      const unsigned char* buf = smem + b * BYTES;
+      const uint32_t* nbt = (const uint32_t*)(buf + S_NB);
+      const float2* wt = (const float2*)(buf + S_W);
+      const float4* ct = (const float4*)(buf + S_CL);
+      const float4* inr = in + r * rs;
+      cplx<float> acc[12];
 #pragma unroll
-  for (int blk = 0; blk < 2; ++blk) {
-    float r[36];
+      for (int k = 0; k < 12; ++k) acc[k] = mk(0.f, 0.f);
+      constexpr bool G5IN = G5 && EPI == EPI_INV;
+      mt_leg<0, G5IN>(nbt, wt, s, inr, sv, acc);
+      mt_leg<1, G5IN>(nbt, wt, s, inr, sv, acc);
+      mt_leg<2, G5IN>(nbt, wt, s, inr, sv, acc);
+      mt_leg<3, G5IN>(nbt, wt, s, inr, sv, acc);
+      mt_leg<4, G5IN>(nbt, wt, s, inr, sv, acc);
+      mt_leg<5, G5IN>(nbt, wt, s, inr, sv, acc);
+      mt_leg<6, G5IN>(nbt, wt, s, inr, sv, acc);
+      mt_leg<7, G5IN>(nbt, wt, s, inr, sv, acc);
+      auto load = [&](const float4* f, cplx<float> v[12]) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      float4 c = sh.clov[blk][k][s];
-      r[4 * k] = c.x;
-      r[4 * k + 1] = c.y;
-      r[4 * k + 2] = c.z;
-      r[4 * k + 3] = c.w;
+        for (int j = 0; j < 6; ++j) {
+          float4 q = __ldg(f + r * rs + j * sv + cb);
+          v[2 * j] = mk(q.x, q.y);
+          v[2 * j + 1] = mk(q.z, q.w);
+        }
+      };
+      auto clover = [&](const cplx<float> v[12], cplx<float> y[12]) {
+#pragma unroll
+        for (int blk = 0; blk < 2; ++blk) {
+          float c[36];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const float4 q = ct[(blk * 9 + k) * MT_S + s];
+            c[4 * k] = q.x;
+            c[4 * k + 1] = q.y;
+            c[4 * k + 2] = q.z;
+            c[4 * k + 3] = q.w;
+          }
+          herm6_apply<float>(c, v + 6 * blk, y + 6 * blk);
+        }
+      };
+      cplx<float> o[12];
+      if (EPI == EPI_HOP) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[k] = coef * acc[k];
+      } else if (EPI == EPI_DFULL || EPI == EPI_DHAT2) {
+        cplx<float> v[12], y[12];
+        load(same, v);
+        clover(v, y);
+        const float c = EPI == EPI_DFULL ? -0.5f : coef;
+        if (EPI == EPI_DHAT2 && G5) {
+#pragma unroll
+          for (int k = 6; k < 12; ++k) acc[k] = neg(acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[k] = y[k] + c * acc[k];
+      } else if (EPI == EPI_INV) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = coef * acc[k];
+        clover(acc, o);
+      } else if (EPI == EPI_INVXPAY) {
+        cplx<float> v[12];
+        load(same, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = v[k] + coef * acc[k];
+        clover(v, o);
+      } else {  // EPI_XPAY
+        cplx<float> v[12];
+        load(same, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[k] = v[k] + coef * acc[k];
+      }
+      float4* outr = out + r * rs;
+#pragma unroll
+      for (int j = 0; j < 6; ++j)
+        outr[j * sv + cb] = make_float4(o[2 * j].re, o[2 * j].im, o[2 * j + 1].re, o[2 * j + 1].im);
     }
-    herm6_apply<float>(r, v + 6 * blk, y + 6 * blk);
+    __syncthreads();  // every thread is done with buffer b before the next iteration refills it
+    if (*failed) break;
+  }
+  if (tid == 0 && *failed) {
+    atomicExch(err, 1);
+    // the copy into the other buffer issued in the last iteration may still be in flight
+    if (pending_next) tc::mbar_wait(&bar[(i & 1) ^ 1], (uint32_t)((i + 1) >> 1) & 1u, MT_WAIT);
   }
 }
 
-// in/same/out: multi-RHS fields, RHS r of parity (1-par)/par/par at base + r * rs (float4s)
+// The tile records of both parities, rebuilt when the gauge field or clover term changed.
+static qxd_status mr_tiles(qxd_lattice* lat, const unsigned char** rec, int** err) {
+  const Geom& g = lat->g;
+  const i64 nt = (g.Vh + MT_S - 1) / MT_S;
+  void *p, *e;
+  const void* before = lat->work[MW_TILES];
+  qxd_status st = ensure_work(lat, MW_TILES, (size_t)2 * nt * MT_REC, &p);
+  if (st != QXD_OK) return st;
+  st = ensure_work(lat, MW_TILE_ERR, sizeof(int), &e);
+  if (st != QXD_OK) return st;
+  if (lat->mrt_epoch != lat->epoch || before != p) {
+    QXD_CUDA(lat, cudaMemsetAsync(e, 0, sizeof(int), lat->stream));
+    for (int par = 0; par < 2; ++par) {
+      const i64 n = nt * MT_S;
+      k_mr_tiles<<<(unsigned)((n + 127) / 128), 128, 0, lat->stream>>>(g, par, lat->W32, lat->C32, lat->Ci32,
+                                                                      (unsigned char*)p + (i64)par * nt * MT_REC, nt);
+      QXD_CHECK_LAUNCH(lat, "k_mr_tiles");
+    }
+    lat->mrt_epoch = lat->epoch;
+  }
+  *rec = (const unsigned char*)p;
+  *err = (int*)e;
+  return QXD_OK;
+}
+
+qxd_status mrhs_tile_status(qxd_lattice* lat) {
+  if (!lat->work[MW_TILE_ERR]) return QXD_OK;
+  int h = 0;
+  QXD_CUDA(lat, cudaMemcpyAsync(&h, lat->work[MW_TILE_ERR], sizeof(int), cudaMemcpyDeviceToHost, lat->stream));
+  QXD_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  if (h) return fail(lat, QXD_ETIMEOUT, "a bounded wait of the multi-RHS hop expired");
+  return QXD_OK;
+}
+
 template <int EPI, bool G5>
-__global__ void __launch_bounds__(MR_SITES* MR_MAXR, 2) k_hop_mrhs(Geom g, int par, int nr, const float4* __restrict__ in,
-                                                               const float4* __restrict__ same, float4* __restrict__ out,
-                                                               i64 rs, const float2* __restrict__ W,
-                                                               const float4* __restrict__ C, float coef) {
-  __shared__ MrShared sh;
-  const int s = threadIdx.x, r = threadIdx.y;
-  constexpr int NTHR = MR_SITES * MR_MAXR;  // the block always has MR_MAXR rows; rows >= nr only load
-  const int tid = r * MR_SITES + s, nthr = NTHR;
-  const uint32_t cb0 = blockIdx.x * MR_SITES;
-  // phase 1: neighbour table (legs unrolled: register-only index math)
-  for (int ss = tid; ss < MR_SITES; ss += nthr) {
-    const uint32_t cb = cb0 + ss;
-    const bool live = cb < (uint32_t)g.Vh;
-    int x[4] = {0, 0, 0, 0};
-    if (live) cb_coords32(g, cb, par, x);
-#pragma unroll
-    for (int leg = 0; leg < 8; ++leg) {
-      bool cr = false;
-      const uint32_t nbv = live ? nbr_cb32(g, x, leg >> 1, (leg & 1) ? -1 : +1, cr) : 0u;
-      sh.nb[leg][ss] = nbv;
-      if (leg < 2) sh.cross[leg][ss] = cr && live;
-    }
-  }
-  __syncthreads();
-  // phase 2: links (and clover), every load of a thread issued before its first shared store
-  // (compile-time trip counts): one memory round trip per block
-  constexpr int NL = (8 * 9 * MR_SITES + NTHR - 1) / NTHR;
+static qxd_status launch_mrhs_t(qxd_lattice* lat, int par, const float4* in, const float4* same, float4* out,
+                                float coef, int nr, i64 rs, const unsigned char* rec, int* err) {
   constexpr bool NEEDC = EPI != EPI_HOP && EPI != EPI_XPAY;
-  constexpr int NC = NEEDC ? (2 * 9 * MR_SITES + NTHR - 1) / NTHR : 0;
-  float2 wl[NL];
-  float4 cvl[NC > 0 ? NC : 1];
-#pragma unroll
-  for (int i = 0; i < NL; ++i) {
-    const int e = tid + i * NTHR;
-    const int ss = e % MR_SITES, rest = e / MR_SITES, leg = rest / 9, k = rest % 9;
-    const uint32_t cb = cb0 + ss;
-    wl[i] = make_float2(0.f, 0.f);
-    if (e < 8 * 9 * MR_SITES && cb < (uint32_t)g.Vh) {
-      const int mu = leg >> 1;
-      const bool fwd = (leg & 1) == 0;
-      const int lp = fwd ? par : 1 - par;
-      const uint32_t site = fwd ? cb : sh.nb[leg][ss];
-      wl[i] = __ldg(W + ((i64)(lp * 4 + mu) * 9 + k) * g.sv + site);
-    }
+  constexpr uint32_t BYTES = NEEDC ? MT_CLOV + MT_NB + MT_W : MT_NB + MT_W;
+  constexpr size_t SMEM = 2 * BYTES + 2 * sizeof(uint64_t) + 16;
+  static int blocks_per_sm = 0, sms = 0;
+  if (!blocks_per_sm) {
+    int dev = 0;
+    QXD_CUDA(lat, cudaGetDevice(&dev));
+    QXD_CUDA(lat, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    QXD_CUDA(lat, cudaFuncSetAttribute((const void*)k_hop_mrhs_t<EPI, G5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SMEM));
+    int b = 0;
+    QXD_CUDA(lat, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hop_mrhs_t<EPI, G5>, MT_S * MR_MAXR, SMEM));
+    blocks_per_sm = b < 1 ? 1 : b;
   }
-#pragma unroll
-  for (int i = 0; i < NC; ++i) {
-    const int e = tid + i * NTHR;
-    const int ss = e % MR_SITES, rest = e / MR_SITES, blk = rest / 9, k = rest % 9;
-    const uint32_t cb = cb0 + ss;
-    cvl[i] = (e < 2 * 9 * MR_SITES && cb < (uint32_t)g.Vh) ? __ldg(C + ((i64)(par * 2 + blk) * 9 + k) * g.sv + cb)
-                                                          : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-#pragma unroll
-  for (int i = 0; i < NL; ++i) {
-    const int e = tid + i * NTHR;
-    if (e < 8 * 9 * MR_SITES) sh.link[(e / MR_SITES) / 9][(e / MR_SITES) % 9][e % MR_SITES] = wl[i];
-  }
-#pragma unroll
-  for (int i = 0; i < NC; ++i) {
-    const int e = tid + i * NTHR;
-    if (e < 2 * 9 * MR_SITES) sh.clov[(e / MR_SITES) / 9][(e / MR_SITES) % 9][e % MR_SITES] = cvl[i];
-  }
-  __syncthreads();
-  const uint32_t cb = cb0 + s;
-  if (cb >= (uint32_t)g.Vh || r >= nr) return;
-  const float4* inr = in + r * rs;
-  cplx<float> acc[12];
-#pragma unroll
-  for (int k = 0; k < 12; ++k) acc[k] = mk(0.f, 0.f);
-  constexpr bool G5IN = G5 && EPI == EPI_INV;
-  mr_leg<0, G5IN>(g, sh, s, inr, g.sv, acc);
-  mr_leg<1, G5IN>(g, sh, s, inr, g.sv, acc);
-  mr_leg<2, G5IN>(g, sh, s, inr, g.sv, acc);
-  mr_leg<3, G5IN>(g, sh, s, inr, g.sv, acc);
-  mr_leg<4, G5IN>(g, sh, s, inr, g.sv, acc);
-  mr_leg<5, G5IN>(g, sh, s, inr, g.sv, acc);
-  mr_leg<6, G5IN>(g, sh, s, inr, g.sv, acc);
-  mr_leg<7, G5IN>(g, sh, s, inr, g.sv, acc);
-  auto load = [&](const float4* f, cplx<float> v[12]) {
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      float4 q = __ldg(f + r * rs + j * g.sv + cb);
-      v[2 * j] = mk(q.x, q.y);
-      v[2 * j + 1] = mk(q.z, q.w);
-    }
-  };
-  cplx<float> o[12];
-  if (EPI == EPI_HOP) {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) o[k] = coef * acc[k];
-  } else if (EPI == EPI_DFULL || EPI == EPI_DHAT2) {
-    cplx<float> v[12], y[12];
-    load(same, v);
-    mr_clover(sh, s, v, y);
-    const float c = EPI == EPI_DFULL ? -0.5f : coef;
-    if (EPI == EPI_DHAT2 && G5) {
-#pragma unroll
-      for (int k = 6; k < 12; ++k) acc[k] = neg(acc[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < 12; ++k) o[k] = y[k] + c * acc[k];
-  } else if (EPI == EPI_INV) {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = coef * acc[k];
-    mr_clover(sh, s, acc, o);
-  } else if (EPI == EPI_INVXPAY) {
-    cplx<float> v[12];
-    load(same, v);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = v[k] + coef * acc[k];
-    mr_clover(sh, s, v, o);
-  } else {  // EPI_XPAY
-    cplx<float> v[12];
-    load(same, v);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) o[k] = v[k] + coef * acc[k];
-  }
-  float4* outr = out + r * rs;
-#pragma unroll
-  for (int j = 0; j < 6; ++j) outr[j * g.sv + cb] = make_float4(o[2 * j].re, o[2 * j].im, o[2 * j + 1].re, o[2 * j + 1].im);
+  const Geom& g = lat->g;
+  const int ntiles = (int)((g.Vh + MT_S - 1) / MT_S);
+  const i64 want = (i64)blocks_per_sm * sms;
+  const unsigned grid = (unsigned)(ntiles < want ? ntiles : want);
+  k_hop_mrhs_t<EPI, G5><<<grid, dim3(MT_S, nr), SMEM, lat->stream>>>(g, nr, in, same, out, rs,
+                                                                      rec + (i64)par * ntiles * MT_REC, ntiles, coef,
+                                                                      err);
+  QXD_CHECK_LAUNCH(lat, "k_hop_mrhs_t");
+  return QXD_OK;
 }
 
 qxd_status hop32_mrhs(qxd_lattice* lat, int par, int epi, int g5, const float4* in, const float4* same, float4* out,
                       float coef, int nrhs, i64 rs) {
   const Geom& g = lat->g;
+  const unsigned char* rec;
+  int* err;
+  qxd_status st = mr_tiles(lat, &rec, &err);
+  if (st != QXD_OK) return st;
   for (int r0 = 0; r0 < nrhs; r0 += MR_MAXR) {
     const int nr = nrhs - r0 < MR_MAXR ? nrhs - r0 : MR_MAXR;
-    dim3 grid((unsigned)((g.Vh + MR_SITES - 1) / MR_SITES)), block(MR_SITES, MR_MAXR);  // rows >= nr only load
     const float4* i0 = in + r0 * rs;
     const float4* s0 = same ? same + r0 * rs : nullptr;
     float4* o0 = out + r0 * rs;
-    const float4* C = (epi == EPI_INV || epi == EPI_INVXPAY) ? lat->Ci32 : lat->C32;
     // bytes: per site and RHS the spinors; links and clover once per site for the whole block
     double sp = 96.0 * (2 + ((epi == EPI_DFULL || epi == EPI_DHAT2 || epi == EPI_INVXPAY || epi == EPI_XPAY) ? 1 : 0));
     double once = 8 * 72.0 + ((epi != EPI_HOP && epi != EPI_XPAY) ? 288.0 : 0.0);
     prof_begin(lat, KSTAT_F32_MRHS, (sp * nr + once) * (double)g.Vh);
-#define QXD_MR_CASE(E, G) \
-  if (epi == E && (g5 != 0) == G) k_hop_mrhs<E, G><<<grid, block, 0, lat->stream>>>(g, par, nr, i0, s0, o0, rs, lat->W32, C, coef); else
-    QXD_MR_CASE(EPI_HOP, false)
-    QXD_MR_CASE(EPI_DFULL, false)
-    QXD_MR_CASE(EPI_INV, false)
-    QXD_MR_CASE(EPI_INV, true)
-    QXD_MR_CASE(EPI_DHAT2, false)
-    QXD_MR_CASE(EPI_DHAT2, true)
-    QXD_MR_CASE(EPI_XPAY, false)
-    QXD_MR_CASE(EPI_INVXPAY, false) {
-      prof_end(lat);
-      return fail(lat, QXD_EINVAL, "unsupported multi-RHS epilogue");
-    }
-#undef QXD_MR_CASE
+#define QXD_MT_CASE(E, G) \
+  if (epi == E && (g5 != 0) == G) st = launch_mrhs_t<E, G>(lat, par, i0, s0, o0, coef, nr, rs, rec, err); else
+    QXD_MT_CASE(EPI_HOP, false)
+    QXD_MT_CASE(EPI_DFULL, false)
+    QXD_MT_CASE(EPI_INV, false)
+    QXD_MT_CASE(EPI_INV, true)
+    QXD_MT_CASE(EPI_DHAT2, false)
+    QXD_MT_CASE(EPI_DHAT2, true)
+    QXD_MT_CASE(EPI_XPAY, false)
+    QXD_MT_CASE(EPI_INVXPAY, false) st = fail(lat, QXD_EINVAL, "unsupported multi-RHS epilogue");
+#undef QXD_MT_CASE
     prof_end(lat);
-    QXD_CHECK_LAUNCH(lat, "k_hop_mrhs");
+    if (st != QXD_OK) return st;
   }
   return QXD_OK;
 }

@@ -87,22 +87,6 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *(uint32_t*)&h;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(mbar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(mbar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   tc::smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(tc::smem_u32(mbar))
-               : "memory");
-}
-
 template <int MODE>  // 0: zero, 1: identity (path 0), 2: forward u h, 3: backward u^+ h
 __device__ __forceinline__ void put_transported_m(unsigned char* a0, int s, int slot, const cplx<float> u[9],
                                                   const float4 raw[6]) {
@@ -297,8 +281,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ptc_layer_tc(TcLayer L) {
   tc::fence_after_sync();
   const uint32_t tmem = tbase;
   if (L.b_resident && tid == 0) {
-    mbar_expect_tx(&bload, bchunk * (uint32_t)L.nchunks);
-    for (int j = 0; j < L.nchunks; ++j) bulk_g2s(sB + (size_t)j * bchunk, L.Bp + (size_t)j * bchunk, bchunk, &bload);
+    tc::mbar_expect_tx(&bload, bchunk * (uint32_t)L.nchunks);
+    for (int j = 0; j < L.nchunks; ++j) tc::bulk_g2s(sB + (size_t)j * bchunk, L.Bp + (size_t)j * bchunk, bchunk, &bload);
   }
   const i64 cs = 12 * g.sv;  // channel stride (float4)
   int my_tiles = 0;
@@ -357,8 +341,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ptc_layer_tc(TcLayer L) {
           break;
         }
         if (!L.b_resident && tid == 0) {
-          mbar_expect_tx(&full[st], bchunk);
-          bulk_g2s(sB + (size_t)st * bchunk, L.Bp + (size_t)j * bchunk, bchunk, &full[st]);
+          tc::mbar_expect_tx(&full[st], bchunk);
+          tc::bulk_g2s(sB + (size_t)st * bchunk, L.Bp + (size_t)j * bchunk, bchunk, &full[st]);
         }
         unsigned char* a0 = sA + st * TC_ABYTES;
         if constexpr (FAST)
@@ -366,7 +350,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ptc_layer_tc(TcLayer L) {
         else
           transport_chunk_pairs<IN16>(L, a0, j, s, grp, live, par, cb, x, cs);
         tc::fence_async_smem();
-        mbar_arrive(&full[st]);
+        tc::mbar_arrive(&full[st]);
       }
       if (!ok || !tc::mbar_wait(&tile_bar, it & 1, TC_WAIT)) {
         if (lane == 0) atomicExch(L.err, 1);

@@ -572,7 +572,8 @@ enum {
   KSTAT_PTC_F32 = 7,  // FP32 CUDA-core PTC layer
   KSTAT_N16_MRHS = 8, // 16-bit multi-RHS hop
   KSTAT_SAP = 9,      // SAP block minimal-residual sweep
-  KSTAT_N = 10
+  KSTAT_MR_BLAS = 10, // vector kernels of the multi-RHS BiCGStab
+  KSTAT_N = 11
 };
 
 // Device scalar slots used by the solvers and reductions.
@@ -593,8 +594,9 @@ struct Field64 {  // FP64 full field: two parities of double2 [12][sv]
 
 // device work buffers owned by a lattice (allocated on first use, grown on demand): slots 0..28 the
 // single-RHS solvers, 24..27 API staging, 29 and 31 FGCR vectors (31 also the training set), 30 the
-// clover singular flag, 32..38 multi-RHS, 39 network application, 40 FGCR coefficients
-#define QXD_WORK_SLOTS 60
+// clover singular flag, 32..38 multi-RHS, 39 network application, 40 FGCR coefficients, 60 and 61
+// the FP32 multi-RHS hop's tile records and its error word
+#define QXD_WORK_SLOTS 62
 struct qxd_lattice {
   qxd::Geom g;
   // device state of qxd_solve_batch when this lattice leads a batch (freed with the lattice)
@@ -604,6 +606,7 @@ struct qxd_lattice {
   void* dfl = nullptr;
   void (*dfl_release)(void*) = nullptr;
   qxd::i64 epoch = 0;  // counts changes of the gauge field or the clover term
+  qxd::i64 mrt_epoch = -1;  // epoch of the multi-RHS hop's tile records (work slot 60)
   int Lphys[4];
   int tbc, cstar, order;
   qxd::i64 V, Vh, sv, Vphys;
@@ -751,6 +754,9 @@ qxd_status hop16_mrhs(qxd_lattice* lat, int bf16, int par, int epi, int g5, cons
                       int nrhs);
 qxd_status hop32_mrhs(qxd_lattice* lat, int par, int epi, int g5, const float4* in, const float4* same, float4* out,
                       float coef, int nrhs, i64 rs);
+// QXD_ETIMEOUT if a bounded wait of the FP32 multi-RHS hop expired since its records were built
+// (synchronises the stream)
+qxd_status mrhs_tile_status(qxd_lattice* lat);
 
 // ---- blas.cu ----
 // n = number of complex entries; arrays are double2 (FP64) or float2-pairs (FP32 as float4 * n/2)

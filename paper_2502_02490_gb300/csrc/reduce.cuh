@@ -1,4 +1,5 @@
-// Deterministic FP64 block and grid reductions shared by the BLAS-1 and hop kernels.
+// Deterministic block and grid reductions shared by the BLAS-1 and hop kernels (FP64 beyond the
+// warp; FP32 within a warp for the FP32-vector kernels).
 //
 // Each block reduces its values with warp shuffles and shared memory; thread 0 stores the
 // block's partial in partial[j * gridDim.x + blockIdx.x]; the last block to finish (ticket
@@ -25,6 +26,28 @@ __device__ __forceinline__ void block_sum(double v[NV]) {
   for (int j = 0; j < NV; ++j) {
     v[j] = warp_sum(v[j]);
     if (lane == 0) sh[j][w] = v[j];
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = warp_sum(lane < BLOCK / 32 ? sh[j][lane] : 0.0);
+  }
+  __syncthreads();
+}
+
+// Block-reduce NV FP32 values: sums over the 32 lanes of a warp in FP32, the warp partials and
+// everything beyond in FP64 (FP64 runs at 1/64 of the FP32 rate on GB300, so an FP64 shuffle tree
+// in every thread would dominate a bandwidth-bound kernel).  Thread 0 holds the totals afterwards.
+template <int NV, int BLOCK>
+__device__ __forceinline__ void block_sum_f32(const float f[NV], double v[NV]) {
+  __shared__ double sh[NV][BLOCK / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    float x = f[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[j][w] = (double)x;
   }
   __syncthreads();
   if (w == 0) {

@@ -104,14 +104,23 @@ static qxd_status inner_mr(qxd_lattice* lat, float4* H, int n, int prec, const s
     nact += on[i];
   }
   int it = 0, rel = 0;
+  // the vector kernels timed as one class; algorithmic bytes: FP32 vectors of 96 B per site and
+  // RHS, 16-bit copies 52 B
+  const double vb = 96.0 * (double)lat->Vh * n, cb16 = low ? 52.0 * (double)lat->Vh * n : 0.0;
+  auto timed = [&](double bytes, auto&& launch) -> qxd_status {
+    prof_begin(lat, KSTAT_MR_BLAS, bytes);
+    const qxd_status st = launch();
+    prof_end(lat);
+    return st;
+  };
   while (nact > 0 && it < maxiter) {
     TRY(dhat_all(p, p16, p16n, v));
-    TRY(bicg_cdot(lat, rh, v, SC_RV, R));
-    TRY(bicg_s(lat, r, v, s, s16, s16n, bf, R));
+    TRY(timed(2 * vb, [&] { return bicg_cdot(lat, rh, v, SC_RV, R); }));
+    TRY(timed(3 * vb + cb16, [&] { return bicg_s(lat, r, v, s, s16, s16n, bf, R); }));
     TRY(dhat_all(s, s16, s16n, t));
-    TRY(bicg_ts(lat, t, s, R));
-    TRY(bicg_xr(lat, x, p, s, t, rh, r, R));
-    TRY(bicg_p(lat, r, v, p, p16, p16n, bf, R));
+    TRY(timed(2 * vb, [&] { return bicg_ts(lat, t, s, R); }));
+    TRY(timed(7 * vb, [&] { return bicg_xr(lat, x, p, s, t, rh, r, R); }));
+    TRY(timed(4 * vb + cb16, [&] { return bicg_p(lat, r, v, p, p16, p16n, bf, R); }));
     ++it;
     if (it % check_every) continue;
     TRY(read_mr(lat, n));
@@ -230,6 +239,7 @@ qxd_status solve_mrhs(qxd_lattice* lat, double2* x, const double2* b, int n, con
     int it = 0, nr = 0;
     TRY(inner_mr(lat, H, n, prm->inner_prec, act, target, prm->reliable_delta, prm->maxiter - total,
                  prm->check_every > 0 ? prm->check_every : 1, &it, &nr));
+    if (prm->inner_prec == QXD_F32) TRY(mrhs_tile_status(lat));
     total += it;
     nrel += nr;
     // reconstruct each corrected RHS: x_e += y;  x_o += A_oo^-1 (r_o + 1/2 H_oe y)

@@ -1,5 +1,6 @@
 // Blackwell (sm_103a) 5th-generation tensor-core helpers: TMEM allocation, tcgen05.mma with
-// shared-memory operand descriptors, commit to an mbarrier, TMEM loads.  Inline PTX only.
+// shared-memory operand descriptors, commit to an mbarrier, TMEM loads; mbarriers and bulk
+// global-to-shared copies (cp.async.bulk).  Inline PTX only.
 //
 // Operand layout used throughout: K-major without swizzle ("interleaved" core matrices).  A core
 // matrix is 8 rows x 16 bytes (8 bf16 along K), stored as 128 contiguous bytes.  Element (r, k) of
@@ -73,6 +74,27 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
 
 __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// arrive and add `bytes` to the transaction count the current phase waits for
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
+// make mbarrier initialisation visible to the async proxy (bulk copies) before first use
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16); completes as
+// transaction bytes on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
 }
 
 // wait for phase `parity` of the mbarrier to complete; gives up after `limit` polls (returns false)
