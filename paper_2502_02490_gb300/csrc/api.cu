@@ -323,7 +323,7 @@ qxd_status qxd_create_lattice(const int L[4], int tbc, int cstar, int order, voi
     qxd_destroy_lattice(lat);                      \
     return st;                                     \
   }
-  ALLOC(U, sizeof(double2) * 72 * sv);
+  ALLOC(U, sizeof(float4) * 72 * sv);
   ALLOC(A, sizeof(double) * 8 * sv);
   ALLOC(W64, sizeof(double2) * 72 * sv);
   ALLOC(W32, sizeof(float2) * 72 * sv);

@@ -13,7 +13,13 @@
 //   A_+ = (4 + m0) + (i/2) sum_l s_l (x) [c_sw G^+_l + q c_sw^QED g^+_l]
 //   A_- = (4 + m0) - (i/2) sum_l s_l (x) [c_sw G^-_l + q c_sw^QED g^-_l]
 // and s_l (x) Y = [[Y_3, Y_1 - i Y_2], [Y_1 + i Y_2, -Y_3]] in the index 3*alpha' + a.
+#include "df64.cuh"
 #include "qxd_internal.cuh"
+
+// minimum resident blocks per SM of the double-float product kernels (register budget)
+#ifndef QXD_CLOVER_MINB
+#define QXD_CLOVER_MINB 3
+#endif
 
 namespace qxd {
 
@@ -39,16 +45,14 @@ __device__ __forceinline__ void step(const Geom& g, int y[4], int mu, int dir) {
   }
 }
 
-__device__ __forceinline__ M3 load_u(const Geom& g, const double2* __restrict__ U, const int y[4], int mu) {
+// SU(3) link U_mu(y) from the double-float copy of the field
+__device__ __forceinline__ M3d load_u(const Geom& g, const float4* __restrict__ U, const int y[4], int mu) {
   i64 lam = lexi(g, y);
   int par = (y[0] + y[1] + y[2] + y[3]) & 1;
-  const double2* b = U + (i64)((par * 4 + mu) * 9) * g.sv + (lam >> 1);
-  M3 r;
+  const float4* b = U + (i64)((par * 4 + mu) * 9) * g.sv + (lam >> 1);
+  M3d r;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    double2 v = b[k * g.sv];
-    r.m[k] = mk(v.x, v.y);
-  }
+  for (int k = 0; k < 9; ++k) r.m[k] = cdf_load(b[k * g.sv]);
   return r;
 }
 
@@ -58,33 +62,14 @@ __device__ __forceinline__ double load_a(const Geom& g, const double* __restrict
   return A[(i64)(par * 4 + mu) * g.sv + (lam >> 1)];
 }
 
-// c = a b, with optional daggers on a and/or b
-template <bool DA, bool DB>
-__device__ __forceinline__ M3 mul(const M3& a, const M3& b) {
-  M3 c;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      cd s = mk(0.0, 0.0);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        cd x = DA ? mk(a.m[3 * k + i].re, -a.m[3 * k + i].im) : a.m[3 * i + k];
-        cd y = DB ? mk(b.m[3 * j + k].re, -b.m[3 * j + k].im) : b.m[3 * k + j];
-        s = cmac(s, x, y);  // fused: four FP64 FMAs per complex term
-      }
-      c.m[3 * i + j] = s;
-    }
-  return c;
-}
-
 // Plaquette half-products of the plane (MU, NU) at every site y: A(y) = U_mu(y) U_nu(y+mu),
-// B(y) = U_nu(y) U_mu(y+nu) (so the plaquette at y is A B^+), and the sine of the U(1)
-// plaquette angle A_mu(y) + A_nu(y+mu) - A_mu(y+nu) - A_nu(y).  Stored [k][2 sv]: k < 9 A,
-// 9 <= k < 18 B (double2), then the sines [2 sv] (doubles).
+// B(y) = U_nu(y) U_mu(y+nu) (so the plaquette at y is A B^+), in double-float arithmetic, and
+// the sine of the U(1) plaquette angle A_mu(y) + A_nu(y+mu) - A_mu(y+nu) - A_nu(y) in FP64.
+// Stored [k][2 sv]: k < 9 A, 9 <= k < 18 B (double-float complex as float4), then the sines
+// [2 sv] (doubles).
 template <int MU, int NU>
-__global__ void __launch_bounds__(128) k_clover_half(Geom g, const double2* __restrict__ U, const double* __restrict__ A,
-                                                     double2* __restrict__ Hb) {
+__global__ void __launch_bounds__(128, QXD_CLOVER_MINB) k_clover_half(Geom g, const float4* __restrict__ U, const double* __restrict__ A,
+                                                     float4* __restrict__ Hb) {
   const i64 n = 2 * g.Vh, st = 2 * g.sv;
   for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < n; e += (i64)gridDim.x * blockDim.x) {
     const int par = e >= g.Vh ? 1 : 0;
@@ -94,27 +79,35 @@ __global__ void __launch_bounds__(128) k_clover_half(Geom g, const double2* __re
     int ym[4] = {y[0], y[1], y[2], y[3]}, yn[4] = {y[0], y[1], y[2], y[3]};
     step(g, ym, MU, +1);
     step(g, yn, NU, +1);
-    const M3 a = mul<false, false>(load_u(g, U, y, MU), load_u(g, U, ym, NU));
-    const M3 b = mul<false, false>(load_u(g, U, y, NU), load_u(g, U, yn, MU));
     const i64 s0 = (i64)par * g.sv + cb;
+    {
+      const M3d a = mul_d<false, false>(load_u(g, U, y, MU), load_u(g, U, ym, NU));
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      Hb[k * st + s0] = make_double2(a.m[k].re, a.m[k].im);
-      Hb[(9 + k) * st + s0] = make_double2(b.m[k].re, b.m[k].im);
+      for (int k = 0; k < 9; ++k) Hb[k * st + s0] = cdf_store(a.m[k]);
+    }
+    {
+      const M3d b = mul_d<false, false>(load_u(g, U, y, NU), load_u(g, U, yn, MU));
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Hb[(9 + k) * st + s0] = cdf_store(b.m[k]);
     }
     ((double*)(Hb + 18 * st))[s0] =
         sin(load_a(g, A, y, MU) + load_a(g, A, ym, NU) - load_a(g, A, yn, MU) - load_a(g, A, y, NU));
   }
 }
 
-__device__ __forceinline__ M3 load_h(const double2* __restrict__ Hb, i64 st, i64 s, int which) {
-  M3 r;
+__device__ __forceinline__ M3d load_h(const float4* __restrict__ Hb, i64 st, i64 s, int which) {
+  M3d r;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const double2 v = Hb[(which * 9 + k) * st + s];
-    r.m[k] = mk(v.x, v.y);
-  }
+  for (int k = 0; k < 9; ++k) r.m[k] = cdf_load(Hb[(which * 9 + k) * st + s]);
   return r;
+}
+
+// the sum of leaves in FP64
+__device__ __forceinline__ M3 q_of(const dacc acc[18]) {
+  M3 Q;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Q.m[k] = mk(df_join(dacc_get(acc[2 * k])), df_join(dacc_get(acc[2 * k + 1])));
+  return Q;
 }
 
 __device__ __forceinline__ i64 site_of(const Geom& g, const int y[4]) {
@@ -155,7 +148,7 @@ __device__ __forceinline__ void store_fs(const M3& Q, double f1, double* __restr
 // (each leaf is its plaquette rotated to start at x, so its U(1) angle is the plaquette's);
 // then Fhat = (Q - Q^+)/8 traceless and fhat = 1/4 sum of the sines, stored in the compact layout below.
 template <int MU, int NU>
-__global__ void __launch_bounds__(128) k_clover_leaves(Geom g, const double2* __restrict__ U, const double2* __restrict__ Hb,
+__global__ void __launch_bounds__(128, QXD_CLOVER_MINB) k_clover_leaves(Geom g, const float4* __restrict__ U, const float4* __restrict__ Hb,
                                                        int p, double* __restrict__ Fb) {
   const i64 n = 2 * g.Vh, st = 2 * g.sv;
   const double* sn = (const double*)(Hb + 18 * st);
@@ -170,23 +163,15 @@ __global__ void __launch_bounds__(128) k_clover_leaves(Geom g, const double2* __
     int xmn[4] = {xm[0], xm[1], xm[2], xm[3]};
     step(g, xmn, NU, -1);
     const i64 s0 = (i64)par * g.sv + cb, s1 = site_of(g, xm), s2 = site_of(g, xmn), s3 = site_of(g, xn);
-    M3 Q = mul<false, true>(load_h(Hb, st, s0, 0), load_h(Hb, st, s0, 1));
-    {
-      const M3 r = mul<false, false>(mul<false, true>(load_u(g, U, x, NU), load_h(Hb, st, s1, 1)), load_u(g, U, xm, MU));
+    // Q = the sum of the four leaves; the last product of every leaf accumulates into Q directly
+    dacc q[18];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
-    }
-    {
-      const M3 r = mul<true, false>(load_h(Hb, st, s2, 1), load_h(Hb, st, s2, 0));
-#pragma unroll
-      for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
-    }
-    {
-      const M3 r = mul<false, true>(mul<true, false>(load_u(g, U, xn, NU), load_h(Hb, st, s3, 0)), load_u(g, U, x, MU));
-#pragma unroll
-      for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
-    }
-    store_fs(Q, 0.25 * (sn[s0] + sn[s1] + sn[s2] + sn[s3]), Fb + (i64)p * 10 * st + s0, st);
+    for (int k = 0; k < 18; ++k) q[k] = dacc_zero();
+    mac3<false, true>(q, load_h(Hb, st, s0, 0), load_h(Hb, st, s0, 1));
+    mac3<false, false>(q, mul_d<false, true>(load_u(g, U, x, NU), load_h(Hb, st, s1, 1)), load_u(g, U, xm, MU));
+    mac3<true, false>(q, load_h(Hb, st, s2, 1), load_h(Hb, st, s2, 0));
+    mac3<false, true>(q, mul_d<true, false>(load_u(g, U, xn, NU), load_h(Hb, st, s3, 0)), load_u(g, U, x, MU));
+    store_fs(q_of(q), 0.25 * (sn[s0] + sn[s1] + sn[s2] + sn[s3]), Fb + (i64)p * 10 * st + s0, st);
   }
 }
 
@@ -195,7 +180,7 @@ __global__ void __launch_bounds__(128) k_clover_leaves(Geom g, const double2* __
 // U(1) part from the four plaquette angles; written in the layout of k_clover_leaves at list
 // position e with stride nl.
 template <int MU, int NU>
-__global__ void __launch_bounds__(128) k_fs_sites(Geom g, const double2* __restrict__ U, const double* __restrict__ A,
+__global__ void __launch_bounds__(128) k_fs_sites(Geom g, const float4* __restrict__ U, const double* __restrict__ A,
                                                   const uint32_t* __restrict__ list, i64 nl, int p,
                                                   double* __restrict__ Fc) {
   for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < nl; e += (i64)gridDim.x * blockDim.x) {
@@ -214,100 +199,66 @@ __global__ void __launch_bounds__(128) k_fs_sites(Geom g, const double2* __restr
     step(g, xmn, NU, -1);
     step(g, xmpn, NU, +1);
     step(g, xnpm, MU, +1);
+    dacc q[18];
+#pragma unroll
+    for (int k = 0; k < 18; ++k) q[k] = dacc_zero();
     // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
-    M3 Q = mul<false, true>(mul<false, true>(mul<false, false>(load_u(g, U, x, MU), load_u(g, U, xpm, NU)),
-                                             load_u(g, U, xpn, MU)),
-                            load_u(g, U, x, NU));
+    mac3<false, true>(q,
+                      mul_d<false, true>(mul_d<false, false>(load_u(g, U, x, MU), load_u(g, U, xpm, NU)),
+                                         load_u(g, U, xpn, MU)),
+                      load_u(g, U, x, NU));
     // leaf 2: U_nu(x) U_mu(x-mu+nu)^+ U_nu(x-mu)^+ U_mu(x-mu)
-    {
-      const M3 r = mul<false, false>(mul<false, true>(mul<false, true>(load_u(g, U, x, NU), load_u(g, U, xmpn, MU)),
-                                                      load_u(g, U, xm, NU)),
-                                     load_u(g, U, xm, MU));
-#pragma unroll
-      for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
-    }
+    mac3<false, false>(q,
+                       mul_d<false, true>(mul_d<false, true>(load_u(g, U, x, NU), load_u(g, U, xmpn, MU)),
+                                          load_u(g, U, xm, NU)),
+                       load_u(g, U, xm, MU));
     // leaf 3: U_mu(x-mu)^+ U_nu(x-mu-nu)^+ U_mu(x-mu-nu) U_nu(x-nu)
-    {
-      const M3 r = mul<false, false>(mul<false, false>(mul<true, true>(load_u(g, U, xm, MU), load_u(g, U, xmn, NU)),
-                                                       load_u(g, U, xmn, MU)),
-                                     load_u(g, U, xn, NU));
-#pragma unroll
-      for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
-    }
+    mac3<false, false>(q,
+                       mul_d<false, false>(mul_d<true, true>(load_u(g, U, xm, MU), load_u(g, U, xmn, NU)),
+                                           load_u(g, U, xmn, MU)),
+                       load_u(g, U, xn, NU));
     // leaf 4: U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^+
-    {
-      const M3 r = mul<false, true>(mul<false, false>(mul<true, false>(load_u(g, U, xn, NU), load_u(g, U, xn, MU)),
-                                                      load_u(g, U, xnpm, NU)),
-                                    load_u(g, U, x, MU));
-#pragma unroll
-      for (int k = 0; k < 9; ++k) Q.m[k] = Q.m[k] + r.m[k];
-    }
+    mac3<false, true>(q,
+                      mul_d<false, false>(mul_d<true, false>(load_u(g, U, xn, NU), load_u(g, U, xn, MU)),
+                                          load_u(g, U, xnpm, NU)),
+                      load_u(g, U, x, MU));
     // U(1): plaquette angle th(c) = A_mu(c) + A_nu(c+mu) - A_mu(c+nu) - A_nu(c) at the corners
     // x, x-mu, x-mu-nu, x-nu of the four leaves
     const double s0 = sin(load_a(g, A, x, MU) + load_a(g, A, xpm, NU) - load_a(g, A, xpn, MU) - load_a(g, A, x, NU));
     const double s1 = sin(load_a(g, A, xm, MU) + load_a(g, A, x, NU) - load_a(g, A, xmpn, MU) - load_a(g, A, xm, NU));
     const double s2 = sin(load_a(g, A, xmn, MU) + load_a(g, A, xn, NU) - load_a(g, A, xm, MU) - load_a(g, A, xmn, NU));
     const double s3 = sin(load_a(g, A, xn, MU) + load_a(g, A, xnpm, NU) - load_a(g, A, x, MU) - load_a(g, A, xn, NU));
-    store_fs(Q, 0.25 * (s0 + s1 + s2 + s3), Fc + (i64)p * 10 * nl + e, nl);
+    store_fs(q_of(q), 0.25 * (s0 + s1 + s2 + s3), Fc + (i64)p * 10 * nl + e, nl);
   }
 }
 
 // Field strengths per site and plane (written by k_clover_leaves): planes 0..2 = (0,1) (0,2)
 // (0,3), 3 = (2,3), 4 = (1,3), 5 = (1,2); 10 doubles [plane][k][2 sv]: Im F_00, Im F_11, Im F_22,
 // (Re, Im) F_01, F_02, F_12 (the lower triangle is -conj), and fhat.
-__device__ __forceinline__ void load_fs(const double* __restrict__ Fb, i64 st, i64 s, int p, cd F[9], double& f1) {
-  const double* o = Fb + (i64)p * 10 * st + s;
-  const cd a01 = mk(o[3 * st], o[4 * st]), a02 = mk(o[5 * st], o[6 * st]), a12 = mk(o[7 * st], o[8 * st]);
-  F[0] = mk(0.0, o[0]);
-  F[4] = mk(0.0, o[st]);
-  F[8] = mk(0.0, o[2 * st]);
-  F[1] = a01;
-  F[2] = a02;
-  F[5] = a12;
-  F[3] = mk(-a01.re, a01.im);  // -conj
-  F[6] = mk(-a02.re, a02.im);
-  F[7] = mk(-a12.re, a12.im);
-  f1 = o[9 * st];
-}
-
-// blk (6x6, full storage) += s * sigma_l (x) Y,  s complex
-__device__ __forceinline__ void add_sigma(cd blk[36], int l, cd s, const cd Y[9]) {
-  // sigma_1: (0,1) = 1, (1,0) = 1; sigma_2: (0,1) = -i, (1,0) = i; sigma_3: (0,0) = 1, (1,1) = -1
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      cd y = cmul(s, Y[3 * a + b]);
-      if (l == 1) {
-        blk[(a) * 6 + (3 + b)] = blk[(a) * 6 + (3 + b)] + y;
-        blk[(3 + a) * 6 + b] = blk[(3 + a) * 6 + b] + y;
-      } else if (l == 2) {
-        blk[(a) * 6 + (3 + b)] = blk[(a) * 6 + (3 + b)] + mk(y.im, -y.re);  // -i y
-        blk[(3 + a) * 6 + b] = blk[(3 + a) * 6 + b] + timesI(y);
-      } else {
-        blk[(a) * 6 + b] = blk[(a) * 6 + b] + y;
-        blk[(3 + a) * 6 + (3 + b)] = blk[(3 + a) * 6 + (3 + b)] - y;
-      }
-    }
-}
-
-__device__ __forceinline__ void pack_block(const cd blk[36], double r[36]) {
-#pragma unroll
-  for (int i = 0; i < 6; ++i) r[i] = blk[7 * i].re;
-  int k = 0;
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int j = i + 1; j < 6; ++j) {
-      // symmetrise the rounding of the two triangles
-      r[6 + 2 * k] = 0.5 * (blk[6 * i + j].re + blk[6 * j + i].re);
-      r[7 + 2 * k] = 0.5 * (blk[6 * i + j].im - blk[6 * j + i].im);
-      ++k;
-    }
+// Y_l = c_sw (F_el + smag F_ml) + i q c_sw^QED (f_el + smag f_ml) 1 (anti-Hermitian, 3x3), as a
+// full 3x3 array (the lower triangle is -conj of the upper).
+__device__ __forceinline__ void y_full(const double* __restrict__ Fb, i64 st, i64 s, int l, double smag, double csw,
+                                       double cq, cd Y[9]) {
+  const double* e = Fb + (i64)l * 10 * st + s;
+  const double* m = Fb + (i64)(3 + l) * 10 * st + s;
+  const double gv = cq * (e[9 * st] + smag * m[9 * st]);
+  Y[0] = mk(0.0, csw * (e[0] + smag * m[0]) + gv);
+  Y[4] = mk(0.0, csw * (e[st] + smag * m[st]) + gv);
+  Y[8] = mk(0.0, csw * (e[2 * st] + smag * m[2 * st]) + gv);
+  Y[1] = mk(csw * (e[3 * st] + smag * m[3 * st]), csw * (e[4 * st] + smag * m[4 * st]));
+  Y[2] = mk(csw * (e[5 * st] + smag * m[5 * st]), csw * (e[6 * st] + smag * m[6 * st]));
+  Y[5] = mk(csw * (e[7 * st] + smag * m[7 * st]), csw * (e[8 * st] + smag * m[8 * st]));
+  Y[3] = mk(-Y[1].re, Y[1].im);
+  Y[6] = mk(-Y[2].re, Y[2].im);
+  Y[7] = mk(-Y[5].re, Y[5].im);
 }
 
 // A_+- of every site from the stored field strengths: G^{+-}_l = F_{0l} -+ sgn_l F_mag(l) with the
-// magnetic planes (2,3), (1,3), (1,2) of sign +1, -1, +1; one chiral block at a time.
+// magnetic planes (2,3), (1,3), (1,2) of sign +1, -1, +1; one chiral block at a time.  With
+// s = side i (side = +1/2 on A_+, -1/2 on A_-) the block is diag 1 + s sum_l sigma_l (x) Y_l, i.e.
+// in 3x3 spin blocks: upper left diag + s Y_3, lower right diag - s Y_3, upper right
+// s Y_1 - i s Y_2 (the lower left is its adjoint).  Only the stored upper triangle is formed, so
+// the block is Hermitian by construction.
 // With a list (link-update path) only the listed sites, their field strengths at list position e
 // with stride nl.
 __global__ void __launch_bounds__(128) k_clover_assemble(Geom g, const double* __restrict__ Fb, double diag, double csw,
@@ -321,33 +272,38 @@ __global__ void __launch_bounds__(128) k_clover_assemble(Geom g, const double* _
     const i64 s = list ? e : (i64)par * g.sv + cb;
 #pragma unroll
     for (int blkid = 0; blkid < 2; ++blkid) {
-      cd blk[36];
-#pragma unroll
-      for (int k = 0; k < 36; ++k) blk[k] = mk(0.0, 0.0);
-#pragma unroll
-      for (int i = 0; i < 6; ++i) blk[7 * i] = mk(diag, 0.0);
-      const double side = blkid == 0 ? 0.5 : -0.5;  // +(i/2) on A_+, -(i/2) on A_-
-#pragma unroll
-      for (int l = 0; l < 3; ++l) {
-        const double sgn = l == 1 ? -1.0 : 1.0;
-        const double smag = blkid == 0 ? -sgn : sgn;
-        cd Fe[9], Fm[9], Y[9];
-        double fe, fm;
-        load_fs(Fb, st, s, l, Fe, fe);
-        load_fs(Fb, st, s, 3 + l, Fm, fm);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Y[k] = csw * (Fe[k] + smag * Fm[k]);
-        const double gv = cq * (fe + smag * fm);
-        Y[0].im += gv;
-        Y[4].im += gv;
-        Y[8].im += gv;
-        add_sigma(blk, l + 1, mk(0.0, side), Y);
-      }
-      double r[36];
-      pack_block(blk, r);
+      const double side = blkid == 0 ? 0.5 : -0.5;
+      const double smag1 = blkid == 0 ? -1.0 : 1.0;  // smag_l = -+ sgn_l, sgn = (+1, -1, +1)
+      cd y1[9], y2[9], y3[9];
+      y_full(Fb, st, s, 0, smag1, csw, cq, y1);
+      y_full(Fb, st, s, 1, -smag1, csw, cq, y2);
+      y_full(Fb, st, s, 2, smag1, csw, cq, y3);
+      // packed block: entries 0..2 the six real diagonal elements in pairs, 3 + k the k-th element
+      // (i < j, row-major) of the upper triangle
       double2* out = C + (i64)((par * 2 + blkid) * 18) * g.sv + cb;
+      // diagonal: diag -+ side Im Y_3,aa (Re of s Y_3,aa = -side Im Y_3,aa)
+      out[0] = make_double2(diag - side * y3[0].im, diag - side * y3[4].im);
+      out[g.sv] = make_double2(diag - side * y3[8].im, diag + side * y3[0].im);
+      out[2 * g.sv] = make_double2(diag + side * y3[4].im, diag + side * y3[8].im);
 #pragma unroll
-      for (int k = 0; k < 18; ++k) out[k * g.sv] = make_double2(r[2 * k], r[2 * k + 1]);
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 6; ++j) {
+          const int k = i * 5 - i * (i - 1) / 2 + (j - i - 1);  // position of (i, j) in the upper triangle
+          const int al = i / 3, a = i % 3, be = j / 3, b = j % 3;
+          cd v;
+          if (al == 0 && be == 0) {  // s Y_3
+            const cd w = y3[3 * a + b];
+            v = mk(-side * w.im, side * w.re);
+          } else if (al == 1) {  // -s Y_3
+            const cd w = y3[3 * a + b];
+            v = mk(side * w.im, -side * w.re);
+          } else {  // s Y_1 - i s Y_2 = side (i Y_1 + Y_2)
+            const cd w1 = y1[3 * a + b], w2 = y2[3 * a + b];
+            v = mk(side * (w2.re - w1.im), side * (w1.re + w2.im));
+          }
+          out[(3 + k) * g.sv] = make_double2(v.re, v.im);
+        }
     }
   }
 }
@@ -534,26 +490,28 @@ static int grid_cap(i64 n, int bs) {
 
 qxd_status clover_build(qxd_lattice* lat) {
   const Geom& g = lat->g;
-  // field strengths of the six planes (one thread per site and plane), then the blocks; the
-  // field-strength buffer (10 doubles per site and plane) is released afterwards
-  // plane by plane: plaquette half-products (and U(1) sines) at every site, then the four leaves
-  // of every site from them (8 3x3 products per site and plane instead of 12)
+  // field strengths of the six planes (one thread per site and plane), then the blocks; plane by
+  // plane: plaquette half-products (and U(1) sines) at every site, then the four leaves of every
+  // site from them (8 3x3 products per site and plane instead of 12).  Both scratch buffers
+  // (field strengths: 10 doubles per site and plane; half-products: 19 x 16 B per site) stay
+  // with the lattice (work slots 62 and 63), so a rebuild allocates nothing.
   double* Fb;
-  double2* Hb;
-  QXD_CUDA(lat, cudaMalloc(&Fb, sizeof(double) * 6 * 10 * 2 * g.sv));
-  if (cudaMalloc(&Hb, sizeof(double2) * 19 * 2 * g.sv) != cudaSuccess) {
-    cudaFree(Fb);
-    return fail(lat, QXD_ENOMEM, "clover build scratch");
+  float4* Hb;
+  {
+    void *f, *h;
+    qxd_status st = ensure_work(lat, 62, sizeof(double) * 6 * 10 * 2 * g.sv, &f);
+    if (st != QXD_OK) return st;
+    st = ensure_work(lat, 63, sizeof(float4) * 19 * 2 * g.sv, &h);
+    if (st != QXD_OK) return st;
+    Fb = (double*)f;
+    Hb = (float4*)h;
   }
-  cudaError_t le = cudaSuccess;
   const int gc = grid_cap(2 * g.Vh, 128);
-#define QXD_PLANE(P, M, N)                                                                  \
-  if (le == cudaSuccess) {                                                                  \
-    k_clover_half<M, N><<<gc, 128, 0, lat->stream>>>(g, lat->U, lat->A, Hb);                \
-    k_clover_leaves<M, N><<<gc, 128, 0, lat->stream>>>(g, lat->U, Hb, P, Fb);               \
-    le = cudaGetLastError();                                                                \
-    if (le == cudaSuccess) lat->launches += 2;                                              \
-  }
+#define QXD_PLANE(P, M, N)                                                     \
+  k_clover_half<M, N><<<gc, 128, 0, lat->stream>>>(g, lat->U, lat->A, Hb);      \
+  QXD_CHECK_LAUNCH(lat, "k_clover_half");                                       \
+  k_clover_leaves<M, N><<<gc, 128, 0, lat->stream>>>(g, lat->U, Hb, P, Fb);     \
+  QXD_CHECK_LAUNCH(lat, "k_clover_leaves");
   QXD_PLANE(0, 0, 1)
   QXD_PLANE(1, 0, 2)
   QXD_PLANE(2, 0, 3)
@@ -561,16 +519,9 @@ qxd_status clover_build(qxd_lattice* lat) {
   QXD_PLANE(4, 1, 3)
   QXD_PLANE(5, 1, 2)
 #undef QXD_PLANE
-  if (le == cudaSuccess) {
-    k_clover_assemble<<<grid_cap(2 * g.Vh, 128), 128, 0, lat->stream>>>(g, Fb, 4.0 + lat->m0, lat->csw,
-                                                                        lat->q * lat->csw_qed, lat->C64, nullptr, 0);
-    le = cudaGetLastError();
-    if (le == cudaSuccess) lat->launches++;
-  }
-  cudaStreamSynchronize(lat->stream);
-  cudaFree(Fb);
-  cudaFree(Hb);
-  if (le != cudaSuccess) return cuda_fail(lat, le, "k_clover_half / k_clover_leaves / k_clover_assemble");
+  k_clover_assemble<<<grid_cap(2 * g.Vh, 128), 128, 0, lat->stream>>>(g, Fb, 4.0 + lat->m0, lat->csw,
+                                                                      lat->q * lat->csw_qed, lat->C64, nullptr, 0);
+  QXD_CHECK_LAUNCH(lat, "k_clover_assemble");
   void* w;
   qxd_status st = ensure_work(lat, 30, sizeof(int), &w);  // slot 30: clover singular flag
   if (st) return st;

@@ -5,6 +5,7 @@
 //   LEXI: boundary index = Lambda(x, L).  IPT: Eq. ipt with the lattice's cache blocks B
 //   (ipt_index / ipt_coords; B = L gives cb + P(x) V/2).
 // Both map onto the device's (parity, cb = floor(Lambda/2)) addressing.
+#include "df64.cuh"
 #include "qxd_internal.cuh"
 
 namespace qxd {
@@ -91,7 +92,7 @@ qxd_status unpack_spinor64(qxd_lattice* lat, const double2* field, double2* bnd,
 // conjugated and whose angle changes sign (Sec. 4.2).  Hop link W = exp(i q A) U (Sec. 4.3).
 __global__ void k_ingest_gauge(Geom g, int order, int Lp1, int Lp2, int Lp3, i64 Vph,
                                const double2* __restrict__ su3, const double* __restrict__ a, double q,
-                               double2* __restrict__ U, double* __restrict__ A, double2* __restrict__ W) {
+                               float4* __restrict__ U, double* __restrict__ A, double2* __restrict__ W) {
   i64 n = 2 * g.Vh * 4;
   for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
     int mu = (int)(t & 3);
@@ -126,7 +127,7 @@ __global__ void k_ingest_gauge(Geom g, int order, int Lp1, int Lp2, int Lp3, i64
     for (int k = 0; k < 9; ++k) {
       double2 u = su3[(src * 4 + mu) * 9 + k];
       if (mirror) u.y = -u.y;
-      U[base + k * g.sv] = u;
+      U[base + k * g.sv] = cdf_split(u.x, u.y);
       W[base + k * g.sv] = make_double2(cs * u.x - sn * u.y, cs * u.y + sn * u.x);
     }
     A[(i64)(par * 4 + mu) * g.sv + cb] = ang;
@@ -139,7 +140,7 @@ __global__ void k_ingest_gauge(Geom g, int order, int Lp1, int Lp2, int Lp3, i64
 // end).  The field is the lattice's own (for C* the
 // doubled lattice, mirror half included): no mirroring here.  One thread per (device site, mu).
 __global__ void k_ingest_openqxd(Geom g, const double2* __restrict__ u8, const double* __restrict__ a8, double q,
-                                 double2* __restrict__ U, double* __restrict__ A, double2* __restrict__ W) {
+                                 float4* __restrict__ U, double* __restrict__ A, double2* __restrict__ W) {
   const i64 n = 2 * g.Vh * 4;
   for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
     const int mu = (int)(t & 3);
@@ -164,7 +165,7 @@ __global__ void k_ingest_openqxd(Geom g, const double2* __restrict__ u8, const d
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const double2 u = u8[e * 9 + k];
-      U[base + k * g.sv] = u;
+      U[base + k * g.sv] = cdf_split(u.x, u.y);
       W[base + k * g.sv] = make_double2(cs * u.x - sn * u.y, cs * u.y + sn * u.x);
     }
     A[(i64)(par * 4 + mu) * g.sv + cb] = ang;
@@ -218,7 +219,7 @@ __device__ __forceinline__ void shift_site(const Geom& g, int y[4], int mu, int 
 
 __global__ void k_update_links(Geom g, int order, int Lp1, int Lp2, int Lp3, i64 n, const int64_t* __restrict__ idx,
                                const double2* __restrict__ su3, const double* __restrict__ a, double q,
-                               double2* __restrict__ U, double* __restrict__ A, double2* __restrict__ W,
+                               float4* __restrict__ U, double* __restrict__ A, double2* __restrict__ W,
                                float2* __restrict__ W32, uint32_t* __restrict__ W16, uint32_t* __restrict__ WB16,
                                unsigned char* __restrict__ mask, int* __restrict__ bad) {
   const int Lp[4] = {g.L[0], Lp1, Lp2, Lp3};
@@ -260,7 +261,7 @@ __global__ void k_update_links(Geom g, int order, int Lp1, int Lp2, int Lp3, i64
         double2 u = su3[j * 9 + k];
         if (copy) u.y = -u.y;
         const double2 w = make_double2(cs * u.x - sn * u.y, cs * u.y + sn * u.x);
-        U[base + k * g.sv] = u;
+        U[base + k * g.sv] = cdf_split(u.x, u.y);
         W[base + k * g.sv] = w;
         W32[base + k * g.sv] = make_float2((float)w.x, (float)w.y);
         W16[base + k * g.sv] = H16::pack((float)w.x, (float)w.y);

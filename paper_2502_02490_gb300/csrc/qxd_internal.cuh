@@ -595,8 +595,8 @@ struct Field64 {  // FP64 full field: two parities of double2 [12][sv]
 // device work buffers owned by a lattice (allocated on first use, grown on demand): slots 0..28 the
 // single-RHS solvers, 24..27 API staging, 29 and 31 FGCR vectors (31 also the training set), 30 the
 // clover singular flag, 32..38 multi-RHS, 39 network application, 40 FGCR coefficients, 60 and 61
-// the FP32 multi-RHS hop's tile records and its error word
-#define QXD_WORK_SLOTS 62
+// the FP32 multi-RHS hop's tile records and its error word, 62 and 63 the clover build's scratch
+#define QXD_WORK_SLOTS 64
 struct qxd_lattice {
   qxd::Geom g;
   // device state of qxd_solve_batch when this lattice leads a batch (freed with the lattice)
@@ -614,7 +614,7 @@ struct qxd_lattice {
   int device = 0;
 
   // gauge field (FP64): SU(3) links, U(1) angles, hop links W = exp(iqA) U
-  double2* U = nullptr;   // [2][4][9][sv]
+  float4* U = nullptr;    // [2][4][9][sv] SU(3) links as double-float {re.hi, re.lo, im.hi, im.lo} (clover build)
   double* A = nullptr;    // [2][4][sv]
   double2* W64 = nullptr; // [2][4][9][sv]
   float2* W32 = nullptr;
