@@ -17,6 +17,12 @@ namespace qxd {
 
 constexpr int MR_MAXR = 12;
 
+// The right-hand sides one launch works on: local row r of a block is right-hand side idx[r]
+// (its fields at base + idx[r] * rs), so frozen right-hand sides cost no hop work.
+struct MrList {
+  int idx[MR_MAXR];
+};
+
 // ------------------------------------------------------------------------------------------
 // Tile records of the FP32 multi-RHS hop.  For each parity and each tile of MT_S consecutive
 // checkerboard sites one contiguous record holds everything the hop reads once per site:
@@ -111,7 +117,7 @@ __device__ __forceinline__ void mt_leg(const uint32_t* __restrict__ nbt, const f
 // copies in flight.
 template <int EPI, bool G5>
 __global__ void __launch_bounds__(MT_S* MR_MAXR, 2)
-    k_hop_mrhs_t(Geom g, int nr, const float4* __restrict__ in, const float4* __restrict__ same,
+    k_hop_mrhs_t(Geom g, int nr, MrList lst, const float4* __restrict__ in, const float4* __restrict__ same,
                  float4* __restrict__ out, i64 rs, const unsigned char* __restrict__ rec0, int ntiles, float coef,
                  int* err) {
   constexpr bool NEEDC = EPI != EPI_HOP && EPI != EPI_XPAY;
@@ -151,7 +157,8 @@ __global__ void __launch_bounds__(MT_S* MR_MAXR, 2)
       const uint32_t* nbt = (const uint32_t*)(buf + S_NB);
       const float2* wt = (const float2*)(buf + S_W);
       const float4* ct = (const float4*)(buf + S_CL);
-      const float4* inr = in + r * rs;
+      const i64 ro = (i64)lst.idx[r] * rs;
+      const float4* inr = in + ro;
       cplx<float> acc[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] = mk(0.f, 0.f);
@@ -167,7 +174,7 @@ __global__ void __launch_bounds__(MT_S* MR_MAXR, 2)
       auto load = [&](const float4* f, cplx<float> v[12]) {
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-          float4 q = __ldg(f + r * rs + j * sv + cb);
+          float4 q = __ldg(f + ro + j * sv + cb);
           v[2 * j] = mk(q.x, q.y);
           v[2 * j + 1] = mk(q.z, q.w);
         }
@@ -218,7 +225,7 @@ __global__ void __launch_bounds__(MT_S* MR_MAXR, 2)
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = v[k] + coef * acc[k];
       }
-      float4* outr = out + r * rs;
+      float4* outr = out + ro;
 #pragma unroll
       for (int j = 0; j < 6; ++j)
         outr[j * sv + cb] = make_float4(o[2 * j].re, o[2 * j].im, o[2 * j + 1].re, o[2 * j + 1].im);
@@ -269,7 +276,7 @@ qxd_status mrhs_tile_status(qxd_lattice* lat) {
 
 template <int EPI, bool G5>
 static qxd_status launch_mrhs_t(qxd_lattice* lat, int par, const float4* in, const float4* same, float4* out,
-                                float coef, int nr, i64 rs, const unsigned char* rec, int* err) {
+                                float coef, int nr, const MrList& lst, i64 rs, const unsigned char* rec, int* err) {
   constexpr bool NEEDC = EPI != EPI_HOP && EPI != EPI_XPAY;
   constexpr uint32_t BYTES = NEEDC ? MT_CLOV + MT_NB + MT_W : MT_NB + MT_W;
   constexpr size_t SMEM = 2 * BYTES + 2 * sizeof(uint64_t) + 16;
@@ -288,7 +295,7 @@ static qxd_status launch_mrhs_t(qxd_lattice* lat, int par, const float4* in, con
   const int ntiles = (int)((g.Vh + MT_S - 1) / MT_S);
   const i64 want = (i64)blocks_per_sm * sms;
   const unsigned grid = (unsigned)(ntiles < want ? ntiles : want);
-  k_hop_mrhs_t<EPI, G5><<<grid, dim3(MT_S, nr), SMEM, lat->stream>>>(g, nr, in, same, out, rs,
+  k_hop_mrhs_t<EPI, G5><<<grid, dim3(MT_S, nr), SMEM, lat->stream>>>(g, nr, lst, in, same, out, rs,
                                                                       rec + (i64)par * ntiles * MT_REC, ntiles, coef,
                                                                       err);
   QXD_CHECK_LAUNCH(lat, "k_hop_mrhs_t");
@@ -296,7 +303,7 @@ static qxd_status launch_mrhs_t(qxd_lattice* lat, int par, const float4* in, con
 }
 
 qxd_status hop32_mrhs(qxd_lattice* lat, int par, int epi, int g5, const float4* in, const float4* same, float4* out,
-                      float coef, int nrhs, i64 rs) {
+                      float coef, int nrhs, i64 rs, const int* rhs) {
   const Geom& g = lat->g;
   const unsigned char* rec;
   int* err;
@@ -304,15 +311,14 @@ qxd_status hop32_mrhs(qxd_lattice* lat, int par, int epi, int g5, const float4* 
   if (st != QXD_OK) return st;
   for (int r0 = 0; r0 < nrhs; r0 += MR_MAXR) {
     const int nr = nrhs - r0 < MR_MAXR ? nrhs - r0 : MR_MAXR;
-    const float4* i0 = in + r0 * rs;
-    const float4* s0 = same ? same + r0 * rs : nullptr;
-    float4* o0 = out + r0 * rs;
+    MrList lst;
+    for (int r = 0; r < MR_MAXR; ++r) lst.idx[r] = r < nr ? (rhs ? rhs[r0 + r] : r0 + r) : 0;
     // bytes: per site and RHS the spinors; links and clover once per site for the whole block
     double sp = 96.0 * (2 + ((epi == EPI_DFULL || epi == EPI_DHAT2 || epi == EPI_INVXPAY || epi == EPI_XPAY) ? 1 : 0));
     double once = 8 * 72.0 + ((epi != EPI_HOP && epi != EPI_XPAY) ? 288.0 : 0.0);
     prof_begin(lat, KSTAT_F32_MRHS, (sp * nr + once) * (double)g.Vh);
 #define QXD_MT_CASE(E, G) \
-  if (epi == E && (g5 != 0) == G) st = launch_mrhs_t<E, G>(lat, par, i0, s0, o0, coef, nr, rs, rec, err); else
+  if (epi == E && (g5 != 0) == G) st = launch_mrhs_t<E, G>(lat, par, in, same, out, coef, nr, lst, rs, rec, err); else
     QXD_MT_CASE(EPI_HOP, false)
     QXD_MT_CASE(EPI_DFULL, false)
     QXD_MT_CASE(EPI_INV, false)

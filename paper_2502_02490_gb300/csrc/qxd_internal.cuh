@@ -752,8 +752,10 @@ qxd_status hop16(qxd_lattice* lat, int bf16, int par, int epi, int g5, const uin
 qxd_status hop16_mrhs(qxd_lattice* lat, int bf16, int par, int epi, int g5, const uint2* in, const float* in_nrm,
                       const uint2* same, const float* same_nrm, uint2* out, float* out_nrm, float4* out32, float coef,
                       int nrhs);
+// nrhs right-hand sides at base + r * rs; rhs (host array of nrhs indices, or null for 0..nrhs-1)
+// selects which ones
 qxd_status hop32_mrhs(qxd_lattice* lat, int par, int epi, int g5, const float4* in, const float4* same, float4* out,
-                      float coef, int nrhs, i64 rs);
+                      float coef, int nrhs, i64 rs, const int* rhs = nullptr);
 // QXD_ETIMEOUT if a bounded wait of the FP32 multi-RHS hop expired since its records were built
 // (synchronises the stream)
 qxd_status mrhs_tile_status(qxd_lattice* lat);

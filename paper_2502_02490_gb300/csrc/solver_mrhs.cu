@@ -28,10 +28,11 @@ qxd_status apply_D64(qxd_lattice* lat, const double2* in, double2* out);
 enum { MW_HALVES = 32, MW_R32 = 33, MW_R64 = 34, MW_T64 = 35, MW_RO = 36, MW_H16 = 46, MW_H16N = 47 };
 enum { H_BH = 0, H_Y, H_X, H_R, H_RH, H_P, H_V, H_S, H_T, H_TMP, H_N };
 
-// Dhat on all n right-hand sides (FP32, multi-RHS hop): out = Dhat in, tmp odd-half scratch
-static qxd_status dhat_mr(qxd_lattice* lat, const float4* in, float4* out, float4* tmp, int n, i64 rs) {
-  TRY(hop32_mrhs(lat, 1, EPI_INV, 0, in, nullptr, tmp, 1.0f, n, rs));
-  TRY(hop32_mrhs(lat, 0, EPI_DHAT2, 0, tmp, in, out, -0.25f, n, rs));
+// Dhat on the n right-hand sides listed in rhs (FP32, multi-RHS hop): out = Dhat in, tmp odd-half
+// scratch
+static qxd_status dhat_mr(qxd_lattice* lat, const float4* in, float4* out, float4* tmp, int n, i64 rs, const int* rhs) {
+  TRY(hop32_mrhs(lat, 1, EPI_INV, 0, in, nullptr, tmp, 1.0f, n, rs, rhs));
+  TRY(hop32_mrhs(lat, 0, EPI_DHAT2, 0, tmp, in, out, -0.25f, n, rs, rhs));
   return QXD_OK;
 }
 
@@ -63,9 +64,16 @@ static qxd_status inner_mr(qxd_lattice* lat, float4* H, int n, int prec, const s
   }
   uint2 *p16 = h16, *s16 = h16 ? h16 + n4 * n : nullptr, *t16 = h16 ? h16 + 2 * n4 * n : nullptr;
   float *p16n = h16n, *s16n = h16n ? h16n + sv * n : nullptr, *t16n = h16n ? h16n + 2 * sv * n : nullptr;
-  // out = Dhat in for every right-hand side (FP32 out)
+  std::vector<char> on(act);  // right-hand sides still iterating
+  // out = Dhat in for every active right-hand side (FP32 out); a frozen one keeps its old out
+  std::vector<int> live;
   auto dhat_all = [&](const float4* in32, const uint2* in16, const float* in16n, float4* out) -> qxd_status {
-    if (!low) return dhat_mr(lat, in32, out, tmp, n, rs);
+    if (!low) {
+      live.clear();
+      for (int i = 0; i < n; ++i)
+        if (on[i]) live.push_back(i);
+      return live.empty() ? QXD_OK : dhat_mr(lat, in32, out, tmp, (int)live.size(), rs, live.data());
+    }
     TRY(hop16_mrhs(lat, bf, 1, EPI_INV, 0, in16, in16n, nullptr, nullptr, t16, t16n, nullptr, 1.0f, n));
     return hop16_mrhs(lat, bf, 0, EPI_DHAT2, 0, t16, t16n, in16, in16n, nullptr, nullptr, out, -0.25f, n);
   };
@@ -82,7 +90,6 @@ static qxd_status inner_mr(qxd_lattice* lat, float4* H, int n, int prec, const s
     q.r0 = i;
     return q;
   };
-  std::vector<char> on(act);
   for (int i = 0; i < n; ++i) TRY(set_scalar_at(lat, lat->mr_scal + (i64)i * SC_N + SC_ACTIVE, on[i] ? 1.0 : 0.0));
   TRY(blas_zero(lat, x, all));
   TRY(blas_copy(lat, r, bh, all));
