@@ -438,7 +438,14 @@ def run_mrhs(args):
     # the survey's multi-RHS convention per site and RHS and launch: in + out spinor plus
     # (8 links + clover) / 12; FP32: 192 + (576 + 288) / 12 = 264 B, 16-bit: 104 + (288 + 148) / 12
     conv = 264.0 if prec == qxd.F32 else 104.0 + 436.0 / 12
-    achieved_conv = conv * 12 * (V // 2) * n_l / (ms_l / 1e3) / 1e9
+    # site-RHS pairs the launches processed: the FP32 hop works on the active right-hand sides only;
+    # its INV and DHAT2 launches come in pairs over the same right-hand sides, with (192 nr + 864)
+    # and (288 nr + 864) bytes per site, so sum(nr) = (bytes / Vh - 864 launches) / 240
+    if prec == qxd.F32:
+        site_rhs = (b_l / (V // 2) - 864.0 * n_l) / 240.0 * (V // 2)
+    else:
+        site_rhs = 12.0 * (V // 2) * n_l
+    achieved_conv = conv * site_rhs / (ms_l / 1e3) / 1e9
     hop_bytes = sum(v[2] for k, v in stats.items() if k != "mrhs_blas") / min(args.steps, 3) * args.steps
     return {"metric": METRIC, "value": hop_bytes / (t * args.steps) / 1e9, "unit": "GB/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
@@ -459,6 +466,7 @@ def run_mrhs(args):
                          "achieved_survey_convention": achieved_conv,
                          "frac_survey_convention": achieved_conv / peak,
                          "survey_convention_bytes_per_site_rhs": conv,
+                         "site_rhs_per_launch": site_rhs / n_l if n_l else None,
                          "timing": "CUDA events around every launch of a separate profiled pass"},
             "kernels": {k: {"launches": v[0], "ms": v[1], "GB": v[2] / 1e9} for k, v in stats.items() if v[0]},
             "gpu_launches": int(launches), "clocks": clk.summary()}
