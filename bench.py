@@ -545,9 +545,9 @@ def run_batch(args):
 
 
 def run_sap(args):
-    """The paper's CPU solver family on the 32^3x64 field: SAP-preconditioned flexible GCR and the
-    deflated two-level version (DFL_SAP_GCR) to the paper's 1e-12, against MP BiCGStab; SAP block
-    kernel time and bytes from a profiled pass."""
+    """The paper's solver families on the 32^3x64 field: SAP-preconditioned flexible GCR, the
+    deflated two-level version (DFL_SAP_GCR) and three-level multigrid GCR to the paper's 1e-12,
+    against MP BiCGStab; SAP block kernel time and bytes from a profiled pass."""
     import torch
 
     from paper_2502_02490_gb300 import qxd, synth
@@ -598,6 +598,25 @@ def run_sap(args):
     t_setup = time.perf_counter() - t0
     res["dfl_sap_gcr"] = timed(solver=qxd.SOLVER_MP_DFL_SAP_GCR, **sap)
     res["dfl"] = {"ns": ns, "block": list(blk), "generate_s": t_gen, "setup_s": t_setup, **qxd.dfl_info(lat)}
+    # three-level multigrid on the same level 1: aggregates of 2^4 deflation blocks, 8 level-2
+    # vectors by inverse iteration on level 1, SAP smoothing before and after the coarse correction
+    agg, ns2 = (2, 2, 2, 2), 8
+    n1 = res["dfl"]["nblocks"] * ns
+    s2 = torch.from_numpy(np.stack([synth.gaussian_spinor((n1, 1, 1, 1), 7100 + k).reshape(-1)[:n1]
+                                    for k in range(ns2)]).view(np.float64)).to(dev)
+    v2 = torch.empty_like(s2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qxd.mg_generate(lat, s2, v2, n_it=3, k=8)
+    torch.cuda.synchronize()
+    t_gen2 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mgp = dict(agg=agg, nu=2, n1=4, n2=8, m=8, ncy_pre=1)
+    qxd.mg_setup(lat, v2, **mgp)
+    torch.cuda.synchronize()
+    t_setup2 = time.perf_counter() - t0
+    res["mg_gcr"] = timed(solver=qxd.SOLVER_MP_MG_GCR, **dict(sap, sap_ncy=1))
+    res["mg"] = {"ns2": ns2, **mgp, "agg": list(agg), "generate_s": t_gen2, "setup_s": t_setup2, **qxd.mg_info(lat)}
     qxd.destroy_lattice(lat)
     peak, kind = measured_peaks()
     k = res["sap_gcr_profiled"]["sap_kernel"]

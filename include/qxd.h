@@ -99,10 +99,16 @@ typedef enum {
                                    network as M^+; FP32 reliable updates (reliable_delta).  Converges
                                    for any invertible D, also where D is indefinite and GCR or
                                    BiCGStab stagnate or break down; inner_prec is not used */
-  QXD_SOLVER_MP_DFL_SAP_GCR = 6  /* as MP_SAP_GCR with the two-level preconditioner of inexact
+  QXD_SOLVER_MP_DFL_SAP_GCR = 6, /* as MP_SAP_GCR with the two-level preconditioner of inexact
                                    deflation: z = P A^-1 P^+ r on the subspace of qxd_dfl_setup
                                    (coarse GCR to its coarse_tol), then z += M_SAP (r - D z)
                                    (QXD_ESTATE without a subspace set up on the current field) */
+  QXD_SOLVER_MP_MG_GCR = 7       /* as MP_SAP_GCR with the three-level multigrid preconditioner of
+                                   qxd_mg_setup (the deflation subspace as level 1, its aggregation
+                                   as level 2; SAP smoothing on the fine lattice with sap_block,
+                                   sap_ncy cycles after and the set-up's ncy_pre cycles before the
+                                   coarse correction, sap_nmr MR steps per block solve); QXD_ESTATE
+                                   without a multigrid set up on the current deflation subspace */
 } qxd_solver;
 
 typedef struct {
@@ -408,6 +414,58 @@ qxd_status qxd_dfl_setup(qxd_lattice *lat, const int block[4], int ns, const dou
 qxd_status qxd_dfl_get_little(qxd_lattice *lat, double *A, int *nbr);
 qxd_status qxd_dfl_info(qxd_lattice *lat, int *nblocks, int *ns, int64_t *coarse_iters, int64_t *coarse_calls);
 
+/* Multigrid (Sec. 5.1: the paper's GPU solves use multigrid GCR; the paper gives no detail).
+ * Three levels: the fine D; level 1, the little Dirac operator A1 = P1^+ D P1 of the deflation
+ * subspace of qxd_dfl_setup (a level-1 vector holds n1 = nblocks * ns complex numbers, entry
+ * b * ns + k for block b in the block order of qxd_dfl_get_little and basis vector k); level 2,
+ * aggregates of agg[0] x agg[1] x agg[2] x agg[3] level-1 blocks, numbered lexicographically by
+ * aggregate coordinates (direction 3 fastest), with a basis of ns2 level-1 vectors orthonormalised
+ * on every aggregate (modified Gram-Schmidt in vector order) and A2 = P2^+ A1 P2.  The
+ * preconditioner of QXD_SOLVER_MP_MG_GCR, on the FP32 fields of the inner flexible GCR:
+ *   z = M_SAP^pre r (ncy_pre cycles; none for 0); z += P1 K1(P1^+ (r - D z)); z += M_SAP (r - D z),
+ *   K1  = n1 flexible GCR steps on A1 from zero, each preconditioned by the two-grid cycle
+ *   T1 f: y = S1 f; y += P2 G2(P2^+ (f - A1 y)); y += S1 (f - A1 y),
+ *   S1  = nu minimal-residual steps on A1 from zero, G2 = n2 GCR steps on A2 from zero.
+ * GCR steps (both coarse levels, restart every m): z = M r, w = A z, classical Gram-Schmidt of w
+ * against the cycle's earlier normalised w (same combination on z), both divided by ||w||,
+ * alpha = <w, r>, x += alpha z, r -= alpha w.  Coarse levels are FP64 with fixed step counts and
+ * every coefficient on the device (no host synchronisation inside the preconditioner).
+ * qxd_mg_setup: vectors [ns2][n1][2] doubles (host, or device with on_device = 1), copied.
+ *   Aggregate extents must divide the deflation block grid, and the aggregates must form a
+ *   nearest-neighbour grid (with C*, the x shift across the y and z boundaries a whole number of
+ *   aggregates), else QXD_EINVAL; likewise for p->version != QXD_MG_VERSION, a parameter outside
+ *   its range or vectors linearly dependent on an aggregate.  QXD_ESTATE without a deflation
+ *   subspace on the current field.  Replaces an earlier multigrid; a later qxd_dfl_setup or field
+ *   change makes it stale (QXD_ESTATE from the solve and the apply calls).  Synchronises.
+ * qxd_mg_generate: level-2 vectors by inverse iteration on level 1: each of the ns2 start vectors
+ *   [ns2][n1][2] is normalised, then n_it times replaced by k GCR steps (restart 16) on
+ *   A1 v' = v, normalised; the results go to out (same layout).  Needs qxd_dfl_setup only.
+ * qxd_mg_get_coarse: A2 as [nb2][9][ns2][ns2][2] doubles (slot 0 the aggregate itself, 1 + 2 mu
+ *   the neighbour in +mu, 2 + 2 mu in -mu) and nbr2 [nb2][9]; host arrays.
+ * qxd_mg_info: the number of aggregates, ns2 and the level-1 solves K1 run so far.
+ * qxd_mg_apply_level1: out = K1(in) for one level-1 vector [n1][2] (FP64 throughout).
+ * qxd_mg_precond: out = M_MG in for full fields [V][4][3][2] (boundary site order), the fine part
+ *   in FP32 as inside the solver; SAP blocks, ncy (post) and nmr as in qxd_sap_apply. */
+#define QXD_MG_VERSION 1
+typedef struct {
+  int version;    /* QXD_MG_VERSION */
+  int agg[4];     /* aggregate extents in deflation blocks */
+  int ns2;        /* level-2 vectors (1..32, at most the entries of an aggregate) */
+  int nu;         /* MR steps of the level-1 smoother, before and after the coarse correction (0..16) */
+  int n1;         /* flexible GCR steps of the level-1 solve K1 (1..64) */
+  int n2;         /* GCR steps of the coarsest solve (1..256) */
+  int m;          /* restart length of both coarse GCRs (1..16) */
+  int ncy_pre;    /* SAP cycles before the coarse correction on the fine lattice (0..8) */
+} qxd_mg_params;
+qxd_status qxd_mg_setup(qxd_lattice *lat, const qxd_mg_params *p, const double *vectors, int on_device);
+qxd_status qxd_mg_generate(qxd_lattice *lat, int ns2, int n_it, int k, const double *start, double *out,
+                           int on_device);
+qxd_status qxd_mg_get_coarse(qxd_lattice *lat, double *A2, int *nbr2);
+qxd_status qxd_mg_info(qxd_lattice *lat, int *nb2, int *ns2, int64_t *level1_solves);
+qxd_status qxd_mg_apply_level1(qxd_lattice *lat, double *out, const double *in, int on_device);
+qxd_status qxd_mg_precond(qxd_lattice *lat, double *out, const double *in, const int sap_block[4], int ncy,
+                          int nmr, int on_device);
+
 /* Dot product for callers that cannot allocate device memory.  The paper has no counterpart:
  * this entry point exists for callers that must not call cudaMalloc -- code inside a framework
  * whose device memory belongs to its own caching allocator, and latency-critical loops that
@@ -418,7 +476,8 @@ qxd_status qxd_dfl_info(qxd_lattice *lat, int *nblocks, int *ns, int64_t *coarse
  * Scratch: a static device array inside the library (64 KiB of per-block partial sums plus a
  * counter), which every GPU that loads the library keeps until process exit.  Limit: n <=
  * QXD_NOALLOC_MAX_N; larger n returns QXD_EINVAL.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and keeps it for the life of the process; after
+ * array's device address (cudaGetSymbolAddress) and keeps it for the life of the process (make
+ * that first call before any stream capture begins); after
  * a cudaDeviceReset on that device the kept address is stale, so do not call this entry point
  * on a device that was reset.  All calls share the one array: calls that overlap on the GPU (e.g. on two
  * streams at once) race and give wrong results; serialise them.  The result is deterministic

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqxd.so")
-SOURCES = ["api.cu", "layout.cu", "clover.cu", "dslash.cu", "blas.cu", "solver.cu", "solver_mrhs.cu", "bicgstab.cu", "mrhs.cu", "ptc.cu", "ptc_tc.cu", "fgcr.cu", "batch.cu", "noalloc.cu", "sap.cu", "dfl.cu"]
+SOURCES = ["api.cu", "layout.cu", "clover.cu", "dslash.cu", "blas.cu", "solver.cu", "solver_mrhs.cu", "bicgstab.cu", "mrhs.cu", "ptc.cu", "ptc_tc.cu", "fgcr.cu", "batch.cu", "noalloc.cu", "sap.cu", "dfl.cu", "mg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

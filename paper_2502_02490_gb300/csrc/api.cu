@@ -175,6 +175,7 @@ static qxd_status alloc(qxd_lattice* lat, T** p, size_t bytes) {
 namespace qxd {
 qxd_status sap_check(qxd_lattice* lat, const int b[4]);  // csrc/sap.cu
 bool dfl_ready(const qxd_lattice* lat);                  // csrc/dfl.cu
+bool mg_ready(const qxd_lattice* lat);                   // csrc/mg.cu
 
 // The caller's params as the current version.  Version 3 ended at `fallback`; version 4 appended
 // use_x0 and restart_f32, which a version-3 caller gets off.
@@ -230,6 +231,7 @@ qxd_status qxd_destroy_lattice(qxd_lattice* lat) {
   if (!lat) return QXD_OK;
   if (lat->stream) cudaStreamSynchronize(lat->stream);
   if (lat->batch && lat->batch_release) lat->batch_release(lat->batch);
+  if (lat->mg && lat->mg_release) lat->mg_release(lat->mg);
   if (lat->dfl && lat->dfl_release) lat->dfl_release(lat->dfl);
   void* bufs[] = {lat->U,    lat->A,     lat->W64,   lat->W32,   lat->W16,   lat->WB16,  lat->C64,
                   lat->Ci64, lat->C32,   lat->Ci32,  lat->C16,   lat->Ci16,  lat->C16n,  lat->Ci16n,
@@ -678,11 +680,14 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
   p = &pv;
   if (p->solver != QXD_SOLVER_CG_EO && p->solver != QXD_SOLVER_MP_CG_EO && p->solver != QXD_SOLVER_MP_BICGSTAB_EO &&
       p->solver != QXD_SOLVER_MP_FGCR_NET && p->solver != QXD_SOLVER_MP_SAP_GCR && p->solver != QXD_SOLVER_MP_CGNR &&
-      p->solver != QXD_SOLVER_MP_DFL_SAP_GCR)
+      p->solver != QXD_SOLVER_MP_DFL_SAP_GCR && p->solver != QXD_SOLVER_MP_MG_GCR)
     return fail(lat, QXD_EINVAL, "bad solver");
   if (p->solver == QXD_SOLVER_MP_DFL_SAP_GCR && !dfl_ready(lat))
     return fail(lat, QXD_ESTATE, "DFL_SAP_GCR needs a deflation subspace set up on the current field (qxd_dfl_setup)");
-  if (p->solver == QXD_SOLVER_MP_SAP_GCR || p->solver == QXD_SOLVER_MP_DFL_SAP_GCR) {
+  if (p->solver == QXD_SOLVER_MP_MG_GCR && !mg_ready(lat))
+    return fail(lat, QXD_ESTATE,
+                "MG_GCR needs a multigrid set up on the current deflation subspace (qxd_dfl_setup, then qxd_mg_setup)");
+  if (p->solver == QXD_SOLVER_MP_SAP_GCR || p->solver == QXD_SOLVER_MP_DFL_SAP_GCR || p->solver == QXD_SOLVER_MP_MG_GCR) {
     TRY(sap_check(lat, p->sap_block));
     if (p->sap_ncy < 1 || p->sap_nmr < 1) return fail(lat, QXD_EINVAL, "sap_ncy and sap_nmr must be >= 1");
   }
@@ -692,7 +697,7 @@ qxd_status qxd_solve(qxd_lattice* lat, double* x, const double* b, const qxd_sol
   if (p->use_x0 != 0 && p->use_x0 != 1) return fail(lat, QXD_EINVAL, "use_x0 must be 0 or 1");
   if (p->restart_f32 != 0 && p->restart_f32 != 1) return fail(lat, QXD_EINVAL, "restart_f32 must be 0 or 1");
   const bool fgcr = p->solver == QXD_SOLVER_MP_FGCR_NET || p->solver == QXD_SOLVER_MP_SAP_GCR ||
-                    p->solver == QXD_SOLVER_MP_DFL_SAP_GCR;
+                    p->solver == QXD_SOLVER_MP_DFL_SAP_GCR || p->solver == QXD_SOLVER_MP_MG_GCR;
   if (fgcr && (p->gcr_reorth < 1 || p->gcr_reorth > 2)) return fail(lat, QXD_EINVAL, "gcr_reorth must be 1 or 2");
   if (fgcr && (p->gcr_restart < 1 || p->gcr_restart > 32)) return fail(lat, QXD_EINVAL, "gcr_restart must be 1..32");
   if (!(p->tol > 0) || p->maxiter <= 0) return fail(lat, QXD_EINVAL, "tol must be > 0 and maxiter > 0");

@@ -21,44 +21,18 @@
 // basis on the self block (c = colour(b)) or on one face layer of b (c = colour(b) ^ (1 << mu))
 // are exactly the entries of A.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
+#include "dfl.cuh"
 #include "reduce.cuh"
-#include "sap.cuh"
 #include "trace.cuh"
 
 namespace qxd {
 
 qxd_status apply_D64(qxd_lattice* lat, const double2* in, double2* out);
-
-constexpr int DFL_MAXVB = 256;  // sites per deflation block (threads of the block kernels)
-constexpr int DFL_SLOTS = 9;    // self, then +mu, -mu for mu = 0..3
-
-struct DflGeom {
-  int b[4], n[4], stride[4];
-  int vb, nb;
-};
-
-struct DflState {
-  DflGeom dg;
-  int ns = 0;
-  double2* basis = nullptr;  // [ns][2][12][sv] FP64, the internal spinor layout, zero off its blocks
-  double2* A = nullptr;      // [nb][9][ns][ns]
-  int* nbr = nullptr;        // [nb][9] block index per slot (device)
-  std::vector<int> hnbr;     // host copy
-  // coarse GCR work: vectors of n = nb ns complex (double2)
-  double2* cw = nullptr;     // [2 m + 4][n]
-  double* cpart = nullptr;   // reduction partials
-  double* hcs = nullptr;     // pinned host scalars
-  int m = 16;                // coarse GCR restart length
-  double coarse_tol = 1e-2;  // relative residual of the coarse solve
-  int coarse_maxiter = 64;
-  i64 coarse_iters = 0;      // coarse iterations since set-up (statistics)
-  i64 coarse_calls = 0;
-  i64 epoch = -1;            // the lattice's field epoch at set-up (a later field change makes it stale)
-};
 
 static void dfl_release(void* p) {
   DflState* d = (DflState*)p;
@@ -101,20 +75,6 @@ static qxd_status dfl_geometry(qxd_lattice* lat, const int b[4], DflGeom* dg) {
   return QXD_OK;
 }
 
-// block coordinates of block index t (lexicographic, direction 3 fastest)
-__host__ __device__ __forceinline__ void block_coords(const DflGeom& dg, int t, int kb[4]) {
-  for (int mu = 3; mu >= 0; --mu) {
-    kb[mu] = t % dg.n[mu];
-    t /= dg.n[mu];
-  }
-}
-__host__ __device__ __forceinline__ int block_index(const DflGeom& dg, const int kb[4]) {
-  return ((kb[0] * dg.n[1] + kb[1]) * dg.n[2] + kb[2]) * dg.n[3] + kb[3];
-}
-__host__ __device__ __forceinline__ int block_colour(const int kb[4]) {
-  return (kb[0] & 1) | ((kb[1] & 1) << 1) | ((kb[2] & 1) << 2) | ((kb[3] & 1) << 3);
-}
-
 // neighbour block of kb in direction mu (dir +-1), with the C* shift of x across the y and z
 // boundaries (shift = physical L1 in sites, a whole number of x blocks)
 static int block_neighbour(const DflGeom& dg, int shift, const int kb[4], int mu, int dir) {
@@ -145,30 +105,6 @@ __device__ __forceinline__ void block_site(const Geom& g, const DflGeom& dg, int
   for (int mu = 0; mu < 4; ++mu) x[mu] = kb[mu] * dg.b[mu] + lc[mu];
   par = (x[0] + x[1] + x[2] + x[3]) & 1;
   cb = lexi(g, x) >> 1;
-}
-
-// FP64 sums of NV values over the CTA (any blockDim <= 256); every thread receives the totals
-template <int NV>
-__device__ __forceinline__ void cta_sum(double v[NV], double* sh /* [NV][8 warps] */) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double a = v[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    v[i] = a;
-  }
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) sh[i * 8 + w] = v[i];
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double a = 0.0;
-    for (int k = 0; k < nw; ++k) a += sh[i * 8 + k];  // fixed order: identical in every thread
-    v[i] = a;
-  }
 }
 
 // Modified Gram-Schmidt of the ns vectors on every block (one CTA per block, one thread per
@@ -421,9 +357,6 @@ __global__ void k_dfl_scale32(i64 n, const double* __restrict__ nn, float4* __re
   }
 }
 
-static int dfl_threads(const DflGeom& dg) { return (dg.vb + 31) / 32 * 32; }
-static int egrid(i64 n) { return (int)std::min<i64>((n + 255) / 256, 152 * 16); }
-
 #define DTRY(x)                      \
   do {                               \
     qxd_status _s = (x);             \
@@ -617,6 +550,8 @@ qxd_status qxd_dfl_setup(qxd_lattice* lat, const int block[4], int ns, const dou
       lat->launches += 2;
     }
   if (cudaStreamSynchronize(lat->stream) != cudaSuccess) return bail(fail(lat, QXD_ECUDA, "dfl_setup"));
+  static std::atomic<i64> generation{0};
+  d->gen = ++generation;
   d->epoch = lat->epoch;
   lat->dfl = d;
   lat->dfl_release = dfl_release;

@@ -246,7 +246,9 @@ qxd_status fgcr32(qxd_lattice* lat, qxd_net* net, const SapSpec* sap, int m, int
   const int every = check_every > 0 ? check_every : 1;
   bool done = !(std::sqrt(rn2) > target);
   while (!done && it < maxiter) {
-    if (sap && sap->dfl)
+    if (sap && sap->mg)
+      TRY_Q(mg_precond32(lat, *sap, r, z(k)));
+    else if (sap && sap->dfl)
       TRY_Q(dfl_precond32(lat, *sap, r, z(k)));
     else if (sap)
       TRY_Q(sap32(lat, sap->block, sap->ncy, sap->nmr, r, z(k)));

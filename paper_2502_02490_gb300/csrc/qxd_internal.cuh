@@ -605,6 +605,9 @@ struct qxd_lattice {
   // deflation subspace and little Dirac operator (qxd_dfl_setup; freed with the lattice)
   void* dfl = nullptr;
   void (*dfl_release)(void*) = nullptr;
+  // level 2 of the multigrid on top of it (qxd_mg_setup; freed with the lattice)
+  void* mg = nullptr;
+  void (*mg_release)(void*) = nullptr;
   qxd::i64 epoch = 0;  // counts changes of the gauge field or the clover term
   qxd::i64 mrt_epoch = -1;  // epoch of the multi-RHS hop's tile records (work slot 60)
   int Lphys[4];

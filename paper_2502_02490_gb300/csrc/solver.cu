@@ -561,7 +561,7 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
   TRY(get(lat, WS_TO64, hb, &to));
   const bool mp = prm->solver == QXD_SOLVER_MP_CG_EO || prm->solver == QXD_SOLVER_MP_BICGSTAB_EO;
   const bool gcr = prm->solver == QXD_SOLVER_MP_FGCR_NET || prm->solver == QXD_SOLVER_MP_SAP_GCR ||
-                   prm->solver == QXD_SOLVER_MP_DFL_SAP_GCR;
+                   prm->solver == QXD_SOLVER_MP_DFL_SAP_GCR || prm->solver == QXD_SOLVER_MP_MG_GCR;
   const bool cgnr = prm->solver == QXD_SOLVER_MP_CGNR;
   float4 *bh32 = nullptr, *y32 = nullptr, *r32 = nullptr, *to32 = nullptr;
   if (mp) {
@@ -652,12 +652,14 @@ static qxd_status solve_impl(qxd_lattice* lat, double2* x, const double2* b, con
       double inner_target = prm->inner_tol * rnorm;
       if (inner_target < target) inner_target = target;
       SapSpec sp;
-      const bool with_sap = prm->solver == QXD_SOLVER_MP_SAP_GCR || prm->solver == QXD_SOLVER_MP_DFL_SAP_GCR;
+      const bool with_sap = prm->solver == QXD_SOLVER_MP_SAP_GCR || prm->solver == QXD_SOLVER_MP_DFL_SAP_GCR ||
+                            prm->solver == QXD_SOLVER_MP_MG_GCR;
       if (with_sap) {
         for (int mu = 0; mu < 4; ++mu) sp.block[mu] = prm->sap_block[mu];
         sp.ncy = prm->sap_ncy;
         sp.nmr = prm->sap_nmr;
         sp.dfl = prm->solver == QXD_SOLVER_MP_DFL_SAP_GCR;
+        sp.mg = prm->solver == QXD_SOLVER_MP_MG_GCR;
       }
       if (!inner_status(fgcr32(lat, with_sap ? nullptr : const_cast<qxd_net*>(prm->net), with_sap ? &sp : nullptr,
                                prm->gcr_restart, prm->gcr_reorth, r32f, e32, inner_target, prm->maxiter - total,

@@ -25,7 +25,8 @@ BC_PERIODIC, BC_ANTIPERIODIC = 0, 1
 ORDER_LEXI, ORDER_IPT = 0, 1
 F64, F32, F16N, BF16N = 0, 1, 2, 3
 (SOLVER_CG_EO, SOLVER_MP_CG_EO, SOLVER_MP_BICGSTAB_EO, SOLVER_MP_FGCR_NET, SOLVER_MP_SAP_GCR, SOLVER_MP_CGNR,
- SOLVER_MP_DFL_SAP_GCR) = range(7)
+ SOLVER_MP_DFL_SAP_GCR, SOLVER_MP_MG_GCR) = range(8)
+MG_VERSION = 1
 PARAMS_VERSION = 5
 TRAIN_VERSION = 2
 PREC = {"f64": F64, "f32": F32, "f16n": F16N, "bf16n": BF16N}
@@ -45,6 +46,11 @@ class TrainParams(C.Structure):
                 ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
                 ("nlayers", C.c_int), ("channels", C.c_int * 9), ("nsamp", C.c_int), ("net_seed", C.c_uint64),
                 ("sample_seed", C.c_uint64), ("loss_hist", C.c_void_p)]
+
+
+class MgParams(C.Structure):
+    _fields_ = [("version", C.c_int), ("agg", C.c_int * 4), ("ns2", C.c_int), ("nu", C.c_int), ("n1", C.c_int),
+                ("n2", C.c_int), ("m", C.c_int), ("ncy_pre", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -98,6 +104,12 @@ _SIGS = {
     "qxd_dfl_setup": [_vp, C.POINTER(C.c_int), _i, _vp, _i, _d, _i],
     "qxd_dfl_get_little": [_vp, _vp, _vp],
     "qxd_dfl_info": [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i64), C.POINTER(_i64)],
+    "qxd_mg_setup": [_vp, C.POINTER(MgParams), _vp, _i],
+    "qxd_mg_generate": [_vp, _i, _i, _i, _vp, _vp, _i],
+    "qxd_mg_get_coarse": [_vp, _vp, _vp],
+    "qxd_mg_info": [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i64)],
+    "qxd_mg_apply_level1": [_vp, _vp, _vp, _i],
+    "qxd_mg_precond": [_vp, _vp, _vp, C.POINTER(C.c_int), _i, _i, _i],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -386,6 +398,66 @@ def dfl_get_little(lat):
     nbr = np.empty((nb, 9), dtype=np.int32)
     _check(lib.qxd_dfl_get_little(lat, A.ctypes.data, nbr.ctypes.data), lat)
     return A, nbr
+
+
+def mg_params(agg, ns2, nu=2, n1=4, n2=8, m=8, ncy_pre=0):
+    p = MgParams()
+    p.version = MG_VERSION
+    p.agg = (C.c_int * 4)(*[int(v) for v in agg])
+    p.ns2, p.nu, p.n1, p.n2, p.m, p.ncy_pre = int(ns2), int(nu), int(n1), int(n2), int(m), int(ncy_pre)
+    return p
+
+
+def mg_setup(lat, vectors, **kw):
+    """qxd_mg_setup with ns2 = len(vectors) level-1 vectors [ns2][n1] complex (host array or CUDA
+    tensor of float64 pairs); keyword arguments as mg_params (agg is required)."""
+    pv, dev = _ptr(vectors)
+    p = mg_params(ns2=int(vectors.shape[0]), **kw)
+    _check(lib.qxd_mg_setup(lat, C.byref(p), pv, int(dev)), lat)
+
+
+def mg_generate(lat, start, out, n_it, k=8):
+    """qxd_mg_generate: level-2 vectors by inverse iteration on level 1 (start, out: [ns2][n1])."""
+    ps, dev = _ptr(start)
+    po, dev2 = _ptr(out)
+    if dev != dev2:
+        raise ValueError("start and out must both be host or both be device buffers")
+    _check(lib.qxd_mg_generate(lat, int(start.shape[0]), int(n_it), int(k), ps, po, int(dev)), lat)
+
+
+def mg_info(lat):
+    nb2, ns2, calls = C.c_int(), C.c_int(), C.c_int64()
+    _check(lib.qxd_mg_info(lat, C.byref(nb2), C.byref(ns2), C.byref(calls)), lat)
+    return {"nb2": nb2.value, "ns2": ns2.value, "level1_solves": calls.value}
+
+
+def mg_get_coarse(lat):
+    """(A2 [nb2][9][ns2][ns2] complex, nbr2 [nb2][9] int) of the current multigrid."""
+    info = mg_info(lat)
+    nb, ns = info["nb2"], info["ns2"]
+    A = np.empty((nb, 9, ns, ns), dtype=np.complex128)
+    nbr = np.empty((nb, 9), dtype=np.int32)
+    _check(lib.qxd_mg_get_coarse(lat, A.ctypes.data, nbr.ctypes.data), lat)
+    return A, nbr
+
+
+def mg_apply_level1(lat, out, inp):
+    """qxd_mg_apply_level1: out = K1(inp) for one level-1 vector (n1 complex)."""
+    po, dev = _ptr(out)
+    pi, dev2 = _ptr(inp)
+    if dev != dev2:
+        raise ValueError("out and in must both be host or both be device buffers")
+    _check(lib.qxd_mg_apply_level1(lat, po, pi, int(dev)), lat)
+
+
+def mg_precond(lat, out, inp, sap_block, ncy=1, nmr=4):
+    """qxd_mg_precond: out = M_MG inp for full fields [V][4][3] complex."""
+    po, dev = _ptr(out)
+    pi, dev2 = _ptr(inp)
+    if dev != dev2:
+        raise ValueError("out and in must both be host or both be device buffers")
+    b = (C.c_int * 4)(*[int(v) for v in sap_block])
+    _check(lib.qxd_mg_precond(lat, po, pi, b, int(ncy), int(nmr), int(dev)), lat)
 
 
 def net_apply(net, out, inp):
