@@ -82,8 +82,6 @@ inline int egrid(i64 n) { return (int)std::min<i64>((n + 255) / 256, 152 * 16); 
 bool dfl_ready(const qxd_lattice* lat);
 
 // kernels of csrc/dfl.cu used by csrc/mg.cu
-__global__ void __launch_bounds__(256) k_dfl_cdots(const double2* __restrict__ Q, i64 n, int nq, const double2* __restrict__ v,
-                            double2* __restrict__ out);
 __global__ void __launch_bounds__(DFL_MAXVB) k_dfl_restrict(Geom g, DflGeom dg, int ns, const double2* __restrict__ V, const float4* __restrict__ r,
                                double2* __restrict__ f);
 __global__ void __launch_bounds__(DFL_MAXVB) k_dfl_prolong(Geom g, DflGeom dg, int ns, const double2* __restrict__ V, const double2* __restrict__ c,

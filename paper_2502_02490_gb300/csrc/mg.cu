@@ -18,8 +18,9 @@
 //              z += M_SAP (r - D z), inside the fine flexible GCR (QXD_SOLVER_MP_MG_GCR).
 //
 // Both coarse levels are FP64 with every coefficient on the device and fixed step counts, so the
-// preconditioner makes no host round trip; the fine smoothing works on the FP32 fields of the
-// inner solver.  GCR steps: z = M r, w = A z, classical Gram-Schmidt of w against the cycle's
+// preconditioner makes no host round trip and the level-1 solve (some 400 small launches) is
+// captured once as a CUDA graph and replayed; inner products sum fixed chunks in a fixed order.
+// The fine smoothing works on the FP32 fields of the inner solver.  GCR steps: z = M r, w = A z, classical Gram-Schmidt of w against the cycle's
 // earlier normalised w_j (the same combination applied to z), w and z divided by ||w||,
 // alpha = <w, r>, x += alpha z, r -= alpha w; a step whose w vanishes changes nothing.
 #include <atomic>
@@ -36,6 +37,8 @@ namespace qxd {
 constexpr int MG_MAXNS2 = 32;
 constexpr int MG_MAXM = 16;
 constexpr int MG_THREADS = 256;
+constexpr int MG_DOT_BLOCKS = 64;    // partial sums per inner product (fixed: results do not depend on the GPU)
+constexpr int MG_DOT_CHUNK = 2048;   // entries per partial at least
 
 struct MgState {
   int agg[4], n2g[4];
@@ -52,15 +55,23 @@ struct MgState {
   double2* w1 = nullptr;    // level-1 work: K1 Z[m], W[m], r; T1 rho, q, t; f1, c1
   double2* w2 = nullptr;    // level-2 work: G2 Z[m], W[m], r; f2, c2
   double2* sc = nullptr;    // device scalars: K1 [m + 2], G2 [m + 2], MR [2]
+  double2* part = nullptr;  // inner-product partials [MG_MAXM][MG_DOT_BLOCKS]
   i64 dfl_gen = -1;         // the deflation set-up it was built on
   i64 coarse_calls = 0;
+  // the level-1 solve f1 -> c1 captured once as a CUDA graph (on a private stream: capture is
+  // refused on the legacy default stream) and replayed on the lattice stream
+  cudaStream_t side = nullptr;
+  cudaGraphExec_t k1_exec = nullptr;
+  i64 k1_launches = 0;
 };
 
 static void mg_release(void* p) {
   MgState* s = (MgState*)p;
-  void* b[] = {s->P2, s->A2, s->nbr2, s->agg_of, s->loc_of, s->blk_of, s->w1, s->w2, s->sc};
+  void* b[] = {s->P2, s->A2, s->nbr2, s->agg_of, s->loc_of, s->blk_of, s->w1, s->w2, s->sc, s->part};
   for (void* q : b)
     if (q) cudaFree(q);
+  if (s->k1_exec) cudaGraphExecDestroy(s->k1_exec);
+  if (s->side) cudaStreamDestroy(s->side);
   delete s;
 }
 
@@ -91,6 +102,41 @@ __global__ void k_mg_cmv(int nb, int ns, const double2* __restrict__ A, const in
     }
     y[e] = f ? make_double2(f[e].x - re, f[e].y - im) : make_double2(re, im);
   }
+}
+
+// partial inner products <Q_j, v> (Q_j at Q + j n) over fixed chunks: block (b, j) sums entries
+// b chunk .. (b + 1) chunk - 1 in a fixed order into part[j][b]
+__global__ void __launch_bounds__(256) k_mg_dots_part(const double2* __restrict__ Q, i64 n, i64 chunk,
+                                                      const double2* __restrict__ v, double2* __restrict__ part) {
+  __shared__ double sh[2 * 8];
+  const int b = blockIdx.x, j = blockIdx.y;
+  const double2* q = Q + (i64)j * n;
+  const i64 lo = (i64)b * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  double a[2] = {0.0, 0.0};
+  for (i64 i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double2 x = q[i], y = v[i];
+    a[0] += x.x * y.x + x.y * y.y;
+    a[1] += x.x * y.y - x.y * y.x;
+  }
+  cta_sum<2>(a, sh);
+  if (threadIdx.x == 0) part[(i64)j * MG_DOT_BLOCKS + b] = make_double2(a[0], a[1]);
+}
+
+// out[j] = sum of the nb partials of product j, in block order (one warp per product)
+__global__ void k_mg_dots_fin(const double2* __restrict__ part, int nb, double2* __restrict__ out) {
+  const int j = blockIdx.x, lane = threadIdx.x;
+  double re = lane < nb ? part[(i64)j * MG_DOT_BLOCKS + lane].x : 0.0;
+  double im = lane < nb ? part[(i64)j * MG_DOT_BLOCKS + lane].y : 0.0;
+  if (lane + 32 < nb) {
+    re += part[(i64)j * MG_DOT_BLOCKS + lane + 32].x;
+    im += part[(i64)j * MG_DOT_BLOCKS + lane + 32].y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) out[j] = make_double2(re, im);
 }
 
 // w -= sum_j c_j W_j and z -= sum_j c_j Z_j for j < k (c: k device slots)
@@ -325,9 +371,18 @@ static qxd_status cmv(qxd_lattice* lat, const CLevel& L, const double2* x, const
   return QXD_OK;
 }
 
-static qxd_status cdots(qxd_lattice* lat, const double2* Q, i64 n, int nq, const double2* v, double2* out) {
-  k_dfl_cdots<<<nq, 256, 0, lat->stream>>>(Q, n, nq, v, out);
-  QXD_CHECK_LAUNCH(lat, "k_dfl_cdots");
+// out[j] = <Q_j, v> for j < nq (nq <= MG_MAXM); deterministic (fixed chunks and order); part:
+// MG_MAXM x MG_DOT_BLOCKS scratch slots
+static qxd_status cdots(qxd_lattice* lat, double2* part, const double2* Q, i64 n, int nq, const double2* v,
+                        double2* out) {
+  i64 nb = (n + MG_DOT_CHUNK - 1) / MG_DOT_CHUNK;
+  if (nb > MG_DOT_BLOCKS) nb = MG_DOT_BLOCKS;
+  if (nb < 1) nb = 1;
+  const i64 chunk = (n + nb - 1) / nb;
+  k_mg_dots_part<<<dim3((unsigned)nb, (unsigned)nq), 256, 0, lat->stream>>>(Q, n, chunk, v, part);
+  QXD_CHECK_LAUNCH(lat, "k_mg_dots_part");
+  k_mg_dots_fin<<<nq, 32, 0, lat->stream>>>(part, (int)nb, out);
+  QXD_CHECK_LAUNCH(lat, "k_mg_dots_fin");
   return QXD_OK;
 }
 
@@ -335,8 +390,8 @@ typedef std::function<qxd_status(const double2*, double2*)> CPre;
 
 // nsteps (flexible) GCR steps on A x = f from x = 0, restart every m; work Z, W: m vectors each,
 // r: one vector; dots: m + 2 device slots.
-static qxd_status gcr_fixed(qxd_lattice* lat, const CLevel& L, const double2* f, double2* x, int nsteps, int m,
-                            double2* Z, double2* W, double2* r, double2* dots, const CPre* pre) {
+static qxd_status gcr_fixed(qxd_lattice* lat, double2* part, const CLevel& L, const double2* f, double2* x, int nsteps,
+                            int m, double2* Z, double2* W, double2* r, double2* dots, const CPre* pre) {
   const i64 n = L.n;
   cudaStream_t S = lat->stream;
   QXD_CUDA(lat, cudaMemsetAsync(x, 0, sizeof(double2) * n, S));
@@ -350,14 +405,14 @@ static qxd_status gcr_fixed(qxd_lattice* lat, const CLevel& L, const double2* f,
       QXD_CUDA(lat, cudaMemcpyAsync(zk, r, sizeof(double2) * n, cudaMemcpyDeviceToDevice, S));
     MTRY(cmv(lat, L, zk, nullptr, wk));
     if (k > 0) {
-      MTRY(cdots(lat, W, n, k, wk, dots));
+      MTRY(cdots(lat, part, W, n, k, wk, dots));
       k_mg_orth<<<egrid(n), 256, 0, S>>>(n, k, dots, W, Z, wk, zk);
       QXD_CHECK_LAUNCH(lat, "k_mg_orth");
     }
-    MTRY(cdots(lat, wk, n, 1, wk, dots + m));
+    MTRY(cdots(lat, part, wk, n, 1, wk, dots + m));
     k_mg_scale<<<egrid(n), 256, 0, S>>>(n, dots + m, wk, zk);
     QXD_CHECK_LAUNCH(lat, "k_mg_scale");
-    MTRY(cdots(lat, wk, n, 1, r, dots + m + 1));
+    MTRY(cdots(lat, part, wk, n, 1, r, dots + m + 1));
     k_mg_axpy2<<<egrid(n), 256, 0, S>>>(n, dots + m + 1, zk, x, wk, r);
     QXD_CHECK_LAUNCH(lat, "k_mg_axpy2");
   }
@@ -374,8 +429,8 @@ static qxd_status mr_smooth(qxd_lattice* lat, MgState* s, const CLevel& L1, cons
   QXD_CUDA(lat, cudaMemcpyAsync(rho, f, sizeof(double2) * n, cudaMemcpyDeviceToDevice, lat->stream));
   for (int i = 0; i < s->nu; ++i) {
     MTRY(cmv(lat, L1, rho, nullptr, q));
-    MTRY(cdots(lat, q, n, 1, rho, d));
-    MTRY(cdots(lat, q, n, 1, q, d + 1));
+    MTRY(cdots(lat, s->part, q, n, 1, rho, d));
+    MTRY(cdots(lat, s->part, q, n, 1, q, d + 1));
     k_mg_mr<<<egrid(n), 256, 0, lat->stream>>>(n, d, rho, q, y);
     QXD_CHECK_LAUNCH(lat, "k_mg_mr");
   }
@@ -400,7 +455,7 @@ static qxd_status two_grid(qxd_lattice* lat, MgState* s, const double2* f, doubl
   k_mg_restrict2<<<(s->nb2 * s->ns2 + 255) / 256, 256, 0, lat->stream>>>(s->nb2, s->ns2, s->E, s->ns1, s->va, s->P2,
                                                                          s->blk_of, t, f2);
   QXD_CHECK_LAUNCH(lat, "k_mg_restrict2");
-  MTRY(gcr_fixed(lat, L2, f2, c2, s->n2s, s->m, s->w2, s->w2 + (i64)s->m * n2, s->w2 + (i64)2 * s->m * n2,
+  MTRY(gcr_fixed(lat, s->part, L2, f2, c2, s->n2s, s->m, s->w2, s->w2 + (i64)s->m * n2, s->w2 + (i64)2 * s->m * n2,
                  s->sc + (s->m + 2), nullptr));
   k_mg_prolong2<<<(int)((n1 + 255) / 256), 256, 0, lat->stream>>>(s->nb1, s->ns1, s->ns2, s->E, s->P2, s->agg_of,
                                                                   s->loc_of, c2, y);
@@ -414,9 +469,40 @@ static qxd_status level1_solve(qxd_lattice* lat, MgState* s, const double2* f, d
   const CLevel L1 = level1(lat);
   const i64 n1 = s->n1;
   CPre pre = [lat, s](const double2* r, double2* z) { return two_grid(lat, s, r, z); };
-  s->coarse_calls += 1;
-  return gcr_fixed(lat, L1, f, x, s->n1s, s->m, s->w1, s->w1 + (i64)s->m * n1, s->w1 + (i64)2 * s->m * n1, s->sc,
+  return gcr_fixed(lat, s->part, L1, f, x, s->n1s, s->m, s->w1, s->w1 + (i64)s->m * n1, s->w1 + (i64)2 * s->m * n1, s->sc,
                    &pre);
+}
+
+// K1 from the work vector f1 into c1, replayed from a CUDA graph captured on first use.  The
+// capture runs on a private non-blocking stream (capture is refused on the legacy default stream)
+// and only records; every replay runs on the lattice stream, after the work already queued there.
+static qxd_status k1_run(qxd_lattice* lat, MgState* s) {
+  double2* f1 = s->w1 + (i64)(2 * s->m + 4) * s->n1;
+  double2* c1 = f1 + s->n1;
+  if (!s->k1_exec) {
+    if (!s->side) QXD_CUDA(lat, cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+    const cudaStream_t saved = lat->stream;
+    const i64 l0 = lat->launches;
+    QXD_CUDA(lat, cudaStreamBeginCapture(s->side, cudaStreamCaptureModeThreadLocal));
+    lat->stream = s->side;
+    const qxd_status st = level1_solve(lat, s, f1, c1);
+    lat->stream = saved;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->side, &graph);
+    if (st == QXD_OK && e == cudaSuccess) e = cudaGraphInstantiate(&s->k1_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    s->k1_launches = lat->launches - l0;
+    lat->launches = l0;
+    if (st != QXD_OK) return st;
+    if (e != cudaSuccess) {
+      s->k1_exec = nullptr;
+      return cuda_fail(lat, e, "CUDA graph of the level-1 solve");
+    }
+  }
+  QXD_CUDA(lat, cudaGraphLaunch(s->k1_exec, lat->stream));
+  lat->launches += s->k1_launches;
+  s->coarse_calls += 1;
+  return QXD_OK;
 }
 
 // the fine preconditioner on FP32 full fields; scratch: work slots 58 and 59
@@ -446,7 +532,7 @@ qxd_status mg_precond32(qxd_lattice* lat, const SapSpec& sap, const float4* r, f
   }
   k_dfl_restrict<<<d->dg.nb, nt, 0, lat->stream>>>(lat->g, d->dg, d->ns, d->basis, rc, f1);
   QXD_CHECK_LAUNCH(lat, "k_dfl_restrict");
-  MTRY(level1_solve(lat, s, f1, c1));
+  MTRY(k1_run(lat, s));
   k_dfl_prolong<<<d->dg.nb, nt, 0, lat->stream>>>(lat->g, d->dg, d->ns, d->basis, c1, dz);
   QXD_CHECK_LAUNCH(lat, "k_dfl_prolong");
   if (s->ncy_pre > 0)
@@ -577,7 +663,8 @@ qxd_status qxd_mg_setup(qxd_lattice* lat, const qxd_mg_params* p, const double* 
             cudaMalloc(&s->blk_of, sizeof(int) * blk_of.size()) == cudaSuccess &&
             cudaMalloc(&s->w1, sizeof(double2) * (size_t)(2 * s->m + 6) * s->n1) == cudaSuccess &&
             cudaMalloc(&s->w2, sizeof(double2) * (size_t)(2 * s->m + 3) * s->n2) == cudaSuccess &&
-            cudaMalloc(&s->sc, sizeof(double2) * (size_t)(2 * (s->m + 2) + 2)) == cudaSuccess;
+            cudaMalloc(&s->sc, sizeof(double2) * (size_t)(2 * (s->m + 2) + 2)) == cudaSuccess &&
+            cudaMalloc(&s->part, sizeof(double2) * (size_t)MG_MAXM * MG_DOT_BLOCKS) == cudaSuccess;
   if (!ok) return bail(fail(lat, QXD_ENOMEM, "multigrid allocation failed"));
   cudaStream_t S = lat->stream;
   if (cudaMemcpyAsync(s->nbr2, s->hnbr2.data(), sizeof(int) * s->hnbr2.size(), cudaMemcpyHostToDevice, S) != cudaSuccess ||
@@ -637,21 +724,22 @@ qxd_status qxd_mg_generate(qxd_lattice* lat, int ns2, int n_it, int k, const dou
   const int m = MG_MAXM;
   const size_t vb = sizeof(double2) * n;
   double2 *w, *sc;
-  // scratch: API slot 24 (vectors), 25 (scalars)
+  // scratch: API slot 24 (vectors), 25 (scalars, then the inner-product partials)
   MTRY(ensure_work(lat, 24, vb * (2 * m + 3), (void**)&w));
-  MTRY(ensure_work(lat, 25, sizeof(double2) * (m + 2), (void**)&sc));
+  MTRY(ensure_work(lat, 25, sizeof(double2) * (m + 2 + MG_MAXM * MG_DOT_BLOCKS), (void**)&sc));
+  double2* part = sc + m + 2;
   double2 *v = w + (i64)(2 * m + 1) * n, *x = v + n;
   cudaStream_t S = lat->stream;
   for (int j = 0; j < ns2; ++j) {
     const double2* src = (const double2*)start + (i64)j * n;
     double2* dst = (double2*)out + (i64)j * n;
     QXD_CUDA(lat, cudaMemcpyAsync(v, src, vb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S));
-    MTRY(cdots(lat, v, n, 1, v, sc));
+    MTRY(cdots(lat, part, v, n, 1, v, sc));
     k_mg_scale1<<<egrid(n), 256, 0, S>>>(n, sc, v);
     QXD_CHECK_LAUNCH(lat, "k_mg_scale1");
     for (int it = 0; it < n_it; ++it) {
-      MTRY(gcr_fixed(lat, L1, v, x, k, m, w, w + (i64)m * n, w + (i64)2 * m * n, sc, nullptr));
-      MTRY(cdots(lat, x, n, 1, x, sc + m));
+      MTRY(gcr_fixed(lat, part, L1, v, x, k, m, w, w + (i64)m * n, w + (i64)2 * m * n, sc, nullptr));
+      MTRY(cdots(lat, part, x, n, 1, x, sc + m));
       k_mg_scale1<<<egrid(n), 256, 0, S>>>(n, sc + m, x);
       QXD_CHECK_LAUNCH(lat, "k_mg_scale1");
       std::swap(v, x);
@@ -697,7 +785,7 @@ qxd_status qxd_mg_apply_level1(qxd_lattice* lat, double* out, const double* in, 
   double2* c1 = f1 + s->n1;
   cudaStream_t S = lat->stream;
   QXD_CUDA(lat, cudaMemcpyAsync(f1, in, vb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S));
-  MTRY(level1_solve(lat, s, f1, c1));
+  MTRY(k1_run(lat, s));
   QXD_CUDA(lat, cudaMemcpyAsync(out, c1, vb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S));
   QXD_CUDA(lat, cudaStreamSynchronize(S));
   return QXD_OK;
