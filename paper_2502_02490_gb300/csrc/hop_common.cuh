@@ -57,6 +57,33 @@ __device__ __forceinline__ void accumulate(cplx<R> acc[12], const cplx<R> g[6]) 
   }
 }
 
+// acc += sc (1 -+ gamma_mu) g: the same reconstruction with the half spinor's real scale (the per-site
+// norm of a 16-bit neighbour spinor and the time-boundary sign) folded into fused multiply-adds
+template <typename R, int MU, bool FWD>
+__device__ __forceinline__ void accumulate_s(cplx<R> acc[12], const cplx<R> g[6], R sc) {
+  auto add = [&](cplx<R>& a, cplx<R> b, R f) { a = mk(fma(f, b.re, a.re), fma(f, b.im, a.im)); };
+  auto addi = [&](cplx<R>& a, cplx<R> b, R f) { a = mk(fma(-f, b.im, a.re), fma(f, b.re, a.im)); };  // a += f i b
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cplx<R> g0 = g[c], g1 = g[3 + c];
+    add(acc[c], g0, sc);
+    add(acc[3 + c], g1, sc);
+    if (MU == 0) {
+      add(acc[6 + c], g0, FWD ? sc : -sc);
+      add(acc[9 + c], g1, FWD ? sc : -sc);
+    } else if (MU == 1) {  // -i s_1 g = (-i g1, -i g0)
+      addi(acc[6 + c], g1, FWD ? -sc : sc);
+      addi(acc[9 + c], g0, FWD ? -sc : sc);
+    } else if (MU == 2) {  // -i s_2 g = (-g1, g0)
+      add(acc[6 + c], g1, FWD ? -sc : sc);
+      add(acc[9 + c], g0, FWD ? sc : -sc);
+    } else {  // -i s_3 g = (-i g0, i g1)
+      addi(acc[6 + c], g0, FWD ? -sc : sc);
+      addi(acc[9 + c], g1, FWD ? sc : -sc);
+    }
+  }
+}
+
 template <typename R, bool DAG>
 __device__ __forceinline__ void link_mul(const cplx<R> u[9], const cplx<R> h[6], cplx<R> g[6]) {
 #pragma unroll

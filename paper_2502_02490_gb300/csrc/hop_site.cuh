@@ -13,8 +13,8 @@ namespace qxd {
 
 // One of the eight hops ("legs": 2*mu + 0 forward, 2*mu + 1 backward) of the software-pipelined
 // kernel: decode the raw neighbour spinor and link fetched PF legs earlier, refill the slot with
-// the raw data of leg LEG + PF, then project, scale (per-site norm and time-boundary sign, applied
-// once to the 6-component half spinor), transport and accumulate.
+// the raw data of leg LEG + PF, then project, transport, and accumulate with the scale (per-site
+// norm and time-boundary sign) folded into the accumulation's fused multiply-adds.
 #ifndef QXD_HOP16_MINB
 #define QXD_HOP16_MINB 5  // min resident blocks per SM for the 16-bit kernels (swept 1,4..7 on GB300; 5 best)
 #endif
@@ -23,6 +23,118 @@ namespace qxd {
 #define QXD_HOP_PF16 4  // prefetch depth of the 16-bit kernels (legs in flight); 4 measured best on GB300
 #endif
 
+#ifndef QXD_HOP16_HMATH
+#define QXD_HOP16_HMATH 1  // 16-bit hops: spin projection and link product in packed 16-bit arithmetic
+#endif
+
+// Packed 16-bit arithmetic of a storage format: one complex number per 32-bit word (re low, im high).
+template <class FMT>
+struct HM;
+template <>
+struct HM<H16> {
+  typedef __half2 T;
+  static __device__ __forceinline__ T word(uint32_t w) {
+    T t;
+    memcpy(&t, &w, 4);
+    return t;
+  }
+  static __device__ __forceinline__ T two(float a, float b) { return __floats2half2_rn(a, b); }
+  static __device__ __forceinline__ T lo2(T a) { return __low2half2(a); }
+  static __device__ __forceinline__ T hi2(T a) { return __high2half2(a); }
+  static __device__ __forceinline__ cplx<float> f32(T a) {
+    const float2 f = __half22float2(a);
+    return mk(f.x, f.y);
+  }
+};
+template <>
+struct HM<B16> {
+  typedef __nv_bfloat162 T;
+  static __device__ __forceinline__ T word(uint32_t w) {
+    T t;
+    memcpy(&t, &w, 4);
+    return t;
+  }
+  static __device__ __forceinline__ T two(float a, float b) { return __floats2bfloat162_rn(a, b); }
+  static __device__ __forceinline__ T lo2(T a) { return __low2bfloat162(a); }
+  static __device__ __forceinline__ T hi2(T a) { return __high2bfloat162(a); }
+  static __device__ __forceinline__ cplx<float> f32(T a) { return mk(__low2float(a), __high2float(a)); }
+};
+
+template <class SIN, class LNK>
+struct half_pair {
+  static constexpr bool value = false;
+};
+template <class FMT>
+struct half_pair<SpinorN16<FMT>, Link16<FMT>> {
+  static constexpr bool value = QXD_HOP16_HMATH != 0;
+  typedef FMT fmt;
+};
+// (not the staged link tile of the 16-bit multi-RHS hop: its per-(site, RHS) threads measured slower
+// with the packed leg, 415 us against 390 us per launch on 24^3x48)
+
+// One leg of a 16-bit hop in packed 16-bit arithmetic: the stored (unscaled) neighbour spinor is
+// projected and multiplied by the stored link without conversion, i z = (-z.im, z.re) as a swap of
+// the halves with a sign pair, every product a packed fused multiply-add; the transported half
+// spinor is then widened to FP32 and accumulated with the per-site norm and the time sign.  Stored
+// values lie in [-1, 1] (spinors divided by their site norm, unitary links), so no intermediate
+// can leave the format's range.
+template <class FMT, int MU, bool FWD, bool G5IN>
+__device__ __forceinline__ void leg_half(const typename SpinorN16<FMT>::Raw& sr, const uint32_t lw[9], float sc,
+                                         cplx<float> acc[12]) {
+  typedef HM<FMT> H;
+  typedef typename H::T T;
+  const T NP = H::two(-1.f, 1.f), PN = H::two(1.f, -1.f);
+  T s[12];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    s[2 * j] = H::word(sr.v[j].x);
+    s[2 * j + 1] = H::word(sr.v[j].y);
+  }
+  // dn enters with the sign of gamma5 (G5IN) and of the projector
+  auto pm = [](T a, T b, bool plus) { return plus ? __hadd2(a, b) : __hsub2(a, b); };
+  auto pmi = [&](T a, T b, bool plus) { return __hfma2(__lowhigh2highlow(b), plus ? NP : PN, a); };  // a +- i b
+  T h[6];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T up0 = s[c], up1 = s[3 + c], dn0 = s[6 + c], dn1 = s[9 + c];
+    const bool f = FWD != G5IN;  // the sign of dn
+    if (MU == 0) {
+      h[c] = pm(up0, dn0, f);
+      h[3 + c] = pm(up1, dn1, f);
+    } else if (MU == 1) {
+      h[c] = pmi(up0, dn1, f);
+      h[3 + c] = pmi(up1, dn0, f);
+    } else if (MU == 2) {
+      h[c] = pm(up0, dn1, f);
+      h[3 + c] = pm(up1, dn0, !f);
+    } else {
+      h[c] = pmi(up0, dn0, f);
+      h[3 + c] = pmi(up1, dn1, !f);
+    }
+  }
+  // t = W h (forward) or W^+ h (backward): u x = u.re x + (-u.im, u.im) swap(x),
+  // conj(u) x = u.re x + (u.im, -u.im) swap(x)
+  T t[6];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const T u = H::word(FWD ? lw[3 * a + b] : lw[3 * b + a]);
+      const T ur = H::lo2(u), ui = __hmul2(H::hi2(u), FWD ? NP : PN);
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+        const T x = h[3 * sp + b];
+        T& y = t[3 * sp + a];
+        y = b == 0 ? __hmul2(ur, x) : __hfma2(ur, x, y);
+        y = __hfma2(ui, __lowhigh2highlow(x), y);
+      }
+    }
+  cplx<float> g[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) g[k] = H::f32(t[k]);
+  accumulate_s<float, MU, FWD>(acc, g, sc);
+}
+
 template <int LEG, int PF, typename R, class SIN, class LNK, bool G5IN>
 __device__ __forceinline__ void leg_step(const Geom& g, int par, uint32_t cb, const uint32_t nb[8], bool cr_f,
                                          bool cr_b, const SIN& in, const LNK& lk, typename SIN::Raw* sr,
@@ -30,6 +142,21 @@ __device__ __forceinline__ void leg_step(const Geom& g, int par, uint32_t cb, co
   constexpr int MU = LEG >> 1;
   constexpr bool FWD = (LEG & 1) == 0;
   constexpr int slot = LEG % PF;
+  if constexpr (half_pair<SIN, LNK>::value) {
+    const typename SIN::Raw sraw = sr[slot];
+    const typename LNK::Raw lraw = lr[slot];
+    if constexpr (LEG + PF < 8) {
+      constexpr int nl = LEG + PF;
+      sr[slot] = in.fetch(nb[nl]);
+      lr[slot] = lk.fetch((nl & 1) ? 1 - par : par, nl >> 1, (nl & 1) ? nb[nl] : cb);
+    }
+    float sc = sraw.n;
+    if (MU == 0 && (FWD ? cr_f : cr_b) && g.anti) sc = -sc;
+    uint32_t lw[9];
+    lk.words(lraw, lw);
+    leg_half<typename half_pair<SIN, LNK>::fmt, MU, FWD, G5IN>(sraw, lw, sc, acc);
+    return;
+  }
   cplx<R> s[12], u[9], h[6], t[6];
   R sc = in.decode(sr[slot], s);
   lk.decode(lr[slot], u);
@@ -44,10 +171,8 @@ __device__ __forceinline__ void leg_step(const Geom& g, int par, uint32_t cb, co
   }
   project<R, MU, FWD>(s, h);
   if (MU == 0 && (FWD ? cr_f : cr_b) && g.anti) sc = -sc;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) h[k] = sc * h[k];
   link_mul<R, !FWD>(u, h, t);
-  accumulate<R, MU, FWD>(acc, t);
+  accumulate_s<R, MU, FWD>(acc, t, sc);
 }
 
 // Epilogue prefetch: for the 16-bit kernels the clover block pair and the diagonal input spinor

@@ -449,6 +449,10 @@ struct Link16 {
 #pragma unroll
     for (int k = 0; k < 9; ++k) u[k] = mk(FMT::lo(r.w[k]), FMT::hi(r.w[k]));
   }
+  __device__ __forceinline__ void words(const Raw& r, uint32_t w[9]) const {  // the stored 16-bit pairs
+#pragma unroll
+    for (int k = 0; k < 9; ++k) w[k] = r.w[k];
+  }
   __device__ __forceinline__ void load(int par, int mu, i64 cb, cplx<float> u[9]) const {
     const uint32_t* b = p + (i64)((par * 4 + mu) * 9) * sv + cb;
 #pragma unroll
