@@ -185,6 +185,61 @@ __device__ __forceinline__ void path_setup(const TcLayer& L, int p, int par, uin
   }
 }
 
+#ifndef QXD_PTC_HMATH
+#define QXD_PTC_HMATH 1  // BF16 activations: gauge transport in packed BF16 arithmetic
+#endif
+
+// Gauge transport of one BF16 input channel in packed BF16 arithmetic, straight into the stage:
+// the stored activation words (one complex number per 32-bit word, re low) times the link entries
+// rounded to BF16, u x = u.re x + (-u.im, u.im) swap(x) and conj(u) x = u.re x + (u.im, -u.im)
+// swap(x) as packed fused multiply-adds; each result word is already the BF16 operand the MMA
+// reads (k = 8 slot + 2 beta + re/im).  MODE as put_transported_m.
+template <int MODE>
+__device__ __forceinline__ void put_transported_b16(unsigned char* a0, int s, int slot, const __nv_bfloat162 ub[9],
+                                                    const uint2 raw[6]) {
+  auto word = [&](int idx) -> __nv_bfloat162 {  // complex component idx = 3 beta + b
+    const uint32_t w = (idx & 1) ? raw[idx >> 1].y : raw[idx >> 1].x;
+    __nv_bfloat162 t;
+    memcpy(&t, &w, 4);
+    return t;
+  };
+  auto bits = [](__nv_bfloat162 v) {
+    uint32_t w;
+    memcpy(&w, &v, 4);
+    return w;
+  };
+  const __nv_bfloat162 NP = __floats2bfloat162_rn(-1.f, 1.f), PN = __floats2bfloat162_rn(1.f, -1.f);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    __nv_bfloat162 t[4];
+    if constexpr (MODE == 0) {
+#pragma unroll
+      for (int be = 0; be < 4; ++be) t[be] = __floats2bfloat162_rn(0.f, 0.f);
+    } else if constexpr (MODE == 1) {
+#pragma unroll
+      for (int be = 0; be < 4; ++be) t[be] = word(3 * be + a);
+    } else {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const __nv_bfloat162 u = MODE == 2 ? ub[3 * a + b] : ub[3 * b + a];
+        const __nv_bfloat162 ur = __low2bfloat162(u), ui = __hmul2(__high2bfloat162(u), MODE == 2 ? NP : PN);
+#pragma unroll
+        for (int be = 0; be < 4; ++be) {
+          const __nv_bfloat162 x = word(3 * be + b);
+          t[be] = b == 0 ? __hmul2(ur, x) : __hfma2(ur, x, t[be]);
+          t[be] = __hfma2(ui, __lowhigh2highlow(x), t[be]);
+        }
+      }
+    }
+    uint4 v;
+    v.x = bits(t[0]);
+    v.y = bits(t[1]);
+    v.z = bits(t[2]);
+    v.w = bits(t[3]);
+    *(uint4*)(a0 + a * (TC_ABYTES / 3) + tc::kmajor_off(s, 8 * slot, TC_KC)) = v;
+  }
+}
+
 // C_in a multiple of 8: chunk j is path j / (C_in / 8) and input channels 8 (j % (C_in / 8)) + 0..7;
 // thread (s, grp) transports channels + 2 grp + 0..1 of its site.  (Seventeen warps per SM leave
 // each thread 96 registers: four SM sub-partitions of 16K registers, five warps on one of them.)
@@ -204,6 +259,23 @@ __device__ __forceinline__ void transport_chunk_path(const TcLayer& L, unsigned 
     if (live) {
       act_load<true>(L.in, off, L.g.sv, raw16[0]);
       act_load<true>(L.in, off + cs, L.g.sv, raw16[1]);
+    }
+    if constexpr (QXD_PTC_HMATH != 0) {
+      __nv_bfloat162 ub[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) ub[k] = __floats2bfloat162_rn(u[k].re, u[k].im);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        if (!live)
+          put_transported_b16<0>(a0, s, 2 * grp + i, ub, raw16[i]);
+        else if (p == 0)
+          put_transported_b16<1>(a0, s, 2 * grp + i, ub, raw16[i]);
+        else if (p < 5)
+          put_transported_b16<2>(a0, s, 2 * grp + i, ub, raw16[i]);
+        else
+          put_transported_b16<3>(a0, s, 2 * grp + i, ub, raw16[i]);
+      }
+      return;
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) {

@@ -16,7 +16,7 @@
 // Kernel: one thread per block site (block volume <= 256).  The block residual lives in
 // shared memory, where the neighbours' hops read it.  Links and the clover come from the FP32
 // fields in global memory (L2-resident across the steps), and each step reduces <D r, r> and
-// ||D r||^2 over the CTA with a shared-memory tree (any block volume, no partial warps).
+// ||D r||^2 over the CTA: warp shuffles, then the warp partials in warp order.
 #include "hop_common.cuh"
 #include "sap.cuh"
 #include "trace.cuh"
@@ -113,7 +113,10 @@ __global__ void __launch_bounds__(SAP_MAXVB, QXD_SAP_MINB) k_sap_block_mr(Geom g
     t /= sg.n[mu];
   }
   if (((kb[0] + kb[1] + kb[2] + kb[3]) & 1) != colour) return;  // the whole CTA: no barrier reached
-  const int s = threadIdx.x;
+  // the CTA is rounded up to whole warps (the shuffle reduction needs full warps): threads beyond
+  // the block volume compute on site 0, add nothing and store nothing
+  const bool act = (int)threadIdx.x < sg.vb;
+  const int s = act ? (int)threadIdx.x : 0;
   int lc[4], xg[4], u = s;
   for (int mu = 3; mu >= 0; --mu) {
     lc[mu] = u % sg.b[mu];
@@ -133,8 +136,9 @@ __global__ void __launch_bounds__(SAP_MAXVB, QXD_SAP_MINB) k_sap_block_mr(Geom g
     }
   };
   cplx<float> e[12];
+  if (act)
 #pragma unroll
-  for (int j = 0; j < 6; ++j) rr[j * sg.vb + s] = __ldg(r + base + (i64)j * g.sv);
+    for (int j = 0; j < 6; ++j) rr[j * sg.vb + s] = __ldg(r + base + (i64)j * g.sv);
 #pragma unroll
   for (int k = 0; k < 12; ++k) e[k] = mk(0.f, 0.f);
   __syncthreads();
@@ -178,23 +182,31 @@ __global__ void __launch_bounds__(SAP_MAXVB, QXD_SAP_MINB) k_sap_block_mr(Geom g
       p_im = fmaf(a.re, me[k].im, fmaf(-a.im, me[k].re, p_im));
       p_nn = fmaf(a.re, a.re, fmaf(a.im, a.im, p_nn));
     }
-    part[s] = p_re;
-    part[SAP_MAXVB + s] = p_im;
-    part[2 * SAP_MAXVB + s] = p_nn;
-    __syncthreads();  // also: every thread has finished reading rr for this step
-    // tree over the vb partials: after the pass with width w the live range is [0, w)
-    for (int w = SAP_MAXVB / 2; w > 0; w >>= 1) {
-      if (s < w && s + w < sg.vb) {
-        part[s] += part[s + w];
-        part[SAP_MAXVB + s] += part[SAP_MAXVB + s + w];
-        part[2 * SAP_MAXVB + s] += part[2 * SAP_MAXVB + s + w];
-      }
-      __syncthreads();
+    // warp sums by shuffles, then thread 0 adds the warp partials in warp order (fixed order:
+    // the same bits every run); two barriers per step
+    if (!act) p_re = p_im = p_nn = 0.f;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (sg.vb + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      p_re += __shfl_xor_sync(0xffffffffu, p_re, o);
+      p_im += __shfl_xor_sync(0xffffffffu, p_im, o);
+      p_nn += __shfl_xor_sync(0xffffffffu, p_nn, o);
     }
-    if (s == 0) {
-      const float nn = part[2 * SAP_MAXVB];
-      alpha_sm[0] = nn > 0.f ? part[0] / nn : 0.f;
-      alpha_sm[1] = nn > 0.f ? part[SAP_MAXVB] / nn : 0.f;
+    if (lane == 0) {
+      part[wid] = p_re;
+      part[SAP_MAXVB + wid] = p_im;
+      part[2 * SAP_MAXVB + wid] = p_nn;
+    }
+    __syncthreads();  // also: every thread has finished reading rr for this step
+    if (threadIdx.x == 0) {
+      float sre = 0.f, sim = 0.f, nn = 0.f;
+      for (int k = 0; k < nw; ++k) {
+        sre += part[k];
+        sim += part[SAP_MAXVB + k];
+        nn += part[2 * SAP_MAXVB + k];
+      }
+      alpha_sm[0] = nn > 0.f ? sre / nn : 0.f;
+      alpha_sm[1] = nn > 0.f ? sim / nn : 0.f;
     }
     __syncthreads();
     const cplx<float> alpha = mk(alpha_sm[0], alpha_sm[1]);
@@ -204,11 +216,13 @@ __global__ void __launch_bounds__(SAP_MAXVB, QXD_SAP_MINB) k_sap_block_mr(Geom g
       e[k] = cmac(e[k], alpha, me[k]);
       me[k] = me[k] - cmul(alpha, acc[k]);
     }
+    if (act)
 #pragma unroll
-    for (int j = 0; j < 6; ++j)
-      rr[j * sg.vb + s] = make_float4(me[2 * j].re, me[2 * j].im, me[2 * j + 1].re, me[2 * j + 1].im);
+      for (int j = 0; j < 6; ++j)
+        rr[j * sg.vb + s] = make_float4(me[2 * j].re, me[2 * j].im, me[2 * j + 1].re, me[2 * j + 1].im);
     __syncthreads();  // the new residual is complete before the next step's hops read it
   }
+  if (!act) return;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     float4 q = x[base + (i64)j * g.sv];
@@ -244,7 +258,7 @@ qxd_status sap32(qxd_lattice* lat, const int b[4], int ncy, int nmr, const float
       // algorithmic bytes of a sweep, per site of the colour: the residual read, x read and
       // written, 8 links and the clover pair once (the MR steps re-read them through L1/L2)
       prof_begin(lat, KSTAT_SAP, (3 * 96.0 + 8 * 72.0 + 288.0) * (double)lat->Vh);
-      k_sap_block_mr<<<sg.nblocks, sg.vb, smem, lat->stream>>>(lat->g, sg, colour, nmr, rcur, z, lat->W32,
+      k_sap_block_mr<<<sg.nblocks, (sg.vb + 31) / 32 * 32, smem, lat->stream>>>(lat->g, sg, colour, nmr, rcur, z, lat->W32,
                                                                 lat->C32);
       prof_end(lat);
       QXD_CHECK_LAUNCH(lat, "k_sap_block_mr");

@@ -90,7 +90,8 @@ UNIT16 = {"f16n": 2.0 ** -11, "bf16n": 2.0 ** -8}
 def test_mrhs16_apply_per_site(qxd, prec, L, nrhs, cstar):
     """The 16-bit multi-RHS hop (tile-staged links and clover, groups of right-hand sides) against
     the FP64 oracle site by site: max error over a site's 12 entries <= 8 u max |ref| there, and
-    equal to the single-RHS 16-bit operator up to FP32 rounding of the accumulation order."""
+    within 4 u per site of the single-RHS 16-bit operator (which projects and transports in packed
+    16-bit arithmetic, where the multi-RHS hop computes in FP32 on the same stored values)."""
     c = Case(qxd, torch, L, cstar=cstar)
     try:
         psis = np.stack([synth.gaussian_spinor(c.dims, 3100 + k) for k in range(nrhs)])
@@ -104,7 +105,8 @@ def test_mrhs16_apply_per_site(qxd, prec, L, nrhs, cstar):
             e = np.abs(got[k] - ref).reshape(c.V, -1).max(axis=1) / np.abs(ref).reshape(c.V, -1).max(axis=1)
             worst = max(worst, float(e.max()) / UNIT16[prec])
             single = c.apply_D(psis[k], qxd.PREC[prec])
-            assert np.abs(got[k] - single).max() <= 1e-5 * np.abs(single).max(), k
+            d = np.abs(got[k] - single).reshape(c.V, -1).max(axis=1) / np.abs(single).reshape(c.V, -1).max(axis=1)
+            assert d.max() <= 4 * UNIT16[prec], (k, d.max() / UNIT16[prec])
         assert worst <= 8, worst
         print(f"{L} nrhs={nrhs} {prec}: worst per-site error {worst:.2f} u")
     finally:
