@@ -251,7 +251,9 @@ def run_ours(args, rank, world):
     # the solve is deterministic (fixed-order reductions), so every step repeats the same launches
     same_work = all(i["iters_inner"] == infos[0]["iters_inner"] for i in infos + prof_infos)
     hop_bytes = sum(b for (_, _, b) in stats.values()) / prof_steps * args.steps
-    # ---- end-to-end through host buffers ----
+    # ---- end-to-end through host buffers (one untimed host step first: the library allocates
+    # its staging buffers for host arguments on first use) ----
+    step(host=True)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):

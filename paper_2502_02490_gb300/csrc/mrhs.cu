@@ -240,338 +240,6 @@ __global__ void __launch_bounds__(MT_S* MR_MAXR, 2)
   }
 }
 
-// ------------------------------------------------------------------------------------------
-// Two right-hand sides per thread with packed FP32 arithmetic (fma.rn.f32x2 and friends).  A pair
-// value holds the same quantity of two right-hand sides, lane x for the first and lane y for the
-// second; a complex number of the pair is two such values, (re_a, re_b) and (im_a, im_b).  Every
-// product of a link or clover entry with a spinor component then becomes packed multiply-adds
-// whose one operand, the broadcast entry, is formed once and serves both right-hand sides and
-// both spin rows: about a quarter fewer FP32 instructions per (site, RHS) than k_hop_mrhs_t.
-// ------------------------------------------------------------------------------------------
-struct P2 {
-  float2 re, im;
-};
-__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 f2neg(float2 a) { return __fmul2_rn(a, make_float2(-1.f, -1.f)); }
-__device__ __forceinline__ P2 p2(cplx<float> a, cplx<float> b) {
-  P2 r;
-  r.re = make_float2(a.re, b.re);
-  r.im = make_float2(a.im, b.im);
-  return r;
-}
-
-// g = U h (DAG: U^+ h) for the 2-spin x 3-colour half spinors of both right-hand sides; the link
-// row-major in the tile record, lane stride MT_S.  Per entry u: y.re += u.re x.re + u.im (-x.im),
-// y.im += u.re x.im + u.im x.re (DAG: conj(u) with the signs of the u.im terms swapped).
-template <bool DAG>
-__device__ __forceinline__ void link_mul2(const float2* __restrict__ wt, int s, const P2 h[6], P2 g[6]) {
-  float2 nre[6], nim[6];  // -h.re, -h.im
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    if (DAG)
-      nre[k] = f2neg(h[k].re);
-    else
-      nim[k] = f2neg(h[k].im);
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const float2 w = DAG ? wt[(3 * b + a) * MT_S + s] : wt[(3 * a + b) * MT_S + s];
-      const float2 ur = bc2(w.x), ui = bc2(w.y);
-#pragma unroll
-      for (int sp = 0; sp < 2; ++sp) {
-        const P2& x = h[3 * sp + b];
-        P2& y = g[3 * sp + a];
-        if (b == 0) {
-          y.re = f2mul(ur, x.re);
-          y.im = f2mul(ur, x.im);
-        } else {
-          y.re = f2fma(ur, x.re, y.re);
-          y.im = f2fma(ur, x.im, y.im);
-        }
-        if (!DAG) {
-          y.re = f2fma(ui, nim[3 * sp + b], y.re);
-          y.im = f2fma(ui, x.re, y.im);
-        } else {
-          y.re = f2fma(ui, x.im, y.re);
-          y.im = f2fma(ui, nre[3 * sp + b], y.im);
-        }
-      }
-    }
-}
-
-// acc += (1 -+ gamma_mu) reconstructed from the transported half spinors (pair form of
-// accumulate(): i z = (-z.im, z.re) is a renaming)
-template <int MU, bool FWD>
-__device__ __forceinline__ void accumulate2(P2 acc[12], const P2 g[6]) {
-  auto add = [](P2& a, const P2& b) {
-    a.re = f2add(a.re, b.re);
-    a.im = f2add(a.im, b.im);
-  };
-  auto sub = [](P2& a, const P2& b) {
-    a.re = f2fma(b.re, make_float2(-1.f, -1.f), a.re);
-    a.im = f2fma(b.im, make_float2(-1.f, -1.f), a.im);
-  };
-  auto addi = [](P2& a, const P2& b) {  // a += i b
-    a.re = f2fma(b.im, make_float2(-1.f, -1.f), a.re);
-    a.im = f2add(a.im, b.re);
-  };
-  auto subi = [](P2& a, const P2& b) {  // a -= i b
-    a.re = f2add(a.re, b.im);
-    a.im = f2fma(b.re, make_float2(-1.f, -1.f), a.im);
-  };
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const P2 &g0 = g[c], &g1 = g[3 + c];
-    add(acc[c], g0);
-    add(acc[3 + c], g1);
-    if (MU == 0) {
-      if (FWD) {
-        add(acc[6 + c], g0);
-        add(acc[9 + c], g1);
-      } else {
-        sub(acc[6 + c], g0);
-        sub(acc[9 + c], g1);
-      }
-    } else if (MU == 1) {  // -i s_1 g = (-i g1, -i g0)
-      if (FWD) {
-        subi(acc[6 + c], g1);
-        subi(acc[9 + c], g0);
-      } else {
-        addi(acc[6 + c], g1);
-        addi(acc[9 + c], g0);
-      }
-    } else if (MU == 2) {  // -i s_2 g = (-g1, g0)
-      if (FWD) {
-        sub(acc[6 + c], g1);
-        add(acc[9 + c], g0);
-      } else {
-        add(acc[6 + c], g1);
-        sub(acc[9 + c], g0);
-      }
-    } else {  // -i s_3 g = (-i g0, i g1)
-      if (FWD) {
-        subi(acc[6 + c], g0);
-        addi(acc[9 + c], g1);
-      } else {
-        addi(acc[6 + c], g0);
-        subi(acc[9 + c], g1);
-      }
-    }
-  }
-}
-
-template <int LEG, bool G5IN>
-__device__ __forceinline__ void mt_leg2(const uint32_t* __restrict__ nbt, const float2* __restrict__ wt, int s,
-                                        const float4* __restrict__ ina, const float4* __restrict__ inb, i64 sv,
-                                        P2 acc[12]) {
-  constexpr int MU = LEG >> 1;
-  constexpr bool FWD = (LEG & 1) == 0;
-  const uint32_t e = nbt[LEG * MT_S + s];
-  const uint32_t n = e & 0x7fffffffu;
-  float4 qa[6], qb[6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    qa[j] = __ldg(ina + j * sv + n);
-    qb[j] = __ldg(inb + j * sv + n);
-  }
-  cplx<float> va[12], vb[12], ha[6], hb[6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    va[2 * j] = mk(qa[j].x, qa[j].y);
-    va[2 * j + 1] = mk(qa[j].z, qa[j].w);
-    vb[2 * j] = mk(qb[j].x, qb[j].y);
-    vb[2 * j + 1] = mk(qb[j].z, qb[j].w);
-  }
-  if (G5IN) {
-#pragma unroll
-    for (int k = 6; k < 12; ++k) {
-      va[k] = neg(va[k]);
-      vb[k] = neg(vb[k]);
-    }
-  }
-  project<float, MU, FWD>(va, ha);
-  project<float, MU, FWD>(vb, hb);
-  const bool flip = MU == 0 && (e >> 31);
-  P2 h[6], t[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) h[k] = flip ? p2(neg(ha[k]), neg(hb[k])) : p2(ha[k], hb[k]);
-  link_mul2<!FWD>(wt + LEG * 9 * MT_S, s, h, t);
-  accumulate2<MU, FWD>(acc, t);
-}
-
-// y = M x for both right-hand sides, M the Hermitian 6x6 block packed in 36 reals (diagonal, then
-// the strict upper triangle row-major) in the tile record (float4 entries, lane stride MT_S)
-__device__ __forceinline__ void herm6_apply2(const float4* __restrict__ ct, int s, const P2 x[6], P2 y[6]) {
-  float r[36];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const float4 q = ct[k * MT_S + s];
-    r[4 * k] = q.x;
-    r[4 * k + 1] = q.y;
-    r[4 * k + 2] = q.z;
-    r[4 * k + 3] = q.w;
-  }
-  float2 nre[6], nim[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const float2 d = bc2(r[i]);
-    y[i].re = f2mul(d, x[i].re);
-    y[i].im = f2mul(d, x[i].im);
-    nre[i] = f2neg(x[i].re);
-    nim[i] = f2neg(x[i].im);
-  }
-  int k = 0;
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int j = i + 1; j < 6; ++j) {
-      const float2 cr = bc2(r[6 + 2 * k]), ci = bc2(r[7 + 2 * k]);
-      // y_i += c x_j
-      y[i].re = f2fma(cr, x[j].re, y[i].re);
-      y[i].re = f2fma(ci, nim[j], y[i].re);
-      y[i].im = f2fma(cr, x[j].im, y[i].im);
-      y[i].im = f2fma(ci, x[j].re, y[i].im);
-      // y_j += conj(c) x_i
-      y[j].re = f2fma(cr, x[i].re, y[j].re);
-      y[j].re = f2fma(ci, x[i].im, y[j].re);
-      y[j].im = f2fma(cr, x[i].im, y[j].im);
-      y[j].im = f2fma(ci, nre[i], y[j].im);
-      ++k;
-    }
-}
-
-// The pair version of k_hop_mrhs_t: a block of MT_S x ceil(nr / 2) threads; thread (s, q) applies
-// the hop at site s of the tile for right-hand sides 2 q and 2 q + 1 (the second only when
-// 2 q + 1 < nr; otherwise it recomputes the first and stores nothing for it).
-template <int EPI, bool G5>
-__global__ void __launch_bounds__(MT_S*(MR_MAXR / 2), 2)
-    k_hop_mrhs_p(Geom g, int nr, MrList lst, const float4* __restrict__ in, const float4* __restrict__ same,
-                 float4* __restrict__ out, i64 rs, const unsigned char* __restrict__ rec0, int ntiles, float coef,
-                 int* err) {
-  constexpr bool NEEDC = EPI != EPI_HOP && EPI != EPI_XPAY;
-  constexpr bool CI = EPI == EPI_INV || EPI == EPI_INVXPAY;
-  constexpr uint32_t SRC = (NEEDC && !CI) ? 0u : MT_OFF_NB;
-  constexpr uint32_t BYTES = NEEDC ? MT_CLOV + MT_NB + MT_W : MT_NB + MT_W;
-  constexpr uint32_t S_NB = (NEEDC && !CI) ? MT_CLOV : 0u, S_W = S_NB + MT_NB, S_CL = CI ? MT_NB + MT_W : 0u;
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = (uint64_t*)(smem + 2 * BYTES);
-  volatile int* failed = (volatile int*)(bar + 2);
-  const int s = threadIdx.x, q = threadIdx.y, tid = q * MT_S + s;
-  const int ra = 2 * q, rb = 2 * q + 1 < nr ? 2 * q + 1 : 2 * q;
-  const bool second = 2 * q + 1 < nr;
-  const i64 sv = g.sv;
-  if (tid == 0) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
-    *failed = 0;
-    tc::fence_mbar_init();
-  }
-  __syncthreads();
-  auto issue = [&](int tile, int b) {
-    tc::mbar_expect_tx(&bar[b], BYTES);
-    tc::bulk_g2s(smem + b * BYTES, rec0 + (i64)tile * MT_REC + SRC, BYTES, &bar[b]);
-  };
-  if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
-  int i = 0;
-  bool pending_next = false;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
-    const int b = i & 1;
-    pending_next = tile + (int)gridDim.x < ntiles;
-    if (tid == 0 && pending_next) issue(tile + gridDim.x, b ^ 1);
-    const bool ok = !*failed && tc::mbar_wait(&bar[b], (uint32_t)(i >> 1) & 1u, MT_WAIT);
-    if (!ok) *failed = 1;
-    const uint32_t cb = (uint32_t)tile * MT_S + s;
-    if (ok && ra < nr && cb < (uint32_t)g.Vh) {
-      const unsigned char* buf = smem + b * BYTES;
-      const uint32_t* nbt = (const uint32_t*)(buf + S_NB);
-      const float2* wt = (const float2*)(buf + S_W);
-      const float4* ct = (const float4*)(buf + S_CL);
-      const i64 oa = (i64)lst.idx[ra] * rs, ob = (i64)lst.idx[rb] * rs;
-      P2 acc[12];
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        acc[k].re = make_float2(0.f, 0.f);
-        acc[k].im = make_float2(0.f, 0.f);
-      }
-      constexpr bool G5IN = G5 && EPI == EPI_INV;
-      mt_leg2<0, G5IN>(nbt, wt, s, in + oa, in + ob, sv, acc);
-      mt_leg2<1, G5IN>(nbt, wt, s, in + oa, in + ob, sv, acc);
-      mt_leg2<2, G5IN>(nbt, wt, s, in + oa, in + ob, sv, acc);
-      mt_leg2<3, G5IN>(nbt, wt, s, in + oa, in + ob, sv, acc);
-      mt_leg2<4, G5IN>(nbt, wt, s, in + oa, in + ob, sv, acc);
-      mt_leg2<5, G5IN>(nbt, wt, s, in + oa, in + ob, sv, acc);
-      mt_leg2<6, G5IN>(nbt, wt, s, in + oa, in + ob, sv, acc);
-      mt_leg2<7, G5IN>(nbt, wt, s, in + oa, in + ob, sv, acc);
-      auto load = [&](const float4* f, P2 v[12]) {
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          const float4 x = __ldg(f + oa + j * sv + cb), y = __ldg(f + ob + j * sv + cb);
-          v[2 * j] = p2(mk(x.x, x.y), mk(y.x, y.y));
-          v[2 * j + 1] = p2(mk(x.z, x.w), mk(y.z, y.w));
-        }
-      };
-      auto clover = [&](const P2 v[12], P2 y[12]) {
-        herm6_apply2(ct, s, v, y);
-        herm6_apply2(ct + 9 * MT_S, s, v + 6, y + 6);
-      };
-      auto scale = [&](float c, P2& v) {
-        v.re = f2mul(bc2(c), v.re);
-        v.im = f2mul(bc2(c), v.im);
-      };
-      auto axpy = [&](float c, const P2& x, P2& y) {  // y += c x
-        y.re = f2fma(bc2(c), x.re, y.re);
-        y.im = f2fma(bc2(c), x.im, y.im);
-      };
-      P2 o[12];
-      if (EPI == EPI_HOP) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-          o[k] = acc[k];
-          scale(coef, o[k]);
-        }
-      } else if (EPI == EPI_DFULL || EPI == EPI_DHAT2) {
-        P2 v[12];
-        load(same, v);
-        clover(v, o);
-        const float c = EPI == EPI_DFULL ? -0.5f : coef;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) axpy((EPI == EPI_DHAT2 && G5 && k >= 6) ? -c : c, acc[k], o[k]);
-      } else if (EPI == EPI_INV) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) scale(coef, acc[k]);
-        clover(acc, o);
-      } else if (EPI == EPI_INVXPAY) {
-        P2 v[12];
-        load(same, v);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) axpy(coef, acc[k], v[k]);
-        clover(v, o);
-      } else {  // EPI_XPAY
-        load(same, o);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) axpy(coef, acc[k], o[k]);
-      }
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        out[oa + j * sv + cb] = make_float4(o[2 * j].re.x, o[2 * j].im.x, o[2 * j + 1].re.x, o[2 * j + 1].im.x);
-        if (second)
-          out[ob + j * sv + cb] = make_float4(o[2 * j].re.y, o[2 * j].im.y, o[2 * j + 1].re.y, o[2 * j + 1].im.y);
-      }
-    }
-    __syncthreads();
-    if (*failed) break;
-  }
-  if (tid == 0 && *failed) {
-    atomicExch(err, 1);
-    if (pending_next) tc::mbar_wait(&bar[(i & 1) ^ 1], (uint32_t)((i + 1) >> 1) & 1u, MT_WAIT);
-  }
-}
-
 // The tile records of both parities, rebuilt when the gauge field or clover term changed.
 static qxd_status mr_tiles(qxd_lattice* lat, const unsigned char** rec, int** err) {
   const Geom& g = lat->g;
@@ -634,37 +302,6 @@ static qxd_status launch_mrhs_t(qxd_lattice* lat, int par, const float4* in, con
   return QXD_OK;
 }
 
-template <int EPI, bool G5>
-static qxd_status launch_mrhs_p(qxd_lattice* lat, int par, const float4* in, const float4* same, float4* out,
-                                float coef, int nr, const MrList& lst, i64 rs, const unsigned char* rec, int* err) {
-  constexpr bool NEEDC = EPI != EPI_HOP && EPI != EPI_XPAY;
-  constexpr uint32_t BYTES = NEEDC ? MT_CLOV + MT_NB + MT_W : MT_NB + MT_W;
-  constexpr size_t SMEM = 2 * BYTES + 2 * sizeof(uint64_t) + 16;
-  static int blocks_per_sm = 0, sms = 0;
-  if (!blocks_per_sm) {
-    int dev = 0;
-    QXD_CUDA(lat, cudaGetDevice(&dev));
-    QXD_CUDA(lat, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    QXD_CUDA(lat, cudaFuncSetAttribute((const void*)k_hop_mrhs_p<EPI, G5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SMEM));
-    int b = 0;
-    QXD_CUDA(lat, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hop_mrhs_p<EPI, G5>, MT_S * (MR_MAXR / 2), SMEM));
-    blocks_per_sm = b < 1 ? 1 : b;
-  }
-  const Geom& g = lat->g;
-  const int ntiles = (int)((g.Vh + MT_S - 1) / MT_S);
-  const i64 want = (i64)blocks_per_sm * sms;
-  const unsigned grid = (unsigned)(ntiles < want ? ntiles : want);
-  k_hop_mrhs_p<EPI, G5><<<grid, dim3(MT_S, (nr + 1) / 2), SMEM, lat->stream>>>(
-      g, nr, lst, in, same, out, rs, rec + (i64)par * ntiles * MT_REC, ntiles, coef, err);
-  QXD_CHECK_LAUNCH(lat, "k_hop_mrhs_p");
-  return QXD_OK;
-}
-
-#ifndef QXD_MRHS_PAIRS
-#define QXD_MRHS_PAIRS 1  // 1: two right-hand sides per thread in packed FP32 (k_hop_mrhs_p)
-#endif
-
 qxd_status hop32_mrhs(qxd_lattice* lat, int par, int epi, int g5, const float4* in, const float4* same, float4* out,
                       float coef, int nrhs, i64 rs, const int* rhs) {
   const Geom& g = lat->g;
@@ -680,11 +317,8 @@ qxd_status hop32_mrhs(qxd_lattice* lat, int par, int epi, int g5, const float4* 
     double sp = 96.0 * (2 + ((epi == EPI_DFULL || epi == EPI_DHAT2 || epi == EPI_INVXPAY || epi == EPI_XPAY) ? 1 : 0));
     double once = 8 * 72.0 + ((epi != EPI_HOP && epi != EPI_XPAY) ? 288.0 : 0.0);
     prof_begin(lat, KSTAT_F32_MRHS, (sp * nr + once) * (double)g.Vh);
-#define QXD_MT_CASE(E, G)                                                                                      \
-  if (epi == E && (g5 != 0) == G)                                                                               \
-    st = QXD_MRHS_PAIRS ? launch_mrhs_p<E, G>(lat, par, in, same, out, coef, nr, lst, rs, rec, err)            \
-                        : launch_mrhs_t<E, G>(lat, par, in, same, out, coef, nr, lst, rs, rec, err);           \
-  else
+#define QXD_MT_CASE(E, G) \
+  if (epi == E && (g5 != 0) == G) st = launch_mrhs_t<E, G>(lat, par, in, same, out, coef, nr, lst, rs, rec, err); else
     QXD_MT_CASE(EPI_HOP, false)
     QXD_MT_CASE(EPI_DFULL, false)
     QXD_MT_CASE(EPI_INV, false)
