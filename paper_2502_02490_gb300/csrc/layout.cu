@@ -264,8 +264,9 @@ __global__ void k_update_links(Geom g, int order, int Lp1, int Lp2, int Lp3, i64
         U[base + k * g.sv] = cdf_split(u.x, u.y);
         W[base + k * g.sv] = w;
         W32[base + k * g.sv] = make_float2((float)w.x, (float)w.y);
-        W16[base + k * g.sv] = H16::pack((float)w.x, (float)w.y);
-        WB16[base + k * g.sv] = B16::pack((float)w.x, (float)w.y);
+        const i64 l16 = link16_index(par * 4 + mu, g.sv, k, cb);
+        W16[l16] = H16::pack((float)w.x, (float)w.y);
+        WB16[l16] = B16::pack((float)w.x, (float)w.y);
       }
       A[(i64)(par * 4 + mu) * g.sv + cb] = ang;
       for (int end = 0; end < 2; ++end) {
@@ -308,20 +309,23 @@ qxd_status compact_mask(qxd_lattice* lat, const unsigned char* mask, uint32_t* l
   return QXD_OK;
 }
 
-// FP64 hop links -> FP32 and the two 16-bit formats (unitary links need no scale).
-__global__ void k_links_low(i64 n, const double2* __restrict__ W, float2* __restrict__ W32,
+// FP64 hop links -> FP32 and the two 16-bit formats (unitary links need no scale; the 16-bit
+// links in the grouped layout of link16_index).
+__global__ void k_links_low(i64 n, i64 sv, const double2* __restrict__ W, float2* __restrict__ W32,
                             uint32_t* __restrict__ W16, uint32_t* __restrict__ WB16) {
   for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n; t += (i64)gridDim.x * blockDim.x) {
     double2 w = W[t];
     W32[t] = make_float2((float)w.x, (float)w.y);
-    W16[t] = H16::pack((float)w.x, (float)w.y);
-    WB16[t] = B16::pack((float)w.x, (float)w.y);
+    const i64 pm = t / (9 * sv), k = (t / sv) % 9, cb = t % sv;
+    const i64 l16 = link16_index(pm, sv, (int)k, cb);
+    W16[l16] = H16::pack((float)w.x, (float)w.y);
+    WB16[l16] = B16::pack((float)w.x, (float)w.y);
   }
 }
 
 qxd_status convert_links_low(qxd_lattice* lat) {
   i64 n = 2 * 4 * 9 * lat->sv;
-  k_links_low<<<grid_cap(n, 256), 256, 0, lat->stream>>>(n, lat->W64, lat->W32, lat->W16, lat->WB16);
+  k_links_low<<<grid_cap(n, 256), 256, 0, lat->stream>>>(n, lat->sv, lat->W64, lat->W32, lat->W16, lat->WB16);
   QXD_CHECK_LAUNCH(lat, "k_links_low");
   return QXD_OK;
 }

@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(MR16_SITES* NRB, MINB)
       const int mu = leg >> 1;
       const bool fwd = (leg & 1) == 0;
       const int lp = fwd ? par : 1 - par;
-      wl[i] = __ldg(W + ((i64)(lp * 4 + mu) * 9 + k) * sv + (fwd ? cb : sh.nbb[mu][ss]));
+      wl[i] = __ldg(W + link16_index(lp * 4 + mu, sv, k, fwd ? cb : sh.nbb[mu][ss]));
     }
   }
 #pragma unroll

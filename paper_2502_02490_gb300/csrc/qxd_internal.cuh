@@ -430,6 +430,14 @@ struct LinkF32 {
     }
   }
 };
+// 16-bit links (one 32-bit word, a complex pair, per entry): each (parity, direction) owns 9 sv
+// words; a site's entries 0..3 form one 16-byte group at word 4 cb, entries 4..7 one at
+// 4 sv + 4 cb, entry 8 sits at 8 sv + cb -- three loads per link instead of nine.
+__host__ __device__ __forceinline__ i64 link16_index(i64 pm, i64 sv, int k, i64 cb) {  // pm = par * 4 + mu
+  const i64 b = pm * 9 * sv;
+  return k < 4 ? b + 4 * cb + k : k < 8 ? b + 4 * sv + 4 * cb + (k - 4) : b + 8 * sv + cb;
+}
+
 template <class FMT>
 struct Link16 {
   typedef float real;
@@ -439,10 +447,18 @@ struct Link16 {
   const uint32_t* p;
   i64 sv;
   __device__ __forceinline__ Raw fetch(int par, int mu, uint32_t cb) const {
-    const uint32_t* b = p + (i64)((par * 4 + mu) * 9) * sv + cb;
+    const uint32_t* b = p + (i64)((par * 4 + mu) * 9) * sv;
+    const uint4 a = __ldg((const uint4*)b + cb), c = __ldg((const uint4*)(b + 4 * sv) + cb);
     Raw r;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) r.w[k] = __ldg(b + k * sv);
+    r.w[0] = a.x;
+    r.w[1] = a.y;
+    r.w[2] = a.z;
+    r.w[3] = a.w;
+    r.w[4] = c.x;
+    r.w[5] = c.y;
+    r.w[6] = c.z;
+    r.w[7] = c.w;
+    r.w[8] = __ldg(b + 8 * sv + cb);
     return r;
   }
   __device__ __forceinline__ void decode(const Raw& r, cplx<float> u[9]) const {
@@ -454,12 +470,8 @@ struct Link16 {
     for (int k = 0; k < 9; ++k) w[k] = r.w[k];
   }
   __device__ __forceinline__ void load(int par, int mu, i64 cb, cplx<float> u[9]) const {
-    const uint32_t* b = p + (i64)((par * 4 + mu) * 9) * sv + cb;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      uint32_t v = __ldg(b + k * sv);
-      u[k] = mk(FMT::lo(v), FMT::hi(v));
-    }
+    const Raw r = fetch(par, mu, (uint32_t)cb);
+    decode(r, u);
   }
 };
 
