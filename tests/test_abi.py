@@ -102,3 +102,23 @@ def test_without_a_gpu_calls_fail_with_a_status_not_an_abort(qxd):
     with pytest.raises(qxd.QxdError) as e:
         qxd.create_lattice((4, 4, 4, 4))
     assert e.value.status == qxd.ECUDA and "cuda" in qxd.last_error(None).lower()
+
+
+def test_multigrid_entry_points_and_params_layout(qxd):
+    """The multigrid calls refuse a NULL lattice with QXD_EINVAL before touching CUDA, and the
+    binding's parameter struct has the header's layout (version, agg[4], then six ints)."""
+    import ctypes as C
+
+    P = qxd.MgParams
+    assert C.sizeof(P) == 11 * C.sizeof(C.c_int) and P.agg.offset == C.sizeof(C.c_int)
+    assert P.ncy_pre.offset == 10 * C.sizeof(C.c_int) and qxd.MG_VERSION == 1
+    p = qxd.mg_params(agg=(2, 2, 2, 2), ns2=8)
+    assert list(p.agg) == [2, 2, 2, 2] and p.version == qxd.MG_VERSION and p.m == 8
+    lib = qxd.lib
+    assert lib.qxd_mg_setup(None, C.byref(p), None, 0) == qxd.EINVAL
+    assert lib.qxd_mg_generate(None, 1, 1, 1, None, None, 0) == qxd.EINVAL
+    assert lib.qxd_mg_get_coarse(None, None, None) == qxd.EINVAL
+    assert lib.qxd_mg_info(None, None, None, None) == qxd.EINVAL
+    assert lib.qxd_mg_apply_level1(None, None, None, 0) == qxd.EINVAL
+    assert lib.qxd_mg_precond(None, None, None, None, 1, 1, 0) == qxd.EINVAL
+    assert qxd.SOLVER_MP_MG_GCR == 7
