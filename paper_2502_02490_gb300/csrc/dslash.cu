@@ -13,10 +13,7 @@
 
 namespace qxd {
 
-#ifndef QXD_HOP_BLOCK
-#define QXD_HOP_BLOCK 128  // threads per block of the hop kernels
-#endif
-constexpr int HOP_BLOCK = QXD_HOP_BLOCK;
+constexpr int HOP_BLOCK = 128;
 
 // (Norms of the output are taken by a separate BLAS pass: a block reduction inside this
 // latency-bound kernel measured slower on GB300 than the extra bandwidth-bound pass.)
