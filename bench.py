@@ -814,7 +814,8 @@ def run_c4(args):
 def profile_run(args):
     """One untimed pass of the step (for ncu launch lists and kernel captures).  c4: 40 steps of
     the learned FGCR with an untrained [1,8,8,1] network at m0 = -0.1; c3b: one batched solve;
-    c3a: one multi-RHS solve of the 12 point sources."""
+    c3a: one multi-RHS solve of the 12 point sources; sap: 8 SAP-GCR steps, then 3 MG-GCR steps
+    after the multigrid set-up."""
     import torch
 
     from paper_2502_02490_gb300 import qxd, synth
@@ -865,6 +866,32 @@ def profile_run(args):
               file=sys.stderr)
         for lat in lats:
             qxd.destroy_lattice(lat)
+        return
+    if args.workload == "sap":
+        # 8 steps of SAP-GCR (4^4 blocks, 2 cycles x 4 MR steps), then the three-level multigrid
+        # of the sap workload and 3 steps of MG-GCR
+        U, A = synth.gauge_field(w["L"], w["gauge_seed"], w["eps"])
+        eta = torch.from_numpy(synth.gaussian_spinor(w["L"], w["source_seed"]).view(np.float64)).to(dev)
+        x = torch.empty_like(eta)
+        lat = qxd.create_lattice(w["L"], qxd.BC_ANTIPERIODIC, 0, qxd.ORDER_LEXI, stream.cuda_stream)
+        qxd.load_gauge(lat, torch.from_numpy(U.view(np.float64)).to(dev), torch.from_numpy(A).to(dev), w["q"])
+        qxd.build_clover(lat, w["m0"], w["csw"], w["csw_qed"])
+        blk = (4, 4, 4, 4)
+        sap = dict(sap_block=blk, sap_nmr=4, gcr_restart=16, tol=1e-12, max_outer=1, check=False)
+        st, info = qxd.solve(lat, x, eta, solver=qxd.SOLVER_MP_SAP_GCR, sap_ncy=2, maxiter=8, **sap)
+        start = torch.from_numpy(np.stack([synth.gaussian_spinor(w["L"], 7000 + k) for k in range(8)])
+                                 .view(np.float64)).to(dev)
+        vecs = torch.empty_like(start)
+        qxd.dfl_generate(lat, blk, start, vecs, n_it=2, ncy=1, nmr=4)
+        qxd.dfl_setup(lat, blk, vecs)
+        n1 = qxd.dfl_info(lat)["nblocks"] * 8
+        v2 = torch.from_numpy(np.stack([synth.gaussian_spinor((n1, 1, 1, 1), 7100 + k).reshape(-1)[:n1]
+                                        for k in range(8)]).view(np.float64)).to(dev)
+        qxd.mg_setup(lat, v2, agg=(2, 2, 2, 2), nu=2, n1=4, n2=8, m=8, ncy_pre=1)
+        st2, info2 = qxd.solve(lat, x, eta, solver=qxd.SOLVER_MP_MG_GCR, sap_ncy=1, maxiter=3, **sap)
+        torch.cuda.synchronize()
+        print(f"profile run: SAP-GCR {info}, MG-GCR {info2}", file=sys.stderr)
+        qxd.destroy_lattice(lat)
         return
     U, A, eta = make_inputs(0)
     su3_d = torch.from_numpy(U.view(np.float64)).to(dev)

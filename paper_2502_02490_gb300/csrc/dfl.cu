@@ -36,7 +36,7 @@ qxd_status apply_D64(qxd_lattice* lat, const double2* in, double2* out);
 
 static void dfl_release(void* p) {
   DflState* d = (DflState*)p;
-  void* b[] = {d->basis, d->A, d->nbr, d->cw, d->cpart};
+  void* b[] = {d->basis, d->basis32, d->A, d->nbr, d->cw, d->cpart};
   for (void* q : b)
     if (q) cudaFree(q);
   if (d->hcs) cudaFreeHost(d->hcs);
@@ -293,60 +293,72 @@ __global__ void k_dfl_cscale(i64 n, const double2* __restrict__ nn, double2* __r
 }
 
 // ---- fine <-> coarse ----
-// f[b][k] = <psi_{b,k}, r> over block b (r: full FP32 field); one CTA per block
-__global__ void __launch_bounds__(DFL_MAXVB) k_dfl_restrict(Geom g, DflGeom dg, int ns, const double2* __restrict__ V,
+// The preconditioner applies P and P^+ to the FP32 fields of the inner solver with an FP32 copy
+// of the (FP64-orthonormalised) basis, V32 [ns][2][6][sv] float4: FP32 products, FP64 block sums.
+// f[b][k] = <psi_{b,k}, r> over block b (r: full FP32 field); one CTA per block, eight basis
+// vectors per block reduction
+__global__ void __launch_bounds__(DFL_MAXVB) k_dfl_restrict(Geom g, DflGeom dg, int ns, const float4* __restrict__ V,
                                                             const float4* __restrict__ r, double2* __restrict__ f) {
-  __shared__ double sh[2 * 8];
+  __shared__ double sh[16 * 8];
   const int t = blockIdx.x, s = threadIdx.x;
   const bool act = s < dg.vb;
   int lc[4], par = 0;
   i64 cb = 0;
   if (act) block_site(g, dg, t, s, lc, par, cb);
-  const i64 fs = 24 * g.sv, base = (i64)par * 12 * g.sv + cb;
+  const i64 fs = 12 * g.sv, base = (i64)par * 6 * g.sv + cb;
   float4 rx[6];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) rx[j] = act ? r[(i64)par * 6 * g.sv + j * g.sv + cb] : make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int k = 0; k < ns; ++k) {
-    const double2* u = V + (i64)k * fs + base;
-    double v[2] = {0.0, 0.0};
-    if (act)
+  for (int j = 0; j < 6; ++j) rx[j] = act ? r[base + j * g.sv] : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k0 = 0; k0 < ns; k0 += 8) {
+    double v[16];
 #pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const double2 a = u[(2 * j) * g.sv], b = u[(2 * j + 1) * g.sv];
-        v[0] += a.x * rx[j].x + a.y * rx[j].y + b.x * rx[j].z + b.y * rx[j].w;
-        v[1] += a.x * rx[j].y - a.y * rx[j].x + b.x * rx[j].w - b.y * rx[j].z;
+    for (int kk = 0; kk < 8; ++kk) {
+      float re = 0.f, im = 0.f;
+      if (act && k0 + kk < ns) {
+        const float4* u = V + (i64)(k0 + kk) * fs + base;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const float4 a = u[j * g.sv], x = rx[j];
+          re += a.x * x.x + a.y * x.y + a.z * x.z + a.w * x.w;  // conj(a) x
+          im += a.x * x.y - a.y * x.x + a.z * x.w - a.w * x.z;
+        }
       }
-    cta_sum<2>(v, sh);
-    if (s == 0) f[(i64)t * ns + k] = make_double2(v[0], v[1]);
+      v[2 * kk] = re;
+      v[2 * kk + 1] = im;
+    }
+    cta_sum<16>(v, sh);
+    if (s == 0)
+      for (int kk = 0; kk < 8 && k0 + kk < ns; ++kk) f[(i64)t * ns + k0 + kk] = make_double2(v[2 * kk], v[2 * kk + 1]);
   }
 }
 
-// z = P c (full FP32 field); one thread per site, grid = blocks
-__global__ void __launch_bounds__(DFL_MAXVB) k_dfl_prolong(Geom g, DflGeom dg, int ns, const double2* __restrict__ V,
+// z = P c (full FP32 field, FP32 basis copy); one thread per site, grid = blocks
+__global__ void __launch_bounds__(DFL_MAXVB) k_dfl_prolong(Geom g, DflGeom dg, int ns, const float4* __restrict__ V,
                                                            const double2* __restrict__ c, float4* __restrict__ z) {
   const int t = blockIdx.x, s = threadIdx.x;
   if (s >= dg.vb) return;  // no reduction in this kernel
   int lc[4], par;
   i64 cb;
   block_site(g, dg, t, s, lc, par, cb);
-  const i64 fs = 24 * g.sv, base = (i64)par * 12 * g.sv + cb;
-  double2 acc[12];
+  const i64 fs = 12 * g.sv, base = (i64)par * 6 * g.sv + cb;
+  float4 acc[6];
 #pragma unroll
-  for (int q = 0; q < 12; ++q) acc[q] = make_double2(0.0, 0.0);
+  for (int j = 0; j < 6; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int k = 0; k < ns; ++k) {
-    const double2 ck = c[(i64)t * ns + k];
-    const double2* u = V + (i64)k * fs + base;
+    const double2 cd = c[(i64)t * ns + k];
+    const float cr = (float)cd.x, ci = (float)cd.y;
+    const float4* u = V + (i64)k * fs + base;
 #pragma unroll
-    for (int q = 0; q < 12; ++q) {
-      const double2 a = u[q * g.sv];
-      acc[q].x += ck.x * a.x - ck.y * a.y;
-      acc[q].y += ck.x * a.y + ck.y * a.x;
+    for (int j = 0; j < 6; ++j) {
+      const float4 a = u[j * g.sv];
+      acc[j].x = fmaf(cr, a.x, fmaf(-ci, a.y, acc[j].x));
+      acc[j].y = fmaf(cr, a.y, fmaf(ci, a.x, acc[j].y));
+      acc[j].z = fmaf(cr, a.z, fmaf(-ci, a.w, acc[j].z));
+      acc[j].w = fmaf(cr, a.w, fmaf(ci, a.z, acc[j].w));
     }
   }
 #pragma unroll
-  for (int j = 0; j < 6; ++j)
-    z[(i64)par * 6 * g.sv + j * g.sv + cb] =
-        make_float4((float)acc[2 * j].x, (float)acc[2 * j].y, (float)acc[2 * j + 1].x, (float)acc[2 * j + 1].y);
+  for (int j = 0; j < 6; ++j) z[base + j * g.sv] = acc[j];
 }
 
 __global__ void k_dfl_scale32(i64 n, const double* __restrict__ nn, float4* __restrict__ v) {
@@ -433,10 +445,10 @@ qxd_status dfl_precond32(qxd_lattice* lat, const SapSpec& sap, const float4* r, 
   double2* f = d->cw + (i64)(2 * d->m + 1) * n;
   double2* c = d->cw + (i64)(2 * d->m + 2) * n;
   const int nt = dfl_threads(d->dg);
-  k_dfl_restrict<<<d->dg.nb, nt, 0, lat->stream>>>(lat->g, d->dg, d->ns, d->basis, r, f);
+  k_dfl_restrict<<<d->dg.nb, nt, 0, lat->stream>>>(lat->g, d->dg, d->ns, d->basis32, r, f);
   QXD_CHECK_LAUNCH(lat, "k_dfl_restrict");
   DTRY(coarse_solve(lat, d, f, c));
-  k_dfl_prolong<<<d->dg.nb, nt, 0, lat->stream>>>(lat->g, d->dg, d->ns, d->basis, c, z);
+  k_dfl_prolong<<<d->dg.nb, nt, 0, lat->stream>>>(lat->g, d->dg, d->ns, d->basis32, c, z);
   QXD_CHECK_LAUNCH(lat, "k_dfl_prolong");
   DTRY(hop32(lat, 0, EPI_DFULL, 0, z + 6 * sv, z, dz, 0.f));
   DTRY(hop32(lat, 1, EPI_DFULL, 0, z, z + 6 * sv, dz + 6 * sv, 0.f));
@@ -474,6 +486,7 @@ qxd_status qxd_dfl_setup(qxd_lattice* lat, const int block[4], int ns, const dou
   const i64 sv = lat->sv, fs = 24 * sv, n = (i64)dg.nb * ns;
   const size_t abytes = sizeof(double2) * (size_t)dg.nb * DFL_SLOTS * ns * ns;
   bool ok = cudaMalloc(&d->basis, sizeof(double2) * fs * ns) == cudaSuccess &&
+            cudaMalloc(&d->basis32, sizeof(float4) * 12 * sv * ns) == cudaSuccess &&
             cudaMalloc(&d->A, abytes) == cudaSuccess &&
             cudaMalloc(&d->nbr, sizeof(int) * dg.nb * DFL_SLOTS) == cudaSuccess &&
             cudaMalloc(&d->cw, sizeof(double2) * (size_t)(2 * d->m + 3) * n) == cudaSuccess &&
@@ -517,6 +530,10 @@ qxd_status qxd_dfl_setup(qxd_lattice* lat, const int block[4], int ns, const dou
   cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, lat->stream);
   if (cudaStreamSynchronize(lat->stream) != cudaSuccess) return bail(fail(lat, QXD_ECUDA, "dfl_setup"));
   if (hbad) return bail(fail(lat, QXD_EINVAL, "deflation vectors are linearly dependent on some block"));
+  for (int k = 0; k < ns; ++k) {  // the FP32 copy the preconditioner applies
+    qxd_status st = f64_to_f32(lat, d->basis + (i64)k * fs, d->basis32 + (i64)k * 12 * sv, 12 * sv);
+    if (st) return bail(st);
+  }
   // neighbour table and the colours present
   d->hnbr.assign((size_t)dg.nb * DFL_SLOTS, 0);
   bool present[16] = {false};

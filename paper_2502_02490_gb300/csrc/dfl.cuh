@@ -21,6 +21,7 @@ struct DflState {
   DflGeom dg;
   int ns = 0;
   double2* basis = nullptr;  // [ns][2][12][sv] FP64, the internal spinor layout, zero off its blocks
+  float4* basis32 = nullptr; // [ns][2][6][sv] FP32 copy for applying P and P^+ to FP32 fields
   double2* A = nullptr;      // [nb][9][ns][ns]
   int* nbr = nullptr;        // [nb][9] block index per slot (device)
   std::vector<int> hnbr;     // host copy
@@ -81,10 +82,10 @@ inline int egrid(i64 n) { return (int)std::min<i64>((n + 255) / 256, 152 * 16); 
 
 bool dfl_ready(const qxd_lattice* lat);
 
-// kernels of csrc/dfl.cu used by csrc/mg.cu
-__global__ void __launch_bounds__(DFL_MAXVB) k_dfl_restrict(Geom g, DflGeom dg, int ns, const double2* __restrict__ V, const float4* __restrict__ r,
-                               double2* __restrict__ f);
-__global__ void __launch_bounds__(DFL_MAXVB) k_dfl_prolong(Geom g, DflGeom dg, int ns, const double2* __restrict__ V, const double2* __restrict__ c,
-                              float4* __restrict__ z);
+// kernels of csrc/dfl.cu used by csrc/mg.cu (V: the FP32 basis copy)
+__global__ void __launch_bounds__(DFL_MAXVB) k_dfl_restrict(Geom g, DflGeom dg, int ns, const float4* __restrict__ V,
+                                                            const float4* __restrict__ r, double2* __restrict__ f);
+__global__ void __launch_bounds__(DFL_MAXVB) k_dfl_prolong(Geom g, DflGeom dg, int ns, const float4* __restrict__ V,
+                                                           const double2* __restrict__ c, float4* __restrict__ z);
 
 }  // namespace qxd

@@ -530,10 +530,10 @@ qxd_status mg_precond32(qxd_lattice* lat, const SapSpec& sap, const float4* r, f
     MTRY(residual());
     rc = t;
   }
-  k_dfl_restrict<<<d->dg.nb, nt, 0, lat->stream>>>(lat->g, d->dg, d->ns, d->basis, rc, f1);
+  k_dfl_restrict<<<d->dg.nb, nt, 0, lat->stream>>>(lat->g, d->dg, d->ns, d->basis32, rc, f1);
   QXD_CHECK_LAUNCH(lat, "k_dfl_restrict");
   MTRY(k1_run(lat, s));
-  k_dfl_prolong<<<d->dg.nb, nt, 0, lat->stream>>>(lat->g, d->dg, d->ns, d->basis, c1, dz);
+  k_dfl_prolong<<<d->dg.nb, nt, 0, lat->stream>>>(lat->g, d->dg, d->ns, d->basis32, c1, dz);
   QXD_CHECK_LAUNCH(lat, "k_dfl_prolong");
   if (s->ncy_pre > 0)
     MTRY(blas_axpy_32(lat, 1.0f, dz, z, n4));
