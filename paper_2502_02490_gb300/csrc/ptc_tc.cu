@@ -43,6 +43,7 @@ struct TcLayer {
   const void* in;              // [cin][2][6][sv] float4 (FP32) or uint2 (BF16 activations)
   void* out;                   // [cout][2][6][sv] float4 (FP32) or uint2 (BF16 activations)
   const float2* W;             // FP32 hop links
+  const uint32_t* Wb;          // the same links as BF16 pairs, grouped layout (link16_index)
   const unsigned char* Bp;     // packed weights: [nchunks][np x 64 BF16, K-major core-matrix layout]
   int ntiles, tiles_per_par;   // tiles over both parities
   uint32_t tcols;              // TMEM columns allocated (power of 2 >= 3 np)
@@ -251,6 +252,52 @@ __device__ __forceinline__ void transport_chunk_path(const TcLayer& L, unsigned 
   uint32_t src;
   int spar;
   cplx<float> u[9];
+  if constexpr (IN16 && QXD_PTC_HMATH != 0) {
+    // BF16 activations with the BF16 transport: the link straight from its BF16 copy (grouped
+    // layout, three loads), the antiperiodic time sign as a flip of both halves' sign bits
+    src = cb;
+    spar = par;
+    uint32_t lw[9] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, sgn = 0u;
+    if (live && p != 0) {
+      const bool fwd = p < 5;
+      const int mu = fwd ? p - 1 : p - 5;
+      bool cr;
+      src = nbr_cb32(L.g, x, mu, fwd ? +1 : -1, cr);
+      spar = 1 - par;
+      if (mu == 0 && cr && L.g.anti) sgn = 0x80008000u;
+      const int lpar = fwd ? par : 1 - par;
+      const uint32_t ls = fwd ? cb : src;
+      const uint32_t* b = L.Wb + (i64)((lpar * 4 + mu) * 9) * L.g.sv;
+      const uint4 w0 = __ldg((const uint4*)b + ls), w1 = __ldg((const uint4*)(b + 4 * L.g.sv) + ls);
+      lw[0] = w0.x; lw[1] = w0.y; lw[2] = w0.z; lw[3] = w0.w;
+      lw[4] = w1.x; lw[5] = w1.y; lw[6] = w1.z; lw[7] = w1.w;
+      lw[8] = __ldg(b + 8 * L.g.sv + ls);
+    }
+    const i64 off = (i64)c0 * cs + (i64)spar * 6 * L.g.sv + src;
+    uint2 raw16[2][6];
+    if (live) {
+      act_load<true>(L.in, off, L.g.sv, raw16[0]);
+      act_load<true>(L.in, off + cs, L.g.sv, raw16[1]);
+    }
+    __nv_bfloat162 ub[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const uint32_t w = lw[k] ^ sgn;
+      memcpy(&ub[k], &w, 4);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      if (!live)
+        put_transported_b16<0>(a0, s, 2 * grp + i, ub, raw16[i]);
+      else if (p == 0)
+        put_transported_b16<1>(a0, s, 2 * grp + i, ub, raw16[i]);
+      else if (p < 5)
+        put_transported_b16<2>(a0, s, 2 * grp + i, ub, raw16[i]);
+      else
+        put_transported_b16<3>(a0, s, 2 * grp + i, ub, raw16[i]);
+    }
+    return;
+  }
   if (live) path_setup(L, p, par, cb, x, src, spar, u);
   const i64 off = (i64)c0 * cs + (i64)spar * 6 * L.g.sv + src;
   if constexpr (IN16) {
@@ -259,23 +306,6 @@ __device__ __forceinline__ void transport_chunk_path(const TcLayer& L, unsigned 
     if (live) {
       act_load<true>(L.in, off, L.g.sv, raw16[0]);
       act_load<true>(L.in, off + cs, L.g.sv, raw16[1]);
-    }
-    if constexpr (QXD_PTC_HMATH != 0) {
-      __nv_bfloat162 ub[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) ub[k] = __floats2bfloat162_rn(u[k].re, u[k].im);
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        if (!live)
-          put_transported_b16<0>(a0, s, 2 * grp + i, ub, raw16[i]);
-        else if (p == 0)
-          put_transported_b16<1>(a0, s, 2 * grp + i, ub, raw16[i]);
-        else if (p < 5)
-          put_transported_b16<2>(a0, s, 2 * grp + i, ub, raw16[i]);
-        else
-          put_transported_b16<3>(a0, s, 2 * grp + i, ub, raw16[i]);
-      }
-      return;
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -600,6 +630,7 @@ static qxd_status launch_tc(qxd_lattice* lat, int cin, int cout, int npaths, con
   L.in = in;
   L.out = out;
   L.W = lat->W32;
+  L.Wb = lat->WB16;
   L.Bp = (const unsigned char*)Bp;
   L.tiles_per_par = (int)((lat->Vh + TC_M - 1) / TC_M);
   L.ntiles = 2 * L.tiles_per_par;
