@@ -241,6 +241,81 @@ __device__ __forceinline__ void put_transported_b16(unsigned char* a0, int s, in
   }
 }
 
+// The raw operands of one chunk for one producer thread of a BF16 layer (C_in a multiple of 8):
+// the path's link as BF16 words from the links' BF16 copy (grouped layout, three loads), the
+// antiperiodic time sign as a flip of both halves' sign bits, and the two input channels' words.
+struct ChunkRaw {
+  uint32_t lw[9];
+  uint2 r[2][6];
+  int p;
+  uint32_t sgn;
+};
+
+__device__ __forceinline__ void chunk_load(const TcLayer& L, int j, int grp, bool live, int par, uint32_t cb,
+                                           const int x[4], i64 cs, ChunkRaw& c) {
+  const Geom& g = L.g;
+  const int G = L.cin >> 3;
+  const int p = j / G, c0 = 8 * (j % G) + 2 * grp;
+  c.p = p;
+  c.sgn = 0u;
+  if (!live) {  // a site past the end of the lattice: zero operands (transported as zeros anyway)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) c.lw[k] = 0u;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) c.r[0][k] = c.r[1][k] = make_uint2(0u, 0u);
+    return;
+  }
+  uint32_t src = cb;
+  int spar = par;
+  if (p == 0) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) c.lw[k] = 0u;  // the identity path uses no link
+  } else {
+    const bool fwd = p < 5;
+    const int mu = fwd ? p - 1 : p - 5;
+    bool cr;
+    src = nbr_cb32(g, x, mu, fwd ? +1 : -1, cr);
+    spar = 1 - par;
+    if (mu == 0 && cr && g.anti) c.sgn = 0x80008000u;
+    const int lpar = fwd ? par : 1 - par;
+    const uint32_t ls = fwd ? cb : src;
+    const uint32_t* b = L.Wb + (i64)((lpar * 4 + mu) * 9) * g.sv;
+    const uint4 w0 = __ldg((const uint4*)b + ls), w1 = __ldg((const uint4*)(b + 4 * g.sv) + ls);
+    c.lw[0] = w0.x;
+    c.lw[1] = w0.y;
+    c.lw[2] = w0.z;
+    c.lw[3] = w0.w;
+    c.lw[4] = w1.x;
+    c.lw[5] = w1.y;
+    c.lw[6] = w1.z;
+    c.lw[7] = w1.w;
+    c.lw[8] = __ldg(b + 8 * g.sv + ls);
+  }
+  const i64 off = (i64)c0 * cs + (i64)spar * 6 * g.sv + src;
+  act_load<true>(L.in, off, g.sv, c.r[0]);
+  act_load<true>(L.in, off + cs, g.sv, c.r[1]);
+}
+
+__device__ __forceinline__ void chunk_put(unsigned char* a0, int s, int grp, bool live, const ChunkRaw& c) {
+  __nv_bfloat162 ub[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const uint32_t w = c.lw[k] ^ c.sgn;
+    memcpy(&ub[k], &w, 4);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    if (!live)
+      put_transported_b16<0>(a0, s, 2 * grp + i, ub, c.r[i]);
+    else if (c.p == 0)
+      put_transported_b16<1>(a0, s, 2 * grp + i, ub, c.r[i]);
+    else if (c.p < 5)
+      put_transported_b16<2>(a0, s, 2 * grp + i, ub, c.r[i]);
+    else
+      put_transported_b16<3>(a0, s, 2 * grp + i, ub, c.r[i]);
+  }
+}
+
 // C_in a multiple of 8: chunk j is path j / (C_in / 8) and input channels 8 (j % (C_in / 8)) + 0..7;
 // thread (s, grp) transports channels + 2 grp + 0..1 of its site.  (Seventeen warps per SM leave
 // each thread 96 registers: four SM sub-partitions of 16K registers, five warps on one of them.)
@@ -253,49 +328,9 @@ __device__ __forceinline__ void transport_chunk_path(const TcLayer& L, unsigned 
   int spar;
   cplx<float> u[9];
   if constexpr (IN16 && QXD_PTC_HMATH != 0) {
-    // BF16 activations with the BF16 transport: the link straight from its BF16 copy (grouped
-    // layout, three loads), the antiperiodic time sign as a flip of both halves' sign bits
-    src = cb;
-    spar = par;
-    uint32_t lw[9] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, sgn = 0u;
-    if (live && p != 0) {
-      const bool fwd = p < 5;
-      const int mu = fwd ? p - 1 : p - 5;
-      bool cr;
-      src = nbr_cb32(L.g, x, mu, fwd ? +1 : -1, cr);
-      spar = 1 - par;
-      if (mu == 0 && cr && L.g.anti) sgn = 0x80008000u;
-      const int lpar = fwd ? par : 1 - par;
-      const uint32_t ls = fwd ? cb : src;
-      const uint32_t* b = L.Wb + (i64)((lpar * 4 + mu) * 9) * L.g.sv;
-      const uint4 w0 = __ldg((const uint4*)b + ls), w1 = __ldg((const uint4*)(b + 4 * L.g.sv) + ls);
-      lw[0] = w0.x; lw[1] = w0.y; lw[2] = w0.z; lw[3] = w0.w;
-      lw[4] = w1.x; lw[5] = w1.y; lw[6] = w1.z; lw[7] = w1.w;
-      lw[8] = __ldg(b + 8 * L.g.sv + ls);
-    }
-    const i64 off = (i64)c0 * cs + (i64)spar * 6 * L.g.sv + src;
-    uint2 raw16[2][6];
-    if (live) {
-      act_load<true>(L.in, off, L.g.sv, raw16[0]);
-      act_load<true>(L.in, off + cs, L.g.sv, raw16[1]);
-    }
-    __nv_bfloat162 ub[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const uint32_t w = lw[k] ^ sgn;
-      memcpy(&ub[k], &w, 4);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      if (!live)
-        put_transported_b16<0>(a0, s, 2 * grp + i, ub, raw16[i]);
-      else if (p == 0)
-        put_transported_b16<1>(a0, s, 2 * grp + i, ub, raw16[i]);
-      else if (p < 5)
-        put_transported_b16<2>(a0, s, 2 * grp + i, ub, raw16[i]);
-      else
-        put_transported_b16<3>(a0, s, 2 * grp + i, ub, raw16[i]);
-    }
+    ChunkRaw c;
+    chunk_load(L, j, grp, live, par, cb, x, cs, c);
+    chunk_put(a0, s, grp, live, c);
     return;
   }
   if (live) path_setup(L, p, par, cb, x, src, spar, u);
