@@ -813,7 +813,8 @@ def run_c4(args):
 
 def profile_run(args):
     """One untimed pass of the step (for ncu launch lists and kernel captures).  c4: 40 steps of
-    the learned FGCR with an untrained [1,8,8,1] network at m0 = -0.1; c3b: one batched solve;
+    the learned FGCR with an untrained [1,8,8,1] network at the physical branch's slowest mass
+    (m0 = -0.12); c3b: one batched solve;
     c3a: one multi-RHS solve of the 12 point sources; sap: 8 SAP-GCR steps, then 3 MG-GCR steps
     after the multigrid set-up."""
     import torch

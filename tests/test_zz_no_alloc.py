@@ -90,3 +90,35 @@ def test_noalloc_dot_refuses_host_and_misaligned_pointers(qxd):
     qxd.vec_dot_noalloc(t[:128], t[:128], 64, out)
     torch.cuda.synchronize()
     assert out.tolist() == [0.0, 0.0]
+
+
+def test_noalloc_dot_inside_a_captured_graph(qxd):
+    """After a first call (which looks up the scratch address), the call records into a CUDA
+    graph: the replay reads whatever the captured input buffers hold at replay time."""
+    dev = torch.device("cuda:0")
+    n = 100_003
+    r = np.random.default_rng(7)
+    ta = torch.zeros(2 * n, dtype=torch.float64, device=dev)
+    tb = torch.zeros(2 * n, dtype=torch.float64, device=dev)
+    out = torch.zeros(2, dtype=torch.float64, device=dev)
+    qxd.vec_dot_noalloc(ta, tb, n, out, torch.cuda.current_stream(dev).cuda_stream)  # first call
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            qxd.vec_dot_noalloc(ta, tb, n, out, side.cuda_stream)
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize()
+    for trial in range(3):
+        a = r.standard_normal(2 * n)
+        b = r.standard_normal(2 * n)
+        ta.copy_(torch.from_numpy(a))
+        tb.copy_(torch.from_numpy(b))
+        g.replay()
+        torch.cuda.synchronize()
+        got = complex(out[0].item(), out[1].item())
+        za, zb = a.view(np.complex128), b.view(np.complex128)
+        scale = float(np.sum(np.abs(za) * np.abs(zb)))
+        assert abs(got - np.vdot(za, zb)) <= 1e-13 * scale, (trial, got)
