@@ -190,54 +190,20 @@ __device__ __forceinline__ void path_setup(const TcLayer& L, int p, int par, uin
 #define QXD_PTC_HMATH 1  // BF16 activations: gauge transport in packed BF16 arithmetic
 #endif
 
-// Gauge transport of one BF16 input channel in packed BF16 arithmetic, straight into the stage:
-// the stored activation words (one complex number per 32-bit word, re low) times the link entries
-// rounded to BF16, u x = u.re x + (-u.im, u.im) swap(x) and conj(u) x = u.re x + (u.im, -u.im)
-// swap(x) as packed fused multiply-adds; each result word is already the BF16 operand the MMA
-// reads (k = 8 slot + 2 beta + re/im).  MODE as put_transported_m.
+// Path 0 (MODE 1: the stored words as they are) or a site past the end of the lattice (MODE 0:
+// zeros) for one BF16 input channel, written into the stage as the MMA operand
+// (k = 8 slot + 2 beta + re/im).
 template <int MODE>
-__device__ __forceinline__ void put_transported_b16(unsigned char* a0, int s, int slot, const __nv_bfloat162 ub[9],
-                                                    const uint2 raw[6]) {
-  auto word = [&](int idx) -> __nv_bfloat162 {  // complex component idx = 3 beta + b
-    const uint32_t w = (idx & 1) ? raw[idx >> 1].y : raw[idx >> 1].x;
-    __nv_bfloat162 t;
-    memcpy(&t, &w, 4);
-    return t;
-  };
-  auto bits = [](__nv_bfloat162 v) {
-    uint32_t w;
-    memcpy(&w, &v, 4);
-    return w;
-  };
-  const __nv_bfloat162 NP = __floats2bfloat162_rn(-1.f, 1.f), PN = __floats2bfloat162_rn(1.f, -1.f);
+__device__ __forceinline__ void put_plain_b16(unsigned char* a0, int s, int slot, const uint2 raw[6]) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    __nv_bfloat162 t[4];
-    if constexpr (MODE == 0) {
+    uint32_t w[4];
 #pragma unroll
-      for (int be = 0; be < 4; ++be) t[be] = __floats2bfloat162_rn(0.f, 0.f);
-    } else if constexpr (MODE == 1) {
-#pragma unroll
-      for (int be = 0; be < 4; ++be) t[be] = word(3 * be + a);
-    } else {
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const __nv_bfloat162 u = MODE == 2 ? ub[3 * a + b] : ub[3 * b + a];
-        const __nv_bfloat162 ur = __low2bfloat162(u), ui = __hmul2(__high2bfloat162(u), MODE == 2 ? NP : PN);
-#pragma unroll
-        for (int be = 0; be < 4; ++be) {
-          const __nv_bfloat162 x = word(3 * be + b);
-          t[be] = b == 0 ? __hmul2(ur, x) : __hfma2(ur, x, t[be]);
-          t[be] = __hfma2(ui, __lowhigh2highlow(x), t[be]);
-        }
-      }
+    for (int be = 0; be < 4; ++be) {
+      const int idx = 3 * be + a;  // complex component 3 beta + colour
+      w[be] = MODE == 0 ? 0u : ((idx & 1) ? raw[idx >> 1].y : raw[idx >> 1].x);
     }
-    uint4 v;
-    v.x = bits(t[0]);
-    v.y = bits(t[1]);
-    v.z = bits(t[2]);
-    v.w = bits(t[3]);
-    *(uint4*)(a0 + a * (TC_ABYTES / 3) + tc::kmajor_off(s, 8 * slot, TC_KC)) = v;
+    *(uint4*)(a0 + a * (TC_ABYTES / 3) + tc::kmajor_off(s, 8 * slot, TC_KC)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -296,23 +262,72 @@ __device__ __forceinline__ void chunk_load(const TcLayer& L, int j, int grp, boo
   act_load<true>(L.in, off + cs, g.sv, c.r[1]);
 }
 
-__device__ __forceinline__ void chunk_put(unsigned char* a0, int s, int grp, bool live, const ChunkRaw& c) {
-  __nv_bfloat162 ub[9];
+// Gauge transport of one BF16 input channel in packed BF16 arithmetic, straight into the stage:
+// the stored activation words (one complex number per 32-bit word, re low) times the link entries
+// rounded to BF16, u x = (Re u, Re u) x + (-Im u, Im u) swap(x) (MODE 2, t = u h) and
+// conj(u) x = (Re u, Re u) x + (Im u, -Im u) swap(x) (MODE 3, t = u^+ h) as packed fused
+// multiply-adds.  ur and ui hold those link words, prepared once per chunk for both channels;
+// each activation word is swapped once and feeds the three colour rows.  Each result word is
+// already the BF16 operand the MMA reads (k = 8 slot + 2 beta + re/im).
+template <int MODE>
+__device__ __forceinline__ void transport_b16(unsigned char* a0, int s, int slot, const __nv_bfloat162 ur[9],
+                                              const __nv_bfloat162 ui[9], const uint2 raw[6]) {
+  __nv_bfloat162 t[3][4];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+#pragma unroll
+    for (int be = 0; be < 4; ++be) {
+      const int idx = 3 * be + b;
+      const uint32_t w = (idx & 1) ? raw[idx >> 1].y : raw[idx >> 1].x;
+      __nv_bfloat162 x;
+      memcpy(&x, &w, 4);
+      const __nv_bfloat162 xs = __lowhigh2highlow(x);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int k = MODE == 2 ? 3 * a + b : 3 * b + a;
+        t[a][be] = b == 0 ? __hmul2(ur[k], x) : __hfma2(ur[k], x, t[a][be]);
+        t[a][be] = __hfma2(ui[k], xs, t[a][be]);
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    uint4 v;
+    memcpy(&v.x, &t[a][0], 4);
+    memcpy(&v.y, &t[a][1], 4);
+    memcpy(&v.z, &t[a][2], 4);
+    memcpy(&v.w, &t[a][3], 4);
+    *(uint4*)(a0 + a * (TC_ABYTES / 3) + tc::kmajor_off(s, 8 * slot, TC_KC)) = v;
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void chunk_transport(unsigned char* a0, int s, int grp, const ChunkRaw& c) {
+  const __nv_bfloat162 sg = MODE == 2 ? __floats2bfloat162_rn(-1.f, 1.f) : __floats2bfloat162_rn(1.f, -1.f);
+  __nv_bfloat162 ur[9], ui[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const uint32_t w = c.lw[k] ^ c.sgn;
-    memcpy(&ub[k], &w, 4);
+    __nv_bfloat162 u;
+    memcpy(&u, &w, 4);
+    ur[k] = __low2bfloat162(u);
+    ui[k] = __hmul2(__high2bfloat162(u), sg);
   }
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    if (!live)
-      put_transported_b16<0>(a0, s, 2 * grp + i, ub, c.r[i]);
-    else if (c.p == 0)
-      put_transported_b16<1>(a0, s, 2 * grp + i, ub, c.r[i]);
-    else if (c.p < 5)
-      put_transported_b16<2>(a0, s, 2 * grp + i, ub, c.r[i]);
-    else
-      put_transported_b16<3>(a0, s, 2 * grp + i, ub, c.r[i]);
+  for (int i = 0; i < 2; ++i) transport_b16<MODE>(a0, s, 2 * grp + i, ur, ui, c.r[i]);
+}
+
+__device__ __forceinline__ void chunk_put(unsigned char* a0, int s, int grp, bool live, const ChunkRaw& c) {
+  if (!live) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) put_plain_b16<0>(a0, s, 2 * grp + i, c.r[i]);
+  } else if (c.p == 0) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) put_plain_b16<1>(a0, s, 2 * grp + i, c.r[i]);
+  } else if (c.p < 5) {
+    chunk_transport<2>(a0, s, grp, c);
+  } else {
+    chunk_transport<3>(a0, s, grp, c);
   }
 }
 
