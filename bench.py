@@ -433,7 +433,7 @@ def run_mrhs(args):
         torch.cuda.synchronize()
         seq[name] = time.perf_counter() - t0
     # the FP32 multi-RHS hop on a full group of 12 right-hand sides (apply_D, both parities with the
-    # clover epilogue): 12 site-RHS per site and launch on the survey's 264 B convention
+    # clover epilogue): 12 site-RHS per site and launch on the amortised 264 B convention
     xin = torch.from_numpy(np.stack([synth.gaussian_spinor(w["L"], 2100 + k) for k in range(12)])
                            .view(np.float64)).to(dev)
     xout = torch.empty_like(xin)
@@ -448,7 +448,7 @@ def run_mrhs(args):
     n_l, ms_l, b_l = stats[kname]
     peak, kind = measured_peaks()
     achieved = b_l / (ms_l / 1e3) / 1e9
-    # the survey's multi-RHS convention per site and RHS and launch: in + out spinor plus
+    # the amortised multi-RHS convention per site and RHS and launch: in + out spinor plus
     # (8 links + clover) / 12; FP32: 192 + (576 + 288) / 12 = 264 B, 16-bit: 104 + (288 + 148) / 12
     conv = 264.0 if prec == qxd.F32 else 104.0 + 436.0 / 12
     # site-RHS pairs the launches processed: the FP32 hop works on the active right-hand sides only;
@@ -476,17 +476,17 @@ def run_mrhs(args):
                          "launches": n_l, "avg_launch_us": ms_l / n_l * 1e3 if n_l else None,
                          "bytes": "the kernel's own: spinors per site and RHS (in, out, diagonal in) plus links and "
                                   "clover once per site and group of RHS",
-                         "achieved_survey_convention": achieved_conv,
-                         "frac_survey_convention": achieved_conv / peak,
-                         "survey_convention_bytes_per_site_rhs": conv,
+                         "achieved_amortised_convention": achieved_conv,
+                         "frac_amortised_convention": achieved_conv / peak,
+                         "amortised_convention_bytes_per_site_rhs": conv,
                          "site_rhs_per_launch": site_rhs / n_l if n_l else None,
                          "timing": "CUDA events around every launch of a separate profiled pass"},
             "hop_f32_mrhs_12rhs": {"launches": n12, "avg_launch_us": ms12 / n12 * 1e3 if n12 else None,
                                    "achieved_own_bytes_GBps": by12 / (ms12 / 1e3) / 1e9 if ms12 else None,
                                    "frac_own_bytes": by12 / (ms12 / 1e3) / 1e9 / peak if ms12 else None,
-                                   "achieved_survey_convention_GBps":
+                                   "achieved_amortised_convention_GBps":
                                        264.0 * 12 * (V // 2) * n12 / (ms12 / 1e3) / 1e9 if ms12 else None,
-                                   "frac_survey_convention":
+                                   "frac_amortised_convention":
                                        264.0 * 12 * (V // 2) * n12 / (ms12 / 1e3) / 1e9 / peak if ms12 else None,
                                    "note": "apply_D in FP32 with nrhs = 12 (clover epilogue, both parities), "
                                            "5 calls, CUDA events around every launch"},
