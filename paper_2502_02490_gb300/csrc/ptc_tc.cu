@@ -163,6 +163,34 @@ __device__ __forceinline__ void put_transported(unsigned char* a0, int s, int sl
     put_transported_m<3>(a0, s, slot, u, raw);
 }
 
+// Checkerboard index of x + dir mu^ for a direction mu known only at run time (the path of a
+// chunk), with `crossed` set on a wrap in direction mu: the map of nbr_cb32 (C* shift included),
+// written with compile-time array indices only so that the coordinates stay in registers.
+__host__ __device__ __forceinline__ uint32_t nbr_path32(const Geom& g, const int x[4], int mu, int dir,
+                                                        bool& crossed) {
+  int y[4];
+  int v = 0, Lm = 1;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    y[k] = x[k];
+    if (k == mu) {
+      v = x[k];
+      Lm = g.L[k];
+    }
+  }
+  v += dir;
+  crossed = v >= Lm || v < 0;
+  v = v >= Lm ? 0 : (v < 0 ? Lm - 1 : v);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (k == mu) y[k] = v;
+  if (crossed && g.shift && mu >= 2) {
+    y[1] += g.shift;
+    if (y[1] >= g.L[1]) y[1] -= g.L[1];
+  }
+  return ((((uint32_t)y[0] * g.L[1] + y[1]) * g.L[2] + y[2]) * g.L[3] + y[3]) >> 1;
+}
+
 // neighbour of site cb along path p (its checkerboard index and parity), and the path's link with
 // the antiperiodic time sign folded in
 __device__ __forceinline__ void path_setup(const TcLayer& L, int p, int par, uint32_t cb, const int x[4],
@@ -174,7 +202,7 @@ __device__ __forceinline__ void path_setup(const TcLayer& L, int p, int par, uin
   const bool fwd = p < 5;
   const int mu = fwd ? p - 1 : p - 5;
   bool cr;
-  src = nbr_cb32(g, x, mu, fwd ? +1 : -1, cr);
+  src = nbr_path32(g, x, mu, fwd ? +1 : -1, cr);
   spar = 1 - par;
   const float sign = (mu == 0 && cr && g.anti) ? -1.f : 1.f;
   const int lpar = fwd ? par : 1 - par;
@@ -217,11 +245,10 @@ struct ChunkRaw {
   uint32_t sgn;
 };
 
-__device__ __forceinline__ void chunk_load(const TcLayer& L, int j, int grp, bool live, int par, uint32_t cb,
-                                           const int x[4], i64 cs, ChunkRaw& c) {
+__device__ __forceinline__ void chunk_load(const TcLayer& L, int p, int cg8, int grp, bool live, int par,
+                                           uint32_t cb, const int x[4], i64 cs, ChunkRaw& c) {
   const Geom& g = L.g;
-  const int G = L.cin >> 3;
-  const int p = j / G, c0 = 8 * (j % G) + 2 * grp;
+  const int c0 = cg8 + 2 * grp;
   c.p = p;
   c.sgn = 0u;
   if (!live) {  // a site past the end of the lattice: zero operands (transported as zeros anyway)
@@ -240,7 +267,7 @@ __device__ __forceinline__ void chunk_load(const TcLayer& L, int j, int grp, boo
     const bool fwd = p < 5;
     const int mu = fwd ? p - 1 : p - 5;
     bool cr;
-    src = nbr_cb32(g, x, mu, fwd ? +1 : -1, cr);
+    src = nbr_path32(g, x, mu, fwd ? +1 : -1, cr);
     spar = 1 - par;
     if (mu == 0 && cr && g.anti) c.sgn = 0x80008000u;
     const int lpar = fwd ? par : 1 - par;
@@ -331,20 +358,21 @@ __device__ __forceinline__ void chunk_put(unsigned char* a0, int s, int grp, boo
   }
 }
 
-// C_in a multiple of 8: chunk j is path j / (C_in / 8) and input channels 8 (j % (C_in / 8)) + 0..7;
-// thread (s, grp) transports channels + 2 grp + 0..1 of its site.  (Seventeen warps per SM leave
-// each thread 96 registers: four SM sub-partitions of 16K registers, five warps on one of them.)
+// C_in a multiple of 8: chunk j is path p = j / (C_in / 8) and input channels cg8 + 0..7 with
+// cg8 = 8 (j % (C_in / 8)); thread (s, grp) transports channels cg8 + 2 grp + 0..1 of its site.
+// (Seventeen warps per SM leave each thread 96 registers: four SM sub-partitions of 16K
+// registers, five warps on one of them.)
 template <bool IN16>
-__device__ __forceinline__ void transport_chunk_path(const TcLayer& L, unsigned char* a0, int j, int s, int grp,
-                                                     bool live, int par, uint32_t cb, const int x[4], i64 cs) {
-  const int G = L.cin >> 3;
-  const int p = j / G, c0 = 8 * (j % G) + 2 * grp;
+__device__ __forceinline__ void transport_chunk_path(const TcLayer& L, unsigned char* a0, int p, int cg8, int s,
+                                                     int grp, bool live, int par, uint32_t cb, const int x[4],
+                                                     i64 cs) {
+  const int c0 = cg8 + 2 * grp;
   uint32_t src;
   int spar;
   cplx<float> u[9];
   if constexpr (IN16 && QXD_PTC_HMATH != 0) {
     ChunkRaw c;
-    chunk_load(L, j, grp, live, par, cb, x, cs, c);
+    chunk_load(L, p, cg8, grp, live, par, cb, x, cs, c);
     chunk_put(a0, s, grp, live, c);
     return;
   }
@@ -486,6 +514,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ptc_layer_tc(TcLayer L) {
       int x[4] = {0, 0, 0, 0};
       if (live) cb_coords32(g, cb, par, x);
       bool ok = true;
+      [[maybe_unused]] int p = 0, jg = 0;  // FAST: chunk j = p (C_in / 8) + jg, counted, not divided
       for (int j = 0; j < L.nchunks; ++j) {
         const uint32_t cg = (uint32_t)(it * L.nchunks + j), st = cg % TC_STAGES, use = cg / TC_STAGES;
         if (use > 0 && !tc::mbar_wait(&empty[st], (use - 1) & 1, TC_WAIT)) {
@@ -497,10 +526,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ptc_layer_tc(TcLayer L) {
           tc::bulk_g2s(sB + (size_t)st * bchunk, L.Bp + (size_t)j * bchunk, bchunk, &full[st]);
         }
         unsigned char* a0 = sA + st * TC_ABYTES;
-        if constexpr (FAST)
-          transport_chunk_path<IN16>(L, a0, j, s, grp, live, par, cb, x, cs);
-        else
+        if constexpr (FAST) {
+          transport_chunk_path<IN16>(L, a0, p, 8 * jg, s, grp, live, par, cb, x, cs);
+          if (++jg == (L.cin >> 3)) {
+            jg = 0;
+            ++p;
+          }
+        } else {
           transport_chunk_pairs<IN16>(L, a0, j, s, grp, live, par, cb, x, cs);
+        }
         tc::fence_async_smem();
         tc::mbar_arrive(&full[st]);
       }
@@ -574,7 +608,7 @@ __global__ void __launch_bounds__(256) k_ptc_pull(Geom g, int cout, const void* 
       const bool fwd = p < 5;
       const int mu = fwd ? p - 1 : p - 5;
       bool cr;
-      const uint32_t src = nbr_cb32(g, x, mu, fwd ? +1 : -1, cr);
+      const uint32_t src = nbr_path32(g, x, mu, fwd ? +1 : -1, cr);
       const float sign = (mu == 0 && cr && g.anti) ? -1.f : 1.f;
       const int lpar = fwd ? par : 1 - par;
       const uint32_t ls = fwd ? cb : src;

@@ -46,7 +46,8 @@ TC_TOL_PER_LAYER = 4 * 2.0 ** -8
 @pytest.mark.parametrize("prec", ["f32", "bf16_tc"])
 @pytest.mark.parametrize("L,cstar,chans", [((4, 2, 2, 4), False, [1, 3, 2, 1]), ((2, 2, 4, 2), True, [1, 4, 1]),
                                            ((6, 4, 4, 6), False, [1, 16, 16, 1]),
-                                           ((8, 6, 6, 4), False, [1, 8, 5, 1])])
+                                           ((8, 6, 6, 4), False, [1, 8, 5, 1]),
+                                           ((4, 2, 2, 4), True, [1, 8, 8, 1])])
 def test_net_forward_matches_oracle(qxd, L, cstar, chans, prec):
     c = Case(qxd, torch, L, cstar=cstar)
     net = qxd.net_create(c.lat, chans, seed=1)
