@@ -1000,6 +1000,27 @@ def cpu_eocg_c1():
             "iterations": info["iterations"], "true_rel_res": info["true_rel_residual"], "processes": 1}
 
 
+def cpu_apply_c1(reps=20):
+    """The oracle's full D on the 4^4 workload (one process, clover built once): sites/s and GB/s
+    on the 2112 B/site FP64 convention.  The oracle's cost per site does not depend on the lattice
+    size, so the 32^3x64 sample stands for the larger lattices."""
+    from oracle import qxd_oracle as O
+    from paper_2502_02490_gb300 import synth
+
+    L = (4, 4, 4, 4)
+    U, A = synth.gauge_field(L, 1000, 0.3)
+    psi = synth.gaussian_spinor(L, 2000)
+    op = O.Operator(O.Lattice(L, antiperiodic=True), U, A, -1 / 3, -0.1, 1.9, 1.0)
+    op.D(psi)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        op.D(psi)
+    dt = (time.perf_counter() - t0) / reps
+    V = int(np.prod(L))
+    return {"lattice": "4^4 (eps=0.3, q=-1/3, m0=-0.1, c_sw=1.9, c_sw^QED=1.0)", "seconds_per_apply": dt,
+            "sites_per_s": V / dt, "GBps_2112B_per_site": V * 2112 / dt / 1e9, "processes": 1}
+
+
 DSLASH_FLOP_PER_SITE = 1824  # clover dslash: 1320 for the Wilson hop + 504 for the clover term
 
 
@@ -1036,6 +1057,7 @@ def run_reference(args, rank, world):
     cb = dict(vals[-1])
     cb["value"] = v
     cb["eocg_c1"] = cpu_eocg_c1()
+    cb["apply_d_c1"] = cpu_apply_c1()
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -1121,6 +1143,7 @@ def main():
                 cpu_sample(pool, nworkers)  # warm-up
                 out["cpu_baseline"] = cpu_sample(pool, nworkers)
                 out["cpu_baseline"]["eocg_c1"] = cpu_eocg_c1()
+                out["cpu_baseline"]["apply_d_c1"] = cpu_apply_c1()
             finally:
                 pool.close()
                 pool.join()
