@@ -477,9 +477,9 @@ qxd_status qxd_mg_precond(qxd_lattice *lat, double *out, const double *in, const
  * counter), which every GPU that loads the library keeps until process exit.  Limit: n <=
  * QXD_NOALLOC_MAX_N; larger n returns QXD_EINVAL.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) and keeps it for the life of the process (make
- * that first call before any stream capture begins); after
- * a cudaDeviceReset on that device the kept address is stale, so do not call this entry point
- * on a device that was reset.  All calls share the one array: calls that overlap on the GPU (e.g. on two
+ * that first call before any stream capture begins); after a cudaDeviceReset on that device the
+ * kept address is stale: call qxd_vec_dot_noalloc_forget first, and then make a fresh first call
+ * before any capture.  All calls share the one array: calls that overlap on the GPU (e.g. on two
  * streams at once) race and give wrong results; serialise them.  The result is deterministic
  * for a given n (fixed blocking) and agrees with qxd_vec_dot to rounding.  Allocates nothing
  * and calls no allocating routine.  Errors: QXD_EINVAL for n < 0, n > QXD_NOALLOC_MAX_N, a
@@ -489,6 +489,11 @@ qxd_status qxd_mg_precond(qxd_lattice *lat, double *out, const double *in, const
 #define QXD_NOALLOC_MAX_N 16777216
 qxd_status qxd_vec_dot_noalloc(const double *a, const double *b, int64_t n, double *out,
                                void *cuda_stream);
+/* Drops the scratch addresses qxd_vec_dot_noalloc keeps (all devices), so that its next call
+ * looks them up again; for use after a device reset.  Host state only: no CUDA call, no device
+ * needed.  Thread-safe (it takes the lock of the lookups); on a device that was not reset it only
+ * costs the next call one more lookup.  Always returns QXD_OK. */
+qxd_status qxd_vec_dot_noalloc_forget(void);
 
 /* Kernel timing.  With profiling on, the library brackets each launch of its hop kernels with
  * CUDA events on the lattice stream; qxd_kernel_stats returns, for the kernel class `which`

@@ -146,3 +146,12 @@ extern "C" qxd_status qxd_vec_dot_noalloc(const double* a, const double* b, int6
   e = cudaGetLastError();
   return e == cudaSuccess ? QXD_OK : qxd::cuda_fail(nullptr, e, "k_dot_noalloc launch");
 }
+
+// Forget the cached scratch addresses (host state only; no CUDA call).  After a device reset the
+// library's module is loaded again and the array may move; the next qxd_vec_dot_noalloc then
+// looks its address up afresh.
+extern "C" qxd_status qxd_vec_dot_noalloc_forget(void) {
+  std::lock_guard<std::mutex> lock(g_mutex);
+  for (void*& a : g_scratch_addr) a = nullptr;
+  return QXD_OK;
+}

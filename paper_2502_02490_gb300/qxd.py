@@ -78,6 +78,7 @@ _SIGS = {
     "qxd_vec_norm2": [_vp, _vp, _i64, C.POINTER(_d)],
     "qxd_vec_axpy": [_vp, _d, _d, _vp, _vp, _i64],
     "qxd_vec_dot_noalloc": [_vp, _vp, _i64, _vp, _vp],
+    "qxd_vec_dot_noalloc_forget": [],
     "qxd_set_profiling": [_vp, _i],
     "qxd_check_guards": [_vp, C.POINTER(_i64)],
     "qxd_sap_apply": [_vp, _vp, _vp, C.POINTER(C.c_int), _i, _i, _i],
@@ -297,6 +298,11 @@ def vec_dot_noalloc(a, b, n, out, stream=None):
     a, b and out must be CUDA tensors; the library also refuses misaligned addresses."""
     _check(lib.qxd_vec_dot_noalloc(_device_ptr(a, "a"), _device_ptr(b, "b"), int(n), _device_ptr(out, "out"),
                                    stream))
+
+
+def vec_dot_noalloc_forget():
+    """qxd_vec_dot_noalloc_forget: drop the cached scratch addresses (after a device reset)."""
+    _check(lib.qxd_vec_dot_noalloc_forget())
 
 
 def set_profiling(lat, on):

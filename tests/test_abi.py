@@ -122,3 +122,10 @@ def test_multigrid_entry_points_and_params_layout(qxd):
     assert lib.qxd_mg_apply_level1(None, None, None, 0) == qxd.EINVAL
     assert lib.qxd_mg_precond(None, None, None, None, 1, 1, 0) == qxd.EINVAL
     assert qxd.SOLVER_MP_MG_GCR == 7
+
+
+def test_noalloc_forget_needs_no_device(qxd):
+    """qxd_vec_dot_noalloc_forget only drops host-side cached addresses: it returns QXD_OK on a
+    machine without a GPU, and calling it twice is harmless."""
+    assert qxd.lib.qxd_vec_dot_noalloc_forget() == qxd.OK
+    qxd.vec_dot_noalloc_forget()

@@ -122,3 +122,18 @@ def test_noalloc_dot_inside_a_captured_graph(qxd):
         za, zb = a.view(np.complex128), b.view(np.complex128)
         scale = float(np.sum(np.abs(za) * np.abs(zb)))
         assert abs(got - np.vdot(za, zb)) <= 1e-13 * scale, (trial, got)
+
+
+def test_noalloc_dot_after_forgetting_the_scratch_address(qxd):
+    """qxd_vec_dot_noalloc_forget drops the cached address; the next call looks it up again."""
+    dev = torch.device("cuda:0")
+    r = np.random.default_rng(3)
+    a, b = r.standard_normal(2 * 5000), r.standard_normal(2 * 5000)
+    ta, tb = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+    out = torch.zeros(2, dtype=torch.float64, device=dev)
+    qxd.vec_dot_noalloc_forget()
+    qxd.vec_dot_noalloc(ta, tb, 5000, out)
+    torch.cuda.synchronize()
+    za, zb = a.view(np.complex128), b.view(np.complex128)
+    got = complex(out[0].item(), out[1].item())
+    assert abs(got - np.vdot(za, zb)) <= 1e-13 * float(np.sum(np.abs(za) * np.abs(zb)))
