@@ -92,3 +92,12 @@ def test_bench_rejects_fewer_than_three_warmup_steps():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--warmup", "2"], capture_output=True,
                        text=True, timeout=120)
     assert r.returncode != 0 and "--warmup must be >= 3" in r.stderr
+
+
+def test_cpu_apply_c1_record():
+    """The CPU baseline's 4^4 apply of the oracle's D: a positive rate on the 2112 B/site
+    convention, consistent with its own time per apply."""
+    r = bench.cpu_apply_c1(reps=2)
+    assert r["seconds_per_apply"] > 0 and r["processes"] == 1
+    assert abs(r["sites_per_s"] * r["seconds_per_apply"] - 256) < 1e-6
+    assert abs(r["GBps_2112B_per_site"] - r["sites_per_s"] * 2112 / 1e9) < 1e-9
